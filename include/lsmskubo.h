@@ -1,0 +1,210 @@
+/*
+ * lsmskubo.h -- C ABI of the GB300 (sm_103a) LSMS Kubo-Greenwood conductivity
+ * library (arXiv 2311.12134).
+ *
+ * The library computes, for every atom m of a supercell, the local interaction
+ * zone (LIZ) KKR matrix M = T^{-1} - g at complex energies z, its LU factors,
+ * the central scattering-path blocks tau^{n0} (Eq. tau-inverse restricted to the
+ * LIZ, Sec. II.A and Fig. 1), the LSMS Kubo-Greenwood traces
+ * (Eq. lsms-conductivity-formula), their four-combination consolidation into
+ * sigma (Eq. sigma-tilde-consolidation) and rho = sigma^{-1} (end of Sec. II.B),
+ * plus the gradient of sigma with respect to the per-site inverse t-matrices.
+ *
+ * Conventions (readings of the paper, which fixes none of them):
+ *  - Rydberg atomic units (hbar = 1, m_e = 1/2): kappa = sqrt(z) (principal
+ *    root) and the prefactor 4 m_e^2 / hbar^3 of Eq. (lsms-conductivity-formula)
+ *    is 1; N Omega is the supercell volume; no spin factor.
+ *  - Real spherical harmonics without the Condon-Shortley phase; channel index
+ *    L = l*l + l + m; K = (lmax+1)^2 channels per site; lmax in 0..3.
+ *  - g^{nm}_{LL'}(z) = -4 pi i kappa sum_L'' i^{l-l'-l''} C_{LL'L''} h1_{l''}(kappa R) Y_L''(R^)
+ *    with R = R_m - R_n (row site n, column site m) for Im z >= 0, and the
+ *    decaying (advanced) form +4 pi i kappa sum ... h2_{l''}(kappa R) ... for
+ *    Im z < 0, so g(z*) = conj g(z).  On-site blocks of g are zero.
+ *  - Energies come in pairs per broadening delta: z[2d] = E_F + i delta_d,
+ *    z[2d+1] = E_F - i delta_d.
+ *  - Current matrices J are indexed by the energy pair (z_a, z_b):
+ *    c = 0 (+,+), 1 (+,-), 2 (-,+), 3 (-,-); in the term of combination
+ *    c = (z1, z2), site m carries J(z2, z1) and site n carries J(z1, z2).
+ *  - t^{-1} blocks must be complex-symmetric (true for scatterers with time
+ *    reversal symmetry in a real-harmonic basis).  Then M^T = M and the row block
+ *    is tau^{0n} = (tau^{n0})^T, which the library uses.
+ *
+ * Memory: "dev" = device pointer on the current CUDA device, "host" = host
+ * pointer.  The caller owns every buffer it passes; the library owns only the
+ * lsms_liz object (host arrays plus device copies made on first use on a
+ * device).  Complex numbers are lsms_complex = two doubles (re, im), i.e. the
+ * layout of numpy/torch complex128.  Matrices are row-major unless stated.
+ *
+ * Calls that take a stream enqueue work on it and return without waiting;
+ * errors found on the host are returned at once.  Per-unit numerical status is
+ * written to device arrays.  The library never aborts and has no CPU fallback:
+ * every step of the computation runs in its CUDA kernels.
+ *
+ * Graph capture: the first compute call with a given lsms_liz on a device
+ * uploads tables and builds the work plan (synchronous); later calls with the
+ * same sizes allocate nothing when a workspace is passed, so they can be
+ * captured into a CUDA graph.
+ */
+#ifndef LSMSKUBO_H
+#define LSMSKUBO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } lsms_complex;
+typedef struct lsms_liz lsms_liz;
+
+enum lsms_status {
+  LSMS_OK = 0,
+  LSMS_ERR_ARG = -1,      /* bad argument; nothing was enqueued */
+  LSMS_ERR_CUDA = -2,     /* a CUDA runtime call failed */
+  LSMS_ERR_SINGULAR = -3, /* per-unit status: zero pivot */
+  LSMS_ERR_NOCONV = -4,   /* per-unit status: refinement did not converge */
+  LSMS_ERR_TIMEOUT = -5,  /* a bounded device wait gave up */
+  LSMS_ERR_NOMEM = -6     /* workspace too small / allocation failed */
+};
+
+enum lsms_precision {
+  LSMS_FP64 = 0,   /* plain form: complex128 LU and solves (DFMA) */
+  LSMS_MIXED = 1   /* complex64 LU and solves, FP64 residual and iterative
+                      refinement of the tau column block to FP64 accuracy */
+};
+
+/* Unit status values written to unit_status[e][m] (0 = fine). */
+#define LSMS_UNIT_OK 0
+#define LSMS_UNIT_ZERO_PIVOT 1
+#define LSMS_UNIT_NOCONV 2
+#define LSMS_UNIT_NONFINITE 4
+#define LSMS_UNIT_BAD_INPUT 8   /* a species index outside 0..n_species-1 */
+
+/* ---------------------------------------------------------------- LIZ
+ * Sec. II.A, Fig. 1: the LIZ of atom m holds every site within r_liz of it.
+ * pos      host [n_atoms][3] atom positions (bohr), not wrapped.
+ * lattice  host [3][3] rows a1, a2, a3 of the periodic cell (bohr), or NULL
+ *          for a finite cluster (no images).
+ * r_liz    LIZ radius (bohr); a site is inside iff |d| <= r_liz + 1e-8.
+ * Periodic images are distinct sites; site = pos[j] + i a1 + j a2 + k a3 with
+ * integer image (i, j, k).  Order within a LIZ: the centre first, then by
+ * (atom j, i, j, k).  Returns LSMS_ERR_ARG for n_atoms < 1, r_liz < 0, a
+ * singular lattice or an empty result, LSMS_ERR_NOMEM if the site count
+ * overflows.  *out is owned by the caller and freed with lsms_liz_destroy. */
+int lsms_build_liz(const double* pos, int n_atoms, const double* lattice, double r_liz,
+                   lsms_liz** out);
+
+/* Sizes of a LIZ set: atoms, total sites S_total = sum_m S_m, max/min S_m.
+ * Any output pointer may be NULL. */
+int lsms_liz_sizes(const lsms_liz* liz, int* n_atoms, int64_t* total_sites, int* max_sites,
+                   int* min_sites);
+
+/* Host copies of the LIZ arrays (any may be NULL):
+ * offsets host [n_atoms+1], site_atom host [S_total], image host [S_total][3],
+ * disp host [S_total][3] (site position minus centre position, bohr). */
+int lsms_liz_export(const lsms_liz* liz, int64_t* offsets, int32_t* site_atom, int32_t* image,
+                    double* disp);
+
+void lsms_liz_destroy(lsms_liz* liz);
+
+/* ---------------------------------------------------------------- inputs
+ * Dipole current-matrix model (input helper; the paper's J are matrix elements
+ * of the current operator that a single-site solver would supply):
+ *   J[s][c][mu][L][L'] = r_ll[s][c][l][l'] * C_{L L' (1, m_mu)}  for |l - l'| = 1,
+ * zero otherwise; mu = x, y, z <-> m = +1, -1, 0; C the real Gaunt coefficient.
+ * r_ll host [n_species][4][lmax+1][lmax+1]; J host [n_species][4][3][K][K]. */
+int lsms_dipole_current(int lmax, const lsms_complex* r_ll, int n_species, lsms_complex* J);
+
+/* Real Gaunt table C[L1][L2][L3] = int Y_L1 Y_L2 Y_L3 dOmega, L1, L2 < (lmax+1)^2,
+ * L3 < (2 lmax + 1)^2, from the Wigner 3j closed form.  host output. */
+int lsms_gaunt_table(int lmax, double* C);
+
+/* ---------------------------------------------------------------- tau
+ * Eq. (tau-inverse) on each LIZ: for every atom m and energy e, assemble
+ * M = T^{-1} - g (n = K S_m), LU-factor it with partial pivoting (largest
+ * |Re| + |Im| in the column, lowest row on ties) and solve M X = E0, E0 the
+ * first K columns of the identity, so X holds the column blocks tau^{p0}.
+ *
+ * species      dev [n_atoms] int32 species index of each atom (< n_species).
+ * tinv         dev [n_species][n_energy][K][K] t^{-1}(z_e), complex-symmetric.
+ * z            host [n_energy] complex energies (Im z != 0 recommended).
+ * precision    LSMS_FP64 or LSMS_MIXED.
+ * tau          dev [n_energy][S_total][K][K] output: tau[e][s] = tau^{s 0} of
+ *              the LIZ that site s belongs to (row L, column L').
+ * unit_status  dev [n_energy][n_atoms] int32 output (bit set of LSMS_UNIT_*),
+ *              or NULL.
+ * workspace    dev scratch of workspace_bytes (>= lsms_tau_workspace_bytes for
+ *              one unit); the units are processed in chunks that fit it.  NULL
+ *              = the library allocates (stream-ordered) and frees it.
+ * lu_store     dev buffer of lu_store_bytes (lsms_lu_store_bytes) that keeps the
+ *              factors for lsms_kubo_sigma_backward, or NULL.
+ * stream       cudaStream_t (NULL = legacy default stream).
+ */
+int lsms_tau_workspace_bytes(const lsms_liz* liz, int lmax, int n_energy, int precision,
+                             size_t* min_bytes, size_t* all_bytes);
+int lsms_lu_store_bytes(const lsms_liz* liz, int lmax, int n_energy, int precision,
+                        size_t* bytes);
+int lsms_tau_blocks(const lsms_liz* liz, int lmax, const int32_t* species, int n_species,
+                    const lsms_complex* tinv, const lsms_complex* z, int n_energy,
+                    int precision, lsms_complex* tau, int32_t* unit_status, void* workspace,
+                    size_t workspace_bytes, void* lu_store, size_t lu_store_bytes,
+                    void* stream);
+
+/* ---------------------------------------------------------------- sigma
+ * Eq. (lsms-conductivity-formula) and Eq. (sigma-tilde-consolidation):
+ *   S_c[mu][nu] = sum_m sum_{n in LIZ_m} Tr[J^{m mu}(z2,z1) tau^{0n}(z1) J^{n nu}(z1,z2) tau^{n0}(z2)]
+ *   sigma_tilde_c = -S_c / (pi V),  sigma = (1/4)(st_0 - st_1 - st_2 + st_3),
+ *   rho = (Re sigma)^{-1}.
+ * J            dev [n_species][4][3][K][K] (+ d * J_delta_stride elements for
+ *              broadening d; stride 0 = the same J for every delta).
+ * tau          dev output of lsms_tau_blocks with n_energy = 2 n_delta.
+ * volume       supercell volume N Omega (bohr^3).
+ * sigma_tilde  dev [n_delta][4][3][3] output or NULL.
+ * sigma        dev [n_delta][3][3] output.
+ * rho          dev [n_delta][3][3] double output or NULL.
+ * Reductions over atoms are in a fixed order (bitwise reproducible). */
+int lsms_kubo_sigma(const lsms_liz* liz, int lmax, const int32_t* species, int n_species,
+                    const lsms_complex* J, int64_t J_delta_stride, const lsms_complex* tau,
+                    int n_delta, double volume, lsms_complex* sigma_tilde, lsms_complex* sigma,
+                    double* rho, void* stream);
+
+/* ---------------------------------------------------------------- gradient
+ * Adjoint of the two calls above.  For f = sum_{d,mu,nu} conj(w[d][mu][nu]) sigma[d][mu][nu]
+ * (w = grad_sigma, dev [n_delta][3][3]) it writes, for every energy e and atom i,
+ *   grad_tinv[e][i] = conj( df / d t^{-1}_i(z_e) )   (K x K, row-major),
+ * the PyTorch gradient of the real loss Re f with respect to a per-site t^{-1}
+ * at energy z_e (all periodic images of atom i summed).  It uses
+ * d tau = -tau dM tau (from Eq. tau-inverse) with one 2K-column solve per
+ * (atom, energy), reusing the LU factors from lu_store when given (same
+ * precision, same inputs), else recomputing them in the workspace.
+ * grad_tinv    dev [n_energy][n_atoms][K][K] output.
+ * grad_tinv_species  dev [n_species][n_energy][K][K] output (the same gradient
+ *              summed over the atoms of each species, i.e. with respect to the
+ *              tinv argument of lsms_tau_blocks), or NULL.
+ * workspace    dev scratch of workspace_bytes (>= lsms_backward_workspace_bytes
+ *              minimum), or NULL for a stream-ordered allocation.
+ * n_energy must be even (energies in (+, -) pairs per delta). */
+int lsms_backward_workspace_bytes(const lsms_liz* liz, int lmax, int n_energy, int precision,
+                                  size_t* min_bytes, size_t* all_bytes);
+int lsms_kubo_sigma_backward(const lsms_liz* liz, int lmax, const int32_t* species,
+                             int n_species, const lsms_complex* tinv, const lsms_complex* z,
+                             int n_energy, int precision, const lsms_complex* J,
+                             int64_t J_delta_stride, const lsms_complex* tau, double volume,
+                             const lsms_complex* grad_sigma, const void* lu_store,
+                             size_t lu_store_bytes, lsms_complex* grad_tinv,
+                             lsms_complex* grad_tinv_species, void* workspace,
+                             size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------- misc */
+/* Message of the last error on the calling thread ("" if none). */
+const char* lsms_last_error(void);
+/* Library version (major * 10000 + minor * 100 + patch). */
+int lsms_version(void);
+/* Number of kernel launches the library has enqueued since load (all threads). */
+long long lsms_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSMSKUBO_H */

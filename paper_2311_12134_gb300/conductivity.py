@@ -1,0 +1,123 @@
+"""User-level API: the LSMS Kubo-Greenwood conductivity of one structure.
+
+``Problem`` holds one structure's LIZ sets and device inputs and calls the C
+ABI (through ``binding``) for tau blocks, sigma and the gradient.
+``SigmaFn`` wraps forward and backward as a ``torch.autograd.Function`` of the
+per-species inverse t-matrices.  ``conductivity`` is the host-to-host call:
+NumPy inputs in, sigma and rho out.
+"""
+import numpy as np
+
+from . import binding as B
+
+
+class Problem:
+    """One structure on one CUDA device.
+
+    pos [N,3], lattice [3,3] or None, r_liz, lmax, species [N] (host), tinv
+    [n_species, 2 n_delta, K, K] (host or device complex128), z [2 n_delta]
+    complex (E_F + i d, E_F - i d per delta), J [n_species, 4, 3, K, K] (host or
+    device complex128), volume (bohr^3).
+    """
+
+    def __init__(self, pos, lattice, r_liz, lmax, species, tinv, z, J, volume, precision="fp64", device="cuda",
+                 keep_factors=True, workspace_bytes=None):
+        import torch
+        self.lmax = int(lmax)
+        self.K = (self.lmax + 1) ** 2
+        self.liz = B.build_liz(pos, lattice, r_liz)
+        self.z = np.ascontiguousarray(z, dtype=np.complex128)
+        if self.z.shape[0] % 2:
+            raise ValueError("energies must come in (+, -) pairs")
+        self.n_delta = self.z.shape[0] // 2
+        self.volume = float(volume)
+        self.precision = precision
+        self.device = torch.device(device)
+        self.species = torch.as_tensor(np.ascontiguousarray(species, dtype=np.int32)).to(self.device)
+        self.tinv = torch.as_tensor(tinv).to(device=self.device, dtype=torch.complex128).contiguous()
+        self.J = torch.as_tensor(J).to(device=self.device, dtype=torch.complex128).contiguous()
+        nE = self.z.shape[0]
+        mn, al = B.tau_workspace_bytes(self.liz, self.lmax, nE, B._prec(precision))
+        ws = al if workspace_bytes is None else max(mn, int(workspace_bytes))
+        self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
+        self.lu_store = None
+        if keep_factors:
+            self.lu_store = torch.empty(B.lu_store_bytes(self.liz, self.lmax, nE, B._prec(precision)),
+                                        dtype=torch.uint8, device=self.device)
+        self.tau = torch.empty((nE, self.liz.total_sites, self.K, self.K), dtype=torch.complex128,
+                               device=self.device)
+        self.unit_status = torch.empty((nE, self.liz.n_atoms), dtype=torch.int32, device=self.device)
+        self.sigma_out = torch.empty((self.n_delta, 3, 3), dtype=torch.complex128, device=self.device)
+        self.sigma_tilde = torch.empty((self.n_delta, 4, 3, 3), dtype=torch.complex128, device=self.device)
+        self.rho = torch.empty((self.n_delta, 3, 3), dtype=torch.float64, device=self.device)
+        self._bw_ws = None
+
+    @property
+    def n_units(self):
+        return self.liz.n_atoms * self.z.shape[0]
+
+    def solve_tau(self, tinv=None, stream=None):
+        t = self.tinv if tinv is None else tinv
+        B.tau_blocks(self.liz, self.lmax, self.species, t, self.z, self.precision, tau=self.tau,
+                     unit_status=self.unit_status, workspace=self.workspace, lu_store=self.lu_store, stream=stream)
+        return self.tau
+
+    def sigma(self, stream=None):
+        B.kubo_sigma(self.liz, self.lmax, self.species, self.J, self.tau, self.n_delta, self.volume,
+                     sigma=self.sigma_out, sigma_tilde=self.sigma_tilde, rho=self.rho, stream=stream)
+        return self.sigma_out
+
+    def forward(self, tinv=None, stream=None):
+        self.solve_tau(tinv, stream)
+        return self.sigma(stream)
+
+    def backward(self, grad_sigma, tinv=None, stream=None):
+        """PyTorch gradients of Re sum(conj(grad_sigma) sigma): per site [nE, N, K, K] and per species."""
+        import torch
+        if self._bw_ws is None:
+            mn, al = B.backward_workspace_bytes(self.liz, self.lmax, self.z.shape[0], B._prec(self.precision))
+            self._bw_ws = torch.empty(min(al, max(mn, self.workspace.numel())), dtype=torch.uint8,
+                                      device=self.device)
+        t = self.tinv if tinv is None else tinv
+        return B.kubo_sigma_backward(self.liz, self.lmax, self.species, t, self.z, self.J, self.tau, self.volume,
+                                     grad_sigma.contiguous(), self.precision, lu_store=self.lu_store,
+                                     workspace=self._bw_ws, stream=stream)
+
+
+def _sigma_fn():
+    import torch
+
+    class SigmaFn(torch.autograd.Function):
+        """sigma [n_delta, 3, 3] as a differentiable function of the per-species tinv."""
+
+        @staticmethod
+        def forward(ctx, tinv, problem):
+            s = problem.forward(tinv.detach().contiguous())
+            ctx.problem = problem
+            ctx.save_for_backward(tinv)
+            return s.clone()
+
+        @staticmethod
+        def backward(ctx, grad_sigma):
+            (tinv,) = ctx.saved_tensors
+            _, g_species = ctx.problem.backward(grad_sigma.to(torch.complex128), tinv.detach().contiguous())
+            return g_species, None
+
+    return SigmaFn
+
+
+SigmaFn = None
+
+
+def sigma_autograd(tinv, problem):
+    global SigmaFn
+    if SigmaFn is None:
+        SigmaFn = _sigma_fn()
+    return SigmaFn.apply(tinv, problem)
+
+
+def conductivity(pos, lattice, r_liz, lmax, species, tinv, z, J, volume, precision="fp64"):
+    """Host-to-host conductivity: returns (sigma [n_delta,3,3] complex128, rho [n_delta,3,3]) as NumPy."""
+    p = Problem(pos, lattice, r_liz, lmax, species, tinv, z, J, volume, precision=precision, keep_factors=False)
+    p.forward()
+    return p.sigma_out.cpu().numpy(), p.rho.cpu().numpy()

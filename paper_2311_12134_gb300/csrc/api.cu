@@ -1,0 +1,865 @@
+// C ABI entry points of liblsmskubo, the per-device tables and work plans, and
+// the kernels that assemble the LIZ KKR matrices and refine the tau blocks.
+//
+// Path per call of lsms_tau_blocks (Eq. tau-inverse on every LIZ):
+//   k_assemble   M = T^{-1} - g, g from Gaunt x h_l(kappa R) x Y_L(R^)
+//   lu (lu.cu)   P M = L U, blocked, all units of a chunk per launch
+//   k_solve      X = M^{-1} E0 -> tau^{p0}
+//   mixed form:  complex64 LU/solves, then k_residual (FP64 B - M X) /
+//                k_solve (complex64 correction) / k_ir_update until the
+//                correction is below 1e-10 of X (at most kIrMaxIter sweeps)
+//   k_write_tau  scatter X into tau[e][site]
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "common.cuh"
+
+namespace lsms {
+
+std::atomic<long long> g_launches{0};
+
+// kernels in kubo.cu
+int kubo_forward(const int64_t* offsets, const int32_t* site_atom, const int32_t* species, int n_species,
+                 const double2* J, int64_t J_dstride, const double2* tau, int64_t S_total, int K, int n_atoms, int n_delta,
+                 double volume, double2* partial, double2* S, double2* sigma_tilde, double2* sigma, double* rho,
+                 cudaStream_t st);
+int adj_abar(const int32_t* species, int n_species, const double2* J, int64_t J_dstride, const double2* w, int K,
+             double volume, int n_atoms, int n_delta, double2* abar, cudaStream_t st);
+int adj_rhs(const Unit* d_units, int n_units, int S_max, const int32_t* site_atom, const int32_t* species,
+            int n_species, const double2* J, int64_t J_dstride, const double2* tau, int64_t S_total,
+            const double2* abar, int n_delta, int K, char* ws, cudaStream_t st);
+int adj_site(const Unit* d_units, int n_units, int S_max, const double2* tau, int64_t S_total, int K, const char* ws,
+             double2* G, cudaStream_t st);
+int adj_reduce(const int64_t* inv_off, const int64_t* inv_sites, const double2* G, int64_t S_total, int K,
+               int n_atoms, int n_energy, double2* grad, cudaStream_t st);
+int adj_species(const int32_t* species, const double2* grad, int K, int n_atoms, int n_species, int n_energy,
+                double2* out, cudaStream_t st);
+
+constexpr int kIrMaxIter = 6;
+constexpr double kIrTol = 1e-10;
+constexpr size_t kAlign = 256;
+static inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// ------------------------------------------------------------------ constant tables
+__constant__ int32_t c_cp_start[kMaxK * kMaxK + 1];
+__constant__ int32_t c_cp_lpp[1024];
+__constant__ double c_cp_coef[1024];
+__constant__ double c_ylm_norm[kMaxK3];
+__constant__ int32_t c_l_of[kMaxK3];
+
+static std::mutex g_dev_mu;
+static bool g_dev_init[64];
+
+static int ensure_device_tables(int dev) {
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (dev < 0 || dev >= 64) return fail(LSMS_ERR_CUDA, "device index %d unsupported", dev);
+  if (g_dev_init[dev]) return LSMS_OK;
+  const Coupling cp = g_coupling(kMaxLmax);
+  if (cp.lpp.size() > 1024) return fail(LSMS_ERR_ARG, "internal: coupling table too large");
+  const std::vector<double> nrm = ylm_norm(kMaxL3);
+  std::vector<int32_t> lof(kMaxK3);
+  for (int L = 0; L < kMaxK3; ++L) {
+    int l = 0;
+    while ((l + 1) * (l + 1) <= L) ++l;
+    lof[L] = l;
+  }
+  LSMS_CUDA_TRY(cudaMemcpyToSymbol(c_cp_start, cp.start.data(), cp.start.size() * sizeof(int32_t)));
+  LSMS_CUDA_TRY(cudaMemcpyToSymbol(c_cp_lpp, cp.lpp.data(), cp.lpp.size() * sizeof(int32_t)));
+  LSMS_CUDA_TRY(cudaMemcpyToSymbol(c_cp_coef, cp.coef.data(), cp.coef.size() * sizeof(double)));
+  LSMS_CUDA_TRY(cudaMemcpyToSymbol(c_ylm_norm, nrm.data(), nrm.size() * sizeof(double)));
+  LSMS_CUDA_TRY(cudaMemcpyToSymbol(c_l_of, lof.data(), lof.size() * sizeof(int32_t)));
+  g_dev_init[dev] = true;
+  return LSMS_OK;
+}
+
+template <typename T>
+static int upload(T** dst, const std::vector<T>& src) {
+  LSMS_CUDA_TRY(cudaMalloc((void**)dst, std::max<size_t>(1, src.size()) * sizeof(T)));
+  if (!src.empty()) LSMS_CUDA_TRY(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return LSMS_OK;
+}
+
+// Device copy of the LIZ arrays (made once per device, synchronous).
+static int device_data(lsms_liz* liz, DeviceData** out) {
+  int dev = 0;
+  LSMS_CUDA_TRY(cudaGetDevice(&dev));
+  int rc = ensure_device_tables(dev);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(liz->mu);
+  auto it = liz->dev.find(dev);
+  if (it == liz->dev.end()) {
+    DeviceData dd;
+    std::vector<double> disp(liz->disp);
+    if ((rc = upload(&dd.offsets, liz->offsets))) return rc;
+    if ((rc = upload(&dd.site_atom, liz->site_atom))) return rc;
+    if ((rc = upload(&dd.disp, disp))) return rc;
+    if ((rc = upload(&dd.inv_off, liz->inv_off))) return rc;
+    if ((rc = upload(&dd.inv_sites, liz->inv_sites))) return rc;
+    if ((rc = upload(&dd.site_centre, liz->site_centre))) return rc;
+    it = liz->dev.emplace(dev, std::move(dd)).first;
+  }
+  *out = &it->second;
+  return LSMS_OK;
+}
+
+// ------------------------------------------------------------------ plans
+struct UnitBytes {
+  size_t fac, piv, m64, x, b, x32;
+};
+
+static UnitBytes unit_bytes(int n, int precision, int nrhs, bool backward) {
+  UnitBytes ub{};
+  const size_t nn = (size_t)n * n;
+  ub.fac = align_up(nn * (precision == LSMS_FP64 ? 16 : 8));
+  ub.piv = align_up((size_t)n * 4);
+  ub.m64 = precision == LSMS_FP64 ? 0 : align_up(nn * 16);
+  ub.x = align_up((size_t)n * nrhs * 16);
+  ub.b = backward ? align_up((size_t)n * nrhs * 16) : 0;
+  ub.x32 = precision == LSMS_FP64 ? 0 : align_up((size_t)n * nrhs * 8);
+  return ub;
+}
+
+static size_t ws_unit_bytes(const UnitBytes& ub, bool store) {
+  return (store ? 0 : ub.fac + ub.piv) + ub.m64 + ub.x + ub.b + ub.x32;
+}
+
+// Atoms sorted by LIZ size (largest first, then atom index); every energy of an atom is adjacent.
+static std::vector<int> atom_order(const lsms_liz* liz) {
+  std::vector<int> order(liz->n_atoms);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (liz->offsets[a + 1] - liz->offsets[a]) > (liz->offsets[b + 1] - liz->offsets[b]);
+  });
+  return order;
+}
+
+struct WsHeader {
+  size_t stat, done, extra, chunk;  // byte offsets
+  size_t total_fixed;
+};
+
+static WsHeader ws_header(const lsms_liz* liz, int n_energy, size_t extra_bytes) {
+  WsHeader h{};
+  const size_t nu = (size_t)liz->n_atoms * n_energy;
+  h.stat = 0;
+  h.done = align_up(nu * 4);
+  h.extra = h.done + align_up(nu * 4);
+  h.chunk = h.extra + align_up(extra_bytes);
+  h.total_fixed = h.chunk;
+  return h;
+}
+
+static size_t backward_extra_bytes(const lsms_liz* liz, int lmax, int n_energy) {
+  const size_t KK = (size_t)(lmax + 1) * (lmax + 1) * (lmax + 1) * (lmax + 1);
+  const int n_delta = n_energy / 2;
+  return align_up((size_t)liz->n_atoms * n_delta * 12 * KK * 16) + align_up((size_t)n_energy * liz->total_sites * KK * 16);
+}
+
+static int get_plan(lsms_liz* liz, DeviceData* dd, int lmax, int n_energy, int precision, int nrhs, bool backward,
+                    bool store, size_t chunk_bytes, Plan** out) {
+  const auto key = std::make_tuple(lmax, n_energy, precision, nrhs * 4 + (backward ? 2 : 0) + (store ? 1 : 0),
+                                   chunk_bytes, 0);
+  std::lock_guard<std::mutex> lk(liz->mu);
+  auto it = dd->plans.find(key);
+  if (it != dd->plans.end()) {
+    *out = &it->second;
+    return LSMS_OK;
+  }
+  const int K = (lmax + 1) * (lmax + 1);
+  Plan p;
+  p.lmax = lmax;
+  p.n_energy = n_energy;
+  p.precision = precision;
+  p.nrhs = nrhs;
+  p.store = store;
+  p.ws_bytes = chunk_bytes;
+  const std::vector<int> order = atom_order(liz);
+  size_t store_off = 0;
+  size_t cur = 0;
+  Chunk ch{0, 0, 0, 0};
+  for (int m : order) {
+    const int S = (int)(liz->offsets[m + 1] - liz->offsets[m]);
+    const int n = K * S;
+    const UnitBytes ub = unit_bytes(n, precision, nrhs, backward);
+    const size_t need = ws_unit_bytes(ub, store);
+    if (need > chunk_bytes) return fail(LSMS_ERR_NOMEM, "workspace of %zu bytes cannot hold one unit (%zu bytes)", chunk_bytes, need);
+    for (int e = 0; e < n_energy; ++e) {
+      if (cur + need > chunk_bytes) {
+        ch.u1 = (int)p.units.size();
+        ch.ws_bytes = cur;
+        p.chunks.push_back(ch);
+        ch = Chunk{(int)p.units.size(), 0, 0, 0};
+        cur = 0;
+      }
+      Unit u{};
+      u.atom = m;
+      u.energy = e;
+      u.n = n;
+      u.S = S;
+      u.site_off = liz->offsets[m];
+      if (store) {
+        u.fac_off = (int64_t)store_off;
+        u.piv_off = (int64_t)(store_off + ub.fac);
+        store_off += ub.fac + ub.piv;
+      } else {
+        u.fac_off = (int64_t)cur;
+        u.piv_off = (int64_t)(cur + ub.fac);
+        cur += ub.fac + ub.piv;
+      }
+      u.m64_off = (int64_t)cur;
+      cur += ub.m64;
+      u.x_off = (int64_t)cur;
+      cur += ub.x;
+      u.r_off = (int64_t)cur;
+      cur += ub.b;
+      u.x32_off = (int64_t)cur;
+      cur += ub.x32;
+      u.stat_off = (int64_t)e * liz->n_atoms + m;  // index of this unit's status word
+      ch.n_max = std::max(ch.n_max, n);
+      p.units.push_back(u);
+    }
+  }
+  ch.u1 = (int)p.units.size();
+  ch.ws_bytes = cur;
+  p.chunks.push_back(ch);
+  int rc = upload(&p.d_units, p.units);
+  if (rc) return rc;
+  it = dd->plans.emplace(key, std::move(p)).first;
+  *out = &it->second;
+  return LSMS_OK;
+}
+
+// ------------------------------------------------------------------ assembly
+__device__ void ylm_hankel(double rx, double ry, double rz, double2 kap, bool adv, double* Y, double2* H, int lane) {
+  const double d = sqrt(rx * rx + ry * ry + rz * rz);
+  const double x = rx / d, y = ry / d, z = rz / d;
+  if (lane <= kMaxL3) {
+    const int m = lane;
+    double tr = 1.0, ti = 0.0;  // (x + i y)^m = sin^m(theta) e^{i m phi}
+    for (int t = 0; t < m; ++t) {
+      const double nr = tr * x - ti * y;
+      ti = tr * y + ti * x;
+      tr = nr;
+    }
+    double qmm = 1.0;  // (2m-1)!!: P_m^m / sin^m without the Condon-Shortley phase
+    for (int t = 1; t <= m; ++t) qmm *= (2 * t - 1);
+    double q2 = 0.0, q1 = 0.0;
+    for (int l = m; l <= kMaxL3; ++l) {
+      double q;
+      if (l == m) q = qmm;
+      else if (l == m + 1) q = (2 * m + 1) * z * qmm;
+      else q = ((2 * l - 1) * z * q1 - (l + m - 1) * q2) / (l - m);
+      q2 = q1;
+      q1 = q;
+      if (m == 0) {
+        Y[l * l + l] = c_ylm_norm[l * l + l] * q;
+      } else {
+        Y[l * l + l + m] = c_ylm_norm[l * l + l + m] * q * tr;
+        Y[l * l + l - m] = c_ylm_norm[l * l + l - m] * q * ti;
+      }
+    }
+  } else if (lane == kMaxL3 + 1) {
+    const double2 xx = mk(kap.x * d, kap.y * d);
+    const double2 ix = crcp(xx);
+    double s, c;
+    sincos(xx.x, &s, &c);
+    double2 ex;
+    if (!adv) {
+      const double f = exp(-xx.y);
+      ex = mk(f * c, f * s);  // e^{i x}
+    } else {
+      const double f = exp(xx.y);
+      ex = mk(f * c, -f * s);  // e^{-i x}
+    }
+    double2 hm = cmul(ex, ix);                                         // h_{-1}
+    double2 h = adv ? mk(-hm.y, hm.x) : mk(hm.y, -hm.x);               // h_0 = +-i e^{-+ix}/x
+    H[0] = h;
+    for (int l = 0; l < kMaxL3; ++l) {
+      const double2 t = cmul(mk((2.0 * l + 1.0) * ix.x, (2.0 * l + 1.0) * ix.y), h);
+      const double2 hn = csub(t, hm);
+      hm = h;
+      h = hn;
+      H[l + 1] = h;
+    }
+  }
+}
+
+// grid (S_max, n_units), block 256: CTA = one row site p of one unit, loop over column sites q.
+// Writes the FP64 matrix (m64 at ws + m64_off when MIXED, else the factor array) and,
+// for MIXED, its complex64 rounding into the factor array.
+template <bool MIXED>
+__global__ void __launch_bounds__(256) k_assemble(const Unit* __restrict__ units, const double* __restrict__ disp,
+                                                  const int32_t* __restrict__ site_atom,
+                                                  const int32_t* __restrict__ species,
+                                                  const double2* __restrict__ tinv, int n_species, int n_energy,
+                                                  EnergyTable E, int K, char* fac_base, char* ws, bool write_fac,
+                                                  int32_t* stat) {
+  const Unit u = units[blockIdx.y];
+  const int p = blockIdx.x;
+  if (p >= u.S) return;
+  const int n = u.n;
+  const double2 z = E.z[u.energy];
+  const double r = hypot(z.x, z.y);
+  const double kre = sqrt(0.5 * (r + z.x));
+  double kim = sqrt(0.5 * fmax(r - z.x, 0.0));
+  if (z.y < 0.0) kim = -kim;
+  const double2 kap = mk(kre, kim);
+  const bool adv = z.y < 0.0;
+  // M = -g:  +4 pi i kappa * sum (retarded), -4 pi i kappa * sum (advanced)
+  const double four_pi = 4.0 * M_PI;
+  const double2 mpref = adv ? mk(four_pi * kim, -four_pi * kre) : mk(-four_pi * kim, four_pi * kre);
+  __shared__ double sY[2][kMaxK3];
+  __shared__ double2 sH[2][kMaxL3 + 1];
+  const int tid = threadIdx.x;
+  const int L = tid & 15, Lp = tid >> 4;
+  const bool act = (L < K) && (Lp < K);
+  const int64_t sp0 = u.site_off + p;
+  const double px = disp[3 * sp0], py = disp[3 * sp0 + 1], pz = disp[3 * sp0 + 2];
+  int spp = species[site_atom[sp0]];
+  int flags = 0;
+  if (spp < 0 || spp >= n_species) {  // reject without reading outside tinv
+    flags |= LSMS_UNIT_BAD_INPUT;
+    spp = 0;
+  }
+  double2* M64 = reinterpret_cast<double2*>(MIXED ? ws + u.m64_off : fac_base + u.fac_off);
+  float2* M32 = reinterpret_cast<float2*>(fac_base + u.fac_off);
+  int t0 = 0, t1 = 0;
+  if (act) {
+    t0 = c_cp_start[L * kMaxK + Lp];
+    t1 = c_cp_start[L * kMaxK + Lp + 1];
+  }
+  for (int q = 0; q < u.S; ++q) {
+    const int buf = q & 1;
+    if (q != p && tid < 32) {
+      const int64_t sq = u.site_off + q;
+      ylm_hankel(disp[3 * sq] - px, disp[3 * sq + 1] - py, disp[3 * sq + 2] - pz, kap, adv, sY[buf], sH[buf], tid);
+    }
+    __syncthreads();
+    if (act) {
+      double2 v;
+      if (q == p) {
+        v = tinv[(((size_t)spp * n_energy) + u.energy) * K * K + L * K + Lp];
+      } else {
+        double2 acc = mk(0.0, 0.0);
+        for (int t = t0; t < t1; ++t) {
+          const int lpp = c_cp_lpp[t];
+          const double w = c_cp_coef[t] * sY[buf][lpp];
+          const double2 h = sH[buf][c_l_of[lpp]];
+          acc.x = fma(w, h.x, acc.x);
+          acc.y = fma(w, h.y, acc.y);
+        }
+        v = cmul(mpref, acc);
+      }
+      if (!finite2(v)) flags |= LSMS_UNIT_NONFINITE;
+      const size_t idx = (size_t)(K * q + Lp) * n + K * p + L;
+      if (MIXED || write_fac) M64[idx] = v;
+      if (MIXED && write_fac) M32[idx] = to32(v);
+    }
+  }
+  if (flags) atomicOr(&stat[u.stat_off], flags);
+}
+
+// ------------------------------------------------------------------ RHS / refinement kernels
+// X (n x nrhs, column-major, complex<R>) = E0 (first K columns of the identity).
+template <typename C>
+__global__ void k_rhs_identity(const Unit* __restrict__ units, char* ws, int which, int K, int nrhs) {
+  const Unit u = units[blockIdx.y];
+  const int n = u.n;
+  C* X = reinterpret_cast<C*>(ws + (which == RHS_X ? u.x_off : u.x32_off));
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)n * nrhs;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n), c = (int)(idx / n);
+    X[idx] = (i == c && c < K) ? cvt<C>(make_double2(1.0, 0.0)) : cvt<C>(make_double2(0.0, 0.0));
+  }
+}
+
+// X32 = B (explicit right-hand side, complex128 at r_off) rounded; or X = B (FP64).
+__global__ void k_copy_b(const Unit* __restrict__ units, char* ws, int nrhs, bool to_x32) {
+  const Unit u = units[blockIdx.y];
+  const int n = u.n;
+  const double2* B = reinterpret_cast<const double2*>(ws + u.r_off);
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)n * nrhs;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    if (to_x32) reinterpret_cast<float2*>(ws + u.x32_off)[idx] = to32(B[idx]);
+    else reinterpret_cast<double2*>(ws + u.x_off)[idx] = B[idx];
+  }
+}
+
+// X = X32 widened.
+__global__ void k_widen(const Unit* __restrict__ units, char* ws, int nrhs) {
+  const Unit u = units[blockIdx.y];
+  const int n = u.n;
+  const float2* X32 = reinterpret_cast<const float2*>(ws + u.x32_off);
+  double2* X = reinterpret_cast<double2*>(ws + u.x_off);
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)n * nrhs;
+       idx += (int64_t)gridDim.x * blockDim.x)
+    X[idx] = to64(X32[idx]);
+}
+
+// FP64 residual, rounded to complex64 for the correction solve:
+//   X32 = B - M X   (B = E0 when explicit_b is false).
+// grid (ceil(n_max / 64), n_units), block 256: 64 rows x nrhs columns per CTA.
+__global__ void __launch_bounds__(256) k_residual(const Unit* __restrict__ units, char* ws, int K, int nrhs,
+                                                  bool explicit_b, const int32_t* __restrict__ done) {
+  const Unit u = units[blockIdx.y];
+  if (done[u.stat_off]) return;
+  const int n = u.n;
+  const int row0 = blockIdx.x * 64;
+  if (row0 >= n) return;
+  const double2* M = reinterpret_cast<const double2*>(ws + u.m64_off);
+  const double2* X = reinterpret_cast<const double2*>(ws + u.x_off);
+  float2* X32 = reinterpret_cast<float2*>(ws + u.x32_off);
+  __shared__ double2 sX[32][33];
+  const int tid = threadIdx.x;
+  const int r = tid & 63, cg = tid >> 6;  // 4 column groups
+  const int row = row0 + r;
+  const int cpg = (nrhs + 3) / 4;          // columns per group (<= 8)
+  double2 acc[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc[c] = mk(0.0, 0.0);
+  for (int j0 = 0; j0 < n; j0 += 32) {
+    const int jn = min(32, n - j0);
+    __syncthreads();
+    for (int idx = tid; idx < 32 * nrhs; idx += 256) {
+      const int jj = idx % 32, c = idx / 32;
+      sX[jj][c] = jj < jn ? X[(size_t)c * n + j0 + jj] : mk(0.0, 0.0);
+    }
+    __syncthreads();
+    if (row < n) {
+      for (int jj = 0; jj < jn; ++jj) {
+        const double2 mv = M[(size_t)(j0 + jj) * n + row];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int col = cg * cpg + c;
+          if (c < cpg && col < nrhs) acc[c] = cfma(mv, sX[jj][col], acc[c]);
+        }
+      }
+    }
+  }
+  if (row < n) {
+    const double2* B = reinterpret_cast<const double2*>(ws + u.r_off);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int col = cg * cpg + c;
+      if (c < cpg && col < nrhs) {
+        double2 b;
+        if (explicit_b) b = B[(size_t)col * n + row];
+        else b = (row == col && col < K) ? mk(1.0, 0.0) : mk(0.0, 0.0);
+        X32[(size_t)col * n + row] = to32(csub(b, acc[c]));
+      }
+    }
+  }
+}
+
+// X += X32 (the correction); done when ||correction||_F <= tol ||X||_F.  One CTA per unit.
+__global__ void __launch_bounds__(256) k_ir_update(const Unit* __restrict__ units, char* ws, int nrhs, double tol,
+                                                   int32_t* done, int32_t* stat) {
+  const Unit u = units[blockIdx.x];
+  if (done[u.stat_off]) return;
+  const int n = u.n;
+  const float2* D = reinterpret_cast<const float2*>(ws + u.x32_off);
+  double2* X = reinterpret_cast<double2*>(ws + u.x_off);
+  double dn = 0.0, xn = 0.0;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)n * nrhs; idx += blockDim.x) {
+    const double2 d = to64(D[idx]);
+    const double2 x = cadd(X[idx], d);
+    X[idx] = x;
+    dn += d.x * d.x + d.y * d.y;
+    xn += x.x * x.x + x.y * x.y;
+  }
+  __shared__ double s1[256], s2[256];
+  s1[threadIdx.x] = dn;
+  s2[threadIdx.x] = xn;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s1[threadIdx.x] += s1[threadIdx.x + w];
+      s2[threadIdx.x] += s2[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double a = s1[0], b = s2[0];
+    if (!isfinite(a) || !isfinite(b)) {
+      atomicOr(&stat[u.stat_off], LSMS_UNIT_NONFINITE);
+      done[u.stat_off] = 1;
+    } else if (a <= tol * tol * b) {
+      done[u.stat_off] = 1;
+    }
+  }
+}
+
+__global__ void k_ir_finish(const Unit* __restrict__ units, int n_units, const int32_t* done, int32_t* stat) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_units) return;
+  const Unit u = units[i];
+  if (!done[u.stat_off]) atomicOr(&stat[u.stat_off], LSMS_UNIT_NOCONV);
+}
+
+// tau[e][site_off + p][L][L'] = X[L' * n + K p + L].  grid (S_max, n_units).
+__global__ void k_write_tau(const Unit* __restrict__ units, const char* ws, int K, int64_t S_total,
+                            double2* __restrict__ tau) {
+  const Unit u = units[blockIdx.y];
+  const int p = blockIdx.x;
+  if (p >= u.S) return;
+  const int tid = threadIdx.x;
+  const int L = tid >> 4, Lp = tid & 15;
+  if (L >= K || Lp >= K) return;
+  const double2* X = reinterpret_cast<const double2*>(ws + u.x_off);
+  tau[(((size_t)u.energy * S_total) + u.site_off + p) * K * K + L * K + Lp] = X[(size_t)Lp * u.n + K * p + L];
+}
+
+__global__ void k_status_out(const int32_t* __restrict__ stat, int n, int32_t* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = stat[i];
+}
+
+// ------------------------------------------------------------------ shared driver
+struct Call {
+  lsms_liz* liz;
+  DeviceData* dd;
+  int lmax, K, n_species, n_energy, precision;
+  const int32_t* species;
+  const double2* tinv;
+  EnergyTable E;
+  cudaStream_t st;
+};
+
+static int check_common(const lsms_liz* liz, int lmax, const void* species, int n_species, int n_energy,
+                        int precision) {
+  if (!liz) return fail(LSMS_ERR_ARG, "NULL liz");
+  if (lmax < 0 || lmax > kMaxLmax) return fail(LSMS_ERR_ARG, "lmax must be in 0..%d", kMaxLmax);
+  if (!species || n_species < 1) return fail(LSMS_ERR_ARG, "species must be given, n_species >= 1");
+  if (n_energy < 1 || n_energy > kMaxEnergies) return fail(LSMS_ERR_ARG, "n_energy must be in 1..%d", kMaxEnergies);
+  if (precision != LSMS_FP64 && precision != LSMS_MIXED) return fail(LSMS_ERR_ARG, "unknown precision %d", precision);
+  return LSMS_OK;
+}
+
+// Assemble + factor one chunk (fac at fac_base), mixed form also writes the FP64 copy.
+static int assemble_factor(const Call& c, const Plan& p, const Chunk& ch, char* fac_base, char* ws, int32_t* stat,
+                           bool factor) {
+  const Unit* du = p.d_units + ch.u0;
+  const int nu = ch.u1 - ch.u0;
+  const int S_max = ch.n_max / c.K;
+  if (c.precision == LSMS_FP64) {
+    if (factor) {
+      LSMS_LAUNCH(k_assemble<false>, dim3(S_max, nu), dim3(256), 0, c.st, du, c.dd->disp, c.dd->site_atom, c.species,
+                  c.tinv, c.n_species, c.n_energy, c.E, c.K, fac_base, ws, true, stat);
+      return lu_factor_chunk<double>(du, nu, ch.n_max, fac_base, stat, c.st);
+    }
+    return LSMS_OK;
+  }
+  LSMS_LAUNCH(k_assemble<true>, dim3(S_max, nu), dim3(256), 0, c.st, du, c.dd->disp, c.dd->site_atom, c.species,
+              c.tinv, c.n_species, c.n_energy, c.E, c.K, fac_base, ws, factor, stat);
+  if (factor) return lu_factor_chunk<float>(du, nu, ch.n_max, fac_base, stat, c.st);
+  return LSMS_OK;
+}
+
+// Solve M X = B for a chunk whose factors exist.  B = E0 (forward) or the explicit
+// complex128 block at r_off (backward).  Result in X (complex128).
+static int solve_refine(const Call& c, const Plan& p, const Chunk& ch, const char* fac_base, char* ws, int32_t* stat,
+                        int32_t* done, bool explicit_b) {
+  const Unit* du = p.d_units + ch.u0;
+  const int nu = ch.u1 - ch.u0;
+  const int nrhs = p.nrhs;
+  const dim3 g1((ch.n_max * nrhs + 255) / 256, nu);
+  int rc;
+  if (c.precision == LSMS_FP64) {
+    if (explicit_b) LSMS_LAUNCH(k_copy_b, g1, dim3(256), 0, c.st, du, ws, nrhs, false);
+    else LSMS_LAUNCH(k_rhs_identity<double2>, g1, dim3(256), 0, c.st, du, ws, (int)RHS_X, c.K, nrhs);
+    return lu_solve_chunk<double>(du, nu, fac_base, ws, RHS_X, nrhs, nullptr, c.st);
+  }
+  if (explicit_b) LSMS_LAUNCH(k_copy_b, g1, dim3(256), 0, c.st, du, ws, nrhs, true);
+  else LSMS_LAUNCH(k_rhs_identity<float2>, g1, dim3(256), 0, c.st, du, ws, (int)RHS_X32, c.K, nrhs);
+  if ((rc = lu_solve_chunk<float>(du, nu, fac_base, ws, RHS_X32, nrhs, nullptr, c.st))) return rc;
+  LSMS_LAUNCH(k_widen, g1, dim3(256), 0, c.st, du, ws, nrhs);
+  // done flags of this chunk's units start cleared (memset by the caller)
+  for (int it = 0; it < kIrMaxIter; ++it) {
+    LSMS_LAUNCH(k_residual, dim3((ch.n_max + 63) / 64, nu), dim3(256), 0, c.st, du, ws, c.K, nrhs, explicit_b, done);
+    if ((rc = lu_solve_chunk<float>(du, nu, fac_base, ws, RHS_X32, nrhs, done, c.st))) return rc;
+    LSMS_LAUNCH(k_ir_update, dim3(nu), dim3(256), 0, c.st, du, ws, nrhs, kIrTol, done, stat);
+  }
+  LSMS_LAUNCH(k_ir_finish, dim3((nu + 255) / 256), dim3(256), 0, c.st, du, nu, done, stat);
+  return LSMS_OK;
+}
+
+static int begin_call(lsms_liz* liz, const lsms_complex* z, int n_energy, Call* c) {
+  for (int e = 0; e < n_energy; ++e) {
+    if (!std::isfinite(z[e].re) || !std::isfinite(z[e].im)) return fail(LSMS_ERR_ARG, "energy %d is not finite", e);
+    c->E.z[e] = make_double2(z[e].re, z[e].im);
+  }
+  for (int e = n_energy; e < kMaxEnergies; ++e) c->E.z[e] = make_double2(0.0, 0.0);
+  return device_data(liz, &c->dd);
+}
+
+}  // namespace lsms
+
+using namespace lsms;
+
+// ------------------------------------------------------------------ C ABI
+extern "C" long long lsms_launch_count(void) { return g_launches.load(); }
+
+extern "C" void lsms_liz_destroy(lsms_liz* liz) {
+  if (!liz) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  for (auto& kv : liz->dev) {
+    if (cudaSetDevice(kv.first) != cudaSuccess) continue;
+    DeviceData& d = kv.second;
+    cudaFree(d.offsets);
+    cudaFree(d.site_atom);
+    cudaFree(d.disp);
+    cudaFree(d.inv_off);
+    cudaFree(d.inv_sites);
+    cudaFree(d.site_centre);
+    for (auto& pk : d.plans) cudaFree(pk.second.d_units);
+  }
+  if (cur >= 0) cudaSetDevice(cur);
+  delete liz;
+}
+
+static size_t unit_ws_max_sum(const lsms_liz* liz, int lmax, int n_energy, int precision, int nrhs, bool backward,
+                              size_t* sum) {
+  const int K = (lmax + 1) * (lmax + 1);
+  size_t mx = 0, s = 0;
+  for (int m = 0; m < liz->n_atoms; ++m) {
+    const int n = K * (int)(liz->offsets[m + 1] - liz->offsets[m]);
+    const size_t b = ws_unit_bytes(unit_bytes(n, precision, nrhs, backward), false);
+    mx = std::max(mx, b);
+    s += b * n_energy;
+  }
+  *sum = s;
+  return mx;
+}
+
+extern "C" int lsms_tau_workspace_bytes(const lsms_liz* liz, int lmax, int n_energy, int precision, size_t* min_bytes,
+                                        size_t* all_bytes) {
+  clear_error();
+  if (!liz || lmax < 0 || lmax > kMaxLmax || n_energy < 1 || n_energy > kMaxEnergies)
+    return fail(LSMS_ERR_ARG, "lsms_tau_workspace_bytes: bad arguments");
+  const int K = (lmax + 1) * (lmax + 1);
+  size_t sum = 0;
+  const size_t mx = unit_ws_max_sum(liz, lmax, n_energy, precision, K, false, &sum);
+  const WsHeader h = ws_header(liz, n_energy, 0);
+  if (min_bytes) *min_bytes = h.total_fixed + mx;
+  if (all_bytes) *all_bytes = h.total_fixed + sum;
+  return LSMS_OK;
+}
+
+extern "C" int lsms_backward_workspace_bytes(const lsms_liz* liz, int lmax, int n_energy, int precision,
+                                             size_t* min_bytes, size_t* all_bytes) {
+  clear_error();
+  if (!liz || lmax < 0 || lmax > kMaxLmax || n_energy < 2 || n_energy > kMaxEnergies || (n_energy & 1))
+    return fail(LSMS_ERR_ARG, "lsms_backward_workspace_bytes: bad arguments");
+  const int K = (lmax + 1) * (lmax + 1);
+  size_t sum = 0;
+  const size_t mx = unit_ws_max_sum(liz, lmax, n_energy, precision, 2 * K, true, &sum);
+  const WsHeader h = ws_header(liz, n_energy, backward_extra_bytes(liz, lmax, n_energy));
+  if (min_bytes) *min_bytes = h.total_fixed + mx;
+  if (all_bytes) *all_bytes = h.total_fixed + sum;
+  return LSMS_OK;
+}
+
+extern "C" int lsms_lu_store_bytes(const lsms_liz* liz, int lmax, int n_energy, int precision, size_t* bytes) {
+  clear_error();
+  if (!liz || !bytes || lmax < 0 || lmax > kMaxLmax || n_energy < 1 || n_energy > kMaxEnergies ||
+      (precision != LSMS_FP64 && precision != LSMS_MIXED))
+    return fail(LSMS_ERR_ARG, "lsms_lu_store_bytes: bad arguments");
+  const int K = (lmax + 1) * (lmax + 1);
+  size_t s = 0;
+  for (int m = 0; m < liz->n_atoms; ++m) {
+    const int n = K * (int)(liz->offsets[m + 1] - liz->offsets[m]);
+    const UnitBytes ub = unit_bytes(n, precision, K, false);
+    s += (ub.fac + ub.piv) * n_energy;
+  }
+  *bytes = s;
+  return LSMS_OK;
+}
+
+static const size_t kDefaultChunkBudget = (size_t)8 << 30;
+
+extern "C" int lsms_tau_blocks(const lsms_liz* liz_c, int lmax, const int32_t* species, int n_species,
+                               const lsms_complex* tinv, const lsms_complex* z, int n_energy, int precision,
+                               lsms_complex* tau, int32_t* unit_status, void* workspace, size_t workspace_bytes,
+                               void* lu_store, size_t lu_store_bytes, void* stream) {
+  clear_error();
+  lsms_liz* liz = const_cast<lsms_liz*>(liz_c);
+  int rc = check_common(liz, lmax, species, n_species, n_energy, precision);
+  if (rc) return rc;
+  if (!tinv || !z || !tau) return fail(LSMS_ERR_ARG, "lsms_tau_blocks: tinv, z and tau are required");
+  Call c{};
+  c.liz = liz;
+  c.lmax = lmax;
+  c.K = (lmax + 1) * (lmax + 1);
+  c.n_species = n_species;
+  c.n_energy = n_energy;
+  c.precision = precision;
+  c.species = species;
+  c.tinv = reinterpret_cast<const double2*>(tinv);
+  c.st = reinterpret_cast<cudaStream_t>(stream);
+  if ((rc = begin_call(liz, z, n_energy, &c))) return rc;
+  size_t need_store = 0;
+  if (lu_store) {
+    if ((rc = lsms_lu_store_bytes(liz, lmax, n_energy, precision, &need_store))) return rc;
+    if (lu_store_bytes < need_store)
+      return fail(LSMS_ERR_NOMEM, "lu_store holds %zu bytes, %zu needed", lu_store_bytes, need_store);
+  }
+  const bool store = lu_store != nullptr;
+  size_t min_b = 0, all_b = 0;
+  lsms_tau_workspace_bytes(liz, lmax, n_energy, precision, &min_b, &all_b);
+  const WsHeader h = ws_header(liz, n_energy, 0);
+  char* ws = static_cast<char*>(workspace);
+  bool own = false;
+  size_t ws_bytes = workspace_bytes;
+  if (!ws) {
+    ws_bytes = std::min(all_b, std::max(min_b, kDefaultChunkBudget));
+    LSMS_CUDA_TRY(cudaMallocAsync((void**)&ws, ws_bytes, c.st));
+    own = true;
+  } else if (ws_bytes < min_b) {
+    return fail(LSMS_ERR_NOMEM, "workspace holds %zu bytes, at least %zu needed", ws_bytes, min_b);
+  }
+  Plan* p = nullptr;
+  if ((rc = get_plan(liz, c.dd, lmax, n_energy, precision, c.K, false, store, ws_bytes - h.total_fixed, &p))) {
+    if (own) cudaFreeAsync(ws, c.st);
+    return rc;
+  }
+  int32_t* stat = reinterpret_cast<int32_t*>(ws + h.stat);
+  int32_t* done = reinterpret_cast<int32_t*>(ws + h.done);
+  const size_t nu_all = (size_t)liz->n_atoms * n_energy;
+  rc = [&]() -> int {
+    LSMS_CUDA_TRY(cudaMemsetAsync(stat, 0, nu_all * 4, c.st));
+    LSMS_CUDA_TRY(cudaMemsetAsync(done, 0, nu_all * 4, c.st));
+    char* chunk = ws + h.chunk;
+    char* fac_base = store ? static_cast<char*>(lu_store) : chunk;
+    for (const Chunk& ch : p->chunks) {
+      int r2 = assemble_factor(c, *p, ch, fac_base, chunk, stat, true);
+      if (r2) return r2;
+      if ((r2 = solve_refine(c, *p, ch, fac_base, chunk, stat, done, false))) return r2;
+      LSMS_LAUNCH(k_write_tau, dim3(ch.n_max / c.K, ch.u1 - ch.u0), dim3(256), 0, c.st, p->d_units + ch.u0, chunk,
+                  c.K, liz->total_sites, reinterpret_cast<double2*>(tau));
+    }
+    if (unit_status)
+      LSMS_LAUNCH(k_status_out, dim3((unsigned)((nu_all + 255) / 256)), dim3(256), 0, c.st, stat, (int)nu_all,
+                  unit_status);
+    return LSMS_OK;
+  }();
+  if (own) cudaFreeAsync(ws, c.st);
+  return rc;
+}
+
+extern "C" int lsms_kubo_sigma(const lsms_liz* liz_c, int lmax, const int32_t* species, int n_species,
+                               const lsms_complex* J, int64_t J_delta_stride, const lsms_complex* tau, int n_delta,
+                               double volume, lsms_complex* sigma_tilde, lsms_complex* sigma, double* rho,
+                               void* stream) {
+  clear_error();
+  lsms_liz* liz = const_cast<lsms_liz*>(liz_c);
+  int rc = check_common(liz, lmax, species, n_species, 2 * std::max(n_delta, 1), LSMS_FP64);
+  if (rc) return rc;
+  if (n_delta < 1 || !J || !tau || !sigma) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma: J, tau, sigma required, n_delta >= 1");
+  if (!(volume > 0.0) || !std::isfinite(volume)) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma: volume must be > 0");
+  if (J_delta_stride < 0) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma: negative J stride");
+  DeviceData* dd = nullptr;
+  if ((rc = device_data(liz, &dd))) return rc;
+  const int K = (lmax + 1) * (lmax + 1);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t part_bytes = align_up((size_t)n_delta * 4 * liz->n_atoms * 9 * 16);
+  const size_t s_bytes = align_up((size_t)n_delta * 36 * 16);
+  char* scratch = nullptr;
+  LSMS_CUDA_TRY(cudaMallocAsync((void**)&scratch, part_bytes + s_bytes, st));
+  rc = kubo_forward(dd->offsets, dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J), J_delta_stride,
+                    reinterpret_cast<const double2*>(tau), liz->total_sites, K, liz->n_atoms, n_delta, volume,
+                    reinterpret_cast<double2*>(scratch), reinterpret_cast<double2*>(scratch + part_bytes),
+                    reinterpret_cast<double2*>(sigma_tilde), reinterpret_cast<double2*>(sigma), rho, st);
+  cudaFreeAsync(scratch, st);
+  return rc;
+}
+
+extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const int32_t* species, int n_species,
+                                        const lsms_complex* tinv, const lsms_complex* z, int n_energy, int precision,
+                                        const lsms_complex* J, int64_t J_delta_stride, const lsms_complex* tau,
+                                        double volume, const lsms_complex* grad_sigma, const void* lu_store,
+                                        size_t lu_store_bytes, lsms_complex* grad_tinv,
+                                        lsms_complex* grad_tinv_species, void* workspace,
+                                        size_t workspace_bytes, void* stream) {
+  clear_error();
+  lsms_liz* liz = const_cast<lsms_liz*>(liz_c);
+  int rc = check_common(liz, lmax, species, n_species, n_energy, precision);
+  if (rc) return rc;
+  if ((n_energy & 1) || !tinv || !z || !J || !tau || !grad_sigma || !grad_tinv)
+    return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_backward: missing argument or odd n_energy");
+  if (!(volume > 0.0)) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_backward: volume must be > 0");
+  Call c{};
+  c.liz = liz;
+  c.lmax = lmax;
+  c.K = (lmax + 1) * (lmax + 1);
+  c.n_species = n_species;
+  c.n_energy = n_energy;
+  c.precision = precision;
+  c.species = species;
+  c.tinv = reinterpret_cast<const double2*>(tinv);
+  c.st = reinterpret_cast<cudaStream_t>(stream);
+  if ((rc = begin_call(liz, z, n_energy, &c))) return rc;
+  const bool store = lu_store != nullptr;
+  if (store) {
+    size_t need = 0;
+    if ((rc = lsms_lu_store_bytes(liz, lmax, n_energy, precision, &need))) return rc;
+    if (lu_store_bytes < need) return fail(LSMS_ERR_NOMEM, "lu_store holds %zu bytes, %zu needed", lu_store_bytes, need);
+  }
+  const int n_delta = n_energy / 2;
+  const size_t KK = (size_t)c.K * c.K;
+  size_t min_b = 0, all_b = 0;
+  lsms_backward_workspace_bytes(liz, lmax, n_energy, precision, &min_b, &all_b);
+  const WsHeader h = ws_header(liz, n_energy, backward_extra_bytes(liz, lmax, n_energy));
+  char* ws = static_cast<char*>(workspace);
+  bool own = false;
+  size_t ws_bytes = workspace_bytes;
+  if (!ws) {
+    ws_bytes = std::min(all_b, std::max(min_b, kDefaultChunkBudget));
+    LSMS_CUDA_TRY(cudaMallocAsync((void**)&ws, ws_bytes, c.st));
+    own = true;
+  } else if (ws_bytes < min_b) {
+    return fail(LSMS_ERR_NOMEM, "workspace holds %zu bytes, at least %zu needed", ws_bytes, min_b);
+  }
+  Plan* p = nullptr;
+  if ((rc = get_plan(liz, c.dd, lmax, n_energy, precision, 2 * c.K, true, store, ws_bytes - h.total_fixed, &p))) {
+    if (own) cudaFreeAsync(ws, c.st);
+    return rc;
+  }
+  int32_t* stat = reinterpret_cast<int32_t*>(ws + h.stat);
+  int32_t* done = reinterpret_cast<int32_t*>(ws + h.done);
+  double2* abar = reinterpret_cast<double2*>(ws + h.extra);
+  double2* G = reinterpret_cast<double2*>(ws + h.extra + align_up((size_t)liz->n_atoms * n_delta * 12 * KK * 16));
+  const size_t nu_all = (size_t)liz->n_atoms * n_energy;
+  rc = [&]() -> int {
+    LSMS_CUDA_TRY(cudaMemsetAsync(stat, 0, nu_all * 4, c.st));
+    LSMS_CUDA_TRY(cudaMemsetAsync(done, 0, nu_all * 4, c.st));
+    int r2 = adj_abar(species, n_species, reinterpret_cast<const double2*>(J), J_delta_stride,
+                      reinterpret_cast<const double2*>(grad_sigma), c.K, volume, liz->n_atoms, n_delta, abar, c.st);
+    if (r2) return r2;
+    char* chunk = ws + h.chunk;
+    char* fac_base = store ? const_cast<char*>(static_cast<const char*>(lu_store)) : chunk;
+    for (const Chunk& ch : p->chunks) {
+      const Unit* du = p->d_units + ch.u0;
+      const int nu = ch.u1 - ch.u0;
+      const int S_max = ch.n_max / c.K;
+      if ((r2 = assemble_factor(c, *p, ch, fac_base, chunk, stat, !store))) return r2;
+      if ((r2 = adj_rhs(du, nu, S_max, c.dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J), J_delta_stride,
+                        reinterpret_cast<const double2*>(tau), liz->total_sites, abar, n_delta, c.K, chunk, c.st)))
+        return r2;
+      if ((r2 = solve_refine(c, *p, ch, fac_base, chunk, stat, done, true))) return r2;
+      if ((r2 = adj_site(du, nu, S_max, reinterpret_cast<const double2*>(tau), liz->total_sites, c.K, chunk, G, c.st)))
+        return r2;
+    }
+    if ((r2 = adj_reduce(c.dd->inv_off, c.dd->inv_sites, G, liz->total_sites, c.K, liz->n_atoms, n_energy,
+                         reinterpret_cast<double2*>(grad_tinv), c.st)))
+      return r2;
+    if (grad_tinv_species)
+      return adj_species(species, reinterpret_cast<const double2*>(grad_tinv), c.K, liz->n_atoms, n_species, n_energy,
+                         reinterpret_cast<double2*>(grad_tinv_species), c.st);
+    return LSMS_OK;
+  }();
+  if (own) cudaFreeAsync(ws, c.st);
+  return rc;
+}

@@ -1,0 +1,110 @@
+// Device helpers and cross-file kernel wrappers of liblsmskubo.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace lsms {
+
+extern std::atomic<long long> g_launches;
+
+#define LSMS_CUDA_TRY(expr)                                                              \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess)                                                               \
+      return ::lsms::fail(LSMS_ERR_CUDA, "%s failed: %s (%s:%d)", #expr,                 \
+                          cudaGetErrorString(_e), __FILE__, __LINE__);                   \
+  } while (0)
+
+// Every kernel launch goes through this: it counts launches and reports a bad
+// launch configuration at once.
+#define LSMS_LAUNCH(kernel, grid, block, smem, stream, ...)                             \
+  do {                                                                                   \
+    kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                         \
+    ::lsms::g_launches.fetch_add(1, std::memory_order_relaxed);                          \
+    cudaError_t _e = cudaGetLastError();                                                 \
+    if (_e != cudaSuccess)                                                               \
+      return ::lsms::fail(LSMS_ERR_CUDA, "launch of %s failed: %s", #kernel,             \
+                          cudaGetErrorString(_e));                                       \
+  } while (0)
+
+constexpr int kMaxEnergies = 64;
+struct EnergyTable {
+  double2 z[kMaxEnergies];
+};
+
+// ------------------------------------------------------------------ complex
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+
+template <typename R> struct CxT;
+template <> struct CxT<double> { using T = double2; };
+template <> struct CxT<float> { using T = float2; };
+template <typename R> using Cx = typename CxT<R>::T;
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc + a*b
+template <typename C> __device__ __forceinline__ C cfma(C a, C b, C acc) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+// acc - a*b
+template <typename C> __device__ __forceinline__ C cfms(C a, C b, C acc) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+  return acc;
+}
+// acc + a^T-free conj(a)*b is not needed; real scale:
+template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) { return mk(a.x * s, a.y * s); }
+
+__device__ __forceinline__ double2 crcp(double2 a) {
+  const double d = a.x * a.x + a.y * a.y;
+  return make_double2(a.x / d, -a.y / d);
+}
+__device__ __forceinline__ float2 crcp(float2 a) {
+  const float d = a.x * a.x + a.y * a.y;
+  return make_float2(a.x / d, -a.y / d);
+}
+__device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
+__device__ __forceinline__ float cabs1(float2 a) { return fabsf(a.x) + fabsf(a.y); }
+
+__device__ __forceinline__ float2 to32(double2 a) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double2 to64(float2 a) { return make_double2((double)a.x, (double)a.y); }
+__device__ __forceinline__ double2 to64(double2 a) { return a; }
+template <typename C> __device__ __forceinline__ C cvt(double2 a);
+template <> __device__ __forceinline__ double2 cvt<double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 cvt<float2>(double2 a) { return to32(a); }
+
+__device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+__device__ __forceinline__ bool finite2(float2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+// ------------------------------------------------------------------ wrappers (lu.cu)
+// Blocked right-looking LU with partial pivoting of every unit of a chunk, in
+// place in the factor arrays (column-major, ld = n).  Pivots are applied to
+// the panel and the trailing columns only ("progressive" form; the solves
+// apply them block by block).
+template <typename R>
+int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
+                    int32_t* stat, cudaStream_t st);
+// Solve L U X = P B in place for the n x nrhs column-major block at
+// ws + unit.<field> (complex<R>), skipping units whose done flag is set.
+template <typename R>
+int lu_solve_chunk(const Unit* d_units, int n_units, const char* fac_base, char* ws,
+                   int which_rhs, int nrhs, const int32_t* done, cudaStream_t st);
+
+enum RhsField { RHS_X = 0, RHS_X32 = 1 };
+
+}  // namespace lsms

@@ -1,0 +1,99 @@
+// Internal declarations shared by the host (C++) and device (CUDA) parts of
+// liblsmskubo.  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/lsmskubo.h"
+
+namespace lsms {
+
+constexpr int kMaxLmax = 3;
+constexpr int kMaxK = 16;                       // (kMaxLmax + 1)^2
+constexpr int kMaxL3 = 2 * kMaxLmax;            // l'' range of g
+constexpr int kMaxK3 = (kMaxL3 + 1) * (kMaxL3 + 1);
+
+// Error reporting (thread-local message; returns the code for chaining).
+int fail(int code, const char* fmt, ...);
+void clear_error();
+
+// One (atom, energy) LIZ problem inside a chunk of the batched solve.
+struct Unit {
+  int32_t atom;      // centre atom m
+  int32_t energy;    // energy index e
+  int32_t n;         // K * S_m
+  int32_t S;         // LIZ size S_m
+  int64_t site_off;  // first site of LIZ_m in the global site arrays
+  int64_t fac_off;   // byte offset of the factor matrix (from fac base)
+  int64_t m64_off;   // byte offset of the FP64 matrix copy (mixed form), from workspace
+  int64_t piv_off;   // byte offset of the pivots (from fac base)
+  int64_t x_off;     // byte offset of the n x RHS complex128 solution block (workspace)
+  int64_t r_off;     // byte offset of the n x RHS complex128 residual block (workspace)
+  int64_t x32_off;   // byte offset of the n x RHS complex64 scratch (workspace)
+  int64_t stat_off;  // index into the per-unit scratch scalars
+};
+
+struct Chunk {
+  int u0, u1;        // unit range in the plan
+  int n_max;         // largest n in the chunk (units are sorted by n, descending)
+  size_t ws_bytes;   // workspace bytes used by the chunk
+};
+
+struct Plan {
+  int lmax = -1, n_energy = 0, precision = 0, nrhs = 0;
+  bool store = false;
+  size_t ws_bytes = 0;
+  std::vector<Unit> units;     // host copy
+  std::vector<Chunk> chunks;
+  Unit* d_units = nullptr;     // device copy
+};
+
+struct DeviceData {
+  int64_t* offsets = nullptr;    // [N+1]
+  int32_t* site_atom = nullptr;  // [S]
+  double* disp = nullptr;        // [S][3]
+  int64_t* inv_off = nullptr;    // [N+1] sites of each atom (images included)
+  int64_t* inv_sites = nullptr;  // [S]
+  int32_t* site_centre = nullptr;// [S] centre atom of the LIZ holding site s
+  std::map<std::tuple<int, int, int, int, size_t, int>, Plan> plans;
+};
+
+}  // namespace lsms
+
+struct lsms_liz {
+  int n_atoms = 0;
+  int64_t total_sites = 0;
+  int max_sites = 0, min_sites = 0;
+  bool periodic = false;
+  std::vector<int64_t> offsets;
+  std::vector<int32_t> site_atom;
+  std::vector<int32_t> image;
+  std::vector<double> disp;
+  std::vector<int64_t> inv_off;
+  std::vector<int64_t> inv_sites;
+  std::vector<int32_t> site_centre;
+  std::mutex mu;
+  std::map<int, lsms::DeviceData> dev;  // per CUDA device
+};
+
+namespace lsms {
+// Host tables (host.cpp).
+// Real Gaunt C[L1][L2][L3], L1, L2 < (lmax+1)^2, L3 < (2 lmax+1)^2.
+std::vector<double> gaunt_real(int lmax);
+// Sparse coupling of g: for each (L, L') the list of (L'', s C_{LL'L''}),
+// s = i^{l - l' - l''} = +-1 (the exponent is even whenever C != 0).
+struct Coupling {
+  std::vector<int32_t> start;   // [K*K + 1]
+  std::vector<int32_t> lpp;     // [nnz] L''
+  std::vector<double> coef;     // [nnz]
+};
+Coupling g_coupling(int lmax);
+// Y_L normalisation N_l^|m| * (sqrt 2 for m != 0), L < (l3max+1)^2.
+std::vector<double> ylm_norm(int l3max);
+}  // namespace lsms

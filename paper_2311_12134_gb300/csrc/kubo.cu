@@ -1,0 +1,353 @@
+// Kubo-Greenwood traces, their fixed-order reduction into sigma and rho, and
+// the adjoint (gradient) kernels.
+//
+// Eq. (lsms-conductivity-formula): for centre atom m and energy pair
+// c = (z1, z2),
+//   S_c[mu][nu](m) = sum_{n in LIZ_m} Tr[ J^{m mu}(z2,z1) tau^{0n}(z1) J^{n nu}(z1,z2) tau^{n0}(z2) ]
+// with tau^{0n} = (tau^{n0})^T (complex-symmetric M).  Eq.
+// (sigma-tilde-consolidation) then combines the four pairs at finite delta.
+// All arithmetic here is FP64; sums over atoms and sites run in a fixed order.
+#include "common.cuh"
+
+namespace lsms {
+
+// c = 2a + b for (z1, z2) = (a, b), a/b = 0 for +, 1 for -; the swapped pair is 2b + a.
+__device__ __forceinline__ int swap_combo(int c) { return ((c & 1) << 1) | (c >> 1); }
+
+// ------------------------------------------------------------------ forward traces
+// grid (n_atoms, n_delta * 4), block 256 = 16 x 16 element threads.
+__global__ void __launch_bounds__(256) k_kubo_partial(const int64_t* __restrict__ offsets,
+                                                      const int32_t* __restrict__ site_atom,
+                                                      const int32_t* __restrict__ species,
+                                                      const double2* __restrict__ J, int64_t J_dstride,
+                                                      const double2* __restrict__ tau, int64_t S_total, int K,
+                                                      int n_atoms, int n_species, double2* __restrict__ partial) {
+  const int m = blockIdx.x;
+  const int d = blockIdx.y >> 2, c = blockIdx.y & 3;
+  const int a = c >> 1, b = c & 1;
+  const int e1 = 2 * d + a, e2 = 2 * d + b;
+  const int cb = swap_combo(c);
+  const int KK = K * K;
+  const double2* Jd = J + (size_t)d * J_dstride;
+  __shared__ double2 sT1[16][17], sT2[16][17];
+  __shared__ double2 sB[3][16][17];
+  __shared__ double2 sP[3][16][17];
+  const int tid = threadIdx.x;
+  const int i = tid >> 4, j = tid & 15;
+  const bool act = (i < K) && (j < K);
+  double2 Y[3];
+#pragma unroll
+  for (int v = 0; v < 3; ++v) Y[v] = mk(0.0, 0.0);
+  const int64_t s0 = offsets[m], s1 = offsets[m + 1];
+  for (int64_t s = s0; s < s1; ++s) {
+    const int sp = min(max(0, species[site_atom[s]]), n_species - 1);  // out-of-range ids never index J
+    if (act) {
+      sT1[i][j] = tau[((size_t)e1 * S_total + s) * KK + i * K + j];
+      sT2[i][j] = tau[((size_t)e2 * S_total + s) * KK + i * K + j];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) sB[v][i][j] = Jd[(((size_t)sp * 4 + c) * 3 + v) * KK + i * K + j];
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        double2 acc = mk(0.0, 0.0);
+        for (int q = 0; q < K; ++q) acc = cfma(sB[v][i][q], sT2[q][j], acc);  // J^nu tau^{n0}(z2)
+        sP[v][i][j] = acc;
+      }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        double2 acc = Y[v];
+        for (int q = 0; q < K; ++q) acc = cfma(sT1[q][i], sP[v][q][j], acc);  // tau^{0n}(z1) = tau^{n0}(z1)^T
+        Y[v] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  // S[mu][nu] = Tr[J^{m mu} Y^nu] = sum_ij Jm[i][j] Y[j][i]
+  if (act) {
+#pragma unroll
+    for (int v = 0; v < 3; ++v) sP[v][i][j] = Y[v];
+  }
+  const int spm = min(max(0, species[m]), n_species - 1);
+  if (act) {
+#pragma unroll
+    for (int u = 0; u < 3; ++u) sB[u][i][j] = Jd[(((size_t)spm * 4 + cb) * 3 + u) * KK + i * K + j];
+  }
+  __syncthreads();
+  __shared__ double2 red[9][8];
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int u = 0; u < 3; ++u)
+    for (int v = 0; v < 3; ++v) {
+      double2 t = act ? cmul(sB[u][i][j], sP[v][j][i]) : mk(0.0, 0.0);
+#pragma unroll
+      for (int off = 16; off; off >>= 1) {
+        t.x += __shfl_xor_sync(0xffffffffu, t.x, off);
+        t.y += __shfl_xor_sync(0xffffffffu, t.y, off);
+      }
+      if (lane == 0) red[u * 3 + v][warp] = t;
+    }
+  __syncthreads();
+  if (tid < 9) {
+    double2 t = mk(0.0, 0.0);
+    for (int w = 0; w < 8; ++w) t = cadd(t, red[tid][w]);
+    partial[((size_t)(d * 4 + c) * n_atoms + m) * 9 + tid] = t;
+  }
+}
+
+// grid (n_delta * 4 * 9), block 256: fixed-order sum over atoms.
+__global__ void __launch_bounds__(256) k_kubo_reduce(const double2* __restrict__ partial, int n_atoms,
+                                                     double2* __restrict__ S) {
+  const int dc = blockIdx.x / 9, e = blockIdx.x % 9;
+  double2 t = mk(0.0, 0.0);
+  for (int m = threadIdx.x; m < n_atoms; m += blockDim.x) t = cadd(t, partial[((size_t)dc * n_atoms + m) * 9 + e]);
+  __shared__ double2 sh[256];
+  sh[threadIdx.x] = t;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] = cadd(sh[threadIdx.x], sh[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) S[(size_t)dc * 9 + e] = sh[0];
+}
+
+// one block: sigma~ = -S/(pi V), sigma = (st0 - st1 - st2 + st3)/4, rho = (Re sigma)^{-1}
+__global__ void k_kubo_finish(const double2* __restrict__ S, int n_delta, double volume,
+                              double2* __restrict__ sigma_tilde, double2* __restrict__ sigma,
+                              double* __restrict__ rho) {
+  const double pref = -1.0 / (M_PI * volume);
+  for (int d = threadIdx.x; d < n_delta; d += blockDim.x) {
+    double2 sg[9];
+    for (int e = 0; e < 9; ++e) {
+      double2 acc = mk(0.0, 0.0);
+      for (int c = 0; c < 4; ++c) {
+        const double2 st = mk(pref * S[(size_t)(d * 4 + c) * 9 + e].x, pref * S[(size_t)(d * 4 + c) * 9 + e].y);
+        if (sigma_tilde) sigma_tilde[(size_t)(d * 4 + c) * 9 + e] = st;
+        const double sgn = (c == 0 || c == 3) ? 0.25 : -0.25;
+        acc.x += sgn * st.x;
+        acc.y += sgn * st.y;
+      }
+      sg[e] = acc;
+      sigma[(size_t)d * 9 + e] = acc;
+    }
+    if (rho) {
+      const double a0 = sg[0].x, a1 = sg[1].x, a2 = sg[2].x, a3 = sg[3].x, a4 = sg[4].x, a5 = sg[5].x,
+                   a6 = sg[6].x, a7 = sg[7].x, a8 = sg[8].x;
+      const double c0 = a4 * a8 - a5 * a7, c1 = a5 * a6 - a3 * a8, c2 = a3 * a7 - a4 * a6;
+      const double det = a0 * c0 + a1 * c1 + a2 * c2;
+      const double id = 1.0 / det;
+      double* o = rho + (size_t)d * 9;
+      o[0] = c0 * id;
+      o[1] = (a2 * a7 - a1 * a8) * id;
+      o[2] = (a1 * a5 - a2 * a4) * id;
+      o[3] = c1 * id;
+      o[4] = (a0 * a8 - a2 * a6) * id;
+      o[5] = (a2 * a3 - a0 * a5) * id;
+      o[6] = c2 * id;
+      o[7] = (a1 * a6 - a0 * a7) * id;
+      o[8] = (a0 * a4 - a1 * a3) * id;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ adjoint
+// f = sum conj(w) sigma.  Abar^nu_{m,d,c} = a_c sum_mu conj(w[d][mu][nu]) J^{m mu}(swap c),
+// a_c = -s_c / (4 pi V).  grid (n_atoms, n_delta * 4), block 256.
+__global__ void __launch_bounds__(256) k_adj_abar(const int32_t* __restrict__ species,
+                                                  const double2* __restrict__ J, int64_t J_dstride,
+                                                  const double2* __restrict__ w, int K, double volume,
+                                                  int n_delta, int n_species, double2* __restrict__ abar) {
+  const int m = blockIdx.x;
+  const int d = blockIdx.y >> 2, c = blockIdx.y & 3;
+  const int cb = swap_combo(c);
+  const int KK = K * K;
+  const int tid = threadIdx.x;
+  if (tid >= KK) return;
+  const double2* Jd = J + (size_t)d * J_dstride;
+  const int sp = min(max(0, species[m]), n_species - 1);
+  const double ac = ((c == 0 || c == 3) ? -1.0 : 1.0) / (4.0 * M_PI * volume);
+  for (int v = 0; v < 3; ++v) {
+    double2 acc = mk(0.0, 0.0);
+    for (int u = 0; u < 3; ++u) {
+      const double2 wc = w[(size_t)d * 9 + u * 3 + v];
+      const double2 cw = mk(ac * wc.x, -ac * wc.y);
+      acc = cfma(cw, Jd[(((size_t)sp * 4 + cb) * 3 + u) * KK + tid], acc);
+    }
+    abar[((((size_t)m * n_delta + d) * 4 + c) * 3 + v) * KK + tid] = acc;
+  }
+}
+
+// Right-hand sides of the adjoint solves for unit (m, e), one CTA per LIZ site n:
+//   B[:, 0:K]  rows of site n = sum_{c: z1 = z_e} sum_nu J^{n nu}(c) tau^{n0}(z2) Abar^nu_c
+//   B[:, K:2K] rows of site n = sum_{c: z2 = z_e} sum_nu J^{n nu}(c)^T tau^{n0}(z1) (Abar^nu_c)^T
+// B is column-major n x 2K complex128 at ws + unit.r_off.  grid (S_max, n_units).
+__global__ void __launch_bounds__(256) k_adj_rhs(const Unit* __restrict__ units, const int32_t* __restrict__ site_atom,
+                                                 const int32_t* __restrict__ species, const double2* __restrict__ J,
+                                                 int64_t J_dstride, const double2* __restrict__ tau, int64_t S_total,
+                                                 const double2* __restrict__ abar, int n_delta, int n_species, int K,
+                                                 char* ws) {
+  const Unit u = units[blockIdx.y];
+  const int nsite = blockIdx.x;
+  if (nsite >= u.S) return;
+  const int KK = K * K;
+  const int m = u.atom, e = u.energy;
+  const int d = e >> 1, sgn = e & 1;
+  const int64_t s = u.site_off + nsite;
+  const int sp = min(max(0, species[site_atom[s]]), n_species - 1);
+  const double2* Jd = J + (size_t)d * J_dstride;
+  __shared__ double2 sT[16][17], sJ[16][17], sA[16][17], sQ[16][17];
+  const int tid = threadIdx.x, i = tid >> 4, j = tid & 15;
+  const bool act = (i < K) && (j < K);
+  double2 acc1 = mk(0.0, 0.0), acc2 = mk(0.0, 0.0);
+  for (int part = 0; part < 2; ++part) {
+    for (int cc = 0; cc < 2; ++cc) {
+      // combos with z1 = z_e (part 0) or z2 = z_e (part 1)
+      int c;
+      if (part == 0) c = (sgn << 1) | cc;  // a = sgn, b = cc
+      else c = (cc << 1) | sgn;            // a = cc, b = sgn
+      const int a = c >> 1, b = c & 1;
+      const int eo = (part == 0) ? (2 * d + b) : (2 * d + a);  // the other energy's tau
+      if (act) sT[i][j] = tau[((size_t)eo * S_total + s) * KK + i * K + j];
+      for (int v = 0; v < 3; ++v) {
+        if (act) {
+          sJ[i][j] = Jd[(((size_t)sp * 4 + c) * 3 + v) * KK + i * K + j];
+          sA[i][j] = abar[((((size_t)m * n_delta + d) * 4 + c) * 3 + v) * KK + i * K + j];
+        }
+        __syncthreads();
+        if (act) {
+          double2 q = mk(0.0, 0.0);
+          if (part == 0)
+            for (int t = 0; t < K; ++t) q = cfma(sJ[i][t], sT[t][j], q);  // J tau
+          else
+            for (int t = 0; t < K; ++t) q = cfma(sJ[t][i], sT[t][j], q);  // J^T tau
+          sQ[i][j] = q;
+        }
+        __syncthreads();
+        if (act) {
+          if (part == 0)
+            for (int t = 0; t < K; ++t) acc1 = cfma(sQ[i][t], sA[t][j], acc1);  // (J tau) Abar
+          else
+            for (int t = 0; t < K; ++t) acc2 = cfma(sQ[i][t], sA[j][t], acc2);  // (J^T tau) Abar^T
+        }
+        __syncthreads();
+      }
+    }
+  }
+  if (act) {
+    double2* B = reinterpret_cast<double2*>(ws + u.r_off);
+    const int n = u.n;
+    B[(size_t)j * n + K * nsite + i] = acc1;
+    B[(size_t)(K + j) * n + K * nsite + i] = acc2;
+  }
+}
+
+// Per-site gradient contribution for unit (m, e), site p (one CTA each):
+//   D_p = - tau^{p0} (X1_p)^T - X2_p (tau^{p0})^T,  X = M^{-1} B  (n x 2K at ws + unit.x_off)
+// written to G[e][s] (K x K row-major).  grid (S_max, n_units).
+__global__ void __launch_bounds__(256) k_adj_site(const Unit* __restrict__ units, const double2* __restrict__ tau,
+                                                  int64_t S_total, int K, const char* ws, double2* __restrict__ G) {
+  const Unit u = units[blockIdx.y];
+  const int p = blockIdx.x;
+  if (p >= u.S) return;
+  const int KK = K * K;
+  const int e = u.energy, n = u.n;
+  const int64_t s = u.site_off + p;
+  const double2* X = reinterpret_cast<const double2*>(ws + u.x_off);
+  __shared__ double2 sT[16][17], sX1[16][17], sX2[16][17];
+  const int tid = threadIdx.x, i = tid >> 4, j = tid & 15;
+  const bool act = (i < K) && (j < K);
+  if (act) {
+    sT[i][j] = tau[((size_t)e * S_total + s) * KK + i * K + j];
+    sX1[i][j] = X[(size_t)j * n + K * p + i];
+    sX2[i][j] = X[(size_t)(K + j) * n + K * p + i];
+  }
+  __syncthreads();
+  if (act) {
+    double2 acc = mk(0.0, 0.0);
+    for (int t = 0; t < K; ++t) {
+      acc = cfma(sT[i][t], sX1[j][t], acc);   // tau^{p0} X1^T
+      acc = cfma(sX2[i][t], sT[j][t], acc);   // X2 tau^{p0 T}
+    }
+    G[((size_t)e * S_total + s) * KK + i * K + j] = mk(-acc.x, -acc.y);
+  }
+}
+
+// grad_tinv[e][i] = conj( sum over the sites of atom i, in site order ).  grid (n_atoms, n_energy).
+__global__ void __launch_bounds__(256) k_adj_reduce(const int64_t* __restrict__ inv_off,
+                                                    const int64_t* __restrict__ inv_sites,
+                                                    const double2* __restrict__ G, int64_t S_total, int K,
+                                                    int n_atoms, double2* __restrict__ grad) {
+  const int a = blockIdx.x, e = blockIdx.y;
+  const int KK = K * K;
+  const int t = threadIdx.x;
+  if (t >= KK) return;
+  double2 acc = mk(0.0, 0.0);
+  for (int64_t q = inv_off[a]; q < inv_off[a + 1]; ++q) acc = cadd(acc, G[((size_t)e * S_total + inv_sites[q]) * KK + t]);
+  grad[((size_t)e * n_atoms + a) * KK + t] = mk(acc.x, -acc.y);
+}
+
+// grad_species[s][e] = sum over atoms of species s (atom order) of grad[e][atom].
+// grid (n_species, n_energy).
+__global__ void __launch_bounds__(256) k_adj_species(const int32_t* __restrict__ species,
+                                                     const double2* __restrict__ grad, int K, int n_atoms,
+                                                     int n_energy, double2* __restrict__ out) {
+  const int s = blockIdx.x, e = blockIdx.y;
+  const int KK = K * K;
+  const int t = threadIdx.x;
+  if (t >= KK) return;
+  double2 acc = mk(0.0, 0.0);
+  for (int a = 0; a < n_atoms; ++a)
+    if (species[a] == s) acc = cadd(acc, grad[((size_t)e * n_atoms + a) * KK + t]);
+  out[((size_t)s * n_energy + e) * KK + t] = acc;
+}
+
+// ------------------------------------------------------------------ wrappers
+int kubo_forward(const int64_t* offsets, const int32_t* site_atom, const int32_t* species, int n_species,
+                 const double2* J, int64_t J_dstride, const double2* tau, int64_t S_total, int K, int n_atoms, int n_delta,
+                 double volume, double2* partial, double2* S, double2* sigma_tilde, double2* sigma, double* rho,
+                 cudaStream_t st) {
+  LSMS_LAUNCH(k_kubo_partial, dim3(n_atoms, n_delta * 4), dim3(256), 0, st, offsets, site_atom, species, J,
+              J_dstride, tau, S_total, K, n_atoms, n_species, partial);
+  LSMS_LAUNCH(k_kubo_reduce, dim3(n_delta * 4 * 9), dim3(256), 0, st, partial, n_atoms, S);
+  LSMS_LAUNCH(k_kubo_finish, dim3(1), dim3(32), 0, st, S, n_delta, volume, sigma_tilde, sigma, rho);
+  return LSMS_OK;
+}
+
+int adj_abar(const int32_t* species, int n_species, const double2* J, int64_t J_dstride, const double2* w, int K,
+             double volume, int n_atoms, int n_delta, double2* abar, cudaStream_t st) {
+  LSMS_LAUNCH(k_adj_abar, dim3(n_atoms, n_delta * 4), dim3(256), 0, st, species, J, J_dstride, w, K, volume,
+              n_delta, n_species, abar);
+  return LSMS_OK;
+}
+
+int adj_rhs(const Unit* d_units, int n_units, int S_max, const int32_t* site_atom, const int32_t* species,
+            int n_species, const double2* J, int64_t J_dstride, const double2* tau, int64_t S_total,
+            const double2* abar, int n_delta, int K, char* ws, cudaStream_t st) {
+  LSMS_LAUNCH(k_adj_rhs, dim3(S_max, n_units), dim3(256), 0, st, d_units, site_atom, species, J, J_dstride, tau,
+              S_total, abar, n_delta, n_species, K, ws);
+  return LSMS_OK;
+}
+
+int adj_site(const Unit* d_units, int n_units, int S_max, const double2* tau, int64_t S_total, int K, const char* ws,
+             double2* G, cudaStream_t st) {
+  LSMS_LAUNCH(k_adj_site, dim3(S_max, n_units), dim3(256), 0, st, d_units, tau, S_total, K, ws, G);
+  return LSMS_OK;
+}
+
+int adj_reduce(const int64_t* inv_off, const int64_t* inv_sites, const double2* G, int64_t S_total, int K,
+               int n_atoms, int n_energy, double2* grad, cudaStream_t st) {
+  LSMS_LAUNCH(k_adj_reduce, dim3(n_atoms, n_energy), dim3(256), 0, st, inv_off, inv_sites, G, S_total, K, n_atoms,
+              grad);
+  return LSMS_OK;
+}
+
+int adj_species(const int32_t* species, const double2* grad, int K, int n_atoms, int n_species, int n_energy,
+                double2* out, cudaStream_t st) {
+  LSMS_LAUNCH(k_adj_species, dim3(n_species, n_energy), dim3(256), 0, st, species, grad, K, n_atoms, n_energy, out);
+  return LSMS_OK;
+}
+
+}  // namespace lsms

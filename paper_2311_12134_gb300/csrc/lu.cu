@@ -1,0 +1,373 @@
+// Batched blocked LU with partial pivoting, the block solves for the tau
+// column blocks, and the FP64 iterative refinement of the mixed form.
+//
+// Eq. (tau-inverse) needs [T^{-1} - g]^{-1}; for each (atom, energy) unit the
+// LIZ matrix M (n = K S, column-major, ld = n) is factored P M = L U in place.
+// Pivoting: the row with the largest |Re| + |Im| in the column, the lowest row
+// on ties.  Right-looking, panel width NB:
+//   k_panel      factor the n-k x NB panel (pivot search by warp shuffles),
+//   k_swap_trsm  apply the panel's row swaps to the trailing columns and form
+//                U12 = L11^{-1} A12 (one warp per column),
+//   k_gemm       A22 -= L21 U12 (register-tiled complex GEMM).
+// Units of a chunk are sorted by n (largest first); each launch covers every
+// unit and units already finished return at once.  Row swaps are applied only
+// to the panel and the columns to its right; k_solve applies them block by
+// block during forward substitution, which is consistent with that storage.
+#include "common.cuh"
+
+namespace lsms {
+
+template <typename R> struct LuCfg { static constexpr int NB = 32; };
+
+__device__ __forceinline__ double2 shfl2(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// ------------------------------------------------------------------ panel
+template <typename R, int NB>
+__global__ void __launch_bounds__(256) k_panel(const Unit* __restrict__ units, char* fac_base, int k,
+                                               int32_t* stat) {
+  using C = Cx<R>;
+  const Unit u = units[blockIdx.x];
+  const int n = u.n;
+  if (k >= n) return;
+  C* A = reinterpret_cast<C*>(fac_base + u.fac_off);
+  int32_t* piv = reinterpret_cast<int32_t*>(fac_base + u.piv_off);
+  const int nbp = min(NB, n - k);
+  __shared__ R s_val[8];
+  __shared__ int s_idx[8];
+  __shared__ C s_row[NB];
+  __shared__ int s_piv;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = blockDim.x >> 5;
+  int flags = 0;
+  for (int j = 0; j < nbp; ++j) {
+    const int col = k + j;
+    const C* Ac = A + (size_t)col * n;
+    R best = R(-1);
+    int bidx = n;
+    for (int i = col + tid; i < n; i += blockDim.x) {
+      const R v = cabs1(Ac[i]);
+      if (v > best) { best = v; bidx = i; }  // strict: first (lowest) row kept; NaN never wins
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+      const R ov = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
+      if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
+    }
+    if (lane == 0) { s_val[warp] = best; s_idx[warp] = bidx; }
+    __syncthreads();
+    if (warp == 0) {
+      best = lane < nwarps ? s_val[lane] : R(-1);
+      bidx = lane < nwarps ? s_idx[lane] : n;
+#pragma unroll
+      for (int off = 16; off; off >>= 1) {
+        const R ov = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
+        if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
+      }
+      if (lane == 0) s_piv = (bidx < n) ? bidx : col;
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (p != col) {
+      for (int c = tid; c < nbp; c += blockDim.x) {
+        C* a = A + (size_t)(k + c) * n;
+        const C t = a[col];
+        a[col] = a[p];
+        a[p] = t;
+      }
+    }
+    if (tid == 0) piv[col] = p;
+    __syncthreads();
+    for (int c = tid; c < nbp; c += blockDim.x) s_row[c] = A[(size_t)(k + c) * n + col];
+    __syncthreads();
+    const C pv = s_row[j];
+    const bool zero = (pv.x == R(0) && pv.y == R(0));
+    if (zero) flags |= LSMS_UNIT_ZERO_PIVOT;
+    if (!finite2(pv)) flags |= LSMS_UNIT_NONFINITE;
+    const C r = zero ? mk(R(0), R(0)) : crcp(pv);
+    for (int i = col + 1 + tid; i < n; i += blockDim.x) {
+      C* ai = A + (size_t)col * n + i;
+      const C l = cmul(*ai, r);
+      if (!zero) *ai = l;
+      for (int c = j + 1; c < nbp; ++c) {
+        C* a = A + (size_t)(k + c) * n + i;
+        *a = cfms(l, s_row[c], *a);
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && flags) atomicOr(&stat[u.stat_off], flags);
+}
+
+// ------------------------------------------------------------------ swap + trsm
+// One warp per trailing column; lane i holds rows k+i (+32 r).
+template <typename R, int NB>
+__global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ units, char* fac_base, int k) {
+  using C = Cx<R>;
+  constexpr int RPL = NB / 32;
+  const Unit u = units[blockIdx.y];
+  const int n = u.n;
+  const int c0 = k + NB;
+  if (c0 >= n) return;  // then the panel was the last block; nothing trails it
+  C* A = reinterpret_cast<C*>(fac_base + u.fac_off);
+  const int32_t* piv = reinterpret_cast<const int32_t*>(fac_base + u.piv_off);
+  __shared__ C sL[NB][NB + 1];
+  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+    const int i = idx % NB, j = idx / NB;
+    sL[i][j] = A[(size_t)(k + j) * n + k + i];
+  }
+  __shared__ int sp[NB];
+  for (int j = threadIdx.x; j < NB; j += blockDim.x) sp[j] = piv[k + j];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = c0 + blockIdx.x * (blockDim.x >> 5) + warp;
+  if (c >= n) return;
+  C* Ac = A + (size_t)c * n;
+  C x[RPL];
+#pragma unroll
+  for (int r = 0; r < RPL; ++r) x[r] = Ac[k + lane + 32 * r];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    const int p = sp[j];
+    if (p == k + j) continue;
+    if (p < k + NB) {
+      const int b = p - k;
+      const C va = shfl2(x[j / 32], j % 32);
+      C vb = x[0];
+#pragma unroll
+      for (int r = 0; r < RPL; ++r)
+        if (b / 32 == r) vb = shfl2(x[r], b % 32);
+      if (lane == j % 32) x[j / 32] = vb;
+#pragma unroll
+      for (int r = 0; r < RPL; ++r)
+        if (b / 32 == r && lane == b % 32) x[r] = va;
+    } else {
+      if (lane == j % 32) {
+        const C t = Ac[p];
+        Ac[p] = x[j / 32];
+        x[j / 32] = t;
+      }
+      __syncwarp();
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NB - 1; ++j) {
+    const C xj = shfl2(x[j / 32], j % 32);
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+      const int i = lane + 32 * r;
+      if (i > j) x[r] = cfms(sL[i][j], xj, x[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RPL; ++r) Ac[k + lane + 32 * r] = x[r];
+}
+
+// ------------------------------------------------------------------ trailing GEMM (SIMT)
+// Tile 64 x 64, K slices of 16; thread (ty, tx) owns rows ty + 16 r, columns tx + 16 c.
+template <typename R, int NB>
+__global__ void __launch_bounds__(256) k_gemm(const Unit* __restrict__ units, char* fac_base, int k,
+                                              int tiles_max) {
+  using C = Cx<R>;
+  const Unit u = units[blockIdx.y];
+  const int n = u.n;
+  const int t0 = k + NB;
+  const int mt = n - t0;
+  if (mt <= 0) return;
+  const int tiles = (mt + 63) >> 6;
+  const int ti = blockIdx.x / tiles_max, tj = blockIdx.x % tiles_max;
+  if (ti >= tiles || tj >= tiles) return;
+  C* A = reinterpret_cast<C*>(fac_base + u.fac_off);
+  const int row0 = t0 + 64 * ti, col0 = t0 + 64 * tj;
+  __shared__ C sA[16][64];
+  __shared__ C sB[16][65];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  C acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = mk(R(0), R(0));
+  for (int ks = 0; ks < NB; ks += 16) {
+    for (int idx = threadIdx.x; idx < 16 * 64; idx += 256) {
+      const int i = idx & 63, kk = idx >> 6;
+      const int row = row0 + i;
+      sA[kk][i] = row < n ? A[(size_t)(k + ks + kk) * n + row] : mk(R(0), R(0));
+      const int kk2 = idx & 15, j = idx >> 4;
+      const int col = col0 + j;
+      sB[kk2][j] = col < n ? A[(size_t)col * n + k + ks + kk2] : mk(R(0), R(0));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      C a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = sA[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = sB[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = cfma(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int col = col0 + tx + 16 * c;
+    if (col >= n) continue;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int row = row0 + ty + 16 * r;
+      if (row < n) {
+        C* a = A + (size_t)col * n + row;
+        *a = csub(*a, acc[r][c]);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ solve
+// One CTA per unit: forward substitution with block-wise pivots, then backward
+// substitution, on the n x nrhs column-major block X (nrhs <= 32).
+template <typename R, int NB>
+__global__ void __launch_bounds__(256) k_solve(const Unit* __restrict__ units, const char* fac_base, char* ws,
+                                               int which, int nrhs, const int32_t* done) {
+  using C = Cx<R>;
+  const Unit u = units[blockIdx.x];
+  if (done && done[u.stat_off]) return;
+  const int n = u.n;
+  const C* A = reinterpret_cast<const C*>(fac_base + u.fac_off);
+  const int32_t* piv = reinterpret_cast<const int32_t*>(fac_base + u.piv_off);
+  C* X = reinterpret_cast<C*>(ws + (which == RHS_X ? u.x_off : u.x32_off));
+  __shared__ C sX[NB][33];
+  const int tid = threadIdx.x;
+  // forward: L y = P b
+  for (int k = 0; k < n; k += NB) {
+    const int nbp = min(NB, n - k);
+    if (tid < nrhs) {
+      C* xc = X + (size_t)tid * n;
+      for (int j = 0; j < nbp; ++j) {
+        const int p = piv[k + j];
+        if (p != k + j) {
+          const C t = xc[k + j];
+          xc[k + j] = xc[p];
+          xc[p] = t;
+        }
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nbp * nrhs; idx += blockDim.x) {
+      const int j = idx % nbp, c = idx / nbp;
+      sX[j][c] = X[(size_t)c * n + k + j];
+    }
+    __syncthreads();
+    for (int j = 0; j < nbp - 1; ++j) {
+      const C* Lj = A + (size_t)(k + j) * n + k;
+      for (int idx = tid; idx < (nbp - 1 - j) * nrhs; idx += blockDim.x) {
+        const int i = j + 1 + idx % (nbp - 1 - j), c = idx / (nbp - 1 - j);
+        sX[i][c] = cfms(Lj[i], sX[j][c], sX[i][c]);
+      }
+      __syncthreads();
+    }
+    for (int idx = tid; idx < nbp * nrhs; idx += blockDim.x) {
+      const int j = idx % nbp, c = idx / nbp;
+      X[(size_t)c * n + k + j] = sX[j][c];
+    }
+    for (int g = 0; g < nrhs; g += 8) {
+      const int gc = min(8, nrhs - g);
+      for (int i = k + nbp + tid; i < n; i += blockDim.x) {
+        C acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = c < gc ? X[(size_t)(g + c) * n + i] : mk(R(0), R(0));
+        for (int j = 0; j < nbp; ++j) {
+          const C l = A[(size_t)(k + j) * n + i];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) acc[c] = cfms(l, sX[j][g + (c < gc ? c : 0)], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          if (c < gc) X[(size_t)(g + c) * n + i] = acc[c];
+      }
+    }
+    __syncthreads();
+  }
+  // backward: U x = y
+  const int last = ((n - 1) / NB) * NB;
+  for (int k = last; k >= 0; k -= NB) {
+    const int nbp = min(NB, n - k);
+    for (int idx = tid; idx < nbp * nrhs; idx += blockDim.x) {
+      const int j = idx % nbp, c = idx / nbp;
+      sX[j][c] = X[(size_t)c * n + k + j];
+    }
+    __syncthreads();
+    for (int j = nbp - 1; j >= 0; --j) {
+      const C* Uj = A + (size_t)(k + j) * n + k;
+      if (tid < nrhs) sX[j][tid] = cmul(sX[j][tid], crcp(Uj[j]));
+      __syncthreads();
+      for (int idx = tid; idx < j * nrhs; idx += blockDim.x) {
+        const int i = idx % j, c = idx / j;
+        sX[i][c] = cfms(Uj[i], sX[j][c], sX[i][c]);
+      }
+      __syncthreads();
+    }
+    for (int idx = tid; idx < nbp * nrhs; idx += blockDim.x) {
+      const int j = idx % nbp, c = idx / nbp;
+      X[(size_t)c * n + k + j] = sX[j][c];
+    }
+    for (int g = 0; g < nrhs; g += 8) {
+      const int gc = min(8, nrhs - g);
+      for (int i = tid; i < k; i += blockDim.x) {
+        C acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = c < gc ? X[(size_t)(g + c) * n + i] : mk(R(0), R(0));
+        for (int j = 0; j < nbp; ++j) {
+          const C uu = A[(size_t)(k + j) * n + i];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) acc[c] = cfms(uu, sX[j][g + (c < gc ? c : 0)], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          if (c < gc) X[(size_t)(g + c) * n + i] = acc[c];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ wrappers
+template <typename R>
+int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base, int32_t* stat,
+                    cudaStream_t st) {
+  constexpr int NB = LuCfg<R>::NB;
+  for (int k = 0; k < n_max; k += NB) {
+    LSMS_LAUNCH((k_panel<R, NB>), dim3(n_units), dim3(256), 0, st, d_units, fac_base, k, stat);
+    const int trail = n_max - k - NB;
+    if (trail <= 0) break;
+    LSMS_LAUNCH((k_swap_trsm<R, NB>), dim3((trail + 7) / 8, n_units), dim3(256), 0, st, d_units, fac_base, k);
+    const int tiles = (trail + 63) / 64;
+    LSMS_LAUNCH((k_gemm<R, NB>), dim3(tiles * tiles, n_units), dim3(256), 0, st, d_units, fac_base, k, tiles);
+  }
+  return LSMS_OK;
+}
+
+template <typename R>
+int lu_solve_chunk(const Unit* d_units, int n_units, const char* fac_base, char* ws, int which_rhs, int nrhs,
+                   const int32_t* done, cudaStream_t st) {
+  if (nrhs < 1 || nrhs > 32) return fail(LSMS_ERR_ARG, "internal: nrhs %d out of range", nrhs);
+  constexpr int NB = LuCfg<R>::NB;
+  LSMS_LAUNCH((k_solve<R, NB>), dim3(n_units), dim3(256), 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
+  return LSMS_OK;
+}
+
+template int lu_factor_chunk<double>(const Unit*, int, int, char*, int32_t*, cudaStream_t);
+template int lu_factor_chunk<float>(const Unit*, int, int, char*, int32_t*, cudaStream_t);
+template int lu_solve_chunk<double>(const Unit*, int, const char*, char*, int, int, const int32_t*, cudaStream_t);
+template int lu_solve_chunk<float>(const Unit*, int, const char*, char*, int, int, const int32_t*, cudaStream_t);
+
+}  // namespace lsms
