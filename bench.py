@@ -1,0 +1,415 @@
+"""Benchmark of the LSMS Kubo-Greenwood hot path on GB300.
+
+Workload: the 256-atom random binary fcc alloy (4x4x4 conventional cells,
+a = 7.65 bohr, A/B 128/128, lmax = 3, LIZ of 43 sites -> 688 x 688 complex
+LIZ matrices), E_F = 0.60 Ry, delta = 0.002 Ry, energies E_F +- i delta:
+512 (atom, energy) units per step.  Synthetic, seeded inputs.
+
+One step = the whole path: KKR matrix assembly, LU, tau column blocks
+(+ FP64 refinement in the mixed form), Kubo-Greenwood traces, sigma and rho,
+and the adjoint d sigma / d t^{-1} (reusing the stored LU factors).
+Metric: (atom, energy) LIZ tau-solves per second; value = units / step time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+                    [--impl ours|reference]
+
+For N > 1 (torchrun, one rank per GPU) each rank runs an independent replica of
+the workload (the path has no exchange step on one structure of this size).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "atom-energy LIZ tau-solves/s (forward sigma + adjoint), fcc256 alloy, n=688"
+UNIT = "units/s"
+WORKLOAD = "fcc256_AB50_liz43: 256-atom fcc A/B alloy, lmax=3, LIZ 43 sites (n=688), E_F=0.60 Ry, delta=0.002 Ry"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64-form comparison leg")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed helpers
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return world > 1
+
+
+def barrier(active):
+    if active:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, active, device="cpu"):
+    if not active:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- workload / algorithmic work
+def workload():
+    from paper_2311_12134_gb300 import workload as wl
+    return wl.fcc_alloy_256()
+
+
+def lu_flops(n_list):
+    """(8/3) n^3 + 128 n^2 real flops per unit (LU + 16-RHS solve), summed."""
+    n = np.asarray(n_list, dtype=np.float64)
+    return float(np.sum(8.0 / 3.0 * n ** 3 + 128.0 * n ** 2))
+
+
+def gemm_flops(n_list, nb):
+    """Algorithmic flops of the trailing-update GEMMs of a blocked LU with panel width nb."""
+    tot = 0.0
+    for n in n_list:
+        for k in range(0, n, nb):
+            t = n - k - nb
+            if t > 0:
+                tot += 8.0 * nb * t * t
+    return tot
+
+
+def peaks():
+    p = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            m = json.load(f)
+        p.update({k: m[k] for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained") if k in m})
+        p["source"] = "measured"
+    return p
+
+
+# ---------------------------------------------------------------- CPU oracle timing
+def time_oracle(w, n_atoms_sample, budget_s=25.0):
+    """Oracle (NumPy FP64, LAPACK) on a bounded sample: tau blocks of the first atoms
+    for both energies + their trace terms.  Returns (units/s, units, seconds, cores)."""
+    from oracle import kkr as okkr
+    from oracle import kubo as okubo
+    from oracle import liz as oliz
+    L = oliz.build_liz(w.pos, w.lattice, w.r_liz)
+    J = okubo.dipole_current(w.lmax, w.r_ll)[w.species]
+    tin = w.tinv[w.species]
+    t0 = time.perf_counter()
+    done = 0
+    for m in range(n_atoms_sample):
+        col, row = okkr.tau_blocks(w.lmax, L, tin, w.z, atoms=[m], return_rows=True)
+        okubo.sigma_tilde(L, J, col, row, w.n_delta, w.volume, atoms=[m])
+        done += len(w.z)
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt, os.cpu_count()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return 0
+    w = workload()
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, units, dt, cores = time_oracle(w, n_atoms_sample=2, budget_s=20.0)
+        if i >= args.warmup:
+            vals.append((v, units, dt))
+    v = float(np.mean([x[0] for x in vals]))
+    ms = float(np.mean([x[2] / x[1] for x in vals])) * 1e3 * 2 * w.n_atoms
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": 2 * w.n_atoms, "parallelism": "host cores"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "2 atoms x 2 energies per step (tau blocks via LAPACK + their trace terms); "
+                                       "ms_per_step extrapolates to all 512 units"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our path
+def run_ours(args):
+    import torch
+
+    from paper_2311_12134_gb300 import binding as B
+    from paper_2311_12134_gb300.conductivity import Problem
+
+    rank, world, local = dist_env()
+    active = init_dist(world, "nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if not os.path.exists(B.LIB_PATH):
+        if rank == 0:
+            from paper_2311_12134_gb300 import build
+            build.build()
+        barrier(active)
+    w = workload()
+    J = B.dipole_current(w.lmax, w.r_ll)
+    grad_sigma = np.zeros((w.n_delta, 3, 3), dtype=np.complex128)
+    grad_sigma[:, 0, 0] = 1.0  # d Re sigma_xx
+    gs_d = torch.as_tensor(grad_sigma).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def make(precision):
+        return Problem(w.pos, w.lattice, w.r_liz, w.lmax, w.species, w.tinv, w.z, J, w.volume,
+                       precision=precision, device=dev, keep_factors=True)
+
+    def step(p):
+        p.forward()
+        p.backward(gs_d)
+
+    def timed(p, steps, warmup, kernel_timer=False):
+        for _ in range(warmup):
+            step(p)
+        torch.cuda.synchronize(dev)
+        barrier(active)
+        torch.cuda.synchronize(dev)
+        l0 = B.launch_count()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            step(p)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(active)
+        ms = ev0.elapsed_time(ev1) / steps
+        return max_over_ranks(ms, active, device=dev), B.launch_count() - l0
+
+    main = make(args.precision)
+    units = main.n_units
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms, launches = timed(main, args.steps, args.warmup)
+    clocks = sampler.stop()
+    status = main.unit_status.cpu().numpy()
+    # forward-only time (sigma time) on the same problem
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        main.forward()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    sigma_ms = ev0.elapsed_time(ev1) / args.steps
+    value = world * units / (ms * 1e-3)
+
+    # kernel-level timing of the dominant kernel (library CUDA-event timers on the launch stream)
+    kt = kernel_times(B, main, step, stream, dev, args.steps)
+
+    # end-to-end through the public host-to-host API
+    e2e = measure_e2e(w, J, args, dev, stream, active, world)
+
+    fp64 = None
+    if not args.no_fp64_leg and args.precision != "fp64":
+        del main
+        torch.cuda.empty_cache()
+        p64 = make("fp64")
+        ms64, _ = timed(p64, max(1, min(args.steps, 2)), 1)
+        fp64 = {"value": world * units / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64}
+        del p64
+        torch.cuda.empty_cache()
+
+    if rank != 0:
+        return 0
+    pk = peaks()
+    n_list = [w.K * s for s in np.repeat(np.diff(main_offsets(w)), len(w.z))]
+    roof = roofline(kt, n_list, pk, args.precision)
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, u, dt, cores = time_oracle(w, n_atoms_sample=8, budget_s=25.0)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{u} units ({u // len(w.z)} atoms x {len(w.z)} energies): tau blocks + trace terms, "
+                         f"{dt:.1f} s"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": units * world, "units_per_gpu": units,
+                   "precision": args.precision, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (per-step working set > 4 GB)"},
+        "sigma_ms": sigma_ms,
+        "effective_tflops": units * world * (lu_flops([688]) ) / (ms * 1e-3) / 1e12,
+        "unit_status_clean": bool((status == 0).all()),
+        "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
+        "cpu_baseline": cpu, "fp64_form": fp64,
+    }
+    if fp64:
+        line["speedup_vs_fp64_form"] = value / fp64["value"]
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main_offsets(w):
+    from paper_2311_12134_gb300 import binding as B
+    return B.build_liz(w.pos, w.lattice, w.r_liz).export()["offsets"]
+
+
+def kernel_times(B, p, step, stream, dev, steps):
+    """Per-kernel device time over `steps` steps via the library's event timers."""
+    import torch
+    if not hasattr(B, "kernel_timer_start"):
+        return None
+    B.kernel_timer_start()
+    for _ in range(steps):
+        step(p)
+    torch.cuda.synchronize(dev)
+    return B.kernel_timer_stop(steps)
+
+
+def roofline(kt, n_list, pk, precision):
+    if not kt:
+        return None
+    name, (ms, launches) = max(kt.items(), key=lambda kv: kv[1][0])
+    nb = 32
+    if "gemm" in name:
+        flops = gemm_flops(n_list, nb)  # per step, both forward and backward factorizations
+        ach = flops / (ms * 1e-3) / 1e12
+        if precision == "mixed":
+            peak, bound, unit = 2.0 * 152 * 128 * 2.07e9 / 1e12, "alu", "TFLOP/s"
+        else:
+            peak, bound, unit = 1.25, "alu", "TFLOP/s"
+        return {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+                "frac": ach / peak, "traffic": None, "ms_per_step": ms, "launches_per_step": launches,
+                "peak_source": "derived from unit counts and max clock"}
+    return {"kernel": name, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None, "ms_per_step": ms, "launches_per_step": launches,
+            "all_kernels_ms": {k: v[0] for k, v in kt.items()}}
+
+
+def measure_e2e(w, J, args, dev, stream, active, world):
+    """Host-to-host: LIZ build + pinned H2D inputs + forward + adjoint + D2H sigma, rho, gradient."""
+    import torch
+
+    from paper_2311_12134_gb300 import binding as B
+    from paper_2311_12134_gb300.conductivity import Problem
+    p = Problem(w.pos, w.lattice, w.r_liz, w.lmax, w.species, w.tinv, w.z, J, w.volume,
+                precision=args.precision, device=dev, keep_factors=True)
+    h_species = torch.as_tensor(w.species).pin_memory()
+    h_tinv = torch.as_tensor(w.tinv).pin_memory()
+    h_J = torch.as_tensor(J).pin_memory()
+    gs = np.zeros((w.n_delta, 3, 3), dtype=np.complex128)
+    gs[:, 0, 0] = 1.0
+    h_gs = torch.as_tensor(gs).pin_memory()
+    out_sig = torch.empty((w.n_delta, 3, 3), dtype=torch.complex128).pin_memory()
+    out_rho = torch.empty((w.n_delta, 3, 3), dtype=torch.float64).pin_memory()
+    out_g = torch.empty((len(w.z), w.n_atoms, w.K, w.K), dtype=torch.complex128).pin_memory()
+    h2d = h_species.numel() * 4 + h_tinv.numel() * 16 + h_J.numel() * 16 + h_gs.numel() * 16 + w.pos.nbytes
+    d2h = out_sig.numel() * 16 + out_rho.numel() * 8 + out_g.numel() * 16
+    d_gs = torch.empty_like(h_gs, device=dev)
+
+    def one():
+        p.liz = B.build_liz(w.pos, w.lattice, w.r_liz)
+        p.species.copy_(h_species, non_blocking=True)
+        p.tinv.copy_(h_tinv, non_blocking=True)
+        p.J.copy_(h_J, non_blocking=True)
+        d_gs.copy_(h_gs, non_blocking=True)
+        p.forward()
+        g, _ = p.backward(d_gs)
+        out_sig.copy_(p.sigma_out, non_blocking=True)
+        out_rho.copy_(p.rho, non_blocking=True)
+        out_g.copy_(g, non_blocking=True)
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(1, args.warmup)):
+        one()
+    barrier(active)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = (time.perf_counter() - t0) / args.steps
+    dt = max_over_ranks(dt, active, device=dev)
+    return {"value": world * p.n_units / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3,
+            "note": "public API per step: lsms_build_liz + pinned H2D of inputs + forward + adjoint + D2H"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

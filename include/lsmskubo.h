@@ -203,6 +203,13 @@ const char* lsms_last_error(void);
 int lsms_version(void);
 /* Number of kernel launches the library has enqueued since load (all threads). */
 long long lsms_launch_count(void);
+/* Per-launch CUDA-event timers (profiling aid, off by default).  enable != 0
+ * clears previous records and records an event pair on the launch stream around
+ * every later kernel launch; 0 stops recording.  After the caller has
+ * synchronized, lsms_kernel_timer_report writes one line per kernel name,
+ * "name<TAB>total_ms<TAB>launches", into buf (NUL-terminated). */
+int lsms_kernel_timer_enable(int enable);
+int lsms_kernel_timer_report(char* buf, size_t len);
 
 #ifdef __cplusplus
 }

@@ -48,6 +48,8 @@ SIGNATURES = {
     "lsms_last_error": (ctypes.c_char_p, []),
     "lsms_version": (_I, []),
     "lsms_launch_count": (ctypes.c_longlong, []),
+    "lsms_kernel_timer_enable": (_I, [_I]),
+    "lsms_kernel_timer_report": (_I, [ctypes.c_char_p, _SZ]),
 }
 
 
@@ -270,6 +272,22 @@ def kubo_sigma_backward(liz, lmax, species, tinv, z, J, tau, volume, grad_sigma,
         _dev(grad_tinv_species, torch.complex128, (n_species, nE, K, K), "grad_tinv_species"), ws_p, ws_n,
         _stream(stream)))
     return grad_tinv, grad_tinv_species
+
+
+def kernel_timer_start():
+    _check(lib().lsms_kernel_timer_enable(1))
+
+
+def kernel_timer_stop(steps=1):
+    """Call after synchronizing.  Returns {kernel: (ms per step, launches per step)}."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(lib().lsms_kernel_timer_report(buf, len(buf)))
+    _check(lib().lsms_kernel_timer_enable(0))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, ms, cnt = line.split("\t")
+        out[name.strip("()")] = (float(ms) / steps, int(cnt) / steps)
+    return out
 
 
 def launch_count():

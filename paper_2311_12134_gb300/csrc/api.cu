@@ -19,6 +19,43 @@
 namespace lsms {
 
 std::atomic<long long> g_launches{0};
+std::atomic<bool> g_timer_on{false};
+
+namespace {
+struct TimerRec {
+  std::string name;
+  int ev;  // index of the start event; the stop event is ev + 1
+};
+std::mutex g_timer_mu;
+std::vector<cudaEvent_t> g_timer_events;
+std::vector<TimerRec> g_timer_recs;
+size_t g_timer_next = 0;
+
+cudaEvent_t timer_event() {
+  if (g_timer_next == g_timer_events.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    g_timer_events.push_back(e);
+  }
+  return g_timer_events[g_timer_next++];
+}
+}  // namespace
+
+void timer_begin(const char* name, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_timer_mu);
+  const int idx = (int)g_timer_next;
+  cudaEvent_t a = timer_event();
+  if (!a) return;
+  cudaEventRecord(a, st);
+  g_timer_recs.push_back(TimerRec{name, idx});
+}
+
+void timer_end(cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_timer_mu);
+  cudaEvent_t b = timer_event();
+  if (!b) return;
+  cudaEventRecord(b, st);
+}
 
 // kernels in kubo.cu
 int kubo_forward(const int64_t* offsets, const int32_t* site_atom, const int32_t* species, int n_species,
@@ -600,6 +637,39 @@ using namespace lsms;
 
 // ------------------------------------------------------------------ C ABI
 extern "C" long long lsms_launch_count(void) { return g_launches.load(); }
+
+extern "C" int lsms_kernel_timer_enable(int on) {
+  clear_error();
+  std::lock_guard<std::mutex> lk(g_timer_mu);
+  g_timer_recs.clear();
+  g_timer_next = 0;
+  g_timer_on.store(on != 0);
+  return LSMS_OK;
+}
+
+extern "C" int lsms_kernel_timer_report(char* buf, size_t len) {
+  clear_error();
+  if (!buf || len == 0) return fail(LSMS_ERR_ARG, "lsms_kernel_timer_report: empty buffer");
+  std::lock_guard<std::mutex> lk(g_timer_mu);
+  std::map<std::string, std::pair<double, long long>> agg;
+  for (const TimerRec& r : g_timer_recs) {
+    float ms = 0.f;
+    if (r.ev + 1 >= (int)g_timer_next) continue;
+    if (cudaEventElapsedTime(&ms, g_timer_events[r.ev], g_timer_events[r.ev + 1]) != cudaSuccess) continue;
+    auto& a = agg[r.name];
+    a.first += ms;
+    a.second += 1;
+  }
+  std::string out;
+  char line[512];
+  for (auto& kv : agg) {
+    snprintf(line, sizeof(line), "%s\t%.6f\t%lld\n", kv.first.c_str(), kv.second.first, kv.second.second);
+    out += line;
+  }
+  if (out.size() + 1 > len) return fail(LSMS_ERR_NOMEM, "lsms_kernel_timer_report: buffer too small");
+  std::memcpy(buf, out.c_str(), out.size() + 1);
+  return LSMS_OK;
+}
 
 extern "C" void lsms_liz_destroy(lsms_liz* liz) {
   if (!liz) return;

@@ -12,6 +12,12 @@ namespace lsms {
 
 extern std::atomic<long long> g_launches;
 
+// Optional per-launch CUDA-event timers (off by default), recorded on the
+// launch stream around each kernel; read back by lsms_kernel_timer_report.
+extern std::atomic<bool> g_timer_on;
+void timer_begin(const char* name, cudaStream_t st);
+void timer_end(cudaStream_t st);
+
 #define LSMS_CUDA_TRY(expr)                                                              \
   do {                                                                                   \
     cudaError_t _e = (expr);                                                             \
@@ -24,7 +30,10 @@ extern std::atomic<long long> g_launches;
 // launch configuration at once.
 #define LSMS_LAUNCH(kernel, grid, block, smem, stream, ...)                             \
   do {                                                                                   \
+    const bool _tm = ::lsms::g_timer_on.load(std::memory_order_relaxed);                 \
+    if (_tm) ::lsms::timer_begin(#kernel, (stream));                                     \
     kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                         \
+    if (_tm) ::lsms::timer_end((stream));                                                \
     ::lsms::g_launches.fetch_add(1, std::memory_order_relaxed);                          \
     cudaError_t _e = cudaGetLastError();                                                 \
     if (_e != cudaSuccess)                                                               \
