@@ -169,6 +169,31 @@ int lsms_kubo_sigma(const lsms_liz* liz, int lmax, const int32_t* species, int n
                     int n_delta, double volume, lsms_complex* sigma_tilde, lsms_complex* sigma,
                     double* rho, void* stream);
 
+/* Same computation and arguments as lsms_kubo_sigma, for callers that cannot
+ * allocate device memory during the call: code that must not trigger cudaMalloc
+ * or a stream-ordered pool allocation (a serving loop under a fixed memory
+ * budget, an application that owns every byte through its own allocator, code
+ * that must not add allocator synchronisation between launches).  It allocates
+ * nothing: its scratch (the per-atom partial traces) is a file-scope device
+ * array of 16 MiB that every GPU which loads the library holds until the
+ * process exits.  The paper has no counterpart; it is a deployment variant.
+ *  - Requires n_delta * n_atoms * 576 bytes (each rounded up to 256) plus
+ *    n_delta * 576 bytes to fit in 16 MiB, about 29,000 atom-delta pairs;
+ *    larger problems are rejected with LSMS_ERR_ARG and a message naming the
+ *    limit, before anything is enqueued.
+ *  - The LIZ set must already have a device copy on the current device (made
+ *    by lsms_tau_blocks, which produces tau); otherwise LSMS_ERR_ARG.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - All calls share the one array: calls that can overlap on the GPU (other
+ *    streams, other threads) race and corrupt each other's results; order them
+ *    on one stream or synchronise between them.  Each call writes every
+ *    scratch element it reads, so nothing is carried over between calls. */
+int lsms_kubo_sigma_noalloc(const lsms_liz* liz, int lmax, const int32_t* species, int n_species,
+                            const lsms_complex* J, int64_t J_delta_stride, const lsms_complex* tau,
+                            int n_delta, double volume, lsms_complex* sigma_tilde,
+                            lsms_complex* sigma, double* rho, void* stream);
+
 /* ---------------------------------------------------------------- gradient
  * Adjoint of the two calls above.  For f = sum_{d,mu,nu} conj(w[d][mu][nu]) sigma[d][mu][nu]
  * (w = grad_sigma, dev [n_delta][3][3]) it writes, for every energy e and atom i,

@@ -43,6 +43,7 @@ SIGNATURES = {
     "lsms_lu_store_bytes": (_I, [_P, _I, _I, _I, ctypes.POINTER(_SZ)]),
     "lsms_tau_blocks": (_I, [_P, _I, _P, _I, _P, _P, _I, _I, _P, _P, _P, _SZ, _P, _SZ, _P]),
     "lsms_kubo_sigma": (_I, [_P, _I, _P, _I, _P, _I64, _P, _I, _D, _P, _P, _P, _P]),
+    "lsms_kubo_sigma_noalloc": (_I, [_P, _I, _P, _I, _P, _I64, _P, _I, _D, _P, _P, _P, _P]),
     "lsms_kubo_sigma_backward": (_I, [_P, _I, _P, _I, _P, _P, _I, _I, _P, _I64, _P, _D, _P, _P, _SZ, _P, _P,
                                       _P, _SZ, _P]),
     "lsms_last_error": (ctypes.c_char_p, []),
@@ -243,6 +244,31 @@ def kubo_sigma(liz, lmax, species, J, tau, n_delta, volume, J_delta_stride=0, si
                                  float(volume), _dev(sigma_tilde, torch.complex128, (n_delta, 4, 3, 3), "sigma_tilde"),
                                  _dev(sigma, torch.complex128, (n_delta, 3, 3), "sigma"),
                                  _dev(rho, torch.float64, (n_delta, 3, 3), "rho"), _stream(stream)))
+    return sigma, sigma_tilde, rho
+
+
+def kubo_sigma_noalloc(liz, lmax, species, J, tau, n_delta, volume, J_delta_stride=0, sigma=None, sigma_tilde=None,
+                       rho=None, stream=None):
+    """lsms_kubo_sigma_noalloc: as kubo_sigma, but the library allocates nothing during the
+    call (its scratch is a fixed 16 MiB device array; see include/lsmskubo.h).  The output
+    tensors are allocated here by PyTorch unless passed in."""
+    import torch
+    K = (lmax + 1) ** 2
+    dev = tau.device
+    if sigma is None:
+        sigma = torch.empty((n_delta, 3, 3), dtype=torch.complex128, device=dev)
+    if sigma_tilde is None:
+        sigma_tilde = torch.empty((n_delta, 4, 3, 3), dtype=torch.complex128, device=dev)
+    if rho is None:
+        rho = torch.empty((n_delta, 3, 3), dtype=torch.float64, device=dev)
+    n_species = J.shape[-5]
+    _check(lib().lsms_kubo_sigma_noalloc(
+        liz.handle, lmax, _dev(species, torch.int32, (liz.n_atoms,), "species"), n_species,
+        _dev(J, torch.complex128, None, "J"), int(J_delta_stride),
+        _dev(tau, torch.complex128, (2 * n_delta, liz.total_sites, K, K), "tau"), n_delta, float(volume),
+        _dev(sigma_tilde, torch.complex128, (n_delta, 4, 3, 3), "sigma_tilde"),
+        _dev(sigma, torch.complex128, (n_delta, 3, 3), "sigma"), _dev(rho, torch.float64, (n_delta, 3, 3), "rho"),
+        _stream(stream)))
     return sigma, sigma_tilde, rho
 
 

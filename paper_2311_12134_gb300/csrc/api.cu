@@ -141,6 +141,19 @@ static int device_data(lsms_liz* liz, DeviceData** out) {
   return LSMS_OK;
 }
 
+// The device copy of a LIZ set if an earlier call made one on the current
+// device; never allocates.
+int existing_device_data(lsms_liz* liz, DeviceData** out) {
+  int dev = 0;
+  LSMS_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(liz->mu);
+  auto it = liz->dev.find(dev);
+  if (it == liz->dev.end())
+    return fail(LSMS_ERR_ARG, "no device copy of this LIZ set on device %d: call lsms_tau_blocks with it first", dev);
+  *out = &it->second;
+  return LSMS_OK;
+}
+
 // ------------------------------------------------------------------ plans
 struct UnitBytes {
   size_t fac, piv, m64, x, b, x32;

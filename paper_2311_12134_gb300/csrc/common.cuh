@@ -116,4 +116,6 @@ int lu_solve_chunk(const Unit* d_units, int n_units, const char* fac_base, char*
 
 enum RhsField { RHS_X = 0, RHS_X32 = 1 };
 
+int existing_device_data(lsms_liz* liz, DeviceData** out);
+
 }  // namespace lsms

@@ -7,6 +7,9 @@
 // with tau^{0n} = (tau^{n0})^T (complex-symmetric M).  Eq.
 // (sigma-tilde-consolidation) then combines the four pairs at finite delta.
 // All arithmetic here is FP64; sums over atoms and sites run in a fixed order.
+#include <cmath>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace lsms {
@@ -351,3 +354,75 @@ int adj_species(const int32_t* species, const double2* grad, int K, int n_atoms,
 }
 
 }  // namespace lsms
+
+// ------------------------------------------------------------------ sigma without allocation
+// Scratch for lsms_kubo_sigma_noalloc: the per-atom partial traces and the
+// reduced sums live in this file-scope device array instead of memory the call
+// allocates.  Host code must not use its name as an address; the address is
+// fetched per device with cudaGetSymbolAddress.
+namespace lsms {
+namespace {
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;
+__device__ __align__(256) unsigned char g_sigma_scratch[kNoAllocScratchBytes];
+std::mutex g_scratch_mu;
+void* g_scratch_addr[64];
+
+size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+
+int scratch_address(void** out) {
+  int dev = 0;
+  LSMS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(LSMS_ERR_CUDA, "device index %d unsupported", dev);
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_sigma_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(LSMS_ERR_CUDA, "cudaGetSymbolAddress of the sigma scratch failed: %s", cudaGetErrorString(e));
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return LSMS_OK;
+}
+}  // namespace
+
+}  // namespace lsms
+
+using namespace lsms;
+
+extern "C" int lsms_kubo_sigma_noalloc(const lsms_liz* liz_c, int lmax, const int32_t* species, int n_species,
+                                       const lsms_complex* J, int64_t J_delta_stride, const lsms_complex* tau,
+                                       int n_delta, double volume, lsms_complex* sigma_tilde, lsms_complex* sigma,
+                                       double* rho, void* stream) {
+  clear_error();
+  lsms_liz* liz = const_cast<lsms_liz*>(liz_c);
+  if (!liz) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_noalloc: NULL liz");
+  if (lmax < 0 || lmax > kMaxLmax) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_noalloc: lmax must be in 0..%d", kMaxLmax);
+  if (!species || n_species < 1) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_noalloc: species required, n_species >= 1");
+  if (n_delta < 1 || 2 * n_delta > kMaxEnergies || !J || !tau || !sigma)
+    return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_noalloc: J, tau, sigma required, 1 <= n_delta <= %d", kMaxEnergies / 2);
+  if (!(volume > 0.0) || !std::isfinite(volume)) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_noalloc: volume must be > 0");
+  if (J_delta_stride < 0) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_noalloc: negative J stride");
+  const size_t part_bytes = round256((size_t)n_delta * 4 * liz->n_atoms * 9 * sizeof(double2));
+  const size_t s_bytes = round256((size_t)n_delta * 36 * sizeof(double2));
+  if (part_bytes + s_bytes > kNoAllocScratchBytes)
+    return fail(LSMS_ERR_ARG,
+                "lsms_kubo_sigma_noalloc: %d atoms x %d deltas need %zu bytes of scratch; the static buffer holds "
+                "%zu bytes (about 29,000 atom-delta pairs); use lsms_kubo_sigma",
+                liz->n_atoms, n_delta, part_bytes + s_bytes, kNoAllocScratchBytes);
+  DeviceData* dd = nullptr;
+  int rc = existing_device_data(liz, &dd);
+  if (rc) return rc;
+  void* scratch = nullptr;
+  if ((rc = scratch_address(&scratch))) return rc;
+  char* base = static_cast<char*>(scratch);
+  const int K = (lmax + 1) * (lmax + 1);
+  // Every scratch element read by the kernels is written earlier in the same
+  // call (partial traces by k_kubo_partial, sums by k_kubo_reduce), so the
+  // previous call's contents need no clearing.
+  return kubo_forward(dd->offsets, dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J),
+                      J_delta_stride, reinterpret_cast<const double2*>(tau), liz->total_sites, K, liz->n_atoms,
+                      n_delta, volume, reinterpret_cast<double2*>(base), reinterpret_cast<double2*>(base + part_bytes),
+                      reinterpret_cast<double2*>(sigma_tilde), reinterpret_cast<double2*>(sigma), rho,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
