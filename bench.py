@@ -310,7 +310,8 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (per-step working set > 4 GB)"},
         "sigma_ms": sigma_ms,
         "effective_tflops": units * world * (lu_flops([688]) ) / (ms * 1e-3) / 1e12,
-        "unit_status_clean": bool((status == 0).all()),
+        "unit_status_clean": bool(((status & 0xff) == 0).all()),
+        "ir_passes_mean": float((status >> 8).mean()), "ir_passes_max": int((status >> 8).max()),
         "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
         "cpu_baseline": cpu, "fp64_form": fp64,
     }

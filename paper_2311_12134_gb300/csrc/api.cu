@@ -5,9 +5,10 @@
 //   k_assemble   M = T^{-1} - g, g from Gaunt x h_l(kappa R) x Y_L(R^)
 //   lu (lu.cu)   P M = L U, blocked, all units of a chunk per launch
 //   k_solve      X = M^{-1} E0 -> tau^{p0}
-//   mixed form:  complex64 LU/solves, then k_residual (FP64 B - M X) /
-//                k_solve (complex64 correction) / k_ir_update until the
-//                correction is below 1e-10 of X (at most kIrMaxIter sweeps)
+//   mixed form:  complex64 LU/solves, then k_residual (B - M X to about
+//                2^-48, double-float arithmetic on the FP32 pipes) / k_solve
+//                (complex64 correction) / k_ir_update until the correction is
+//                below 1e-10 of X (at most kIrMaxIter sweeps)
 //   k_write_tau  scatter X into tau[e][site]
 #include <algorithm>
 #include <cmath>
@@ -80,9 +81,10 @@ constexpr size_t kAlign = 256;
 static inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // ------------------------------------------------------------------ constant tables
+constexpr int kCpMax = 768;  // nonzero Gaunt couplings for lmax = 3: 708
 __constant__ int32_t c_cp_start[kMaxK * kMaxK + 1];
-__constant__ int32_t c_cp_lpp[1024];
-__constant__ double c_cp_coef[1024];
+__constant__ int32_t c_cp_lpp[kCpMax];
+__constant__ double c_cp_coef[kCpMax];
 __constant__ double c_ylm_norm[kMaxK3];
 __constant__ int32_t c_l_of[kMaxK3];
 
@@ -94,7 +96,7 @@ static int ensure_device_tables(int dev) {
   if (dev < 0 || dev >= 64) return fail(LSMS_ERR_CUDA, "device index %d unsupported", dev);
   if (g_dev_init[dev]) return LSMS_OK;
   const Coupling cp = g_coupling(kMaxLmax);
-  if (cp.lpp.size() > 1024) return fail(LSMS_ERR_ARG, "internal: coupling table too large");
+  if (cp.lpp.size() > (size_t)kCpMax) return fail(LSMS_ERR_ARG, "internal: coupling table too large");
   const std::vector<double> nrm = ylm_norm(kMaxL3);
   std::vector<int32_t> lof(kMaxK3);
   for (int L = 0; L < kMaxK3; ++L) {
@@ -163,7 +165,7 @@ static UnitBytes unit_bytes(int n, int precision, int nrhs, bool backward) {
   UnitBytes ub{};
   const size_t nn = (size_t)n * n;
   ub.fac = align_up(nn * (precision == LSMS_FP64 ? 16 : 8));
-  ub.piv = align_up((size_t)n * 4);
+  ub.piv = align_up((size_t)n * 4 * 3);  // pivots, perm, iperm
   ub.m64 = precision == LSMS_FP64 ? 0 : align_up(nn * 16);
   ub.x = align_up((size_t)n * nrhs * 16);
   ub.b = backward ? align_up((size_t)n * nrhs * 16) : 0;
@@ -234,15 +236,17 @@ static int get_plan(lsms_liz* liz, DeviceData* dd, int lmax, int n_energy, int p
     const int n = K * S;
     const UnitBytes ub = unit_bytes(n, precision, nrhs, backward);
     const size_t need = ws_unit_bytes(ub, store);
-    if (need > chunk_bytes) return fail(LSMS_ERR_NOMEM, "workspace of %zu bytes cannot hold one unit (%zu bytes)", chunk_bytes, need);
+    if (need * n_energy > chunk_bytes)
+      return fail(LSMS_ERR_NOMEM, "workspace of %zu bytes cannot hold the %d energies of one atom (%zu bytes)",
+                  chunk_bytes, n_energy, need * n_energy);
+    if (cur + need * n_energy > chunk_bytes) {  // chunks hold whole atoms (all energies)
+      ch.u1 = (int)p.units.size();
+      ch.ws_bytes = cur;
+      p.chunks.push_back(ch);
+      ch = Chunk{(int)p.units.size(), 0, 0, 0};
+      cur = 0;
+    }
     for (int e = 0; e < n_energy; ++e) {
-      if (cur + need > chunk_bytes) {
-        ch.u1 = (int)p.units.size();
-        ch.ws_bytes = cur;
-        p.chunks.push_back(ch);
-        ch = Chunk{(int)p.units.size(), 0, 0, 0};
-        cur = 0;
-      }
       Unit u{};
       u.atom = m;
       u.energy = e;
@@ -282,158 +286,213 @@ static int get_plan(lsms_liz* liz, DeviceData* dd, int lmax, int n_energy, int p
 }
 
 // ------------------------------------------------------------------ assembly
-__device__ void ylm_hankel(double rx, double ry, double rz, double2 kap, bool adv, double* Y, double2* H, int lane) {
+constexpr int kAsmQ = 16;  // column sites per set-up round
+constexpr int kAsmE = 2;   // energies per set-up round
+
+// V[L''] = mpref * h_{l''}(kappa |R|) * Y_{L''}(R^) for one separation R and
+// energy z, where mpref * sum_L'' i^{l-l'-l''} C_{LL'L''} V[L''] is the block -g:
+// kappa = principal sqrt(z); Im z >= 0: h = h^(1), mpref = +4 pi i kappa;
+// Im z < 0: h = h^(2), mpref = -4 pi i kappa (the decaying, advanced branch).
+// Y_L: real harmonics without the Condon-Shortley phase from the upward
+// associated-Legendre recurrence for P_l^m / sin^m and (x + i y)^m.
+__device__ void pair_setup(double rx, double ry, double rz, double2 z, double2* V) {
+  const double r = hypot(z.x, z.y);
+  const double kre = sqrt(0.5 * (r + z.x));
+  double kim = sqrt(0.5 * fmax(r - z.x, 0.0));
+  const bool adv = z.y < 0.0;
+  if (adv) kim = -kim;
+  const double four_pi = 4.0 * M_PI;
+  const double2 mpref = adv ? mk(four_pi * kim, -four_pi * kre) : mk(-four_pi * kim, four_pi * kre);
   const double d = sqrt(rx * rx + ry * ry + rz * rz);
-  const double x = rx / d, y = ry / d, z = rz / d;
-  if (lane <= kMaxL3) {
-    const int m = lane;
-    double tr = 1.0, ti = 0.0;  // (x + i y)^m = sin^m(theta) e^{i m phi}
-    for (int t = 0; t < m; ++t) {
+  const double id = 1.0 / d;
+  const double x = rx * id, y = ry * id, zc = rz * id;
+  // spherical Hankel functions by upward recurrence h_{l+1} = (2l+1)/x h_l - h_{l-1}
+  double2 hp[kMaxL3 + 1];
+  {
+    const double2 xx = mk(kre * d, kim * d);
+    const double2 ix = crcp(xx);
+    double sn, cs;
+    sincos(xx.x, &sn, &cs);
+    const double f = exp(adv ? xx.y : -xx.y);
+    const double2 ex = adv ? mk(f * cs, -f * sn) : mk(f * cs, f * sn);  // e^{-+ix}
+    double2 hm = cmul(ex, ix);                                             // h_{-1}
+    double2 h = adv ? mk(-hm.y, hm.x) : mk(hm.y, -hm.x);                  // h_0
+    hp[0] = cmul(mpref, h);
+#pragma unroll
+    for (int l = 0; l < kMaxL3; ++l) {
+      const double2 hn = csub(cmul(mk((2.0 * l + 1.0) * ix.x, (2.0 * l + 1.0) * ix.y), h), hm);
+      hm = h;
+      h = hn;
+      hp[l + 1] = cmul(mpref, h);
+    }
+  }
+  double tr = 1.0, ti = 0.0;  // (x + i y)^m
+  double qmm = 1.0;           // (2m - 1)!!
+#pragma unroll
+  for (int m = 0; m <= kMaxL3; ++m) {
+    if (m > 0) {
       const double nr = tr * x - ti * y;
       ti = tr * y + ti * x;
       tr = nr;
+      qmm *= (2 * m - 1);
     }
-    double qmm = 1.0;  // (2m-1)!!: P_m^m / sin^m without the Condon-Shortley phase
-    for (int t = 1; t <= m; ++t) qmm *= (2 * t - 1);
     double q2 = 0.0, q1 = 0.0;
+#pragma unroll
     for (int l = m; l <= kMaxL3; ++l) {
       double q;
       if (l == m) q = qmm;
-      else if (l == m + 1) q = (2 * m + 1) * z * qmm;
-      else q = ((2 * l - 1) * z * q1 - (l + m - 1) * q2) / (l - m);
+      else if (l == m + 1) q = (2 * m + 1) * zc * qmm;
+      else q = ((2 * l - 1) * zc * q1 - (l + m - 1) * q2) * (1.0 / (l - m));
       q2 = q1;
       q1 = q;
+      const int L0 = l * l + l;
       if (m == 0) {
-        Y[l * l + l] = c_ylm_norm[l * l + l] * q;
+        const double yv = c_ylm_norm[L0] * q;
+        V[L0] = mk(hp[l].x * yv, hp[l].y * yv);
       } else {
-        Y[l * l + l + m] = c_ylm_norm[l * l + l + m] * q * tr;
-        Y[l * l + l - m] = c_ylm_norm[l * l + l - m] * q * ti;
+        const double yc = c_ylm_norm[L0 + m] * q * tr;
+        const double ys = c_ylm_norm[L0 - m] * q * ti;
+        V[L0 + m] = mk(hp[l].x * yc, hp[l].y * yc);
+        V[L0 - m] = mk(hp[l].x * ys, hp[l].y * ys);
       }
-    }
-  } else if (lane == kMaxL3 + 1) {
-    const double2 xx = mk(kap.x * d, kap.y * d);
-    const double2 ix = crcp(xx);
-    double s, c;
-    sincos(xx.x, &s, &c);
-    double2 ex;
-    if (!adv) {
-      const double f = exp(-xx.y);
-      ex = mk(f * c, f * s);  // e^{i x}
-    } else {
-      const double f = exp(xx.y);
-      ex = mk(f * c, -f * s);  // e^{-i x}
-    }
-    double2 hm = cmul(ex, ix);                                         // h_{-1}
-    double2 h = adv ? mk(-hm.y, hm.x) : mk(hm.y, -hm.x);               // h_0 = +-i e^{-+ix}/x
-    H[0] = h;
-    for (int l = 0; l < kMaxL3; ++l) {
-      const double2 t = cmul(mk((2.0 * l + 1.0) * ix.x, (2.0 * l + 1.0) * ix.y), h);
-      const double2 hn = csub(t, hm);
-      hm = h;
-      h = hn;
-      H[l + 1] = h;
     }
   }
 }
 
-// grid (S_max, n_units), block 256: CTA = one row site p of one unit, loop over column sites q.
-// Writes the FP64 matrix (m64 at ws + m64_off when MIXED, else the factor array) and,
-// for MIXED, its complex64 rounding into the factor array.
+// grid (S_max, atoms in the chunk), block 256: one CTA per row site p of one
+// atom's LIZ, for all energies of that atom.  Warp 0 prepares V for 16 column
+// sites x 2 energies at a time (one lane each); then thread (L, L') forms
+// sum_L'' s C_{LL'L''} V[L''] for those blocks (diagonal blocks: t^{-1}).
+// FP64 form: writes M (complex128) into the factor array.  Mixed form: writes
+// (hi, lo) float pairs of M (float4 per element, at ws + m64_off) for the
+// refinement residual and, if write_fac, the hi part (complex64) as the matrix
+// to factor.
 template <bool MIXED>
-__global__ void __launch_bounds__(256) k_assemble(const Unit* __restrict__ units, const double* __restrict__ disp,
+__global__ void __launch_bounds__(256) k_assemble(const Unit* __restrict__ units, int nE,
+                                                  const double* __restrict__ disp,
                                                   const int32_t* __restrict__ site_atom,
                                                   const int32_t* __restrict__ species,
                                                   const double2* __restrict__ tinv, int n_species, int n_energy,
                                                   EnergyTable E, int K, char* fac_base, char* ws, bool write_fac,
                                                   int32_t* stat) {
-  const Unit u = units[blockIdx.y];
+  const Unit* ua = units + (size_t)blockIdx.y * nE;
+  const Unit u0 = ua[0];
   const int p = blockIdx.x;
-  if (p >= u.S) return;
-  const int n = u.n;
-  const double2 z = E.z[u.energy];
-  const double r = hypot(z.x, z.y);
-  const double kre = sqrt(0.5 * (r + z.x));
-  double kim = sqrt(0.5 * fmax(r - z.x, 0.0));
-  if (z.y < 0.0) kim = -kim;
-  const double2 kap = mk(kre, kim);
-  const bool adv = z.y < 0.0;
-  // M = -g:  +4 pi i kappa * sum (retarded), -4 pi i kappa * sum (advanced)
-  const double four_pi = 4.0 * M_PI;
-  const double2 mpref = adv ? mk(four_pi * kim, -four_pi * kre) : mk(-four_pi * kim, four_pi * kre);
-  __shared__ double sY[2][kMaxK3];
-  __shared__ double2 sH[2][kMaxL3 + 1];
+  if (p >= u0.S) return;
+  const int S = u0.S, n = u0.n;
+  __shared__ double2 sV[kAsmE][kAsmQ][kMaxK3];
+  // Gaunt coupling table in shared memory: threads index it divergently, which
+  // constant memory would serialise.
+  __shared__ double s_coef[kCpMax];
+  __shared__ int32_t s_lpp[kCpMax];
+  __shared__ int32_t s_start[kMaxK * kMaxK + 1];
   const int tid = threadIdx.x;
+  for (int i = tid; i < kMaxK * kMaxK + 1; i += blockDim.x) s_start[i] = c_cp_start[i];
+  const int n_cp = c_cp_start[kMaxK * kMaxK];
+  for (int i = tid; i < n_cp; i += blockDim.x) {
+    s_coef[i] = c_cp_coef[i];
+    s_lpp[i] = c_cp_lpp[i];
+  }
+  __syncthreads();
   const int L = tid & 15, Lp = tid >> 4;
   const bool act = (L < K) && (Lp < K);
-  const int64_t sp0 = u.site_off + p;
+  const int64_t sp0 = u0.site_off + p;
   const double px = disp[3 * sp0], py = disp[3 * sp0 + 1], pz = disp[3 * sp0 + 2];
   int spp = species[site_atom[sp0]];
-  int flags = 0;
+  int bad = 0;
   if (spp < 0 || spp >= n_species) {  // reject without reading outside tinv
-    flags |= LSMS_UNIT_BAD_INPUT;
+    bad = LSMS_UNIT_BAD_INPUT;
     spp = 0;
   }
-  double2* M64 = reinterpret_cast<double2*>(MIXED ? ws + u.m64_off : fac_base + u.fac_off);
-  float2* M32 = reinterpret_cast<float2*>(fac_base + u.fac_off);
   int t0 = 0, t1 = 0;
   if (act) {
-    t0 = c_cp_start[L * kMaxK + Lp];
-    t1 = c_cp_start[L * kMaxK + Lp + 1];
+    t0 = s_start[L * kMaxK + Lp];
+    t1 = s_start[L * kMaxK + Lp + 1];
   }
-  for (int q = 0; q < u.S; ++q) {
-    const int buf = q & 1;
-    if (q != p && tid < 32) {
-      const int64_t sq = u.site_off + q;
-      ylm_hankel(disp[3 * sq] - px, disp[3 * sq + 1] - py, disp[3 * sq + 2] - pz, kap, adv, sY[buf], sH[buf], tid);
-    }
-    __syncthreads();
-    if (act) {
-      double2 v;
-      if (q == p) {
-        v = tinv[(((size_t)spp * n_energy) + u.energy) * K * K + L * K + Lp];
-      } else {
-        double2 acc = mk(0.0, 0.0);
-        for (int t = t0; t < t1; ++t) {
-          const int lpp = c_cp_lpp[t];
-          const double w = c_cp_coef[t] * sY[buf][lpp];
-          const double2 h = sH[buf][c_l_of[lpp]];
-          acc.x = fma(w, h.x, acc.x);
-          acc.y = fma(w, h.y, acc.y);
+  for (int e0 = 0; e0 < nE; e0 += kAsmE) {
+    int flags[kAsmE];
+#pragma unroll
+    for (int ee = 0; ee < kAsmE; ++ee) flags[ee] = bad;
+    const int ne = min(kAsmE, nE - e0);
+    for (int q0 = 0; q0 < S; q0 += kAsmQ) {
+      const int nq = min(kAsmQ, S - q0);
+      __syncthreads();
+      if (tid < kAsmE * kAsmQ) {
+        const int ee = tid / kAsmQ, qq = tid % kAsmQ, q = q0 + qq;
+        if (ee < ne && qq < nq && q != p) {
+          const int64_t sq = u0.site_off + q;
+          pair_setup(disp[3 * sq] - px, disp[3 * sq + 1] - py, disp[3 * sq + 2] - pz, E.z[ua[e0 + ee].energy],
+                     sV[ee][qq]);
         }
-        v = cmul(mpref, acc);
       }
-      if (!finite2(v)) flags |= LSMS_UNIT_NONFINITE;
-      const size_t idx = (size_t)(K * q + Lp) * n + K * p + L;
-      if (MIXED || write_fac) M64[idx] = v;
-      if (MIXED && write_fac) M32[idx] = to32(v);
+      __syncthreads();
+      if (!act) continue;
+      for (int ee = 0; ee < ne; ++ee) {
+        const Unit& u = ua[e0 + ee];
+        for (int qq = 0; qq < nq; ++qq) {
+          const int q = q0 + qq;
+          double2 v;
+          if (q == p) {
+            v = tinv[(((size_t)spp * n_energy) + u.energy) * K * K + L * K + Lp];
+          } else {
+            v = mk(0.0, 0.0);
+            const double2* Vq = sV[ee][qq];
+            for (int t = t0; t < t1; ++t) {
+              const double c = s_coef[t];
+              const double2 w = Vq[s_lpp[t]];
+              v.x = fma(c, w.x, v.x);
+              v.y = fma(c, w.y, v.y);
+            }
+          }
+          if (!finite2(v)) flags[ee] |= LSMS_UNIT_NONFINITE;
+          const size_t idx = (size_t)(K * q + Lp) * n + K * p + L;
+          if (MIXED) {
+            const float hr = (float)v.x, hi = (float)v.y;
+            const float4 hl = make_float4(hr, hi, (float)(v.x - (double)hr), (float)(v.y - (double)hi));
+            reinterpret_cast<float4*>(ws + u.m64_off)[idx] = hl;
+            if (write_fac) reinterpret_cast<float2*>(fac_base + u.fac_off)[idx] = make_float2(hr, hi);
+          } else {
+            reinterpret_cast<double2*>(fac_base + u.fac_off)[idx] = v;
+          }
+        }
+      }
     }
+    for (int ee = 0; ee < ne; ++ee)
+      if (flags[ee]) atomicOr(&stat[ua[e0 + ee].stat_off], flags[ee]);
   }
-  if (flags) atomicOr(&stat[u.stat_off], flags);
 }
 
 // ------------------------------------------------------------------ RHS / refinement kernels
-// X (n x nrhs, column-major, complex<R>) = E0 (first K columns of the identity).
+// Right-hand sides enter the solves already permuted by P (P M = L U):
+// row position i holds original row perm[i].
+
+// X = P E0 (E0 = first K columns of the identity), complex<R>.
 template <typename C>
-__global__ void k_rhs_identity(const Unit* __restrict__ units, char* ws, int which, int K, int nrhs) {
+__global__ void k_rhs_identity(const Unit* __restrict__ units, const char* fac_base, char* ws, int which, int K,
+                               int nrhs) {
   const Unit u = units[blockIdx.y];
   const int n = u.n;
+  const int32_t* perm = reinterpret_cast<const int32_t*>(fac_base + u.piv_off) + n;
   C* X = reinterpret_cast<C*>(ws + (which == RHS_X ? u.x_off : u.x32_off));
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)n * nrhs;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(idx % n), c = (int)(idx / n);
-    X[idx] = (i == c && c < K) ? cvt<C>(make_double2(1.0, 0.0)) : cvt<C>(make_double2(0.0, 0.0));
+    X[idx] = (perm[i] == c && c < K) ? cvt<C>(make_double2(1.0, 0.0)) : cvt<C>(make_double2(0.0, 0.0));
   }
 }
 
-// X32 = B (explicit right-hand side, complex128 at r_off) rounded; or X = B (FP64).
-__global__ void k_copy_b(const Unit* __restrict__ units, char* ws, int nrhs, bool to_x32) {
+// X32 = P B rounded (mixed form) or X = P B (FP64 form); B complex128 at r_off.
+__global__ void k_copy_b(const Unit* __restrict__ units, const char* fac_base, char* ws, int nrhs, bool to_x32) {
   const Unit u = units[blockIdx.y];
   const int n = u.n;
+  const int32_t* perm = reinterpret_cast<const int32_t*>(fac_base + u.piv_off) + n;
   const double2* B = reinterpret_cast<const double2*>(ws + u.r_off);
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)n * nrhs;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    if (to_x32) reinterpret_cast<float2*>(ws + u.x32_off)[idx] = to32(B[idx]);
-    else reinterpret_cast<double2*>(ws + u.x_off)[idx] = B[idx];
+    const int i = (int)(idx % n), c = (int)(idx / n);
+    const double2 b = B[(size_t)c * n + perm[i]];
+    if (to_x32) reinterpret_cast<float2*>(ws + u.x32_off)[idx] = to32(b);
+    else reinterpret_cast<double2*>(ws + u.x_off)[idx] = b;
   }
 }
 
@@ -448,48 +507,85 @@ __global__ void k_widen(const Unit* __restrict__ units, char* ws, int nrhs) {
     X[idx] = to64(X32[idx]);
 }
 
-// FP64 residual, rounded to complex64 for the correction solve:
-//   X32 = B - M X   (B = E0 when explicit_b is false).
-// grid (ceil(n_max / 64), n_units), block 256: 64 rows x nrhs columns per CTA.
-__global__ void __launch_bounds__(256) k_residual(const Unit* __restrict__ units, char* ws, int K, int nrhs,
-                                                  bool explicit_b, const int32_t* __restrict__ done) {
+// (s, t) += p with the rounding error of s + p kept exactly (two-sum).
+__device__ __forceinline__ void df_add(float& s, float& t, float p) {
+  const float a = s + p;
+  const float bb = a - s;
+  t += (s - (a - bb)) + (p - bb);
+  s = a;
+}
+
+// (s, t) += (ah + al)(bh + bl): exact ah*bh (two-product by FMA) plus the cross terms.
+__device__ __forceinline__ void df_mac(float& s, float& t, float ah, float al, float bh, float bl) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  df_add(s, t, p);
+  t += e;
+}
+
+// Refinement residual, FP64-accurate, on the FP32 pipes: B - M X with M held as
+// (hi, lo) float pairs and X split the same way, products by the FMA two-product
+// and sums by two-sum (double-float arithmetic, unit roundoff about 2^-48).
+// Output rounded to complex64 and permuted by P into X32 for the correction
+// solve.  grid (ceil(n_max / 64), n_units), block 256: 64 rows x nrhs columns.
+__global__ void __launch_bounds__(256) k_residual(const Unit* __restrict__ units, const char* fac_base, char* ws,
+                                                  int K, int nrhs, bool explicit_b, const int32_t* __restrict__ done) {
   const Unit u = units[blockIdx.y];
   if (done[u.stat_off]) return;
   const int n = u.n;
   const int row0 = blockIdx.x * 64;
   if (row0 >= n) return;
-  const double2* M = reinterpret_cast<const double2*>(ws + u.m64_off);
+  const float4* M = reinterpret_cast<const float4*>(ws + u.m64_off);
   const double2* X = reinterpret_cast<const double2*>(ws + u.x_off);
+  const int32_t* iperm = reinterpret_cast<const int32_t*>(fac_base + u.piv_off) + 2 * n;
   float2* X32 = reinterpret_cast<float2*>(ws + u.x32_off);
-  __shared__ double2 sX[32][33];
+  __shared__ float4 sX[32][33];
   const int tid = threadIdx.x;
   const int r = tid & 63, cg = tid >> 6;  // 4 column groups
   const int row = row0 + r;
   const int cpg = (nrhs + 3) / 4;          // columns per group (<= 8)
-  double2 acc[8];
+  float sr[8], tr[8], si[8], ti[8];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) acc[c] = mk(0.0, 0.0);
+  for (int c = 0; c < 8; ++c) sr[c] = tr[c] = si[c] = ti[c] = 0.f;
   for (int j0 = 0; j0 < n; j0 += 32) {
     const int jn = min(32, n - j0);
     __syncthreads();
     for (int idx = tid; idx < 32 * nrhs; idx += 256) {
       const int jj = idx % 32, c = idx / 32;
-      sX[jj][c] = jj < jn ? X[(size_t)c * n + j0 + jj] : mk(0.0, 0.0);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (jj < jn) {
+        const double2 xv = X[(size_t)c * n + j0 + jj];
+        v.x = (float)xv.x;
+        v.y = (float)xv.y;
+        v.z = (float)(xv.x - (double)v.x);
+        v.w = (float)(xv.y - (double)v.y);
+      }
+      sX[jj][c] = v;
     }
     __syncthreads();
     if (row < n) {
       for (int jj = 0; jj < jn; ++jj) {
-        const double2 mv = M[(size_t)(j0 + jj) * n + row];
+        const float4 m = M[(size_t)(j0 + jj) * n + row];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           const int col = cg * cpg + c;
-          if (c < cpg && col < nrhs) acc[c] = cfma(mv, sX[jj][col], acc[c]);
+          if (c < cpg && col < nrhs) {
+            const float4 x = sX[jj][col];
+            // Re += m.re x.re - m.im x.im ; Im += m.re x.im + m.im x.re
+            df_mac(sr[c], tr[c], m.x, m.z, x.x, x.z);
+            df_mac(sr[c], tr[c], -m.y, -m.w, x.y, x.w);
+            df_mac(si[c], ti[c], m.x, m.z, x.y, x.w);
+            df_mac(si[c], ti[c], m.y, m.w, x.x, x.z);
+          }
         }
       }
     }
   }
   if (row < n) {
     const double2* B = reinterpret_cast<const double2*>(ws + u.r_off);
+    const int pos = iperm[row];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int col = cg * cpg + c;
@@ -497,13 +593,16 @@ __global__ void __launch_bounds__(256) k_residual(const Unit* __restrict__ units
         double2 b;
         if (explicit_b) b = B[(size_t)col * n + row];
         else b = (row == col && col < K) ? mk(1.0, 0.0) : mk(0.0, 0.0);
-        X32[(size_t)col * n + row] = to32(csub(b, acc[c]));
+        const double re = b.x - ((double)sr[c] + (double)tr[c]);
+        const double im = b.y - ((double)si[c] + (double)ti[c]);
+        X32[(size_t)col * n + pos] = make_float2((float)re, (float)im);
       }
     }
   }
 }
 
-// X += X32 (the correction); done when ||correction||_F <= tol ||X||_F.  One CTA per unit.
+// X += X32 (the correction); done when ||correction||_F <= tol ||X||_F.  One CTA
+// per unit.  Each sweep adds 1 << 8 to the unit's status word (pass count).
 __global__ void __launch_bounds__(256) k_ir_update(const Unit* __restrict__ units, char* ws, int nrhs, double tol,
                                                    int32_t* done, int32_t* stat) {
   const Unit u = units[blockIdx.x];
@@ -532,6 +631,7 @@ __global__ void __launch_bounds__(256) k_ir_update(const Unit* __restrict__ unit
   }
   if (threadIdx.x == 0) {
     const double a = s1[0], b = s2[0];
+    atomicAdd(&stat[u.stat_off], 1 << 8);
     if (!isfinite(a) || !isfinite(b)) {
       atomicOr(&stat[u.stat_off], LSMS_UNIT_NONFINITE);
       done[u.stat_off] = 1;
@@ -593,16 +693,17 @@ static int assemble_factor(const Call& c, const Plan& p, const Chunk& ch, char* 
   const Unit* du = p.d_units + ch.u0;
   const int nu = ch.u1 - ch.u0;
   const int S_max = ch.n_max / c.K;
+  const int n_at = nu / c.n_energy;  // chunks hold whole atoms
   if (c.precision == LSMS_FP64) {
     if (factor) {
-      LSMS_LAUNCH(k_assemble<false>, dim3(S_max, nu), dim3(256), 0, c.st, du, c.dd->disp, c.dd->site_atom, c.species,
-                  c.tinv, c.n_species, c.n_energy, c.E, c.K, fac_base, ws, true, stat);
+      LSMS_LAUNCH(k_assemble<false>, dim3(S_max, n_at), dim3(256), 0, c.st, du, c.n_energy, c.dd->disp,
+                  c.dd->site_atom, c.species, c.tinv, c.n_species, c.n_energy, c.E, c.K, fac_base, ws, true, stat);
       return lu_factor_chunk<double>(du, nu, ch.n_max, fac_base, stat, c.st);
     }
     return LSMS_OK;
   }
-  LSMS_LAUNCH(k_assemble<true>, dim3(S_max, nu), dim3(256), 0, c.st, du, c.dd->disp, c.dd->site_atom, c.species,
-              c.tinv, c.n_species, c.n_energy, c.E, c.K, fac_base, ws, factor, stat);
+  LSMS_LAUNCH(k_assemble<true>, dim3(S_max, n_at), dim3(256), 0, c.st, du, c.n_energy, c.dd->disp, c.dd->site_atom,
+              c.species, c.tinv, c.n_species, c.n_energy, c.E, c.K, fac_base, ws, factor, stat);
   if (factor) return lu_factor_chunk<float>(du, nu, ch.n_max, fac_base, stat, c.st);
   return LSMS_OK;
 }
@@ -617,17 +718,18 @@ static int solve_refine(const Call& c, const Plan& p, const Chunk& ch, const cha
   const dim3 g1((ch.n_max * nrhs + 255) / 256, nu);
   int rc;
   if (c.precision == LSMS_FP64) {
-    if (explicit_b) LSMS_LAUNCH(k_copy_b, g1, dim3(256), 0, c.st, du, ws, nrhs, false);
-    else LSMS_LAUNCH(k_rhs_identity<double2>, g1, dim3(256), 0, c.st, du, ws, (int)RHS_X, c.K, nrhs);
+    if (explicit_b) LSMS_LAUNCH(k_copy_b, g1, dim3(256), 0, c.st, du, fac_base, ws, nrhs, false);
+    else LSMS_LAUNCH(k_rhs_identity<double2>, g1, dim3(256), 0, c.st, du, fac_base, ws, (int)RHS_X, c.K, nrhs);
     return lu_solve_chunk<double>(du, nu, fac_base, ws, RHS_X, nrhs, nullptr, c.st);
   }
-  if (explicit_b) LSMS_LAUNCH(k_copy_b, g1, dim3(256), 0, c.st, du, ws, nrhs, true);
-  else LSMS_LAUNCH(k_rhs_identity<float2>, g1, dim3(256), 0, c.st, du, ws, (int)RHS_X32, c.K, nrhs);
+  if (explicit_b) LSMS_LAUNCH(k_copy_b, g1, dim3(256), 0, c.st, du, fac_base, ws, nrhs, true);
+  else LSMS_LAUNCH(k_rhs_identity<float2>, g1, dim3(256), 0, c.st, du, fac_base, ws, (int)RHS_X32, c.K, nrhs);
   if ((rc = lu_solve_chunk<float>(du, nu, fac_base, ws, RHS_X32, nrhs, nullptr, c.st))) return rc;
   LSMS_LAUNCH(k_widen, g1, dim3(256), 0, c.st, du, ws, nrhs);
   // done flags of this chunk's units start cleared (memset by the caller)
   for (int it = 0; it < kIrMaxIter; ++it) {
-    LSMS_LAUNCH(k_residual, dim3((ch.n_max + 63) / 64, nu), dim3(256), 0, c.st, du, ws, c.K, nrhs, explicit_b, done);
+    LSMS_LAUNCH(k_residual, dim3((ch.n_max + 63) / 64, nu), dim3(256), 0, c.st, du, fac_base, ws, c.K, nrhs,
+                explicit_b, done);
     if ((rc = lu_solve_chunk<float>(du, nu, fac_base, ws, RHS_X32, nrhs, done, c.st))) return rc;
     LSMS_LAUNCH(k_ir_update, dim3(nu), dim3(256), 0, c.st, du, ws, nrhs, kIrTol, done, stat);
   }
@@ -710,7 +812,7 @@ static size_t unit_ws_max_sum(const lsms_liz* liz, int lmax, int n_energy, int p
   for (int m = 0; m < liz->n_atoms; ++m) {
     const int n = K * (int)(liz->offsets[m + 1] - liz->offsets[m]);
     const size_t b = ws_unit_bytes(unit_bytes(n, precision, nrhs, backward), false);
-    mx = std::max(mx, b);
+    mx = std::max(mx, b * n_energy);
     s += b * n_energy;
   }
   *sum = s;

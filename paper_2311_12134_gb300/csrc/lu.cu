@@ -1,18 +1,20 @@
-// Batched blocked LU with partial pivoting, the block solves for the tau
-// column blocks, and the FP64 iterative refinement of the mixed form.
+// Batched blocked LU with partial pivoting and the block solves for the tau
+// column blocks.
 //
 // Eq. (tau-inverse) needs [T^{-1} - g]^{-1}; for each (atom, energy) unit the
 // LIZ matrix M (n = K S, column-major, ld = n) is factored P M = L U in place.
 // Pivoting: the row with the largest |Re| + |Im| in the column, the lowest row
 // on ties.  Right-looking, panel width NB:
 //   k_panel      factor the n-k x NB panel (pivot search by warp shuffles),
-//   k_swap_trsm  apply the panel's row swaps to the trailing columns and form
+//   k_swap_trsm  apply the panel's row swaps to every other column (left ones
+//                too, so L ends up in the final row order) and form
 //                U12 = L11^{-1} A12 (one warp per column),
-//   k_gemm       A22 -= L21 U12 (register-tiled complex GEMM).
+//   k_gemm       A22 -= L21 U12 (register-tiled complex GEMM),
+//   k_perm       the permutation P as perm[i] (original row at position i) and
+//                its inverse iperm.
 // Units of a chunk are sorted by n (largest first); each launch covers every
-// unit and units already finished return at once.  Row swaps are applied only
-// to the panel and the columns to its right; k_solve applies them block by
-// block during forward substitution, which is consistent with that storage.
+// unit and units already finished return at once.  k_solve then runs plain
+// forward/backward substitution on right-hand sides already permuted by P.
 #include "common.cuh"
 
 namespace lsms {
@@ -106,32 +108,49 @@ __global__ void __launch_bounds__(256) k_panel(const Unit* __restrict__ units, c
 }
 
 // ------------------------------------------------------------------ swap + trsm
-// One warp per trailing column; lane i holds rows k+i (+32 r).
+// One warp per column outside the panel; lane i holds rows k+i (+32 r).
+// Columns left of the panel only take the row swaps; columns to its right also
+// get U12 = L11^{-1} A12.
 template <typename R, int NB>
 __global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ units, char* fac_base, int k) {
   using C = Cx<R>;
   constexpr int RPL = NB / 32;
   const Unit u = units[blockIdx.y];
   const int n = u.n;
-  const int c0 = k + NB;
-  if (c0 >= n) return;  // then the panel was the last block; nothing trails it
+  if (k >= n) return;
+  const int nbp = min(NB, n - k);
   C* A = reinterpret_cast<C*>(fac_base + u.fac_off);
   const int32_t* piv = reinterpret_cast<const int32_t*>(fac_base + u.piv_off);
   __shared__ C sL[NB][NB + 1];
-  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
-    const int i = idx % NB, j = idx / NB;
-    sL[i][j] = A[(size_t)(k + j) * n + k + i];
-  }
   __shared__ int sp[NB];
-  for (int j = threadIdx.x; j < NB; j += blockDim.x) sp[j] = piv[k + j];
+  const bool any_right = k + NB < n;
+  if (any_right) {
+    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+      const int i = idx % NB, j = idx / NB;
+      sL[i][j] = A[(size_t)(k + j) * n + k + i];
+    }
+  }
+  for (int j = threadIdx.x; j < NB; j += blockDim.x) sp[j] = j < nbp ? piv[k + j] : k + j;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = c0 + blockIdx.x * (blockDim.x >> 5) + warp;
-  if (c >= n) return;
+  const int v = blockIdx.x * (blockDim.x >> 5) + warp;  // virtual column: [0, k) left, then right
+  int c;
+  bool right;
+  if (v < k) {
+    c = v;
+    right = false;
+  } else {
+    c = v - k + k + NB;
+    right = true;
+    if (c >= n) return;
+  }
   C* Ac = A + (size_t)c * n;
   C x[RPL];
 #pragma unroll
-  for (int r = 0; r < RPL; ++r) x[r] = Ac[k + lane + 32 * r];
+  for (int r = 0; r < RPL; ++r) {
+    const int i = lane + 32 * r;
+    x[r] = i < nbp ? Ac[k + i] : mk(R(0), R(0));
+  }
 #pragma unroll
   for (int j = 0; j < NB; ++j) {
     const int p = sp[j];
@@ -156,17 +175,41 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ unit
       __syncwarp();
     }
   }
+  if (right) {
 #pragma unroll
-  for (int j = 0; j < NB - 1; ++j) {
-    const C xj = shfl2(x[j / 32], j % 32);
+    for (int j = 0; j < NB - 1; ++j) {
+      const C xj = shfl2(x[j / 32], j % 32);
 #pragma unroll
-    for (int r = 0; r < RPL; ++r) {
-      const int i = lane + 32 * r;
-      if (i > j) x[r] = cfms(sL[i][j], xj, x[r]);
+      for (int r = 0; r < RPL; ++r) {
+        const int i = lane + 32 * r;
+        if (i > j) x[r] = cfms(sL[i][j], xj, x[r]);
+      }
     }
   }
 #pragma unroll
-  for (int r = 0; r < RPL; ++r) Ac[k + lane + 32 * r] = x[r];
+  for (int r = 0; r < RPL; ++r) {
+    const int i = lane + 32 * r;
+    if (i < nbp) Ac[k + i] = x[r];
+  }
+}
+
+// perm[i] = original row now at position i, iperm[perm[i]] = i.  One thread per unit.
+__global__ void k_perm(const Unit* __restrict__ units, int n_units, char* fac_base) {
+  const int ui = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ui >= n_units) return;
+  const Unit u = units[ui];
+  const int n = u.n;
+  int32_t* piv = reinterpret_cast<int32_t*>(fac_base + u.piv_off);
+  int32_t* perm = piv + n;
+  int32_t* iperm = piv + 2 * n;
+  for (int i = 0; i < n; ++i) perm[i] = i;
+  for (int i = 0; i < n; ++i) {
+    const int p = piv[i];
+    const int t = perm[i];
+    perm[i] = perm[p];
+    perm[p] = t;
+  }
+  for (int i = 0; i < n; ++i) iperm[perm[i]] = i;
 }
 
 // ------------------------------------------------------------------ trailing GEMM (SIMT)
@@ -233,108 +276,97 @@ __global__ void __launch_bounds__(256) k_gemm(const Unit* __restrict__ units, ch
 }
 
 // ------------------------------------------------------------------ solve
-// One CTA per unit: forward substitution with block-wise pivots, then backward
-// substitution, on the n x nrhs column-major block X (nrhs <= 32).
+// One CTA of 32 * nrhs threads per unit: L y = b (unit lower), then U x = y,
+// for the n x nrhs column-major block X whose rows are already permuted by P.
+// The NB x NB triangles are solved by one warp per column (lane = row, values
+// passed by shuffles); the rows below/above are updated by the whole CTA.
 template <typename R, int NB>
-__global__ void __launch_bounds__(256) k_solve(const Unit* __restrict__ units, const char* fac_base, char* ws,
-                                               int which, int nrhs, const int32_t* done) {
+__global__ void __launch_bounds__(1024) k_solve(const Unit* __restrict__ units, const char* fac_base, char* ws,
+                                                int which, int nrhs, const int32_t* done) {
   using C = Cx<R>;
+  static_assert(NB == 32, "one lane per row of the diagonal block");
   const Unit u = units[blockIdx.x];
   if (done && done[u.stat_off]) return;
   const int n = u.n;
   const C* A = reinterpret_cast<const C*>(fac_base + u.fac_off);
-  const int32_t* piv = reinterpret_cast<const int32_t*>(fac_base + u.piv_off);
   C* X = reinterpret_cast<C*>(ws + (which == RHS_X ? u.x_off : u.x32_off));
+  __shared__ C sT[NB][NB + 1];
   __shared__ C sX[NB][33];
-  const int tid = threadIdx.x;
-  // forward: L y = P b
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nthr = blockDim.x;
+  // forward
   for (int k = 0; k < n; k += NB) {
     const int nbp = min(NB, n - k);
-    if (tid < nrhs) {
-      C* xc = X + (size_t)tid * n;
+    for (int idx = tid; idx < NB * NB; idx += nthr) {
+      const int i = idx % NB, j = idx / NB;
+      sT[i][j] = (i < nbp && j < nbp) ? A[(size_t)(k + j) * n + k + i] : mk(R(0), R(0));
+    }
+    __syncthreads();
+    if (warp < nrhs) {
+      C x = lane < nbp ? X[(size_t)warp * n + k + lane] : mk(R(0), R(0));
+      for (int j = 0; j < nbp - 1; ++j) {
+        const C xj = shfl2(x, j);
+        if (lane > j) x = cfms(sT[lane][j], xj, x);
+      }
+      if (lane < nbp) {
+        X[(size_t)warp * n + k + lane] = x;
+        sX[lane][warp] = x;
+      }
+    }
+    __syncthreads();
+    const int ngrp = (nrhs + 7) / 8;
+    for (int idx = tid; idx < (n - k - nbp) * ngrp; idx += nthr) {
+      const int i = k + nbp + idx % (n - k - nbp), g = (idx / (n - k - nbp)) * 8;
+      C acc[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[c] = (g + c < nrhs) ? X[(size_t)(g + c) * n + i] : mk(R(0), R(0));
       for (int j = 0; j < nbp; ++j) {
-        const int p = piv[k + j];
-        if (p != k + j) {
-          const C t = xc[k + j];
-          xc[k + j] = xc[p];
-          xc[p] = t;
-        }
-      }
-    }
-    __syncthreads();
-    for (int idx = tid; idx < nbp * nrhs; idx += blockDim.x) {
-      const int j = idx % nbp, c = idx / nbp;
-      sX[j][c] = X[(size_t)c * n + k + j];
-    }
-    __syncthreads();
-    for (int j = 0; j < nbp - 1; ++j) {
-      const C* Lj = A + (size_t)(k + j) * n + k;
-      for (int idx = tid; idx < (nbp - 1 - j) * nrhs; idx += blockDim.x) {
-        const int i = j + 1 + idx % (nbp - 1 - j), c = idx / (nbp - 1 - j);
-        sX[i][c] = cfms(Lj[i], sX[j][c], sX[i][c]);
-      }
-      __syncthreads();
-    }
-    for (int idx = tid; idx < nbp * nrhs; idx += blockDim.x) {
-      const int j = idx % nbp, c = idx / nbp;
-      X[(size_t)c * n + k + j] = sX[j][c];
-    }
-    for (int g = 0; g < nrhs; g += 8) {
-      const int gc = min(8, nrhs - g);
-      for (int i = k + nbp + tid; i < n; i += blockDim.x) {
-        C acc[8];
+        const C l = A[(size_t)(k + j) * n + i];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = c < gc ? X[(size_t)(g + c) * n + i] : mk(R(0), R(0));
-        for (int j = 0; j < nbp; ++j) {
-          const C l = A[(size_t)(k + j) * n + i];
-#pragma unroll
-          for (int c = 0; c < 8; ++c) acc[c] = cfms(l, sX[j][g + (c < gc ? c : 0)], acc[c]);
-        }
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-          if (c < gc) X[(size_t)(g + c) * n + i] = acc[c];
+        for (int c = 0; c < 8; ++c) acc[c] = cfms(l, sX[j][(g + c < nrhs) ? g + c : 0], acc[c]);
       }
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        if (g + c < nrhs) X[(size_t)(g + c) * n + i] = acc[c];
     }
     __syncthreads();
   }
-  // backward: U x = y
+  // backward
   const int last = ((n - 1) / NB) * NB;
   for (int k = last; k >= 0; k -= NB) {
     const int nbp = min(NB, n - k);
-    for (int idx = tid; idx < nbp * nrhs; idx += blockDim.x) {
-      const int j = idx % nbp, c = idx / nbp;
-      sX[j][c] = X[(size_t)c * n + k + j];
+    for (int idx = tid; idx < NB * NB; idx += nthr) {
+      const int i = idx % NB, j = idx / NB;
+      sT[i][j] = (i < nbp && j < nbp) ? A[(size_t)(k + j) * n + k + i] : mk(R(1), R(0));
     }
     __syncthreads();
-    for (int j = nbp - 1; j >= 0; --j) {
-      const C* Uj = A + (size_t)(k + j) * n + k;
-      if (tid < nrhs) sX[j][tid] = cmul(sX[j][tid], crcp(Uj[j]));
-      __syncthreads();
-      for (int idx = tid; idx < j * nrhs; idx += blockDim.x) {
-        const int i = idx % j, c = idx / j;
-        sX[i][c] = cfms(Uj[i], sX[j][c], sX[i][c]);
+    if (warp < nrhs) {
+      C x = lane < nbp ? X[(size_t)warp * n + k + lane] : mk(R(0), R(0));
+      for (int j = nbp - 1; j >= 0; --j) {
+        if (lane == j) x = cmul(x, crcp(sT[j][j]));
+        const C xj = shfl2(x, j);
+        if (lane < j) x = cfms(sT[lane][j], xj, x);
       }
-      __syncthreads();
-    }
-    for (int idx = tid; idx < nbp * nrhs; idx += blockDim.x) {
-      const int j = idx % nbp, c = idx / nbp;
-      X[(size_t)c * n + k + j] = sX[j][c];
-    }
-    for (int g = 0; g < nrhs; g += 8) {
-      const int gc = min(8, nrhs - g);
-      for (int i = tid; i < k; i += blockDim.x) {
-        C acc[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = c < gc ? X[(size_t)(g + c) * n + i] : mk(R(0), R(0));
-        for (int j = 0; j < nbp; ++j) {
-          const C uu = A[(size_t)(k + j) * n + i];
-#pragma unroll
-          for (int c = 0; c < 8; ++c) acc[c] = cfms(uu, sX[j][g + (c < gc ? c : 0)], acc[c]);
-        }
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-          if (c < gc) X[(size_t)(g + c) * n + i] = acc[c];
+      if (lane < nbp) {
+        X[(size_t)warp * n + k + lane] = x;
+        sX[lane][warp] = x;
       }
+    }
+    __syncthreads();
+    const int ngrp = (nrhs + 7) / 8;
+    for (int idx = tid; idx < k * ngrp; idx += nthr) {
+      const int i = idx % k, g = (idx / k) * 8;
+      C acc[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[c] = (g + c < nrhs) ? X[(size_t)(g + c) * n + i] : mk(R(0), R(0));
+      for (int j = 0; j < nbp; ++j) {
+        const C uu = A[(size_t)(k + j) * n + i];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = cfms(uu, sX[j][(g + c < nrhs) ? g + c : 0], acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        if (g + c < nrhs) X[(size_t)(g + c) * n + i] = acc[c];
     }
     __syncthreads();
   }
@@ -347,12 +379,14 @@ int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
   constexpr int NB = LuCfg<R>::NB;
   for (int k = 0; k < n_max; k += NB) {
     LSMS_LAUNCH((k_panel<R, NB>), dim3(n_units), dim3(256), 0, st, d_units, fac_base, k, stat);
+    // one warp per column outside the panel: left ones [0, k), right ones [k + NB, n)
+    LSMS_LAUNCH((k_swap_trsm<R, NB>), dim3((n_max + 7) / 8, n_units), dim3(256), 0, st, d_units, fac_base, k);
     const int trail = n_max - k - NB;
-    if (trail <= 0) break;
-    LSMS_LAUNCH((k_swap_trsm<R, NB>), dim3((trail + 7) / 8, n_units), dim3(256), 0, st, d_units, fac_base, k);
+    if (trail <= 0) continue;
     const int tiles = (trail + 63) / 64;
     LSMS_LAUNCH((k_gemm<R, NB>), dim3(tiles * tiles, n_units), dim3(256), 0, st, d_units, fac_base, k, tiles);
   }
+  LSMS_LAUNCH(k_perm, dim3((n_units + 127) / 128), dim3(128), 0, st, d_units, n_units, fac_base);
   return LSMS_OK;
 }
 
@@ -361,7 +395,7 @@ int lu_solve_chunk(const Unit* d_units, int n_units, const char* fac_base, char*
                    const int32_t* done, cudaStream_t st) {
   if (nrhs < 1 || nrhs > 32) return fail(LSMS_ERR_ARG, "internal: nrhs %d out of range", nrhs);
   constexpr int NB = LuCfg<R>::NB;
-  LSMS_LAUNCH((k_solve<R, NB>), dim3(n_units), dim3(256), 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
+  LSMS_LAUNCH((k_solve<R, NB>), dim3(n_units), dim3(32 * nrhs), 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
   return LSMS_OK;
 }
 
