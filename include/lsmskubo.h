@@ -132,8 +132,9 @@ int lsms_gaunt_table(int lmax, double* C);
  * precision    LSMS_FP64 or LSMS_MIXED.
  * tau          dev [n_energy][S_total][K][K] output: tau[e][s] = tau^{s 0} of
  *              the LIZ that site s belongs to (row L, column L').
- * unit_status  dev [n_energy][n_atoms] int32 output (bit set of LSMS_UNIT_*),
- *              or NULL.
+ * unit_status  dev [n_energy][n_atoms] int32 output, or NULL: bits 0-7 the
+ *              LSMS_UNIT_* flags, bits 8-15 the number of refinement sweeps
+ *              (mixed form; 0 for FP64).
  * workspace    dev scratch of workspace_bytes (>= lsms_tau_workspace_bytes for
  *              one unit); the units are processed in chunks that fit it.  NULL
  *              = the library allocates (stream-ordered) and frees it.
@@ -207,6 +208,8 @@ int lsms_kubo_sigma_noalloc(const lsms_liz* liz, int lmax, const int32_t* specie
  * grad_tinv_species  dev [n_species][n_energy][K][K] output (the same gradient
  *              summed over the atoms of each species, i.e. with respect to the
  *              tinv argument of lsms_tau_blocks), or NULL.
+ * unit_status  dev [n_energy][n_atoms] int32 output of the adjoint solves (as
+ *              for lsms_tau_blocks), or NULL.
  * workspace    dev scratch of workspace_bytes (>= lsms_backward_workspace_bytes
  *              minimum), or NULL for a stream-ordered allocation.
  * n_energy must be even (energies in (+, -) pairs per delta). */
@@ -218,8 +221,8 @@ int lsms_kubo_sigma_backward(const lsms_liz* liz, int lmax, const int32_t* speci
                              int64_t J_delta_stride, const lsms_complex* tau, double volume,
                              const lsms_complex* grad_sigma, const void* lu_store,
                              size_t lu_store_bytes, lsms_complex* grad_tinv,
-                             lsms_complex* grad_tinv_species, void* workspace,
-                             size_t workspace_bytes, void* stream);
+                             lsms_complex* grad_tinv_species, int32_t* unit_status,
+                             void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------- misc */
 /* Message of the last error on the calling thread ("" if none). */

@@ -45,7 +45,7 @@ SIGNATURES = {
     "lsms_kubo_sigma": (_I, [_P, _I, _P, _I, _P, _I64, _P, _I, _D, _P, _P, _P, _P]),
     "lsms_kubo_sigma_noalloc": (_I, [_P, _I, _P, _I, _P, _I64, _P, _I, _D, _P, _P, _P, _P]),
     "lsms_kubo_sigma_backward": (_I, [_P, _I, _P, _I, _P, _P, _I, _I, _P, _I64, _P, _D, _P, _P, _SZ, _P, _P,
-                                      _P, _SZ, _P]),
+                                      _P, _P, _SZ, _P]),
     "lsms_last_error": (ctypes.c_char_p, []),
     "lsms_version": (_I, []),
     "lsms_launch_count": (ctypes.c_longlong, []),
@@ -273,7 +273,8 @@ def kubo_sigma_noalloc(liz, lmax, species, J, tau, n_delta, volume, J_delta_stri
 
 
 def kubo_sigma_backward(liz, lmax, species, tinv, z, J, tau, volume, grad_sigma, precision="fp64", lu_store=None,
-                        J_delta_stride=0, grad_tinv=None, grad_tinv_species=None, workspace=None, stream=None):
+                        J_delta_stride=0, grad_tinv=None, grad_tinv_species=None, unit_status=None, workspace=None,
+                        stream=None):
     """lsms_kubo_sigma_backward.  Returns (grad_tinv [n_energy, N, K, K], grad_tinv_species [n_species, n_energy, K, K])."""
     import torch
     K = (lmax + 1) ** 2
@@ -295,8 +296,8 @@ def kubo_sigma_backward(liz, lmax, species, tinv, z, J, tau, volume, grad_sigma,
         _dev(tau, torch.complex128, (nE, liz.total_sites, K, K), "tau"), float(volume),
         _dev(grad_sigma, torch.complex128, (nE // 2, 3, 3), "grad_sigma"), st_p, st_n,
         _dev(grad_tinv, torch.complex128, (nE, liz.n_atoms, K, K), "grad_tinv"),
-        _dev(grad_tinv_species, torch.complex128, (n_species, nE, K, K), "grad_tinv_species"), ws_p, ws_n,
-        _stream(stream)))
+        _dev(grad_tinv_species, torch.complex128, (n_species, nE, K, K), "grad_tinv_species"),
+        _opt(unit_status, torch.int32, (nE, liz.n_atoms), "unit_status"), ws_p, ws_n, _stream(stream)))
     return grad_tinv, grad_tinv_species
 
 

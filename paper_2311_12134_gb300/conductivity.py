@@ -50,6 +50,7 @@ class Problem:
         self.sigma_out = torch.empty((self.n_delta, 3, 3), dtype=torch.complex128, device=self.device)
         self.sigma_tilde = torch.empty((self.n_delta, 4, 3, 3), dtype=torch.complex128, device=self.device)
         self.rho = torch.empty((self.n_delta, 3, 3), dtype=torch.float64, device=self.device)
+        self.bw_status = torch.empty((nE, self.liz.n_atoms), dtype=torch.int32, device=self.device)
         self._bw_ws = None
 
     @property
@@ -81,7 +82,7 @@ class Problem:
         t = self.tinv if tinv is None else tinv
         return B.kubo_sigma_backward(self.liz, self.lmax, self.species, t, self.z, self.J, self.tau, self.volume,
                                      grad_sigma.contiguous(), self.precision, lu_store=self.lu_store,
-                                     workspace=self._bw_ws, stream=stream)
+                                     unit_status=self.bw_status, workspace=self._bw_ws, stream=stream)
 
 
 def _sigma_fn():

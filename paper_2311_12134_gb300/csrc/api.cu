@@ -966,8 +966,8 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
                                         const lsms_complex* J, int64_t J_delta_stride, const lsms_complex* tau,
                                         double volume, const lsms_complex* grad_sigma, const void* lu_store,
                                         size_t lu_store_bytes, lsms_complex* grad_tinv,
-                                        lsms_complex* grad_tinv_species, void* workspace,
-                                        size_t workspace_bytes, void* stream) {
+                                        lsms_complex* grad_tinv_species, int32_t* unit_status,
+                                        void* workspace, size_t workspace_bytes, void* stream) {
   clear_error();
   lsms_liz* liz = const_cast<lsms_liz*>(liz_c);
   int rc = check_common(liz, lmax, species, n_species, n_energy, precision);
@@ -1040,6 +1040,9 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
     if ((r2 = adj_reduce(c.dd->inv_off, c.dd->inv_sites, G, liz->total_sites, c.K, liz->n_atoms, n_energy,
                          reinterpret_cast<double2*>(grad_tinv), c.st)))
       return r2;
+    if (unit_status)
+      LSMS_LAUNCH(k_status_out, dim3((unsigned)((nu_all + 255) / 256)), dim3(256), 0, c.st, stat, (int)nu_all,
+                  unit_status);
     if (grad_tinv_species)
       return adj_species(species, reinterpret_cast<const double2*>(grad_tinv), c.K, liz->n_atoms, n_species, n_energy,
                          reinterpret_cast<double2*>(grad_tinv_species), c.st);

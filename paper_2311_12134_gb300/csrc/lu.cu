@@ -151,28 +151,62 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ unit
     const int i = lane + 32 * r;
     x[r] = i < nbp ? Ac[k + i] : mk(R(0), R(0));
   }
+  // Rows below the panel that the swaps touch: when all of them are distinct
+  // (the usual case) each is read once up front and written once at the end;
+  // the swap sequence then runs in registers.  Repeated targets take the
+  // sequential path through memory.
+  bool fast = false;
+  C y = mk(R(0), R(0));
+  int pj = k + lane;
+  if (RPL == 1) {
+    pj = sp[lane];
+    const bool outj = pj >= k + NB;
+    const unsigned same = __match_any_sync(0xffffffffu, outj ? pj : -1 - lane);
+    fast = !__any_sync(0xffffffffu, outj && __popc(same) > 1);
+    if (fast && outj) y = Ac[pj];
+  }
+  if (fast) {
 #pragma unroll
-  for (int j = 0; j < NB; ++j) {
-    const int p = sp[j];
-    if (p == k + j) continue;
-    if (p < k + NB) {
-      const int b = p - k;
-      const C va = shfl2(x[j / 32], j % 32);
-      C vb = x[0];
-#pragma unroll
-      for (int r = 0; r < RPL; ++r)
-        if (b / 32 == r) vb = shfl2(x[r], b % 32);
-      if (lane == j % 32) x[j / 32] = vb;
-#pragma unroll
-      for (int r = 0; r < RPL; ++r)
-        if (b / 32 == r && lane == b % 32) x[r] = va;
-    } else {
-      if (lane == j % 32) {
-        const C t = Ac[p];
-        Ac[p] = x[j / 32];
-        x[j / 32] = t;
+    for (int j = 0; j < NB; ++j) {
+      const int p = sp[j];
+      if (p == k + j) continue;
+      if (p < k + NB) {
+        const int b = p - k;
+        const C va = shfl2(x[0], j);
+        const C vb = shfl2(x[0], b);
+        if (lane == j) x[0] = vb;
+        if (lane == b) x[0] = va;
+      } else if (lane == j) {
+        const C t = y;
+        y = x[0];
+        x[0] = t;
       }
-      __syncwarp();
+    }
+    if (pj >= k + NB) Ac[pj] = y;
+  } else {
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int p = sp[j];
+      if (p == k + j) continue;
+      if (p < k + NB) {
+        const int b = p - k;
+        const C va = shfl2(x[j / 32], j % 32);
+        C vb = x[0];
+#pragma unroll
+        for (int r = 0; r < RPL; ++r)
+          if (b / 32 == r) vb = shfl2(x[r], b % 32);
+        if (lane == j % 32) x[j / 32] = vb;
+#pragma unroll
+        for (int r = 0; r < RPL; ++r)
+          if (b / 32 == r && lane == b % 32) x[r] = va;
+      } else {
+        if (lane == j % 32) {
+          const C t = Ac[p];
+          Ac[p] = x[j / 32];
+          x[j / 32] = t;
+        }
+        __syncwarp();
+      }
     }
   }
   if (right) {
@@ -276,12 +310,41 @@ __global__ void __launch_bounds__(256) k_gemm(const Unit* __restrict__ units, ch
 }
 
 // ------------------------------------------------------------------ solve
-// One CTA of 32 * nrhs threads per unit: L y = b (unit lower), then U x = y,
+// X[i][c] -= sum_j A[i][k + j] sX[j][c] for rows i in [r0, r1): one thread per
+// (row, group of 8 right-hand sides); the NB column entries of A are loaded 8 at
+// a time before use so that the loads overlap.
+template <typename R, int NB>
+__device__ __forceinline__ void update_rows(const Cx<R>* __restrict__ A, Cx<R>* X, const Cx<R> (*sX)[33], int n, int k,
+                                            int nbp, int r0, int r1, int nrhs, int tid, int nthr) {
+  using C = Cx<R>;
+  const int rows = r1 - r0;
+  if (rows <= 0) return;
+  const int ngrp = (nrhs + 7) / 8;
+  for (int idx = tid; idx < rows * ngrp; idx += nthr) {
+    const int i = r0 + idx % rows, g = (idx / rows) * 8;
+    C acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = (g + c < nrhs) ? X[(size_t)(g + c) * n + i] : mk(R(0), R(0));
+    for (int j0 = 0; j0 < nbp; j0 += 8) {
+      C l[8];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) l[jj] = (j0 + jj < nbp) ? A[(size_t)(k + j0 + jj) * n + i] : mk(R(0), R(0));
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = cfms(l[jj], sX[j0 + jj][(g + c < nrhs) ? g + c : 0], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      if (g + c < nrhs) X[(size_t)(g + c) * n + i] = acc[c];
+  }
+}
+// One CTA of 512 threads per unit: L y = b (unit lower), then U x = y,
 // for the n x nrhs column-major block X whose rows are already permuted by P.
-// The NB x NB triangles are solved by one warp per column (lane = row, values
+// The NB x NB triangles are solved by warps taking columns in turn (lane = row, values
 // passed by shuffles); the rows below/above are updated by the whole CTA.
 template <typename R, int NB>
-__global__ void __launch_bounds__(1024) k_solve(const Unit* __restrict__ units, const char* fac_base, char* ws,
+__global__ void __launch_bounds__(512) k_solve(const Unit* __restrict__ units, const char* fac_base, char* ws,
                                                 int which, int nrhs, const int32_t* done) {
   using C = Cx<R>;
   static_assert(NB == 32, "one lane per row of the diagonal block");
@@ -302,33 +365,19 @@ __global__ void __launch_bounds__(1024) k_solve(const Unit* __restrict__ units, 
       sT[i][j] = (i < nbp && j < nbp) ? A[(size_t)(k + j) * n + k + i] : mk(R(0), R(0));
     }
     __syncthreads();
-    if (warp < nrhs) {
-      C x = lane < nbp ? X[(size_t)warp * n + k + lane] : mk(R(0), R(0));
+    for (int col = warp; col < nrhs; col += nthr >> 5) {
+      C x = lane < nbp ? X[(size_t)col * n + k + lane] : mk(R(0), R(0));
       for (int j = 0; j < nbp - 1; ++j) {
         const C xj = shfl2(x, j);
         if (lane > j) x = cfms(sT[lane][j], xj, x);
       }
       if (lane < nbp) {
-        X[(size_t)warp * n + k + lane] = x;
-        sX[lane][warp] = x;
+        X[(size_t)col * n + k + lane] = x;
+        sX[lane][col] = x;
       }
     }
     __syncthreads();
-    const int ngrp = (nrhs + 7) / 8;
-    for (int idx = tid; idx < (n - k - nbp) * ngrp; idx += nthr) {
-      const int i = k + nbp + idx % (n - k - nbp), g = (idx / (n - k - nbp)) * 8;
-      C acc[8];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) acc[c] = (g + c < nrhs) ? X[(size_t)(g + c) * n + i] : mk(R(0), R(0));
-      for (int j = 0; j < nbp; ++j) {
-        const C l = A[(size_t)(k + j) * n + i];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = cfms(l, sX[j][(g + c < nrhs) ? g + c : 0], acc[c]);
-      }
-#pragma unroll
-      for (int c = 0; c < 8; ++c)
-        if (g + c < nrhs) X[(size_t)(g + c) * n + i] = acc[c];
-    }
+    update_rows<R, NB>(A, X, sX, n, k, nbp, k + nbp, n, nrhs, tid, nthr);
     __syncthreads();
   }
   // backward
@@ -340,34 +389,20 @@ __global__ void __launch_bounds__(1024) k_solve(const Unit* __restrict__ units, 
       sT[i][j] = (i < nbp && j < nbp) ? A[(size_t)(k + j) * n + k + i] : mk(R(1), R(0));
     }
     __syncthreads();
-    if (warp < nrhs) {
-      C x = lane < nbp ? X[(size_t)warp * n + k + lane] : mk(R(0), R(0));
+    for (int col = warp; col < nrhs; col += nthr >> 5) {
+      C x = lane < nbp ? X[(size_t)col * n + k + lane] : mk(R(0), R(0));
       for (int j = nbp - 1; j >= 0; --j) {
         if (lane == j) x = cmul(x, crcp(sT[j][j]));
         const C xj = shfl2(x, j);
         if (lane < j) x = cfms(sT[lane][j], xj, x);
       }
       if (lane < nbp) {
-        X[(size_t)warp * n + k + lane] = x;
-        sX[lane][warp] = x;
+        X[(size_t)col * n + k + lane] = x;
+        sX[lane][col] = x;
       }
     }
     __syncthreads();
-    const int ngrp = (nrhs + 7) / 8;
-    for (int idx = tid; idx < k * ngrp; idx += nthr) {
-      const int i = idx % k, g = (idx / k) * 8;
-      C acc[8];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) acc[c] = (g + c < nrhs) ? X[(size_t)(g + c) * n + i] : mk(R(0), R(0));
-      for (int j = 0; j < nbp; ++j) {
-        const C uu = A[(size_t)(k + j) * n + i];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = cfms(uu, sX[j][(g + c < nrhs) ? g + c : 0], acc[c]);
-      }
-#pragma unroll
-      for (int c = 0; c < 8; ++c)
-        if (g + c < nrhs) X[(size_t)(g + c) * n + i] = acc[c];
-    }
+    update_rows<R, NB>(A, X, sX, n, k, nbp, 0, k, nrhs, tid, nthr);
     __syncthreads();
   }
 }
@@ -395,7 +430,7 @@ int lu_solve_chunk(const Unit* d_units, int n_units, const char* fac_base, char*
                    const int32_t* done, cudaStream_t st) {
   if (nrhs < 1 || nrhs > 32) return fail(LSMS_ERR_ARG, "internal: nrhs %d out of range", nrhs);
   constexpr int NB = LuCfg<R>::NB;
-  LSMS_LAUNCH((k_solve<R, NB>), dim3(n_units), dim3(32 * nrhs), 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
+  LSMS_LAUNCH((k_solve<R, NB>), dim3(n_units), dim3(512), 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
   return LSMS_OK;
 }
 
