@@ -80,6 +80,7 @@ enum lsms_precision {
 #define LSMS_UNIT_NOCONV 2
 #define LSMS_UNIT_NONFINITE 4
 #define LSMS_UNIT_BAD_INPUT 8   /* a species index outside 0..n_species-1 */
+#define LSMS_UNIT_TIMEOUT 128   /* a bounded device wait gave up (results invalid) */
 
 /* ---------------------------------------------------------------- LIZ
  * Sec. II.A, Fig. 1: the LIZ of atom m holds every site within r_liz of it.

@@ -116,6 +116,10 @@ int lu_solve_chunk(const Unit* d_units, int n_units, const char* fac_base, char*
 
 enum RhsField { RHS_X = 0, RHS_X32 = 1 };
 
+// Trailing update A22 -= L21 U12 of the complex64 LU on the tensor cores (tc_gemm.cu).
+int gemm_tc_chunk(const Unit* d_units, int n_units, int n_max, int k, char* fac_base, int32_t* stat,
+                  cudaStream_t st);
+
 int existing_device_data(lsms_liz* liz, DeviceData** out);
 
 }  // namespace lsms

@@ -9,12 +9,16 @@
 //   k_swap_trsm  apply the panel's row swaps to every other column (left ones
 //                too, so L ends up in the final row order) and form
 //                U12 = L11^{-1} A12 (one warp per column),
-//   k_gemm       A22 -= L21 U12 (register-tiled complex GEMM),
+//   k_gemm       A22 -= L21 U12: register-tiled complex GEMM on the FP64 pipe
+//                (FP64 form); the complex64 form uses k_gemm_tc (tc_gemm.cu),
+//                the same update on the tensor cores,
 //   k_perm       the permutation P as perm[i] (original row at position i) and
 //                its inverse iperm.
 // Units of a chunk are sorted by n (largest first); each launch covers every
 // unit and units already finished return at once.  k_solve then runs plain
 // forward/backward substitution on right-hand sides already permuted by P.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace lsms {
@@ -418,8 +422,14 @@ int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
     LSMS_LAUNCH((k_swap_trsm<R, NB>), dim3((n_max + 7) / 8, n_units), dim3(256), 0, st, d_units, fac_base, k);
     const int trail = n_max - k - NB;
     if (trail <= 0) continue;
-    const int tiles = (trail + 63) / 64;
-    LSMS_LAUNCH((k_gemm<R, NB>), dim3(tiles * tiles, n_units), dim3(256), 0, st, d_units, fac_base, k, tiles);
+    if constexpr (std::is_same<R, float>::value) {
+      // complex64: the trailing update runs on the tensor cores (3xTF32, tc_gemm.cu)
+      const int rc = gemm_tc_chunk(d_units, n_units, n_max, k, fac_base, stat, st);
+      if (rc) return rc;
+    } else {
+      const int tiles = (trail + 63) / 64;
+      LSMS_LAUNCH((k_gemm<R, NB>), dim3(tiles * tiles, n_units), dim3(256), 0, st, d_units, fac_base, k, tiles);
+    }
   }
   LSMS_LAUNCH(k_perm, dim3((n_units + 127) / 128), dim3(128), 0, st, d_units, n_units, fac_base);
   return LSMS_OK;

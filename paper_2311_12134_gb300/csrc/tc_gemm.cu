@@ -1,0 +1,289 @@
+// Trailing update of the complex64 LU on the 5th-generation tensor cores
+// (tcgen05, sm_103a): A22 -= L21 U12 for every unit of a chunk.
+//
+// The complex product is written as one real GEMM (real embedding):
+//   [C_re | C_im] -= [L_re  L_im] x [ U_re  U_im ]
+//                                   [-U_im  U_re ]
+// i.e. A^ = [L_re, L_im] (128 rows x 2 NB), B^ = the 2 NB x 2 N block above.
+// Each fp32 operand is split into TF32 hi + lo parts and the product is formed
+// as hi*hi + hi*lo + lo*hi ("3xTF32"), accumulated in FP32 in tensor memory,
+// which keeps complex64 accuracy for the refinement that follows.
+//
+// One CTA (4 warps) per 128 x 32 complex output tile:
+//   all threads  load L21 (128 x 32) and U12 (32 x 32), split hi/lo, and store
+//                them K-major into shared memory with the 128-byte swizzle,
+//   one thread   issues 24 tcgen05.mma (M = 128, N = 64, K = 8, kind::tf32)
+//                into a 64-column TMEM accumulator and commits to an mbarrier,
+//   all threads  wait (bounded), read the accumulator with tcgen05.ld
+//                (warp w owns TMEM lanes 32w..32w+31) and update C in place.
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace lsms {
+
+namespace tc {
+
+constexpr int NB = 32;            // complex panel width (K of the complex product)
+constexpr int TM = 128;           // tile rows (TMEM lanes)
+constexpr int TNC = 32;           // complex columns per tile
+constexpr int TN = 2 * TNC;       // real accumulator columns: [re | im]
+constexpr int CHUNK_A = TM * 128;           // one 128-byte-wide K chunk of A (bytes)
+constexpr int CHUNK_B = TN * 128;           // one K chunk of B
+constexpr int OP_A = 2 * CHUNK_A;           // real K = 2 NB = 64 tf32 = two chunks
+constexpr int OP_B = 2 * CHUNK_B;
+constexpr int SMEM_BYTES = 2 * OP_A + 2 * OP_B + 64;  // hi/lo of A and B + barrier + TMEM slot
+constexpr uint32_t TMEM_COLS = 64;
+constexpr long long kWaitLimit = 1ll << 24;  // bounded mbarrier wait (polls)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Byte offset of element (row, k) of a K-major operand with 128-byte swizzle:
+// rows are 128 B apart inside a 16 KB K chunk (32 fp32 of K); the 16-byte unit
+// index inside a row is XOR-ed with the row index modulo 8.
+__device__ __forceinline__ uint32_t swz(int row, int k, int chunk_bytes) {
+  const int kc = k >> 5, kb = (k & 31) * 4;
+  return (uint32_t)(kc * chunk_bytes + row * 128 + ((((kb >> 4) ^ (row & 7))) << 4) + (kb & 15));
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 B apart (stride byte offset), version bits 46-47 = 1.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);        // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: D f32, A/B tf32, both K-major, N and M.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4)                 // D format f32
+         | (2u << 7)               // A format tf32
+         | (2u << 10)              // B format tf32
+         | ((uint32_t)(N >> 3) << 17)
+         | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+      :
+      : "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(mbar), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+}  // namespace tc
+
+// grid (tiles_m_max * tiles_n_max, n_units), block 128, dynamic smem tc::SMEM_BYTES.
+__global__ void __launch_bounds__(128) k_gemm_tc(const Unit* __restrict__ units, char* fac_base, int k,
+                                                 int tiles_n_max, int32_t* stat) {
+  using namespace tc;
+  const Unit u = units[blockIdx.y];
+  const int n = u.n;
+  const int t0 = k + NB;
+  const int mt = n - t0;
+  if (mt <= 0) return;
+  const int ti = blockIdx.x / tiles_n_max, tj = blockIdx.x % tiles_n_max;
+  if (ti * TM >= mt || tj * TNC >= mt) return;
+  const int row0 = t0 + ti * TM, col0 = t0 + tj * TNC;
+  float2* A = reinterpret_cast<float2*>(fac_base + u.fac_off);
+
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sAh = smem;
+  uint8_t* sAl = smem + OP_A;
+  uint8_t* sBh = smem + 2 * OP_A;
+  uint8_t* sBl = smem + 2 * OP_A + OP_B;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * OP_A + 2 * OP_B);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 2 * OP_A + 2 * OP_B + 16);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // TMEM accumulator (warp 0 allocates; the address lands in shared memory)
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+
+  // A^ row r: [L_re(r, 0..31) | L_im(r, 0..31)], hi and lo parts.  All global
+  // loads of a thread are issued before any shared-memory store so they overlap.
+  {
+    const int r = tid;
+    const int row = row0 + r;
+    const bool ok = row < n;
+    float2 v[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) v[j] = ok ? __ldg(&A[(size_t)(k + j) * n + row]) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < NB / 4; ++q) {
+      float4 h, l;
+      h.x = tf32_hi(v[4 * q].x); h.y = tf32_hi(v[4 * q + 1].x); h.z = tf32_hi(v[4 * q + 2].x); h.w = tf32_hi(v[4 * q + 3].x);
+      l.x = v[4 * q].x - h.x; l.y = v[4 * q + 1].x - h.y; l.z = v[4 * q + 2].x - h.z; l.w = v[4 * q + 3].x - h.w;
+      *reinterpret_cast<float4*>(sAh + swz(r, 4 * q, CHUNK_A)) = h;
+      *reinterpret_cast<float4*>(sAl + swz(r, 4 * q, CHUNK_A)) = l;
+      h.x = tf32_hi(v[4 * q].y); h.y = tf32_hi(v[4 * q + 1].y); h.z = tf32_hi(v[4 * q + 2].y); h.w = tf32_hi(v[4 * q + 3].y);
+      l.x = v[4 * q].y - h.x; l.y = v[4 * q + 1].y - h.y; l.z = v[4 * q + 2].y - h.z; l.w = v[4 * q + 3].y - h.w;
+      *reinterpret_cast<float4*>(sAh + swz(r, NB + 4 * q, CHUNK_A)) = h;
+      *reinterpret_cast<float4*>(sAl + swz(r, NB + 4 * q, CHUNK_A)) = l;
+    }
+  }
+  // B^ row nn (output column): nn < 32: [U_re(., c) | -U_im(., c)]; nn >= 32: [U_im(., c) | U_re(., c)].
+  // Threads 0..63 build one row each; the column's 32 entries are 256 contiguous bytes.
+  if (tid < TN) {
+    const int nn = tid;
+    const int c = nn & (TNC - 1), part = nn >> 5;
+    const int col = col0 + c;
+    const bool ok = col < n;
+    float2 w[NB];  // 8-byte loads: n may be odd when lmax = 0, so 16-byte alignment is not given
+    const float2* src = A + (size_t)col * n + k;
+#pragma unroll
+    for (int q = 0; q < NB; ++q) w[q] = ok ? __ldg(src + q) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < NB / 4; ++q) {
+      const float re[4] = {w[4 * q].x, w[4 * q + 1].x, w[4 * q + 2].x, w[4 * q + 3].x};
+      const float im[4] = {w[4 * q].y, w[4 * q + 1].y, w[4 * q + 2].y, w[4 * q + 3].y};
+      float first[4], second[4];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        first[jj] = part == 0 ? re[jj] : im[jj];
+        second[jj] = part == 0 ? -im[jj] : re[jj];
+      }
+      float4 h, l;
+      h.x = tf32_hi(first[0]); h.y = tf32_hi(first[1]); h.z = tf32_hi(first[2]); h.w = tf32_hi(first[3]);
+      l.x = first[0] - h.x; l.y = first[1] - h.y; l.z = first[2] - h.z; l.w = first[3] - h.w;
+      *reinterpret_cast<float4*>(sBh + swz(nn, 4 * q, CHUNK_B)) = h;
+      *reinterpret_cast<float4*>(sBl + swz(nn, 4 * q, CHUNK_B)) = l;
+      h.x = tf32_hi(second[0]); h.y = tf32_hi(second[1]); h.z = tf32_hi(second[2]); h.w = tf32_hi(second[3]);
+      l.x = second[0] - h.x; l.y = second[1] - h.y; l.z = second[2] - h.z; l.w = second[3] - h.w;
+      *reinterpret_cast<float4*>(sBh + swz(nn, NB + 4 * q, CHUNK_B)) = h;
+      *reinterpret_cast<float4*>(sBl + swz(nn, NB + 4 * q, CHUNK_B)) = l;
+    }
+  }
+  // make the generic-proxy stores visible to the tensor core (async proxy)
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+
+  if (tid == 0) {
+    const uint32_t idesc = make_idesc(TM, TN);
+    const uint32_t a_hi = smem_u32(sAh), a_lo = smem_u32(sAl), b_hi = smem_u32(sBh), b_lo = smem_u32(sBl);
+    uint32_t acc = 0;
+    // hi*hi, hi*lo, lo*hi
+    for (int s = 0; s < 3; ++s) {
+      const uint32_t ab = (s == 2) ? a_lo : a_hi;
+      const uint32_t bb = (s == 1) ? b_lo : b_hi;
+#pragma unroll
+      for (int kc = 0; kc < 2; ++kc)
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4) {
+          const uint64_t da = make_desc(ab + kc * CHUNK_A + k4 * 32);
+          const uint64_t db = make_desc(bb + kc * CHUNK_B + k4 * 32);
+          mma_tf32(tmem, da, db, idesc, acc);
+          acc = 1;
+        }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+                 : "memory");
+  }
+  // C tile of this thread's row, fetched while the tensor core works
+  const int crow = row0 + warp * 32 + lane;
+  float2 cv[TNC];
+#pragma unroll
+  for (int c = 0; c < TNC; ++c)
+    cv[c] = (crow < n && col0 + c < n) ? A[(size_t)(col0 + c) * n + crow] : make_float2(0.f, 0.f);
+  // bounded wait for the accumulator; the outcome is made CTA-uniform because
+  // tcgen05.ld below is a warp-collective instruction
+  bool ready = false;
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    if (tc::mbar_try_wait(smem_u32(mbar), 0)) {
+      ready = true;
+      break;
+    }
+  }
+  ready = __syncthreads_and(ready);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ready) {
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    float dre[32], dim[32];
+    tc::tmem_ld32(lane_base + 0, dre);     // columns 0..31: real parts
+    tc::tmem_ld32(lane_base + 32, dim);    // columns 32..63: imaginary parts
+    if (crow < n) {
+#pragma unroll
+      for (int c = 0; c < TNC; ++c)
+        if (col0 + c < n) A[(size_t)(col0 + c) * n + crow] = make_float2(cv[c].x - dre[c], cv[c].y - dim[c]);
+    }
+  } else if (tid == 0) {
+    atomicOr(&stat[u.stat_off], LSMS_UNIT_TIMEOUT);
+    // give the tensor core a second bounded window before the accumulator is freed
+    for (long long it = 0; it < kWaitLimit; ++it)
+      if (tc::mbar_try_wait(smem_u32(mbar), 0)) break;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+int gemm_tc_chunk(const Unit* d_units, int n_units, int n_max, int k, char* fac_base, int32_t* stat,
+                  cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    LSMS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+    attr_set = true;
+  }
+  const int mt = n_max - k - tc::NB;
+  if (mt <= 0) return LSMS_OK;
+  const int tm = (mt + tc::TM - 1) / tc::TM, tn = (mt + tc::TNC - 1) / tc::TNC;
+  LSMS_LAUNCH(k_gemm_tc, dim3(tm * tn, n_units), dim3(128), tc::SMEM_BYTES, st, d_units, fac_base, k, tn, stat);
+  return LSMS_OK;
+}
+
+}  // namespace lsms

@@ -315,3 +315,20 @@ def test_full_size_fcc256_sampled(precision):
         s = slice(L["offsets"][m], L["offsets"][m + 1])
         for e in range(2):
             assert rel_err_blocks(t[e, s][None], col[e, s][None]) < TOL[precision]
+
+
+@pytest.mark.parametrize("lmax", [0, 1])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tau_odd_sizes_several_panels(lmax, precision):
+    """45-atom cluster covered by every LIZ: n = 45 (odd, lmax = 0) or 180, so the
+    factorization runs several panels with a ragged last one and odd strides."""
+    w = wl.cluster(n_atoms=45, lmax=lmax, r_liz=200.0, seed=9, spread=13.0)
+    lz, tau, st, _ = gpu_tau(w, precision)
+    assert int((st & 0xff).abs().sum()) == 0
+    atoms = [0, 17, 44]
+    L, col, _ = oracle_tau(w, atoms=atoms)
+    t = tau.cpu().numpy()
+    for m in atoms:
+        s = slice(L["offsets"][m], L["offsets"][m + 1])
+        for e in range(2):
+            assert rel_err_blocks(t[e, s][None], col[e, s][None]) < TOL[precision]
