@@ -67,7 +67,7 @@ int adj_abar(const int32_t* species, int n_species, const double2* J, int64_t J_
              double volume, int n_atoms, int n_delta, double2* abar, cudaStream_t st);
 int adj_rhs(const Unit* d_units, int n_units, int S_max, const int32_t* site_atom, const int32_t* species,
             int n_species, const double2* J, int64_t J_dstride, const double2* tau, int64_t S_total,
-            const double2* abar, int n_delta, int K, char* ws, cudaStream_t st);
+            const double2* abar, int n_delta, int K, char* ws, bool df, cudaStream_t st);
 int adj_site(const Unit* d_units, int n_units, int S_max, const double2* tau, int64_t S_total, int K, const char* ws,
              double2* G, cudaStream_t st);
 int adj_reduce(const int64_t* inv_off, const int64_t* inv_sites, const double2* G, int64_t S_total, int K,
@@ -289,43 +289,9 @@ static int get_plan(lsms_liz* liz, DeviceData* dd, int lmax, int n_energy, int p
 constexpr int kAsmQ = 16;  // column sites per set-up round
 constexpr int kAsmE = 2;   // energies per set-up round
 
-// V[L''] = mpref * h_{l''}(kappa |R|) * Y_{L''}(R^) for one separation R and
-// energy z, where mpref * sum_L'' i^{l-l'-l''} C_{LL'L''} V[L''] is the block -g:
-// kappa = principal sqrt(z); Im z >= 0: h = h^(1), mpref = +4 pi i kappa;
-// Im z < 0: h = h^(2), mpref = -4 pi i kappa (the decaying, advanced branch).
-// Y_L: real harmonics without the Condon-Shortley phase from the upward
-// associated-Legendre recurrence for P_l^m / sin^m and (x + i y)^m.
-__device__ void pair_setup(double rx, double ry, double rz, double2 z, double2* V) {
-  const double r = hypot(z.x, z.y);
-  const double kre = sqrt(0.5 * (r + z.x));
-  double kim = sqrt(0.5 * fmax(r - z.x, 0.0));
-  const bool adv = z.y < 0.0;
-  if (adv) kim = -kim;
-  const double four_pi = 4.0 * M_PI;
-  const double2 mpref = adv ? mk(four_pi * kim, -four_pi * kre) : mk(-four_pi * kim, four_pi * kre);
-  const double d = sqrt(rx * rx + ry * ry + rz * rz);
-  const double id = 1.0 / d;
-  const double x = rx * id, y = ry * id, zc = rz * id;
-  // spherical Hankel functions by upward recurrence h_{l+1} = (2l+1)/x h_l - h_{l-1}
-  double2 hp[kMaxL3 + 1];
-  {
-    const double2 xx = mk(kre * d, kim * d);
-    const double2 ix = crcp(xx);
-    double sn, cs;
-    sincos(xx.x, &sn, &cs);
-    const double f = exp(adv ? xx.y : -xx.y);
-    const double2 ex = adv ? mk(f * cs, -f * sn) : mk(f * cs, f * sn);  // e^{-+ix}
-    double2 hm = cmul(ex, ix);                                             // h_{-1}
-    double2 h = adv ? mk(-hm.y, hm.x) : mk(hm.y, -hm.x);                  // h_0
-    hp[0] = cmul(mpref, h);
-#pragma unroll
-    for (int l = 0; l < kMaxL3; ++l) {
-      const double2 hn = csub(cmul(mk((2.0 * l + 1.0) * ix.x, (2.0 * l + 1.0) * ix.y), h), hm);
-      hm = h;
-      h = hn;
-      hp[l + 1] = cmul(mpref, h);
-    }
-  }
+// Y_L(R^), l <= 6: real harmonics without the Condon-Shortley phase from the
+// upward associated-Legendre recurrence for P_l^m / sin^m and (x + i y)^m.
+__device__ void ylm6(double x, double y, double z, double* Y) {
   double tr = 1.0, ti = 0.0;  // (x + i y)^m
   double qmm = 1.0;           // (2m - 1)!!
 #pragma unroll
@@ -341,34 +307,63 @@ __device__ void pair_setup(double rx, double ry, double rz, double2 z, double2* 
     for (int l = m; l <= kMaxL3; ++l) {
       double q;
       if (l == m) q = qmm;
-      else if (l == m + 1) q = (2 * m + 1) * zc * qmm;
-      else q = ((2 * l - 1) * zc * q1 - (l + m - 1) * q2) * (1.0 / (l - m));
+      else if (l == m + 1) q = (2 * m + 1) * z * qmm;
+      else q = ((2 * l - 1) * z * q1 - (l + m - 1) * q2) * (1.0 / (l - m));
       q2 = q1;
       q1 = q;
       const int L0 = l * l + l;
       if (m == 0) {
-        const double yv = c_ylm_norm[L0] * q;
-        V[L0] = mk(hp[l].x * yv, hp[l].y * yv);
+        Y[L0] = c_ylm_norm[L0] * q;
       } else {
-        const double yc = c_ylm_norm[L0 + m] * q * tr;
-        const double ys = c_ylm_norm[L0 - m] * q * ti;
-        V[L0 + m] = mk(hp[l].x * yc, hp[l].y * yc);
-        V[L0 - m] = mk(hp[l].x * ys, hp[l].y * ys);
+        Y[L0 + m] = c_ylm_norm[L0 + m] * q * tr;
+        Y[L0 - m] = c_ylm_norm[L0 - m] * q * ti;
       }
     }
   }
 }
 
+// hp[l] = mpref * h_l(kappa d), l <= 6, where mpref * sum_L'' i^{l-l'-l''} C_{LL'L''}
+// h_l''(kappa d) Y_L''(R^) is the block -g: kappa = principal sqrt(z); Im z >= 0:
+// h = h^(1), mpref = +4 pi i kappa; Im z < 0: h = h^(2), mpref = -4 pi i kappa (the
+// decaying, advanced branch).  Upward recurrence h_{l+1} = (2l+1)/x h_l - h_{l-1}.
+__device__ void hankel6(double d, double2 z, double2* hp) {
+  const double r = hypot(z.x, z.y);
+  const double kre = sqrt(0.5 * (r + z.x));
+  double kim = sqrt(0.5 * fmax(r - z.x, 0.0));
+  const bool adv = z.y < 0.0;
+  if (adv) kim = -kim;
+  const double four_pi = 4.0 * M_PI;
+  const double2 mpref = adv ? mk(four_pi * kim, -four_pi * kre) : mk(-four_pi * kim, four_pi * kre);
+  const double2 xx = mk(kre * d, kim * d);
+  const double2 ix = crcp(xx);
+  double sn, cs;
+  sincos(xx.x, &sn, &cs);
+  const double f = exp(adv ? xx.y : -xx.y);
+  const double2 ex = adv ? mk(f * cs, -f * sn) : mk(f * cs, f * sn);  // e^{-+ix}
+  double2 hm = cmul(ex, ix);                                             // h_{-1}
+  double2 h = adv ? mk(-hm.y, hm.x) : mk(hm.y, -hm.x);                  // h_0
+  hp[0] = cmul(mpref, h);
+#pragma unroll
+  for (int l = 0; l < kMaxL3; ++l) {
+    const double2 hn = csub(cmul(mk((2.0 * l + 1.0) * ix.x, (2.0 * l + 1.0) * ix.y), h), hm);
+    hm = h;
+    h = hn;
+    hp[l + 1] = cmul(mpref, h);
+  }
+}
+
 // grid (S_max, atoms in the chunk), block 256: one CTA per row site p of one
-// atom's LIZ, for all energies of that atom.  Warp 0 prepares V for 16 column
-// sites x 2 energies at a time (one lane each); then thread (L, L') forms
-// sum_L'' s C_{LL'L''} V[L''] for those blocks (diagonal blocks: t^{-1}).
-// FP64 form: writes M (complex128) into the factor array.  Mixed form: writes
-// (hi, lo) float pairs of M (float4 per element, at ws + m64_off) for the
-// refinement residual and, if write_fac, the hi part (complex64) as the matrix
-// to factor.
+// atom's LIZ, for all energies of that atom.  Per round of 16 column sites q:
+// 16 lanes compute Y_L(R^) (shared by the energies), 32 lanes compute
+// V[L''] = mpref h_l''(kappa R) Y_L''(R^) for 2 energies, then thread (L, L')
+// forms sum_L'' s C_{LL'L''} V[L''] for those blocks (diagonal blocks: t^{-1}).
+// FP64 form: FP64 sums, M (complex128) written into the factor array.
+// Mixed form: the sums in double-float arithmetic on the FP32 pipes (FP64
+// accuracy); writes M as (hi, lo) float pairs (float4 per element, at
+// ws + m64_off) for the refinement residual and, if write_fac, the hi part
+// (complex64) as the matrix to factor.
 template <bool MIXED>
-__global__ void __launch_bounds__(256) k_assemble(const Unit* __restrict__ units, int nE,
+__global__ void __launch_bounds__(256, 2) k_assemble(const Unit* __restrict__ units, int nE,
                                                   const double* __restrict__ disp,
                                                   const int32_t* __restrict__ site_atom,
                                                   const int32_t* __restrict__ species,
@@ -380,20 +375,25 @@ __global__ void __launch_bounds__(256) k_assemble(const Unit* __restrict__ units
   const int p = blockIdx.x;
   if (p >= u0.S) return;
   const int S = u0.S, n = u0.n;
-  __shared__ double2 sV[kAsmE][kAsmQ][kMaxK3];
+  __shared__ double sY[kAsmQ][kMaxK3];
+  __shared__ double sD[kAsmQ];
+  __shared__ __align__(16) unsigned char sVraw[kAsmE * kAsmQ * kMaxK3 * 16];
   // Gaunt coupling table in shared memory: threads index it divergently, which
   // constant memory would serialise.
   __shared__ double s_coef[kCpMax];
+  __shared__ float2 s_coef2[kCpMax];
   __shared__ int32_t s_lpp[kCpMax];
   __shared__ int32_t s_start[kMaxK * kMaxK + 1];
   const int tid = threadIdx.x;
   for (int i = tid; i < kMaxK * kMaxK + 1; i += blockDim.x) s_start[i] = c_cp_start[i];
   const int n_cp = c_cp_start[kMaxK * kMaxK];
   for (int i = tid; i < n_cp; i += blockDim.x) {
-    s_coef[i] = c_cp_coef[i];
+    const double c = c_cp_coef[i];
+    s_coef[i] = c;
+    const float ch = (float)c;
+    s_coef2[i] = make_float2(ch, (float)(c - (double)ch));
     s_lpp[i] = c_cp_lpp[i];
   }
-  __syncthreads();
   const int L = tid & 15, Lp = tid >> 4;
   const bool act = (L < K) && (Lp < K);
   const int64_t sp0 = u0.site_off + p;
@@ -404,6 +404,7 @@ __global__ void __launch_bounds__(256) k_assemble(const Unit* __restrict__ units
     bad = LSMS_UNIT_BAD_INPUT;
     spp = 0;
   }
+  __syncthreads();
   int t0 = 0, t1 = 0;
   if (act) {
     t0 = s_start[L * kMaxK + Lp];
@@ -417,12 +418,32 @@ __global__ void __launch_bounds__(256) k_assemble(const Unit* __restrict__ units
     for (int q0 = 0; q0 < S; q0 += kAsmQ) {
       const int nq = min(kAsmQ, S - q0);
       __syncthreads();
+      if (tid < kAsmQ) {
+        const int q = q0 + tid;
+        if (tid < nq && q != p) {
+          const int64_t sq = u0.site_off + q;
+          const double rx = disp[3 * sq] - px, ry = disp[3 * sq + 1] - py, rz = disp[3 * sq + 2] - pz;
+          const double d = sqrt(rx * rx + ry * ry + rz * rz);
+          const double id = 1.0 / d;
+          sD[tid] = d;
+          ylm6(rx * id, ry * id, rz * id, sY[tid]);
+        }
+      }
+      __syncthreads();
       if (tid < kAsmE * kAsmQ) {
         const int ee = tid / kAsmQ, qq = tid % kAsmQ, q = q0 + qq;
         if (ee < ne && qq < nq && q != p) {
-          const int64_t sq = u0.site_off + q;
-          pair_setup(disp[3 * sq] - px, disp[3 * sq + 1] - py, disp[3 * sq + 2] - pz, E.z[ua[e0 + ee].energy],
-                     sV[ee][qq]);
+          double2 hp[kMaxL3 + 1];
+          hankel6(sD[qq], E.z[ua[e0 + ee].energy], hp);
+          const int base = (ee * kAsmQ + qq) * kMaxK3;
+#pragma unroll
+          for (int l = 0; l <= kMaxL3; ++l)
+            for (int Lpp = l * l; Lpp < (l + 1) * (l + 1); ++Lpp) {
+              const double y = sY[qq][Lpp];
+              const double2 v = mk(hp[l].x * y, hp[l].y * y);
+              if (MIXED) reinterpret_cast<float4*>(sVraw)[base + Lpp] = df_split(v);
+              else reinterpret_cast<double2*>(sVraw)[base + Lpp] = v;
+            }
         }
       }
       __syncthreads();
@@ -431,27 +452,41 @@ __global__ void __launch_bounds__(256) k_assemble(const Unit* __restrict__ units
         const Unit& u = ua[e0 + ee];
         for (int qq = 0; qq < nq; ++qq) {
           const int q = q0 + qq;
-          double2 v;
-          if (q == p) {
-            v = tinv[(((size_t)spp * n_energy) + u.energy) * K * K + L * K + Lp];
-          } else {
-            v = mk(0.0, 0.0);
-            const double2* Vq = sV[ee][qq];
-            for (int t = t0; t < t1; ++t) {
-              const double c = s_coef[t];
-              const double2 w = Vq[s_lpp[t]];
-              v.x = fma(c, w.x, v.x);
-              v.y = fma(c, w.y, v.y);
-            }
-          }
-          if (!finite2(v)) flags[ee] |= LSMS_UNIT_NONFINITE;
           const size_t idx = (size_t)(K * q + Lp) * n + K * p + L;
+          const int base = (ee * kAsmQ + qq) * kMaxK3;
           if (MIXED) {
-            const float hr = (float)v.x, hi = (float)v.y;
-            const float4 hl = make_float4(hr, hi, (float)(v.x - (double)hr), (float)(v.y - (double)hi));
-            reinterpret_cast<float4*>(ws + u.m64_off)[idx] = hl;
-            if (write_fac) reinterpret_cast<float2*>(fac_base + u.fac_off)[idx] = make_float2(hr, hi);
+            float4 v4;
+            if (q == p) {
+              v4 = df_split(tinv[(((size_t)spp * n_energy) + u.energy) * K * K + L * K + Lp]);
+            } else {
+              DfAcc acc = df_zero();
+              const float4* Vq = reinterpret_cast<const float4*>(sVraw) + base;
+              for (int t = t0; t < t1; ++t) {
+                const float2 c = s_coef2[t];
+                const float4 w = Vq[s_lpp[t]];
+                df_mac(acc.sr, acc.tr, c.x, c.y, w.x, w.y);
+                df_mac(acc.si, acc.ti, c.x, c.y, w.z, w.w);
+              }
+              v4 = df_value(acc);
+            }
+            if (!(isfinite(v4.x) && isfinite(v4.z))) flags[ee] |= LSMS_UNIT_NONFINITE;
+            reinterpret_cast<float4*>(ws + u.m64_off)[idx] = make_float4(v4.x, v4.z, v4.y, v4.w);
+            if (write_fac) reinterpret_cast<float2*>(fac_base + u.fac_off)[idx] = make_float2(v4.x, v4.z);
           } else {
+            double2 v;
+            if (q == p) {
+              v = tinv[(((size_t)spp * n_energy) + u.energy) * K * K + L * K + Lp];
+            } else {
+              v = mk(0.0, 0.0);
+              const double2* Vq = reinterpret_cast<const double2*>(sVraw) + base;
+              for (int t = t0; t < t1; ++t) {
+                const double c = s_coef[t];
+                const double2 w = Vq[s_lpp[t]];
+                v.x = fma(c, w.x, v.x);
+                v.y = fma(c, w.y, v.y);
+              }
+            }
+            if (!finite2(v)) flags[ee] |= LSMS_UNIT_NONFINITE;
             reinterpret_cast<double2*>(fac_base + u.fac_off)[idx] = v;
           }
         }
@@ -505,24 +540,6 @@ __global__ void k_widen(const Unit* __restrict__ units, char* ws, int nrhs) {
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)n * nrhs;
        idx += (int64_t)gridDim.x * blockDim.x)
     X[idx] = to64(X32[idx]);
-}
-
-// (s, t) += p with the rounding error of s + p kept exactly (two-sum).
-__device__ __forceinline__ void df_add(float& s, float& t, float p) {
-  const float a = s + p;
-  const float bb = a - s;
-  t += (s - (a - bb)) + (p - bb);
-  s = a;
-}
-
-// (s, t) += (ah + al)(bh + bl): exact ah*bh (two-product by FMA) plus the cross terms.
-__device__ __forceinline__ void df_mac(float& s, float& t, float ah, float al, float bh, float bl) {
-  const float p = ah * bh;
-  float e = fmaf(ah, bh, -p);
-  e = fmaf(ah, bl, e);
-  e = fmaf(al, bh, e);
-  df_add(s, t, p);
-  t += e;
 }
 
 // Refinement residual, FP64-accurate, on the FP32 pipes: B - M X with M held as
@@ -1031,7 +1048,8 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
       const int S_max = ch.n_max / c.K;
       if ((r2 = assemble_factor(c, *p, ch, fac_base, chunk, stat, !store))) return r2;
       if ((r2 = adj_rhs(du, nu, S_max, c.dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J), J_delta_stride,
-                        reinterpret_cast<const double2*>(tau), liz->total_sites, abar, n_delta, c.K, chunk, c.st)))
+                        reinterpret_cast<const double2*>(tau), liz->total_sites, abar, n_delta, c.K, chunk,
+                        precision == LSMS_MIXED, c.st)))
         return r2;
       if ((r2 = solve_refine(c, *p, ch, fac_base, chunk, stat, done, true))) return r2;
       if ((r2 = adj_site(du, nu, S_max, reinterpret_cast<const double2*>(tau), liz->total_sites, c.K, chunk, G, c.st)))

@@ -100,6 +100,58 @@ template <> __device__ __forceinline__ float2 cvt<float2>(double2 a) { return to
 __device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
 __device__ __forceinline__ bool finite2(float2 a) { return isfinite(a.x) && isfinite(a.y); }
 
+// ------------------------------------------------------------------ double-float
+// A real number held as hi + lo in two floats (unit roundoff about 2^-48), for
+// FP64-accurate arithmetic on the FP32 pipes: products by the FMA two-product,
+// sums by two-sum.  Complex values are float4 (re.hi, re.lo, im.hi, im.lo).
+
+// (s, t) += p with the rounding error of s + p kept exactly (two-sum).
+__device__ __forceinline__ void df_add(float& s, float& t, float p) {
+  const float a = s + p;
+  const float bb = a - s;
+  t += (s - (a - bb)) + (p - bb);
+  s = a;
+}
+
+// (s, t) += (ah + al)(bh + bl): exact ah*bh (FMA two-product) plus the cross terms.
+__device__ __forceinline__ void df_mac(float& s, float& t, float ah, float al, float bh, float bl) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  df_add(s, t, p);
+  t += e;
+}
+
+__device__ __forceinline__ float4 df_split(double2 a) {
+  const float rh = (float)a.x, ih = (float)a.y;
+  return make_float4(rh, (float)(a.x - (double)rh), ih, (float)(a.y - (double)ih));
+}
+
+__device__ __forceinline__ double2 df_join(float4 a) {
+  return make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
+}
+
+// complex accumulator: re = sr + tr, im = si + ti
+struct DfAcc {
+  float sr, tr, si, ti;
+};
+__device__ __forceinline__ DfAcc df_zero() { return DfAcc{0.f, 0.f, 0.f, 0.f}; }
+
+// acc += a * b (complex, double-float)
+__device__ __forceinline__ void dfc_mac(DfAcc& acc, float4 a, float4 b) {
+  df_mac(acc.sr, acc.tr, a.x, a.y, b.x, b.y);
+  df_mac(acc.sr, acc.tr, -a.z, -a.w, b.z, b.w);
+  df_mac(acc.si, acc.ti, a.x, a.y, b.z, b.w);
+  df_mac(acc.si, acc.ti, a.z, a.w, b.x, b.y);
+}
+
+// normalised (hi, lo) pairs of an accumulator
+__device__ __forceinline__ float4 df_value(const DfAcc& a) {
+  const float rh = a.sr + a.tr, ih = a.si + a.ti;
+  return make_float4(rh, a.tr - (rh - a.sr), ih, a.ti - (ih - a.si));
+}
+
 // ------------------------------------------------------------------ wrappers (lu.cu)
 // Blocked right-looking LU with partial pivoting of every unit of a chunk, in
 // place in the factor arrays (column-major, ld = n).  Pivots are applied to

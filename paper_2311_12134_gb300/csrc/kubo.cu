@@ -9,6 +9,7 @@
 // All arithmetic here is FP64; sums over atoms and sites run in a fixed order.
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -187,11 +188,15 @@ __global__ void __launch_bounds__(256) k_adj_abar(const int32_t* __restrict__ sp
 //   B[:, 0:K]  rows of site n = sum_{c: z1 = z_e} sum_nu J^{n nu}(c) tau^{n0}(z2) Abar^nu_c
 //   B[:, K:2K] rows of site n = sum_{c: z2 = z_e} sum_nu J^{n nu}(c)^T tau^{n0}(z1) (Abar^nu_c)^T
 // B is column-major n x 2K complex128 at ws + unit.r_off.  grid (S_max, n_units).
+// DF: the products in double-float arithmetic on the FP32 pipes (FP64 accuracy,
+// mixed form); otherwise FP64.
+template <bool DF>
 __global__ void __launch_bounds__(256) k_adj_rhs(const Unit* __restrict__ units, const int32_t* __restrict__ site_atom,
                                                  const int32_t* __restrict__ species, const double2* __restrict__ J,
                                                  int64_t J_dstride, const double2* __restrict__ tau, int64_t S_total,
                                                  const double2* __restrict__ abar, int n_delta, int n_species, int K,
                                                  char* ws) {
+  using V = typename std::conditional<DF, float4, double2>::type;
   const Unit u = units[blockIdx.y];
   const int nsite = blockIdx.x;
   if (nsite >= u.S) return;
@@ -201,9 +206,14 @@ __global__ void __launch_bounds__(256) k_adj_rhs(const Unit* __restrict__ units,
   const int64_t s = u.site_off + nsite;
   const int sp = min(max(0, species[site_atom[s]]), n_species - 1);
   const double2* Jd = J + (size_t)d * J_dstride;
-  __shared__ double2 sT[16][17], sJ[16][17], sA[16][17], sQ[16][17];
+  __shared__ V sT[16][17], sJ[16][17], sA[16][17], sQ[16][17];
   const int tid = threadIdx.x, i = tid >> 4, j = tid & 15;
   const bool act = (i < K) && (j < K);
+  auto load = [](double2 x) -> V {
+    if constexpr (DF) return df_split(x);
+    else return x;
+  };
+  DfAcc f1 = df_zero(), f2 = df_zero();
   double2 acc1 = mk(0.0, 0.0), acc2 = mk(0.0, 0.0);
   for (int part = 0; part < 2; ++part) {
     for (int cc = 0; cc < 2; ++cc) {
@@ -213,33 +223,53 @@ __global__ void __launch_bounds__(256) k_adj_rhs(const Unit* __restrict__ units,
       else c = (cc << 1) | sgn;            // a = cc, b = sgn
       const int a = c >> 1, b = c & 1;
       const int eo = (part == 0) ? (2 * d + b) : (2 * d + a);  // the other energy's tau
-      if (act) sT[i][j] = tau[((size_t)eo * S_total + s) * KK + i * K + j];
+      if (act) sT[i][j] = load(tau[((size_t)eo * S_total + s) * KK + i * K + j]);
       for (int v = 0; v < 3; ++v) {
         if (act) {
-          sJ[i][j] = Jd[(((size_t)sp * 4 + c) * 3 + v) * KK + i * K + j];
-          sA[i][j] = abar[((((size_t)m * n_delta + d) * 4 + c) * 3 + v) * KK + i * K + j];
+          sJ[i][j] = load(Jd[(((size_t)sp * 4 + c) * 3 + v) * KK + i * K + j]);
+          sA[i][j] = load(abar[((((size_t)m * n_delta + d) * 4 + c) * 3 + v) * KK + i * K + j]);
         }
         __syncthreads();
         if (act) {
-          double2 q = mk(0.0, 0.0);
-          if (part == 0)
-            for (int t = 0; t < K; ++t) q = cfma(sJ[i][t], sT[t][j], q);  // J tau
-          else
-            for (int t = 0; t < K; ++t) q = cfma(sJ[t][i], sT[t][j], q);  // J^T tau
-          sQ[i][j] = q;
+          if constexpr (DF) {
+            DfAcc q = df_zero();
+            if (part == 0)
+              for (int t = 0; t < K; ++t) dfc_mac(q, sJ[i][t], sT[t][j]);  // J tau
+            else
+              for (int t = 0; t < K; ++t) dfc_mac(q, sJ[t][i], sT[t][j]);  // J^T tau
+            sQ[i][j] = df_value(q);
+          } else {
+            double2 q = mk(0.0, 0.0);
+            if (part == 0)
+              for (int t = 0; t < K; ++t) q = cfma(sJ[i][t], sT[t][j], q);
+            else
+              for (int t = 0; t < K; ++t) q = cfma(sJ[t][i], sT[t][j], q);
+            sQ[i][j] = q;
+          }
         }
         __syncthreads();
         if (act) {
-          if (part == 0)
-            for (int t = 0; t < K; ++t) acc1 = cfma(sQ[i][t], sA[t][j], acc1);  // (J tau) Abar
-          else
-            for (int t = 0; t < K; ++t) acc2 = cfma(sQ[i][t], sA[j][t], acc2);  // (J^T tau) Abar^T
+          if constexpr (DF) {
+            if (part == 0)
+              for (int t = 0; t < K; ++t) dfc_mac(f1, sQ[i][t], sA[t][j]);  // (J tau) Abar
+            else
+              for (int t = 0; t < K; ++t) dfc_mac(f2, sQ[i][t], sA[j][t]);  // (J^T tau) Abar^T
+          } else {
+            if (part == 0)
+              for (int t = 0; t < K; ++t) acc1 = cfma(sQ[i][t], sA[t][j], acc1);
+            else
+              for (int t = 0; t < K; ++t) acc2 = cfma(sQ[i][t], sA[j][t], acc2);
+          }
         }
         __syncthreads();
       }
     }
   }
   if (act) {
+    if constexpr (DF) {
+      acc1 = df_join(df_value(f1));
+      acc2 = df_join(df_value(f2));
+    }
     double2* B = reinterpret_cast<double2*>(ws + u.r_off);
     const int n = u.n;
     B[(size_t)j * n + K * nsite + i] = acc1;
@@ -328,9 +358,13 @@ int adj_abar(const int32_t* species, int n_species, const double2* J, int64_t J_
 
 int adj_rhs(const Unit* d_units, int n_units, int S_max, const int32_t* site_atom, const int32_t* species,
             int n_species, const double2* J, int64_t J_dstride, const double2* tau, int64_t S_total,
-            const double2* abar, int n_delta, int K, char* ws, cudaStream_t st) {
-  LSMS_LAUNCH(k_adj_rhs, dim3(S_max, n_units), dim3(256), 0, st, d_units, site_atom, species, J, J_dstride, tau,
-              S_total, abar, n_delta, n_species, K, ws);
+            const double2* abar, int n_delta, int K, char* ws, bool df, cudaStream_t st) {
+  if (df)
+    LSMS_LAUNCH(k_adj_rhs<true>, dim3(S_max, n_units), dim3(256), 0, st, d_units, site_atom, species, J, J_dstride,
+                tau, S_total, abar, n_delta, n_species, K, ws);
+  else
+    LSMS_LAUNCH(k_adj_rhs<false>, dim3(S_max, n_units), dim3(256), 0, st, d_units, site_atom, species, J, J_dstride,
+                tau, S_total, abar, n_delta, n_species, K, ws);
   return LSMS_OK;
 }
 
