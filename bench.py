@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64-form comparison leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--chunk-mb", type=int, default=0,
+                    help="workspace size in MiB (units are processed in chunks that fit); 0 = all units at once")
     ap.add_argument("--workload", default="fcc256", choices=["fcc256", "fcc108"],
                     help="fcc108: the same alloy recipe on 3x3x3 cells (216 units), for profiler captures")
     return ap.parse_args()
@@ -151,6 +153,18 @@ def lu_flops(n_list):
     return float(np.sum(8.0 / 3.0 * n ** 3 + 128.0 * n ** 2))
 
 
+def gemm_bytes(n_list, nb):
+    """Algorithmic DRAM bytes of the complex64 trailing updates: A22 read + written,
+    L21 and U12 read once per panel step."""
+    tot = 0.0
+    for n in n_list:
+        for k in range(0, n, nb):
+            t = n - k - nb
+            if t > 0:
+                tot += 16.0 * t * t + 2 * 8.0 * nb * t
+    return tot
+
+
 def gemm_flops(n_list, nb):
     """Algorithmic flops of the trailing-update GEMMs of a blocked LU with panel width nb."""
     tot = 0.0
@@ -162,6 +176,9 @@ def gemm_flops(n_list, nb):
     return tot
 
 
+PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
 def peaks():
     p = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -170,6 +187,7 @@ def peaks():
             m = json.load(f)
         p.update({k: m[k] for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained") if k in m})
         p["source"] = "measured"
+    PEAKS.update(p)
     return p
 
 
@@ -244,7 +262,8 @@ def run_ours(args):
 
     def make(precision):
         return Problem(w.pos, w.lattice, w.r_liz, w.lmax, w.species, w.tinv, w.z, J, w.volume,
-                       precision=precision, device=dev, keep_factors=True)
+                       precision=precision, device=dev, keep_factors=True,
+                       workspace_bytes=(args.chunk_mb << 20) if args.chunk_mb else None)
 
     def step(p):
         p.forward()
@@ -320,6 +339,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "global_batch": units * world, "units_per_gpu": units,
+                   "workspace_mib": args.chunk_mb or "all units",
                    "precision": args.precision, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (per-step working set > 4 GB)"},
         "sigma_ms": sigma_ms,
@@ -357,6 +377,8 @@ def kernel_times(B, p, step, stream, dev, steps):
 # FP32 instruction issue rate of the chip: 152 SMs x 128 lanes at the 2070 MHz
 # maximum clock.  FP64 DFMA: 1.25 TFLOP/s nominal (1.197 measured by a DFMA loop).
 FP32_OPS = 152 * 128 * 2.07e9
+# dense TF32 / BF16 tensor rate ratio from the nominal table (1.1 / 2.25 PFLOP/s)
+TF32_OVER_BF16 = 1.1 / 2.25
 FP64_PEAK_TFLOPS = 1.25
 # Double-float complex multiply-accumulate: 4 real products x 11 FP32 ops
 # (FMA two-product 2, cross terms 2, two-sum 6, carry 1).
@@ -372,8 +394,14 @@ def kernel_models(w, n_list, fwd_passes, bwd_passes, precision, nb=32):
     mixed = precision == "mixed"
     simt_peak = 2.0 * FP32_OPS / 1e12 if mixed else FP64_PEAK_TFLOPS
     m = {}
-    m["k_gemm"] = (gemm_flops([int(x) for x in n_list], nb), simt_peak,
-                   "complex trailing update, %s" % ("FP32 FMA pipe" if mixed else "FP64 DFMA pipe"))
+    if mixed:
+        # tensor cores, 3xTF32 on the real embedding: 24 tensor flops per complex MAC (8 algorithmic)
+        tf32 = PEAKS["bf16_tflops_sustained"] * TF32_OVER_BF16
+        m["k_gemm_tc"] = (gemm_flops([int(x) for x in n_list], nb), tf32 / 3.0,
+                          "complex trailing update on tcgen05 (3xTF32); peak = sustained TF32 / 3",
+                          gemm_bytes([int(x) for x in n_list], nb))
+    else:
+        m["k_gemm"] = (gemm_flops([int(x) for x in n_list], nb), simt_peak, "complex trailing update, FP64 DFMA pipe")
     # each solve: forward + backward substitution = n^2 complex MACs per right-hand side
     fwd_solves = (1 + fwd_passes) if mixed else np.ones_like(n)
     bwd_solves = (1 + bwd_passes) if mixed else np.ones_like(n)
@@ -386,10 +414,16 @@ def kernel_models(w, n_list, fwd_passes, bwd_passes, precision, nb=32):
     # assembly: 708 nonzero Gaunt couplings x (complex x real) per off-diagonal block, forward
     # (and the backward's re-assembly of the FP64 copy in the mixed form)
     blocks = float(np.sum(S * (S - 1)))
-    m["k_assemble"] = (blocks * 708 * 4.0 * (2 if mixed else 1), FP64_PEAK_TFLOPS, "FP64 Gaunt sums")
+    m["k_assemble"] = (blocks * 708 * 4.0 * (2 if mixed else 1),
+                       (8.0 * FP32_OPS / DF_OPS_PER_CMAC / 1e12) if mixed else FP64_PEAK_TFLOPS,
+                       "Gaunt sums, %s" % ("double-float FP32" if mixed else "FP64"))
     n_atoms = len(n_list) // len(w.z)
     sites = float(np.sum(S)) / len(w.z)
-    m["k_adj_rhs"] = (len(w.z) * sites * 24 * 16 ** 3 * 8.0, FP64_PEAK_TFLOPS, "FP64 16x16 products")
+    if mixed:
+        m["k_adj_rhs"] = (len(w.z) * sites * 24 * 16 ** 3 * 8.0, 8.0 * FP32_OPS / DF_OPS_PER_CMAC / 1e12,
+                          "16x16 complex products in double-float FP32 arithmetic")
+    else:
+        m["k_adj_rhs"] = (len(w.z) * sites * 24 * 16 ** 3 * 8.0, FP64_PEAK_TFLOPS, "FP64 16x16 products")
     m["k_kubo_partial"] = (w.n_delta * 4 * sites * 6 * 16 ** 3 * 8.0, FP64_PEAK_TFLOPS, "FP64 16x16 products")
     return m
 
@@ -403,14 +437,26 @@ def roofline(kt, w, n_list, fwd_passes, bwd_passes, precision, traffic):
         base = name.split("<")[0]
         if base not in models:
             continue
-        flops, peak, what = models[base]
+        flops, peak, what = models[base][:3]
         ach = flops / (ms * 1e-3) / 1e12
-        rows[base] = {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                      "frac": ach / peak, "ms_per_step": ms, "launches_per_step": launches,
-                      "work": what}
-    if not rows:
-        return None, None
-    top = max(rows.values(), key=lambda r: r["ms_per_step"])
+        bound = "tensor" if base == "k_gemm_tc" else "alu"
+        row = {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+               "frac": ach / peak, "ms_per_step": ms, "launches_per_step": launches, "work": what}
+        if len(models[base]) > 3:  # also HBM-limited: keep whichever roof is closer
+            gbs = models[base][3] / (ms * 1e-3) / 1e9
+            if gbs / PEAKS["hbm_gbs"] > row["frac"]:
+                row.update({"bound": "hbm", "achieved": gbs, "peak": PEAKS["hbm_gbs"], "unit": "GB/s",
+                            "frac": gbs / PEAKS["hbm_gbs"]})
+            row["tensor_frac"] = ach / peak
+        rows[base] = row
+    for name, (ms, launches) in kt.items():  # unmodelled kernels: time only
+        base = name.split("<")[0]
+        if base not in rows:
+            rows[base] = {"kernel": name, "ms_per_step": ms, "launches_per_step": launches}
+    modelled = [r for r in rows.values() if "frac" in r]
+    if not modelled:
+        return None, rows
+    top = max(modelled, key=lambda r: r["ms_per_step"])
     t = traffic.get(top["kernel"].split("<")[0]) if traffic else None
     top = dict(top)
     top["traffic"] = t

@@ -546,9 +546,13 @@ __global__ void k_widen(const Unit* __restrict__ units, char* ws, int nrhs) {
 // (hi, lo) float pairs and X split the same way, products by the FMA two-product
 // and sums by two-sum (double-float arithmetic, unit roundoff about 2^-48).
 // Output rounded to complex64 and permuted by P into X32 for the correction
-// solve.  grid (ceil(n_max / 64), n_units), block 256: 64 rows x nrhs columns.
-__global__ void __launch_bounds__(256) k_residual(const Unit* __restrict__ units, const char* fac_base, char* ws,
-                                                  int K, int nrhs, bool explicit_b, const int32_t* __restrict__ done) {
+// solve.  grid (ceil(n_max / 64), n_units), block 256: 64 rows x NRHS columns,
+// 4 column groups of CPG = NRHS / 4 columns per thread.
+template <int NRHS>
+__global__ void __launch_bounds__(256, 3) k_residual(const Unit* __restrict__ units, const char* fac_base, char* ws,
+                                                     int K, bool explicit_b, const int32_t* __restrict__ done) {
+  constexpr int CPG = (NRHS + 3) / 4;
+  constexpr int NCOL = 4 * CPG;  // padded column count; columns >= NRHS are zero and never stored
   const Unit u = units[blockIdx.y];
   if (done[u.stat_off]) return;
   const int n = u.n;
@@ -558,62 +562,68 @@ __global__ void __launch_bounds__(256) k_residual(const Unit* __restrict__ units
   const double2* X = reinterpret_cast<const double2*>(ws + u.x_off);
   const int32_t* iperm = reinterpret_cast<const int32_t*>(fac_base + u.piv_off) + 2 * n;
   float2* X32 = reinterpret_cast<float2*>(ws + u.x32_off);
-  __shared__ float4 sX[32][33];
+  __shared__ float4 sX[32][NCOL + 1];
   const int tid = threadIdx.x;
-  const int r = tid & 63, cg = tid >> 6;  // 4 column groups
+  const int r = tid & 63, cg = tid >> 6;
   const int row = row0 + r;
-  const int cpg = (nrhs + 3) / 4;          // columns per group (<= 8)
-  float sr[8], tr[8], si[8], ti[8];
+  const bool live = row < n;
+  const float4* Mrow = M + (live ? row : 0);
+  float sr[CPG], tr[CPG], si[CPG], ti[CPG];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) sr[c] = tr[c] = si[c] = ti[c] = 0.f;
+  for (int c = 0; c < CPG; ++c) sr[c] = tr[c] = si[c] = ti[c] = 0.f;
   for (int j0 = 0; j0 < n; j0 += 32) {
     const int jn = min(32, n - j0);
     __syncthreads();
-    for (int idx = tid; idx < 32 * nrhs; idx += 256) {
-      const int jj = idx % 32, c = idx / 32;
+    for (int idx = tid; idx < 32 * NCOL; idx += 256) {
+      const int jj = idx & 31, c = idx >> 5;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (jj < jn) {
-        const double2 xv = X[(size_t)c * n + j0 + jj];
-        v.x = (float)xv.x;
-        v.y = (float)xv.y;
-        v.z = (float)(xv.x - (double)v.x);
-        v.w = (float)(xv.y - (double)v.y);
-      }
+      if (jj < jn && c < NRHS) v = df_split(X[(size_t)c * n + j0 + jj]);
       sX[jj][c] = v;
     }
     __syncthreads();
-    if (row < n) {
-      for (int jj = 0; jj < jn; ++jj) {
-        const float4 m = M[(size_t)(j0 + jj) * n + row];
+    if (live) {
+      if (jn == 32) {
+#pragma unroll 4
+        for (int jj = 0; jj < 32; ++jj) {
+          const float4 m = Mrow[(size_t)(j0 + jj) * n];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const int col = cg * cpg + c;
-          if (c < cpg && col < nrhs) {
-            const float4 x = sX[jj][col];
+          for (int c = 0; c < CPG; ++c) {
+            const float4 x = sX[jj][cg * CPG + c];
             // Re += m.re x.re - m.im x.im ; Im += m.re x.im + m.im x.re
-            df_mac(sr[c], tr[c], m.x, m.z, x.x, x.z);
-            df_mac(sr[c], tr[c], -m.y, -m.w, x.y, x.w);
-            df_mac(si[c], ti[c], m.x, m.z, x.y, x.w);
-            df_mac(si[c], ti[c], m.y, m.w, x.x, x.z);
+            df_mac(sr[c], tr[c], m.x, m.z, x.x, x.y);
+            df_mac(sr[c], tr[c], -m.y, -m.w, x.z, x.w);
+            df_mac(si[c], ti[c], m.x, m.z, x.z, x.w);
+            df_mac(si[c], ti[c], m.y, m.w, x.x, x.y);
+          }
+        }
+      } else {
+        for (int jj = 0; jj < jn; ++jj) {
+          const float4 m = Mrow[(size_t)(j0 + jj) * n];
+#pragma unroll
+          for (int c = 0; c < CPG; ++c) {
+            const float4 x = sX[jj][cg * CPG + c];
+            df_mac(sr[c], tr[c], m.x, m.z, x.x, x.y);
+            df_mac(sr[c], tr[c], -m.y, -m.w, x.z, x.w);
+            df_mac(si[c], ti[c], m.x, m.z, x.z, x.w);
+            df_mac(si[c], ti[c], m.y, m.w, x.x, x.y);
           }
         }
       }
     }
   }
-  if (row < n) {
+  if (live) {
     const double2* B = reinterpret_cast<const double2*>(ws + u.r_off);
     const int pos = iperm[row];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int col = cg * cpg + c;
-      if (c < cpg && col < nrhs) {
-        double2 b;
-        if (explicit_b) b = B[(size_t)col * n + row];
-        else b = (row == col && col < K) ? mk(1.0, 0.0) : mk(0.0, 0.0);
-        const double re = b.x - ((double)sr[c] + (double)tr[c]);
-        const double im = b.y - ((double)si[c] + (double)ti[c]);
-        X32[(size_t)col * n + pos] = make_float2((float)re, (float)im);
-      }
+    for (int c = 0; c < CPG; ++c) {
+      const int col = cg * CPG + c;
+      if (NRHS % 4 != 0 && col >= NRHS) continue;
+      double2 b;
+      if (explicit_b) b = B[(size_t)col * n + row];
+      else b = (row == col && col < K) ? mk(1.0, 0.0) : mk(0.0, 0.0);
+      const double re = b.x - ((double)sr[c] + (double)tr[c]);
+      const double im = b.y - ((double)si[c] + (double)ti[c]);
+      X32[(size_t)col * n + pos] = make_float2((float)re, (float)im);
     }
   }
 }
@@ -745,8 +755,15 @@ static int solve_refine(const Call& c, const Plan& p, const Chunk& ch, const cha
   LSMS_LAUNCH(k_widen, g1, dim3(256), 0, c.st, du, ws, nrhs);
   // done flags of this chunk's units start cleared (memset by the caller)
   for (int it = 0; it < kIrMaxIter; ++it) {
-    LSMS_LAUNCH(k_residual, dim3((ch.n_max + 63) / 64, nu), dim3(256), 0, c.st, du, fac_base, ws, c.K, nrhs,
-                explicit_b, done);
+    const dim3 gr((ch.n_max + 63) / 64, nu);
+    switch (nrhs) {  // K or 2K for lmax = 0..3
+#define LSMS_RESID(NR) \
+  case NR: LSMS_LAUNCH(k_residual<NR>, gr, dim3(256), 0, c.st, du, fac_base, ws, c.K, explicit_b, done); break;
+      LSMS_RESID(1) LSMS_RESID(2) LSMS_RESID(4) LSMS_RESID(8) LSMS_RESID(9) LSMS_RESID(18) LSMS_RESID(16)
+      LSMS_RESID(32)
+#undef LSMS_RESID
+      default: return fail(LSMS_ERR_ARG, "internal: no residual kernel for %d right-hand sides", nrhs);
+    }
     if ((rc = lu_solve_chunk<float>(du, nu, fac_base, ws, RHS_X32, nrhs, done, c.st))) return rc;
     LSMS_LAUNCH(k_ir_update, dim3(nu), dim3(256), 0, c.st, du, ws, nrhs, kIrTol, done, stat);
   }

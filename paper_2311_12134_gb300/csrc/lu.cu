@@ -321,14 +321,15 @@ template <typename R, int NB>
 __device__ __forceinline__ void update_rows(const Cx<R>* __restrict__ A, Cx<R>* X, const Cx<R> (*sX)[33], int n, int k,
                                             int nbp, int r0, int r1, int nrhs, int tid, int nthr) {
   using C = Cx<R>;
+  constexpr int G = 4;  // right-hand sides per thread
   const int rows = r1 - r0;
   if (rows <= 0) return;
-  const int ngrp = (nrhs + 7) / 8;
+  const int ngrp = (nrhs + G - 1) / G;
   for (int idx = tid; idx < rows * ngrp; idx += nthr) {
-    const int i = r0 + idx % rows, g = (idx / rows) * 8;
-    C acc[8];
+    const int i = r0 + idx % rows, g = (idx / rows) * G;
+    C acc[G];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] = (g + c < nrhs) ? X[(size_t)(g + c) * n + i] : mk(R(0), R(0));
+    for (int c = 0; c < G; ++c) acc[c] = (g + c < nrhs) ? X[(size_t)(g + c) * n + i] : mk(R(0), R(0));
     for (int j0 = 0; j0 < nbp; j0 += 8) {
       C l[8];
 #pragma unroll
@@ -336,10 +337,10 @@ __device__ __forceinline__ void update_rows(const Cx<R>* __restrict__ A, Cx<R>* 
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = cfms(l[jj], sX[j0 + jj][(g + c < nrhs) ? g + c : 0], acc[c]);
+        for (int c = 0; c < G; ++c) acc[c] = cfms(l[jj], sX[j0 + jj][(g + c < nrhs) ? g + c : 0], acc[c]);
     }
 #pragma unroll
-    for (int c = 0; c < 8; ++c)
+    for (int c = 0; c < G; ++c)
       if (g + c < nrhs) X[(size_t)(g + c) * n + i] = acc[c];
   }
 }
@@ -348,7 +349,7 @@ __device__ __forceinline__ void update_rows(const Cx<R>* __restrict__ A, Cx<R>* 
 // The NB x NB triangles are solved by warps taking columns in turn (lane = row, values
 // passed by shuffles); the rows below/above are updated by the whole CTA.
 template <typename R, int NB>
-__global__ void __launch_bounds__(512) k_solve(const Unit* __restrict__ units, const char* fac_base, char* ws,
+__global__ void __launch_bounds__(512, 2) k_solve(const Unit* __restrict__ units, const char* fac_base, char* ws,
                                                 int which, int nrhs, const int32_t* done) {
   using C = Cx<R>;
   static_assert(NB == 32, "one lane per row of the diagonal block");
