@@ -194,23 +194,56 @@ def peaks():
 # ---------------------------------------------------------------- CPU oracle timing
 def time_oracle(w, n_atoms_sample, budget_s=25.0):
     """Oracle (NumPy FP64, LAPACK) on a bounded sample: tau blocks of the first atoms
-    for both energies + their trace terms.  Returns (units/s, units, seconds, cores)."""
+    for every energy + their trace terms.  Returns (units/s, units, seconds, cores,
+    results); results holds the tau column blocks of the atoms done, the number of
+    atoms done and their summed sigma~ terms."""
     from oracle import kkr as okkr
     from oracle import kubo as okubo
     from oracle import liz as oliz
     L = oliz.build_liz(w.pos, w.lattice, w.r_liz)
     J = okubo.dipole_current(w.lmax, w.r_ll)[w.species]
     tin = w.tinv[w.species]
+    off, sa = L["offsets"], L["site_atom"]
+    nE = len(w.z)
+    col = np.zeros((nE, off[-1], w.K, w.K), dtype=np.complex128)
+    row = np.zeros_like(col)
+    st = np.zeros((w.n_delta, 4, 3, 3), dtype=np.complex128)
     t0 = time.perf_counter()
-    done = 0
+    done = m_done = 0
     for m in range(n_atoms_sample):
-        col, row = okkr.tau_blocks(w.lmax, L, tin, w.z, atoms=[m], return_rows=True)
-        okubo.sigma_tilde(L, J, col, row, w.n_delta, w.volume, atoms=[m])
-        done += len(w.z)
+        s0, s1 = off[m], off[m + 1]
+        for e in range(nE):
+            M = okkr.kkr_matrix(w.lmax, L["disp"][s0:s1], tin[sa[s0:s1], e], w.z[e])
+            col[e, s0:s1], row[e, s0:s1] = okkr.tau_col_row(M, w.K)
+        st += okubo.sigma_tilde(L, J, col, row, w.n_delta, w.volume, atoms=[m])
+        done += nE
+        m_done += 1
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return done / dt, done, dt, os.cpu_count()
+    return done / dt, done, dt, os.cpu_count(), dict(col=col, sigma_tilde=st, atoms=m_done, offsets=off)
+
+
+def accuracy(res, tau_gpu, sigma_gpu, n_atoms):
+    """Errors of a GPU result against the oracle sample (norm-wise, as in the tests)."""
+    if res is None or tau_gpu is None:
+        return None
+    off = res["offsets"]
+    m_done = res["atoms"]
+    s1 = off[m_done]
+    ref = res["col"][:, :s1]
+    got = tau_gpu[:, :s1]
+    errs = []
+    for e in range(ref.shape[0]):
+        for m in range(m_done):
+            sl = slice(off[m], off[m + 1])
+            errs.append(np.linalg.norm(got[e, sl] - ref[e, sl]) / np.linalg.norm(ref[e, sl]))
+    out = {"tau_rel_err_max": float(max(errs)), "oracle_atoms": int(m_done)}
+    if m_done == n_atoms and sigma_gpu is not None:
+        from oracle import kubo as okubo
+        sig = okubo.consolidate(res["sigma_tilde"])
+        out["sigma_rel_err"] = float(np.abs(sigma_gpu - sig).max() / np.abs(sig).max())
+    return out
 
 
 def run_reference(args):
@@ -220,7 +253,7 @@ def run_reference(args):
     w = workload()
     vals = []
     for i in range(args.warmup + args.steps):
-        v, units, dt, cores = time_oracle(w, n_atoms_sample=2, budget_s=20.0)
+        v, units, dt, cores, _ = time_oracle(w, n_atoms_sample=2, budget_s=20.0)
         if i >= args.warmup:
             vals.append((v, units, dt))
     v = float(np.mean([x[0] for x in vals]))
@@ -294,6 +327,11 @@ def run_ours(args):
     clocks = sampler.stop()
     status = main.unit_status.cpu().numpy()
     bw_status = main.bw_status.cpu().numpy()
+    main.forward()
+    torch.cuda.synchronize(dev)
+    main_tau = main.tau.cpu().numpy() if not args.no_cpu_baseline else None
+    main_sigma = main.sigma_out.cpu().numpy()
+    fp64_tau = fp64_sigma = None
     # forward-only time (sigma time) on the same problem
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -317,6 +355,11 @@ def run_ours(args):
         p64 = make("fp64")
         ms64, _ = timed(p64, max(1, min(args.steps, 2)), 1)
         fp64 = {"value": world * units / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64}
+        p64.forward()
+        torch.cuda.synchronize(dev)
+        fp64_tau = p64.tau.cpu().numpy() if not args.no_cpu_baseline else None
+        fp64_sigma = p64.sigma_out.cpu().numpy()
+        fp64["sigma_rel_diff_vs_main"] = float(np.abs(fp64_sigma - main_sigma).max() / np.abs(fp64_sigma).max())
         del p64
         torch.cuda.empty_cache()
 
@@ -329,11 +372,15 @@ def run_ours(args):
     roof, roof_all = roofline(kt, w, n_list, np.sort(fwd_passes), np.sort(bwd_passes), args.precision,
                               load_traffic())
     cpu = None
+    acc = None
     if not args.no_cpu_baseline:
-        v, u, dt, cores = time_oracle(w, n_atoms_sample=8, budget_s=25.0)
+        v, u, dt, cores, res = time_oracle(w, n_atoms_sample=w.n_atoms, budget_s=25.0)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{u} units ({u // len(w.z)} atoms x {len(w.z)} energies): tau blocks + trace terms, "
                          f"{dt:.1f} s"}
+        acc = {args.precision: accuracy(res, main_tau, main_sigma, w.n_atoms)}
+        if fp64:
+            acc["fp64"] = accuracy(res, fp64_tau, fp64_sigma, w.n_atoms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -349,7 +396,7 @@ def run_ours(args):
         "ir_passes_adjoint_mean": float((bw_status >> 8).mean()),
         "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
         "kernels": roof_all,
-        "cpu_baseline": cpu, "fp64_form": fp64,
+        "cpu_baseline": cpu, "fp64_form": fp64, "accuracy_vs_oracle": acc,
     }
     if fp64:
         line["speedup_vs_fp64_form"] = value / fp64["value"]
