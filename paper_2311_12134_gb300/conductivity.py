@@ -122,3 +122,33 @@ def conductivity(pos, lattice, r_liz, lmax, species, tinv, z, J, volume, precisi
     p = Problem(pos, lattice, r_liz, lmax, species, tinv, z, J, volume, precision=precision, keep_factors=False)
     p.forward()
     return p.sigma_out.cpu().numpy(), p.rho.cpu().numpy()
+
+
+class StepGraph:
+    """The whole step (tau blocks, sigma, adjoint) of a Problem captured in one
+    CUDA graph.  The library's first calls on the problem (device tables, work
+    plans, workspaces) happen in a warm-up step before capture; every later call
+    enqueues kernels, memsets and stream-ordered scratch only, so the captured
+    graph replays the same work on the same buffers.  Inputs are read from the
+    problem's tensors at replay time (update them in place to change them)."""
+
+    def __init__(self, problem, grad_sigma, with_backward=True):
+        import torch
+        self.problem = problem
+        self.grad_sigma = grad_sigma.contiguous()
+        self.with_backward = with_backward
+        problem.forward()
+        if with_backward:
+            problem.backward(self.grad_sigma)
+        torch.cuda.synchronize(problem.device)
+        self.graph = torch.cuda.CUDAGraph()
+        stream = torch.cuda.Stream(device=problem.device)
+        stream.wait_stream(torch.cuda.current_stream(problem.device))
+        with torch.cuda.graph(self.graph, stream=stream):
+            problem.forward()
+            if with_backward:
+                self.grads = problem.backward(self.grad_sigma)
+        torch.cuda.synchronize(problem.device)
+
+    def replay(self):
+        self.graph.replay()
