@@ -17,6 +17,7 @@
 // Units of a chunk are sorted by n (largest first); each launch covers every
 // unit and units already finished return at once.  k_solve then runs plain
 // forward/backward substitution on right-hand sides already permuted by P.
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -35,11 +36,11 @@ __device__ __forceinline__ float2 shfl2(float2 v, int src) {
 // ------------------------------------------------------------------ panel
 template <typename R, int NB>
 __global__ void __launch_bounds__(256) k_panel(const Unit* __restrict__ units, char* fac_base, int k,
-                                               int32_t* stat) {
+                                               int32_t* stat, int max_rows) {
   using C = Cx<R>;
   const Unit u = units[blockIdx.x];
   const int n = u.n;
-  if (k >= n) return;
+  if (k >= n || n - k <= max_rows) return;  // k_panel_smem factors those
   C* A = reinterpret_cast<C*>(fac_base + u.fac_off);
   int32_t* piv = reinterpret_cast<int32_t*>(fac_base + u.piv_off);
   const int nbp = min(NB, n - k);
@@ -111,10 +112,96 @@ __global__ void __launch_bounds__(256) k_panel(const Unit* __restrict__ units, c
   if (tid == 0 && flags) atomicOr(&stat[u.stat_off], flags);
 }
 
+// Panel factorization held in shared memory: the m = n - k rows x NB columns of
+// the panel are read once, factored column by column in shared memory (pivot
+// search by warp shuffles), and written back once.  Units whose panel does not
+// fit (m > max_rows) are left to k_panel, which works in global memory.
+template <typename R, int NB>
+__global__ void __launch_bounds__(512) k_panel_smem(const Unit* __restrict__ units, char* fac_base, int k,
+                                                    int32_t* stat, int max_rows) {
+  using C = Cx<R>;
+  const Unit u = units[blockIdx.x];
+  const int n = u.n;
+  if (k >= n) return;
+  const int m = n - k;
+  if (m > max_rows) return;
+  extern __shared__ __align__(16) unsigned char panel_raw[];
+  C* sP = reinterpret_cast<C*>(panel_raw);  // [NB][m], column-major
+  C* A = reinterpret_cast<C*>(fac_base + u.fac_off);
+  int32_t* piv = reinterpret_cast<int32_t*>(fac_base + u.piv_off);
+  const int nbp = min(NB, m);
+  __shared__ R s_val[16];
+  __shared__ int s_idx[16];
+  __shared__ int s_piv;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nthr = blockDim.x, nwarps = nthr >> 5;
+  for (int c = 0; c < nbp; ++c)
+    for (int r = tid; r < m; r += nthr) sP[c * m + r] = A[(size_t)(k + c) * n + k + r];
+  __syncthreads();
+  int flags = 0;
+  for (int j = 0; j < nbp; ++j) {
+    C* Pj = sP + j * m;
+    R best = R(-1);
+    int bidx = m;
+    for (int i = j + tid; i < m; i += nthr) {
+      const R v = cabs1(Pj[i]);
+      if (v > best) { best = v; bidx = i; }  // strict: lowest row kept; NaN never wins
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+      const R ov = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
+      if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
+    }
+    if (lane == 0) { s_val[warp] = best; s_idx[warp] = bidx; }
+    __syncthreads();
+    if (warp == 0) {
+      best = lane < nwarps ? s_val[lane] : R(-1);
+      bidx = lane < nwarps ? s_idx[lane] : m;
+#pragma unroll
+      for (int off = 16; off; off >>= 1) {
+        const R ov = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
+        if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
+      }
+      if (lane == 0) {
+        const int p = (bidx < m) ? bidx : j;
+        s_piv = p;
+        piv[k + j] = k + p;
+      }
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (p != j && tid < nbp) {
+      C* col = sP + tid * m;
+      const C t = col[j];
+      col[j] = col[p];
+      col[p] = t;
+    }
+    __syncthreads();
+    const C pv = Pj[j];
+    const bool zero = (pv.x == R(0) && pv.y == R(0));
+    if (zero) flags |= LSMS_UNIT_ZERO_PIVOT;
+    if (!finite2(pv)) flags |= LSMS_UNIT_NONFINITE;
+    const C r = zero ? mk(R(0), R(0)) : crcp(pv);
+    for (int i = j + 1 + tid; i < m; i += nthr) {
+      const C l = cmul(Pj[i], r);
+      if (!zero) Pj[i] = l;
+      for (int c = j + 1; c < nbp; ++c) sP[c * m + i] = cfms(l, sP[c * m + j], sP[c * m + i]);
+    }
+    __syncthreads();
+  }
+  for (int c = 0; c < nbp; ++c)
+    for (int r = tid; r < m; r += nthr) A[(size_t)(k + c) * n + k + r] = sP[c * m + r];
+  if (tid == 0 && flags) atomicOr(&stat[u.stat_off], flags);
+}
+
 // ------------------------------------------------------------------ swap + trsm
 // One warp per column outside the panel; lane i holds rows k+i (+32 r).
 // Columns left of the panel only take the row swaps; columns to its right also
 // get U12 = L11^{-1} A12.
+constexpr int kSwapCols = 64;  // columns per CTA of k_swap_trsm (8 warps x 8)
+
 template <typename R, int NB>
 __global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ units, char* fac_base, int k) {
   using C = Cx<R>;
@@ -123,11 +210,14 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ unit
   const int n = u.n;
   if (k >= n) return;
   const int nbp = min(NB, n - k);
+  const int v0 = blockIdx.x * kSwapCols;           // virtual columns: [0, k) left, then right
+  const int n_virtual = n - nbp;
+  if (v0 >= n_virtual) return;
   C* A = reinterpret_cast<C*>(fac_base + u.fac_off);
   const int32_t* piv = reinterpret_cast<const int32_t*>(fac_base + u.piv_off);
   __shared__ C sL[NB][NB + 1];
   __shared__ int sp[NB];
-  const bool any_right = k + NB < n;
+  const bool any_right = (k + NB < n) && (v0 + kSwapCols > k);
   if (any_right) {
     for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
       const int i = idx % NB, j = idx / NB;
@@ -137,7 +227,7 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ unit
   for (int j = threadIdx.x; j < NB; j += blockDim.x) sp[j] = j < nbp ? piv[k + j] : k + j;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int v = blockIdx.x * (blockDim.x >> 5) + warp;  // virtual column: [0, k) left, then right
+  for (int v = v0 + warp; v < min(v0 + kSwapCols, n_virtual); v += blockDim.x >> 5) {
   int c;
   bool right;
   if (v < k) {
@@ -146,7 +236,6 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ unit
   } else {
     c = v - k + k + NB;
     right = true;
-    if (c >= n) return;
   }
   C* Ac = A + (size_t)c * n;
   C x[RPL];
@@ -229,6 +318,7 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ unit
     const int i = lane + 32 * r;
     if (i < nbp) Ac[k + i] = x[r];
   }
+  }  // column loop
 }
 
 // perm[i] = original row now at position i, iperm[perm[i]] = i.  One thread per unit.
@@ -315,7 +405,7 @@ __global__ void __launch_bounds__(256) k_gemm(const Unit* __restrict__ units, ch
 
 // ------------------------------------------------------------------ solve
 // X[i][c] -= sum_j A[i][k + j] sX[j][c] for rows i in [r0, r1): one thread per
-// (row, group of 8 right-hand sides); the NB column entries of A are loaded 8 at
+// (row, group of 4 right-hand sides); the NB column entries of A are loaded 8 at
 // a time before use so that the loads overlap.
 template <typename R, int NB>
 __device__ __forceinline__ void update_rows(const Cx<R>* __restrict__ A, Cx<R>* X, const Cx<R> (*sX)[33], int n, int k,
@@ -344,6 +434,7 @@ __device__ __forceinline__ void update_rows(const Cx<R>* __restrict__ A, Cx<R>* 
       if (g + c < nrhs) X[(size_t)(g + c) * n + i] = acc[c];
   }
 }
+
 // One CTA of 512 threads per unit: L y = b (unit lower), then U x = y,
 // for the n x nrhs column-major block X whose rows are already permuted by P.
 // The NB x NB triangles are solved by warps taking columns in turn (lane = row, values
@@ -417,10 +508,25 @@ template <typename R>
 int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base, int32_t* stat,
                     cudaStream_t st) {
   constexpr int NB = LuCfg<R>::NB;
+  // panels up to kPanelSmemBytes stay in shared memory; taller ones use k_panel
+  constexpr int kPanelSmemBytes = 200 * 1024;
+  const int max_rows = kPanelSmemBytes / (NB * (int)sizeof(Cx<R>));
+  static bool attr_set = false;
+  if (!attr_set) {
+    LSMS_CUDA_TRY(cudaFuncSetAttribute(k_panel_smem<R, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kPanelSmemBytes));
+    attr_set = true;
+  }
   for (int k = 0; k < n_max; k += NB) {
-    LSMS_LAUNCH((k_panel<R, NB>), dim3(n_units), dim3(256), 0, st, d_units, fac_base, k, stat);
+    const int m_max = n_max - k;
+    if (m_max > max_rows)
+      LSMS_LAUNCH((k_panel<R, NB>), dim3(n_units), dim3(256), 0, st, d_units, fac_base, k, stat, max_rows);
+    const int rows_smem = std::min(m_max, max_rows);
+    LSMS_LAUNCH((k_panel_smem<R, NB>), dim3(n_units), dim3(512), (size_t)rows_smem * NB * sizeof(Cx<R>), st,
+                d_units, fac_base, k, stat, max_rows);
     // one warp per column outside the panel: left ones [0, k), right ones [k + NB, n)
-    LSMS_LAUNCH((k_swap_trsm<R, NB>), dim3((n_max + 7) / 8, n_units), dim3(256), 0, st, d_units, fac_base, k);
+    LSMS_LAUNCH((k_swap_trsm<R, NB>), dim3((n_max + kSwapCols - 1) / kSwapCols, n_units), dim3(256), 0, st, d_units,
+                fac_base, k);
     const int trail = n_max - k - NB;
     if (trail <= 0) continue;
     if constexpr (std::is_same<R, float>::value) {
