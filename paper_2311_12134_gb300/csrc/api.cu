@@ -86,6 +86,7 @@ __constant__ int32_t c_cp_start[kMaxK * kMaxK + 1];
 __constant__ int32_t c_cp_lpp[kCpMax];
 __constant__ double c_cp_coef[kCpMax];
 __constant__ double c_ylm_norm[kMaxK3];
+__constant__ float2 c_ylm_norm_dd[kMaxK3];  // the same as (hi, lo) float pairs
 __constant__ int32_t c_l_of[kMaxK3];
 
 static std::mutex g_dev_mu;
@@ -108,6 +109,12 @@ static int ensure_device_tables(int dev) {
   LSMS_CUDA_TRY(cudaMemcpyToSymbol(c_cp_lpp, cp.lpp.data(), cp.lpp.size() * sizeof(int32_t)));
   LSMS_CUDA_TRY(cudaMemcpyToSymbol(c_cp_coef, cp.coef.data(), cp.coef.size() * sizeof(double)));
   LSMS_CUDA_TRY(cudaMemcpyToSymbol(c_ylm_norm, nrm.data(), nrm.size() * sizeof(double)));
+  std::vector<float2> nrm_dd(nrm.size());
+  for (size_t i = 0; i < nrm.size(); ++i) {
+    const float h = (float)nrm[i];
+    nrm_dd[i] = make_float2(h, (float)(nrm[i] - (double)h));
+  }
+  LSMS_CUDA_TRY(cudaMemcpyToSymbol(c_ylm_norm_dd, nrm_dd.data(), nrm_dd.size() * sizeof(float2)));
   LSMS_CUDA_TRY(cudaMemcpyToSymbol(c_l_of, lof.data(), lof.size() * sizeof(int32_t)));
   g_dev_init[dev] = true;
   return LSMS_OK;
@@ -352,6 +359,66 @@ __device__ void hankel6(double d, double2 z, double2* hp) {
   }
 }
 
+// The same two set-ups in double-float arithmetic on the FP32 pipes (mixed form):
+// only the square root, the reciprocal, sincos and exp stay in FP64.
+__device__ void ylm6_df(float2 x, float2 y, float2 z, float2* Y) {
+  float2 tr = make_float2(1.f, 0.f), ti = make_float2(0.f, 0.f);  // (x + i y)^m
+  float qmm_f = 1.f;                                               // (2m - 1)!! (exact in float)
+#pragma unroll
+  for (int m = 0; m <= kMaxL3; ++m) {
+    if (m > 0) {
+      const float2 nr = dd_sub(dd_mul(tr, x), dd_mul(ti, y));
+      ti = dd_add(dd_mul(tr, y), dd_mul(ti, x));
+      tr = nr;
+      qmm_f *= (float)(2 * m - 1);
+    }
+    const float2 qmm = make_float2(qmm_f, 0.f);
+    float2 q2 = make_float2(0.f, 0.f), q1 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int l = m; l <= kMaxL3; ++l) {
+      float2 q;
+      if (l == m) q = qmm;
+      else if (l == m + 1) q = dd_mulf(dd_mul(z, qmm), (float)(2 * m + 1));
+      else q = dd_mul(dd_sub(dd_mulf(dd_mul(z, q1), (float)(2 * l - 1)), dd_mulf(q2, (float)(l + m - 1))),
+                      dd_from(1.0 / (l - m)));
+      q2 = q1;
+      q1 = q;
+      const int L0 = l * l + l;
+      if (m == 0) {
+        Y[L0] = dd_mul(c_ylm_norm_dd[L0], q);
+      } else {
+        const float2 qc = dd_mul(c_ylm_norm_dd[L0 + m], q);
+        Y[L0 + m] = dd_mul(qc, tr);
+        Y[L0 - m] = dd_mul(qc, ti);
+      }
+    }
+  }
+}
+
+// hp[l] = mpref h_l(kappa d) in double-float; kappa and mpref of the energy given.
+__device__ void hankel6_df(double d, double2 kap, double2 mpref, bool adv, float4* hp) {
+  const double2 xx = mk(kap.x * d, kap.y * d);
+  const double2 ix = crcp(xx);
+  double sn, cs;
+  sincos(xx.x, &sn, &cs);
+  const double f = exp(adv ? xx.y : -xx.y);
+  const double2 ex = adv ? mk(f * cs, -f * sn) : mk(f * cs, f * sn);  // e^{-+ix}
+  const double2 hm64 = cmul(ex, ix);                                   // h_{-1}
+  const double2 h064 = adv ? mk(-hm64.y, hm64.x) : mk(hm64.y, -hm64.x);  // h_0
+  const float4 ixd = ddc(dd_from(ix.x), dd_from(ix.y));
+  const float4 mp = ddc(dd_from(mpref.x), dd_from(mpref.y));
+  float4 hm = ddc(dd_from(hm64.x), dd_from(hm64.y));
+  float4 h = ddc(dd_from(h064.x), dd_from(h064.y));
+  hp[0] = ddc_mul(mp, h);
+#pragma unroll
+  for (int l = 0; l < kMaxL3; ++l) {
+    const float4 hn = ddc_sub(ddc_mul(ddc_scalef(ixd, (float)(2 * l + 1)), h), hm);
+    hm = h;
+    h = hn;
+    hp[l + 1] = ddc_mul(mp, h);
+  }
+}
+
 // grid (S_max, atoms in the chunk), block 256: one CTA per row site p of one
 // atom's LIZ, for all energies of that atom.  Per round of 16 column sites q:
 // 16 lanes compute Y_L(R^) (shared by the energies), 32 lanes compute
@@ -375,7 +442,7 @@ __global__ void __launch_bounds__(256, 2) k_assemble(const Unit* __restrict__ un
   const int p = blockIdx.x;
   if (p >= u0.S) return;
   const int S = u0.S, n = u0.n;
-  __shared__ double sY[kAsmQ][kMaxK3];
+  __shared__ __align__(16) unsigned char sYraw[kAsmQ * kMaxK3 * 8];  // FP64 or double-float Y_L
   __shared__ double sD[kAsmQ];
   __shared__ __align__(16) unsigned char sVraw[kAsmE * kAsmQ * kMaxK3 * 16];
   // Gaunt coupling table in shared memory: threads index it divergently, which
@@ -426,24 +493,43 @@ __global__ void __launch_bounds__(256, 2) k_assemble(const Unit* __restrict__ un
           const double d = sqrt(rx * rx + ry * ry + rz * rz);
           const double id = 1.0 / d;
           sD[tid] = d;
-          ylm6(rx * id, ry * id, rz * id, sY[tid]);
+          if (MIXED)
+            ylm6_df(dd_from(rx * id), dd_from(ry * id), dd_from(rz * id),
+                    reinterpret_cast<float2*>(sYraw) + tid * kMaxK3);
+          else
+            ylm6(rx * id, ry * id, rz * id, reinterpret_cast<double*>(sYraw) + tid * kMaxK3);
         }
       }
       __syncthreads();
       if (tid < kAsmE * kAsmQ) {
         const int ee = tid / kAsmQ, qq = tid % kAsmQ, q = q0 + qq;
         if (ee < ne && qq < nq && q != p) {
-          double2 hp[kMaxL3 + 1];
-          hankel6(sD[qq], E.z[ua[e0 + ee].energy], hp);
           const int base = (ee * kAsmQ + qq) * kMaxK3;
+          if (MIXED) {
+            const double2 z = E.z[ua[e0 + ee].energy];
+            const double r = hypot(z.x, z.y);
+            const double kre = sqrt(0.5 * (r + z.x));
+            double kim = sqrt(0.5 * fmax(r - z.x, 0.0));
+            const bool adv = z.y < 0.0;
+            if (adv) kim = -kim;
+            const double four_pi = 4.0 * M_PI;
+            const double2 mpref = adv ? mk(four_pi * kim, -four_pi * kre) : mk(-four_pi * kim, four_pi * kre);
+            float4 hp[kMaxL3 + 1];
+            hankel6_df(sD[qq], mk(kre, kim), mpref, adv, hp);
+            const float2* Yq = reinterpret_cast<const float2*>(sYraw) + qq * kMaxK3;
 #pragma unroll
-          for (int l = 0; l <= kMaxL3; ++l)
-            for (int Lpp = l * l; Lpp < (l + 1) * (l + 1); ++Lpp) {
-              const double y = sY[qq][Lpp];
-              const double2 v = mk(hp[l].x * y, hp[l].y * y);
-              if (MIXED) reinterpret_cast<float4*>(sVraw)[base + Lpp] = df_split(v);
-              else reinterpret_cast<double2*>(sVraw)[base + Lpp] = v;
-            }
+            for (int l = 0; l <= kMaxL3; ++l)
+              for (int Lpp = l * l; Lpp < (l + 1) * (l + 1); ++Lpp)
+                reinterpret_cast<float4*>(sVraw)[base + Lpp] = ddc_scale(hp[l], Yq[Lpp]);
+          } else {
+            double2 hp[kMaxL3 + 1];
+            hankel6(sD[qq], E.z[ua[e0 + ee].energy], hp);
+            const double* Yq = reinterpret_cast<const double*>(sYraw) + qq * kMaxK3;
+#pragma unroll
+            for (int l = 0; l <= kMaxL3; ++l)
+              for (int Lpp = l * l; Lpp < (l + 1) * (l + 1); ++Lpp)
+                reinterpret_cast<double2*>(sVraw)[base + Lpp] = mk(hp[l].x * Yq[Lpp], hp[l].y * Yq[Lpp]);
+          }
         }
       }
       __syncthreads();

@@ -152,6 +152,50 @@ __device__ __forceinline__ float4 df_value(const DfAcc& a) {
   return make_float4(rh, a.tr - (rh - a.sr), ih, a.ti - (ih - a.si));
 }
 
+// Real double-float values (hi, lo) as float2, normalised (|lo| <= ulp(hi) / 2).
+__device__ __forceinline__ float2 dd_from(double a) {
+  const float h = (float)a;
+  return make_float2(h, (float)(a - (double)h));
+}
+__device__ __forceinline__ float2 dd_norm(float s, float t) {  // fast two-sum, |s| >= |t|
+  const float h = s + t;
+  return make_float2(h, t - (h - s));
+}
+__device__ __forceinline__ float2 dd_add(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float bb = s - a.x;
+  const float e = (a.x - (s - bb)) + (b.x - bb) + a.y + b.y;
+  return dd_norm(s, e);
+}
+__device__ __forceinline__ float2 dd_sub(float2 a, float2 b) { return dd_add(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 dd_mul(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  return dd_norm(p, e);
+}
+// a * f with f a float (exact small integers in the recurrences)
+__device__ __forceinline__ float2 dd_mulf(float2 a, float f) {
+  const float p = a.x * f;
+  float e = fmaf(a.x, f, -p);
+  e = fmaf(a.y, f, e);
+  return dd_norm(p, e);
+}
+// complex double-float as float4 (re.hi, re.lo, im.hi, im.lo)
+__device__ __forceinline__ float4 ddc(float2 re, float2 im) { return make_float4(re.x, re.y, im.x, im.y); }
+__device__ __forceinline__ float2 ddc_re(float4 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 ddc_im(float4 a) { return make_float2(a.z, a.w); }
+__device__ __forceinline__ float4 ddc_mul(float4 a, float4 b) {
+  return ddc(dd_sub(dd_mul(ddc_re(a), ddc_re(b)), dd_mul(ddc_im(a), ddc_im(b))),
+             dd_add(dd_mul(ddc_re(a), ddc_im(b)), dd_mul(ddc_im(a), ddc_re(b))));
+}
+__device__ __forceinline__ float4 ddc_sub(float4 a, float4 b) {
+  return ddc(dd_sub(ddc_re(a), ddc_re(b)), dd_sub(ddc_im(a), ddc_im(b)));
+}
+__device__ __forceinline__ float4 ddc_scale(float4 a, float2 s) { return ddc(dd_mul(ddc_re(a), s), dd_mul(ddc_im(a), s)); }
+__device__ __forceinline__ float4 ddc_scalef(float4 a, float f) { return ddc(dd_mulf(ddc_re(a), f), dd_mulf(ddc_im(a), f)); }
+
 // ------------------------------------------------------------------ wrappers (lu.cu)
 // Blocked right-looking LU with partial pivoting of every unit of a chunk, in
 // place in the factor arrays (column-major, ld = n).  Pivots are applied to
