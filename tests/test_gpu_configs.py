@@ -139,3 +139,23 @@ def test_fcc500_adjoint_central_differences(B):
             fd = (sigma_xx(tp) - sigma_xx(tm)) / (2 * h)
             ref = G.real if part == "re" else G.imag
             assert abs(fd - ref) < 1e-5 * gmax, (i, e, a, b, part, fd, ref, gmax)
+
+
+def test_liz_radius_sweep_and_extrapolation(B):
+    """The LIZ-radius sweep of the 16,000-site bcc recipe (1.85a, 2.2a, 2.5a: 59, 89
+    and 137 sites) on a 6x6x6-cell supercell of the same recipe, mixed form, then the
+    lower/upper-bound extrapolations of Sec. IV on rho_xx(r)."""
+    from paper_2311_12134_gb300 import extrapolate as ex
+    radii, rho = [], []
+    for roa in (1.85, 2.2, 2.5):
+        w = wl.bcc_large_16000(r_over_a=roa, n_cells=6)
+        lz, tau, st, sig = _run(B, w, "mixed")
+        assert np.all((st & 0xff) == 0)
+        assert lz.max_sites == {1.85: 59, 2.2: 89, 2.5: 137}[roa]
+        radii.append(w.r_liz)
+        rho.append(float(ex.resistivity_xx(sig[0])))
+        del tau
+        torch.cuda.empty_cache()
+    c0, c1 = ex.fit_lower_bound(radii, rho)
+    b0, b1 = ex.fit_upper_bound(radii, rho, two_alpha=0.15)
+    assert np.all(np.isfinite([c0, c1, b0, b1]))
