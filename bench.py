@@ -390,10 +390,14 @@ def run_ours(args):
     if rank != 0:
         return 0
     pk = peaks()
-    n_list = [w.K * s for s in np.repeat(np.diff(main_offsets(w)), len(w.z))]
-    fwd_passes = (status >> 8).reshape(-1).astype(np.float64)
-    bwd_passes = (bw_status >> 8).reshape(-1).astype(np.float64)
-    roof, roof_all = roofline(kt, w, n_list, np.sort(fwd_passes), np.sort(bwd_passes), args.precision,
+    # one n per unit, energy-major like the unit status words
+    n_list = [w.K * s for s in np.tile(np.diff(main_offsets(w)), len(w.z))]
+    # unit status: bits 8-15 refinement sweeps, bits 16-23 convergence probes
+    fwd_passes = ((status >> 8) & 0xff).reshape(-1).astype(np.float64)
+    bwd_passes = ((bw_status >> 8) & 0xff).reshape(-1).astype(np.float64)
+    fwd_probes = ((status >> 16) & 0xff).reshape(-1).astype(np.float64)
+    bwd_probes = ((bw_status >> 16) & 0xff).reshape(-1).astype(np.float64)
+    roof, roof_all = roofline(kt, w, n_list, (fwd_passes, fwd_probes), (bwd_passes, bwd_probes), args.precision,
                               load_traffic())
     cpu = None
     acc = None
@@ -417,8 +421,9 @@ def run_ours(args):
         "timing": "CUDA-graph replay of the whole step (forward + adjoint), CUDA events on the launch stream",
         "effective_tflops": units * world * (lu_flops([688]) ) / (ms * 1e-3) / 1e12,
         "unit_status_clean": bool(((status & 0xff) == 0).all()),
-        "ir_passes_mean": float((status >> 8).mean()), "ir_passes_max": int((status >> 8).max()),
-        "ir_passes_adjoint_mean": float((bw_status >> 8).mean()),
+        "ir_passes_mean": float(fwd_passes.mean()), "ir_passes_max": int(fwd_passes.max()),
+        "ir_passes_adjoint_mean": float(bwd_passes.mean()),
+        "ir_probes_mean": float(fwd_probes.mean()), "ir_probes_adjoint_mean": float(bwd_probes.mean()),
         "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
         "kernels": roof_all,
         "cpu_baseline": cpu, "fp64_form": fp64, "accuracy_vs_oracle": acc,
@@ -455,6 +460,8 @@ FP64_PEAK_TFLOPS = 1.25
 # Double-float complex multiply-accumulate: 4 real products x 11 FP32 ops
 # (FMA two-product 2, cross terms 2, two-sum 6, carry 1).
 DF_OPS_PER_CMAC = 44.0
+# columns of the convergence probe after each refinement sweep (mixed form)
+PROBES = 2
 
 
 def kernel_models(w, n_list, fwd_passes, bwd_passes, precision, nb=32):
@@ -474,15 +481,23 @@ def kernel_models(w, n_list, fwd_passes, bwd_passes, precision, nb=32):
                           gemm_bytes([int(x) for x in n_list], nb))
     else:
         m["k_gemm"] = (gemm_flops([int(x) for x in n_list], nb), simt_peak, "complex trailing update, FP64 DFMA pipe")
-    # each solve: forward + backward substitution = n^2 complex MACs per right-hand side
-    fwd_solves = (1 + fwd_passes) if mixed else np.ones_like(n)
-    bwd_solves = (1 + bwd_passes) if mixed else np.ones_like(n)
-    m["k_solve"] = (float(np.sum(8.0 * n * n * (K * fwd_solves + 2 * K * bwd_solves))), simt_peak,
-                    "triangular solves")
+    # each solve: forward + backward substitution = n^2 complex MACs per right-hand side;
+    # a refinement sweep solves for all columns, a convergence probe for PROBES columns
+    fwd_passes, fwd_probes = fwd_passes
+    bwd_passes, bwd_probes = bwd_passes
     if mixed:
-        m["k_residual"] = (float(np.sum(8.0 * n * n * (K * fwd_passes + 2 * K * bwd_passes))),
-                           8.0 * FP32_OPS / DF_OPS_PER_CMAC / 1e12,
+        rhs = K * (1 + fwd_passes) + 2 * K * (1 + bwd_passes) + PROBES * (fwd_probes + bwd_probes)
+    else:
+        rhs = 3.0 * K * np.ones_like(n)
+    m["k_solve"] = (float(np.sum(8.0 * n * n * rhs)), simt_peak, "triangular solves")
+    if mixed:
+        df_peak = 8.0 * FP32_OPS / DF_OPS_PER_CMAC / 1e12
+        m["k_residual"] = (float(np.sum(8.0 * n * n * (K * fwd_passes + 2 * K * bwd_passes))), df_peak,
                            "FP64-accurate residual in double-float FP32 arithmetic (44 FP32 ops per complex MAC)")
+        # probe residual: PROBES columns; reads M (16 bytes per complex entry, hi/lo float pairs) once
+        m["k_probe_residual"] = (float(np.sum(8.0 * n * n * PROBES * (fwd_probes + bwd_probes))), df_peak,
+                                 "convergence-probe residual, double-float (2 columns)",
+                                 float(np.sum(16.0 * n * n * (fwd_probes + bwd_probes))))
     # assembly: 708 nonzero Gaunt couplings x (complex x real) per off-diagonal block, forward
     # (and the backward's re-assembly of the FP64 copy in the mixed form)
     blocks = float(np.sum(S * (S - 1)))
@@ -519,7 +534,7 @@ def roofline(kt, w, n_list, fwd_passes, bwd_passes, precision, traffic):
             if gbs / PEAKS["hbm_gbs"] > row["frac"]:
                 row.update({"bound": "hbm", "achieved": gbs, "peak": PEAKS["hbm_gbs"], "unit": "GB/s",
                             "frac": gbs / PEAKS["hbm_gbs"]})
-            row["tensor_frac"] = ach / peak
+            row["tensor_frac" if base == "k_gemm_tc" else "alu_frac"] = ach / peak
         rows[base] = row
     for name, (ms, launches) in kt.items():  # unmodelled kernels: time only
         base = name.split("<")[0]

@@ -134,8 +134,16 @@ int lsms_gaunt_table(int lmax, double* C);
  * tau          dev [n_energy][S_total][K][K] output: tau[e][s] = tau^{s 0} of
  *              the LIZ that site s belongs to (row L, column L').
  * unit_status  dev [n_energy][n_atoms] int32 output, or NULL: bits 0-7 the
- *              LSMS_UNIT_* flags, bits 8-15 the number of refinement sweeps
- *              (mixed form; 0 for FP64).
+ *              LSMS_UNIT_* flags, bits 8-15 the number of refinement sweeps,
+ *              bits 16-23 the number of convergence probes (mixed form; both 0
+ *              for FP64).  Mixed form: a sweep adds the complex64 correction
+ *              D = (LU)^-1 (B - M X) (residual in double-float, ~2^-48) to X and
+ *              stops when ||D||_F <= 1e-10 ||X||_F; after each sweep a probe
+ *              takes the same test on 2 random +-1 combinations of the columns
+ *              (y = X w: ||(LU)^-1 (B w - M y)|| <= 1e-10 ||y||) and stops
+ *              there when both pass, so X carries the correction test's error
+ *              bound without a further full sweep.  LSMS_UNIT_NOCONV after 6
+ *              sweeps.
  * workspace    dev scratch of workspace_bytes (>= lsms_tau_workspace_bytes for
  *              one unit); the units are processed in chunks that fit it.  NULL
  *              = the library allocates (stream-ordered) and frees it.

@@ -77,6 +77,7 @@ int adj_species(const int32_t* species, const double2* grad, int K, int n_atoms,
 
 constexpr int kIrMaxIter = 6;
 constexpr double kIrTol = 1e-10;
+constexpr int kProbe = 2;  // random combinations of the right-hand sides in the convergence probe
 constexpr size_t kAlign = 256;
 static inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -165,7 +166,7 @@ int existing_device_data(lsms_liz* liz, DeviceData** out) {
 
 // ------------------------------------------------------------------ plans
 struct UnitBytes {
-  size_t fac, piv, m64, x, b, x32;
+  size_t fac, piv, m64, x, b, x32, probe;
 };
 
 static UnitBytes unit_bytes(int n, int precision, int nrhs, bool backward) {
@@ -176,12 +177,14 @@ static UnitBytes unit_bytes(int n, int precision, int nrhs, bool backward) {
   ub.m64 = precision == LSMS_FP64 ? 0 : align_up(nn * 16);
   ub.x = align_up((size_t)n * nrhs * 16);
   ub.b = backward ? align_up((size_t)n * nrhs * 16) : 0;
-  ub.x32 = precision == LSMS_FP64 ? 0 : align_up((size_t)n * nrhs * 8);
+  // complex64 corrections; the convergence probe uses the first kProbe columns
+  ub.x32 = precision == LSMS_FP64 ? 0 : align_up((size_t)n * std::max(nrhs, kProbe) * 8);
+  ub.probe = precision == LSMS_FP64 ? 0 : align_up((size_t)n * kProbe * 2 * 16);  // y_q and (B w)_q
   return ub;
 }
 
 static size_t ws_unit_bytes(const UnitBytes& ub, bool store) {
-  return (store ? 0 : ub.fac + ub.piv) + ub.m64 + ub.x + ub.b + ub.x32;
+  return (store ? 0 : ub.fac + ub.piv) + ub.m64 + ub.x + ub.b + ub.x32 + ub.probe;
 }
 
 // Atoms sorted by LIZ size (largest first, then atom index); every energy of an atom is adjacent.
@@ -277,6 +280,8 @@ static int get_plan(lsms_liz* liz, DeviceData* dd, int lmax, int n_energy, int p
       cur += ub.b;
       u.x32_off = (int64_t)cur;
       cur += ub.x32;
+      u.p_off = (int64_t)cur;
+      cur += ub.probe;
       u.stat_off = (int64_t)e * liz->n_atoms + m;  // index of this unit's status word
       ch.n_max = std::max(ch.n_max, n);
       p.units.push_back(u);
@@ -714,22 +719,65 @@ __global__ void __launch_bounds__(256, 3) k_residual(const Unit* __restrict__ un
   }
 }
 
+// Probe weights w_q[c] = +-1, from the integer hash "lowbias32" (C. Wellons) of
+// (unit, sweep, q, c): a fixed pseudo-random sign pattern per unit and sweep.
+__device__ __forceinline__ double probe_sign(int64_t unit, int sweep, int q, int c) {
+  uint32_t h = (uint32_t)(((unit * 16 + sweep) * 4 + q) * 64 + c);
+  h ^= h >> 16;
+  h *= 0x7feb352du;
+  h ^= h >> 15;
+  h *= 0x846ca68bu;
+  h ^= h >> 16;
+  return (h & 1u) ? 1.0 : -1.0;
+}
+
 // X += X32 (the correction); done when ||correction||_F <= tol ||X||_F.  One CTA
 // per unit.  Each sweep adds 1 << 8 to the unit's status word (pass count).
-__global__ void __launch_bounds__(256) k_ir_update(const Unit* __restrict__ units, char* ws, int nrhs, double tol,
-                                                   int32_t* done, int32_t* stat) {
+// Mixed form: also forms the convergence-probe inputs y_q = X w_q and
+// (B w)_q for kProbe sign vectors w_q (FP64; the sums are exact up to rounding),
+// stored as [q][n] complex128 at p_off and p_off + kProbe n.
+__global__ void __launch_bounds__(256) k_ir_update(const Unit* __restrict__ units, char* ws, int nrhs, int K,
+                                                   bool explicit_b, int sweep, double tol, int32_t* done,
+                                                   int32_t* stat) {
   const Unit u = units[blockIdx.x];
   if (done[u.stat_off]) return;
   const int n = u.n;
   const float2* D = reinterpret_cast<const float2*>(ws + u.x32_off);
   double2* X = reinterpret_cast<double2*>(ws + u.x_off);
+  const double2* B = reinterpret_cast<const double2*>(ws + u.r_off);
+  double2* Y = reinterpret_cast<double2*>(ws + u.p_off);
+  double2* BW = Y + (size_t)kProbe * n;
+  __shared__ double sw[kProbe][64];
+  for (int idx = threadIdx.x; idx < kProbe * 64; idx += blockDim.x)
+    sw[idx / 64][idx % 64] = probe_sign(u.stat_off, sweep, idx / 64, idx % 64);
+  __syncthreads();
   double dn = 0.0, xn = 0.0;
-  for (int64_t idx = threadIdx.x; idx < (int64_t)n * nrhs; idx += blockDim.x) {
-    const double2 d = to64(D[idx]);
-    const double2 x = cadd(X[idx], d);
-    X[idx] = x;
-    dn += d.x * d.x + d.y * d.y;
-    xn += x.x * x.x + x.y * x.y;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double2 y[kProbe], bw[kProbe];
+#pragma unroll
+    for (int q = 0; q < kProbe; ++q) y[q] = bw[q] = mk(0.0, 0.0);
+    for (int c = 0; c < nrhs; ++c) {
+      const size_t idx = (size_t)c * n + i;
+      const double2 d = to64(D[idx]);
+      const double2 x = cadd(X[idx], d);
+      X[idx] = x;
+      dn += d.x * d.x + d.y * d.y;
+      xn += x.x * x.x + x.y * x.y;
+      const double2 b = explicit_b ? B[idx] : mk(0.0, 0.0);
+#pragma unroll
+      for (int q = 0; q < kProbe; ++q) {
+        const double s = sw[q][c & 63];
+        y[q] = mk(y[q].x + s * x.x, y[q].y + s * x.y);
+        if (explicit_b) bw[q] = mk(bw[q].x + s * b.x, bw[q].y + s * b.y);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kProbe; ++q) {
+      // B = E0 (forward): (B w)_i = w_i for i < K
+      if (!explicit_b && i < K && i < nrhs) bw[q] = mk(sw[q][i], 0.0);
+      Y[(size_t)q * n + i] = y[q];
+      BW[(size_t)q * n + i] = bw[q];
+    }
   }
   __shared__ double s1[256], s2[256];
   s1[threadIdx.x] = dn;
@@ -751,6 +799,146 @@ __global__ void __launch_bounds__(256) k_ir_update(const Unit* __restrict__ unit
     } else if (a <= tol * tol * b) {
       done[u.stat_off] = 1;
     }
+  }
+}
+
+// Convergence probe, residual half: r_q = (B w)_q - M y_q for the kProbe vectors
+// of k_ir_update, double-float as in k_residual, rounded to complex64 and
+// permuted by P into X32 columns q = 0..kProbe-1 for the probe correction solve.
+// grid (ceil(n_max / 64), n_units), block 256: 64 rows x 4 quarters of each
+// 128-column slab of M, the quarters' partial sums added in shared memory.
+__global__ void __launch_bounds__(256, 3) k_probe_residual(const Unit* __restrict__ units, const char* fac_base,
+                                                           char* ws, const int32_t* __restrict__ done) {
+  const Unit u = units[blockIdx.y];
+  if (done[u.stat_off]) return;
+  const int n = u.n;
+  const int row0 = blockIdx.x * 64;
+  if (row0 >= n) return;
+  const float4* M = reinterpret_cast<const float4*>(ws + u.m64_off);
+  const double2* Y = reinterpret_cast<const double2*>(ws + u.p_off);
+  const double2* BW = Y + (size_t)kProbe * n;
+  const int32_t* iperm = reinterpret_cast<const int32_t*>(fac_base + u.piv_off) + 2 * n;
+  float2* X32 = reinterpret_cast<float2*>(ws + u.x32_off);
+  __shared__ float4 sY[128][kProbe];
+  __shared__ float4 sPart[3][kProbe][64];
+  const int tid = threadIdx.x;
+  const int r = tid & 63, grp = tid >> 6;
+  const int row = row0 + r;
+  const bool live = row < n;
+  const float4* Mrow = M + (live ? row : 0);
+  float sr[kProbe], tr[kProbe], si[kProbe], ti[kProbe];
+#pragma unroll
+  for (int q = 0; q < kProbe; ++q) sr[q] = tr[q] = si[q] = ti[q] = 0.f;
+  for (int j0 = 0; j0 < n; j0 += 128) {
+    const int jn = min(128, n - j0);
+    __syncthreads();
+    for (int idx = tid; idx < 128 * kProbe; idx += 256) {
+      const int jj = idx & 127, q = idx >> 7;
+      sY[jj][q] = jj < jn ? df_split(Y[(size_t)q * n + j0 + jj]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    if (live) {
+      const int ja = grp * 32, jb = min(ja + 32, jn);
+      if (jb - ja == 32) {
+#pragma unroll 4
+        for (int jj = ja; jj < ja + 32; ++jj) {
+          const float4 m = Mrow[(size_t)(j0 + jj) * n];
+#pragma unroll
+          for (int q = 0; q < kProbe; ++q) {
+            const float4 x = sY[jj][q];
+            df_mac(sr[q], tr[q], m.x, m.z, x.x, x.y);
+            df_mac(sr[q], tr[q], -m.y, -m.w, x.z, x.w);
+            df_mac(si[q], ti[q], m.x, m.z, x.z, x.w);
+            df_mac(si[q], ti[q], m.y, m.w, x.x, x.y);
+          }
+        }
+      } else {
+        for (int jj = ja; jj < jb; ++jj) {
+          const float4 m = Mrow[(size_t)(j0 + jj) * n];
+#pragma unroll
+          for (int q = 0; q < kProbe; ++q) {
+            const float4 x = sY[jj][q];
+            df_mac(sr[q], tr[q], m.x, m.z, x.x, x.y);
+            df_mac(sr[q], tr[q], -m.y, -m.w, x.z, x.w);
+            df_mac(si[q], ti[q], m.x, m.z, x.z, x.w);
+            df_mac(si[q], ti[q], m.y, m.w, x.x, x.y);
+          }
+        }
+      }
+    }
+  }
+  if (grp > 0) {
+#pragma unroll
+    for (int q = 0; q < kProbe; ++q) sPart[grp - 1][q][r] = make_float4(sr[q], tr[q], si[q], ti[q]);
+  }
+  __syncthreads();
+  if (grp == 0 && live) {
+    const int pos = iperm[row];
+#pragma unroll
+    for (int q = 0; q < kProbe; ++q) {
+#pragma unroll
+      for (int g = 0; g < 3; ++g) {
+        const float4 a = sPart[g][q][r];
+        df_add(sr[q], tr[q], a.x);
+        tr[q] += a.y;
+        df_add(si[q], ti[q], a.z);
+        ti[q] += a.w;
+      }
+      const double2 b = BW[(size_t)q * n + row];
+      const double re = b.x - ((double)sr[q] + (double)tr[q]);
+      const double im = b.y - ((double)si[q] + (double)ti[q]);
+      X32[(size_t)q * n + pos] = make_float2((float)re, (float)im);
+    }
+  }
+}
+
+// Convergence probe, test half: X32 columns q now hold the corrections d_q that
+// the next sweep would add to y_q = X w_q.  The unit is done when every
+// ||d_q|| <= tol ||y_q||: E||D w||^2 = 2 ||D||_F^2 and E||X w||^2 = 2 ||X||_F^2
+// for random signs w, so this is the sweep test of k_ir_update taken on
+// kProbe random combinations of the columns.  Adds 1 << 16 to the status word.
+__global__ void __launch_bounds__(256) k_probe_check(const Unit* __restrict__ units, const char* ws, double tol,
+                                                     int32_t* done, int32_t* stat) {
+  const Unit u = units[blockIdx.x];
+  if (done[u.stat_off]) return;
+  const int n = u.n;
+  const float2* D = reinterpret_cast<const float2*>(ws + u.x32_off);
+  const double2* Y = reinterpret_cast<const double2*>(ws + u.p_off);
+  double dn[kProbe], yn[kProbe];
+#pragma unroll
+  for (int q = 0; q < kProbe; ++q) dn[q] = yn[q] = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < kProbe; ++q) {
+      const double2 d = to64(D[(size_t)q * n + i]);
+      const double2 y = Y[(size_t)q * n + i];
+      dn[q] += d.x * d.x + d.y * d.y;
+      yn[q] += y.x * y.x + y.y * y.y;
+    }
+  }
+  __shared__ double s[2 * kProbe][256];
+#pragma unroll
+  for (int q = 0; q < kProbe; ++q) {
+    s[2 * q][threadIdx.x] = dn[q];
+    s[2 * q + 1][threadIdx.x] = yn[q];
+  }
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+#pragma unroll
+      for (int k = 0; k < 2 * kProbe; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(&stat[u.stat_off], 1 << 16);
+    bool pass = true;
+#pragma unroll
+    for (int q = 0; q < kProbe; ++q) {
+      const double a = s[2 * q][0], b = s[2 * q + 1][0];
+      if (!isfinite(a) || !isfinite(b) || a > tol * tol * b) pass = false;
+    }
+    if (pass) done[u.stat_off] = 1;
   }
 }
 
@@ -851,7 +1039,12 @@ static int solve_refine(const Call& c, const Plan& p, const Chunk& ch, const cha
       default: return fail(LSMS_ERR_ARG, "internal: no residual kernel for %d right-hand sides", nrhs);
     }
     if ((rc = lu_solve_chunk<float>(du, nu, fac_base, ws, RHS_X32, nrhs, done, c.st))) return rc;
-    LSMS_LAUNCH(k_ir_update, dim3(nu), dim3(256), 0, c.st, du, ws, nrhs, kIrTol, done, stat);
+    LSMS_LAUNCH(k_ir_update, dim3(nu), dim3(256), 0, c.st, du, ws, nrhs, c.K, explicit_b, it, kIrTol, done,
+                stat);
+    // probe: would the next sweep's correction pass the test?  If so, stop here.
+    LSMS_LAUNCH(k_probe_residual, gr, dim3(256), 0, c.st, du, fac_base, ws, done);
+    if ((rc = lu_solve_chunk<float>(du, nu, fac_base, ws, RHS_X32, kProbe, done, c.st))) return rc;
+    LSMS_LAUNCH(k_probe_check, dim3(nu), dim3(256), 0, c.st, du, ws, kIrTol, done, stat);
   }
   LSMS_LAUNCH(k_ir_finish, dim3((nu + 255) / 256), dim3(256), 0, c.st, du, nu, done, stat);
   return LSMS_OK;

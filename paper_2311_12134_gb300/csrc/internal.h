@@ -36,6 +36,7 @@ struct Unit {
   int64_t x_off;     // byte offset of the n x RHS complex128 solution block (workspace)
   int64_t r_off;     // byte offset of the n x RHS complex128 residual block (workspace)
   int64_t x32_off;   // byte offset of the n x RHS complex64 scratch (workspace)
+  int64_t p_off;     // byte offset of the convergence-probe vectors (mixed form, workspace)
   int64_t stat_off;  // index into the per-unit scratch scalars
 };
 

@@ -68,7 +68,8 @@ def test_bcc2000_uneven_three_deltas(B):
     sizes = lz.sizes
     assert sizes.min() < sizes.max()                       # uneven LIZ sizes
     assert np.all((st_m & 0xff) == 0)
-    assert (st_m >> 8).max() <= 6
+    assert ((st_m >> 8) & 0xff).max() <= 6
+    assert ((st_m >> 16) & 0xff).max() <= 6
     atoms = [int(np.argmax(sizes)), int(np.argmin(sizes)), 1234]
     _check_sampled(w, lz, tau_m, atoms, TOL["mixed"])
     del tau_m
