@@ -491,6 +491,8 @@ def kernel_models(w, n_list, fwd_passes, bwd_passes, precision, nb=32):
         rhs = 3.0 * K * np.ones_like(n)
     m["k_solve"] = (float(np.sum(8.0 * n * n * rhs)), simt_peak, "triangular solves")
     if mixed:
+        m["k_solve_c64"] = m.pop("k_solve")
+    if mixed:
         df_peak = 8.0 * FP32_OPS / DF_OPS_PER_CMAC / 1e12
         m["k_residual"] = (float(np.sum(8.0 * n * n * (K * fwd_passes + 2 * K * bwd_passes))), df_peak,
                            "FP64-accurate residual in double-float FP32 arithmetic (44 FP32 ops per complex MAC)")
@@ -519,9 +521,19 @@ def roofline(kt, w, n_list, fwd_passes, bwd_passes, precision, traffic):
     if not kt:
         return None, None
     models = kernel_models(w, n_list, fwd_passes, bwd_passes, precision)
-    rows = {}
+    # one row per kernel: the template instances (right-hand-side counts etc.) summed
+    merged = {}
     for name, (ms, launches) in kt.items():
         base = name.split("<")[0]
+        tot = merged.setdefault(base, [base, 0.0, 0.0, []])
+        tot[1] += ms
+        tot[2] += launches
+        tot[3].append(name)
+    kt = {v[0]: (v[1], v[2]) for v in merged.values()}
+    instances = {v[0]: v[3] for v in merged.values()}
+    rows = {}
+    for name, (ms, launches) in kt.items():
+        base = name
         if base not in models:
             continue
         flops, peak, what = models[base][:3]
@@ -535,11 +547,12 @@ def roofline(kt, w, n_list, fwd_passes, bwd_passes, precision, traffic):
                 row.update({"bound": "hbm", "achieved": gbs, "peak": PEAKS["hbm_gbs"], "unit": "GB/s",
                             "frac": gbs / PEAKS["hbm_gbs"]})
             row["tensor_frac" if base == "k_gemm_tc" else "alu_frac"] = ach / peak
+        row["instances"] = instances[base]
         rows[base] = row
     for name, (ms, launches) in kt.items():  # unmodelled kernels: time only
-        base = name.split("<")[0]
-        if base not in rows:
-            rows[base] = {"kernel": name, "ms_per_step": ms, "launches_per_step": launches}
+        if name not in rows:
+            rows[name] = {"kernel": name, "ms_per_step": ms, "launches_per_step": launches,
+                          "instances": instances[name]}
     modelled = [r for r in rows.values() if "frac" in r]
     if not modelled:
         return None, rows

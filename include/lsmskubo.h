@@ -148,7 +148,8 @@ int lsms_gaunt_table(int lmax, double* C);
  *              one unit); the units are processed in chunks that fit it.  NULL
  *              = the library allocates (stream-ordered) and frees it.
  * lu_store     dev buffer of lu_store_bytes (lsms_lu_store_bytes) that keeps the
- *              factors for lsms_kubo_sigma_backward, or NULL.
+ *              factors and pivots (mixed form: also M as double-float pairs) for
+ *              lsms_kubo_sigma_backward, or NULL.
  * stream       cudaStream_t (NULL = legacy default stream).
  */
 int lsms_tau_workspace_bytes(const lsms_liz* liz, int lmax, int n_energy, int precision,
@@ -170,14 +171,18 @@ int lsms_tau_blocks(const lsms_liz* liz, int lmax, const int32_t* species, int n
  *              broadening d; stride 0 = the same J for every delta).
  * tau          dev output of lsms_tau_blocks with n_energy = 2 n_delta.
  * volume       supercell volume N Omega (bohr^3).
+ * precision    LSMS_FP64: the K x K products in FP64.  LSMS_MIXED: the K x K
+ *              products and the site sums in double-float arithmetic on the FP32
+ *              pipes (unit roundoff about 2^-48); the last trace, the sums over
+ *              atoms and sigma, rho in FP64 in both.
  * sigma_tilde  dev [n_delta][4][3][3] output or NULL.
  * sigma        dev [n_delta][3][3] output.
  * rho          dev [n_delta][3][3] double output or NULL.
  * Reductions over atoms are in a fixed order (bitwise reproducible). */
 int lsms_kubo_sigma(const lsms_liz* liz, int lmax, const int32_t* species, int n_species,
                     const lsms_complex* J, int64_t J_delta_stride, const lsms_complex* tau,
-                    int n_delta, double volume, lsms_complex* sigma_tilde, lsms_complex* sigma,
-                    double* rho, void* stream);
+                    int n_delta, double volume, int precision, lsms_complex* sigma_tilde,
+                    lsms_complex* sigma, double* rho, void* stream);
 
 /* Same computation and arguments as lsms_kubo_sigma, for callers that cannot
  * allocate device memory during the call: code that must not trigger cudaMalloc
@@ -201,7 +206,7 @@ int lsms_kubo_sigma(const lsms_liz* liz, int lmax, const int32_t* species, int n
  *    scratch element it reads, so nothing is carried over between calls. */
 int lsms_kubo_sigma_noalloc(const lsms_liz* liz, int lmax, const int32_t* species, int n_species,
                             const lsms_complex* J, int64_t J_delta_stride, const lsms_complex* tau,
-                            int n_delta, double volume, lsms_complex* sigma_tilde,
+                            int n_delta, double volume, int precision, lsms_complex* sigma_tilde,
                             lsms_complex* sigma, double* rho, void* stream);
 
 /* ---------------------------------------------------------------- gradient
@@ -211,8 +216,9 @@ int lsms_kubo_sigma_noalloc(const lsms_liz* liz, int lmax, const int32_t* specie
  * the PyTorch gradient of the real loss Re f with respect to a per-site t^{-1}
  * at energy z_e (all periodic images of atom i summed).  It uses
  * d tau = -tau dM tau (from Eq. tau-inverse) with one 2K-column solve per
- * (atom, energy), reusing the LU factors from lu_store when given (same
- * precision, same inputs), else recomputing them in the workspace.
+ * (atom, energy), reusing the LU factors (and, mixed form, the double-float M
+ * of the refinement residual) from lu_store when given (same precision, same
+ * inputs), else recomputing them in the workspace.
  * grad_tinv    dev [n_energy][n_atoms][K][K] output.
  * grad_tinv_species  dev [n_species][n_energy][K][K] output (the same gradient
  *              summed over the atoms of each species, i.e. with respect to the

@@ -42,8 +42,8 @@ SIGNATURES = {
     "lsms_backward_workspace_bytes": (_I, [_P, _I, _I, _I, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
     "lsms_lu_store_bytes": (_I, [_P, _I, _I, _I, ctypes.POINTER(_SZ)]),
     "lsms_tau_blocks": (_I, [_P, _I, _P, _I, _P, _P, _I, _I, _P, _P, _P, _SZ, _P, _SZ, _P]),
-    "lsms_kubo_sigma": (_I, [_P, _I, _P, _I, _P, _I64, _P, _I, _D, _P, _P, _P, _P]),
-    "lsms_kubo_sigma_noalloc": (_I, [_P, _I, _P, _I, _P, _I64, _P, _I, _D, _P, _P, _P, _P]),
+    "lsms_kubo_sigma": (_I, [_P, _I, _P, _I, _P, _I64, _P, _I, _D, _I, _P, _P, _P, _P]),
+    "lsms_kubo_sigma_noalloc": (_I, [_P, _I, _P, _I, _P, _I64, _P, _I, _D, _I, _P, _P, _P, _P]),
     "lsms_kubo_sigma_backward": (_I, [_P, _I, _P, _I, _P, _P, _I, _I, _P, _I64, _P, _D, _P, _P, _SZ, _P, _P,
                                       _P, _P, _SZ, _P]),
     "lsms_last_error": (ctypes.c_char_p, []),
@@ -226,7 +226,7 @@ def tau_blocks(liz, lmax, species, tinv, z, precision="fp64", tau=None, unit_sta
 
 
 def kubo_sigma(liz, lmax, species, J, tau, n_delta, volume, J_delta_stride=0, sigma=None, sigma_tilde=None,
-               rho=None, stream=None):
+               rho=None, stream=None, precision="fp64"):
     """lsms_kubo_sigma.  Returns (sigma [n_delta,3,3] c128, sigma_tilde [n_delta,4,3,3] c128, rho [n_delta,3,3] f64)."""
     import torch
     K = (lmax + 1) ** 2
@@ -241,14 +241,14 @@ def kubo_sigma(liz, lmax, species, J, tau, n_delta, volume, J_delta_stride=0, si
     _check(lib().lsms_kubo_sigma(liz.handle, lmax, _dev(species, torch.int32, (liz.n_atoms,), "species"), n_species,
                                  _dev(J, torch.complex128, None, "J"), int(J_delta_stride),
                                  _dev(tau, torch.complex128, (2 * n_delta, liz.total_sites, K, K), "tau"), n_delta,
-                                 float(volume), _dev(sigma_tilde, torch.complex128, (n_delta, 4, 3, 3), "sigma_tilde"),
+                                 float(volume), _prec(precision), _dev(sigma_tilde, torch.complex128, (n_delta, 4, 3, 3), "sigma_tilde"),
                                  _dev(sigma, torch.complex128, (n_delta, 3, 3), "sigma"),
                                  _dev(rho, torch.float64, (n_delta, 3, 3), "rho"), _stream(stream)))
     return sigma, sigma_tilde, rho
 
 
 def kubo_sigma_noalloc(liz, lmax, species, J, tau, n_delta, volume, J_delta_stride=0, sigma=None, sigma_tilde=None,
-                       rho=None, stream=None):
+                       rho=None, stream=None, precision="fp64"):
     """lsms_kubo_sigma_noalloc: as kubo_sigma, but the library allocates nothing during the
     call (its scratch is a fixed 16 MiB device array; see include/lsmskubo.h).  The output
     tensors are allocated here by PyTorch unless passed in."""
@@ -266,7 +266,7 @@ def kubo_sigma_noalloc(liz, lmax, species, J, tau, n_delta, volume, J_delta_stri
         liz.handle, lmax, _dev(species, torch.int32, (liz.n_atoms,), "species"), n_species,
         _dev(J, torch.complex128, None, "J"), int(J_delta_stride),
         _dev(tau, torch.complex128, (2 * n_delta, liz.total_sites, K, K), "tau"), n_delta, float(volume),
-        _dev(sigma_tilde, torch.complex128, (n_delta, 4, 3, 3), "sigma_tilde"),
+        _prec(precision), _dev(sigma_tilde, torch.complex128, (n_delta, 4, 3, 3), "sigma_tilde"),
         _dev(sigma, torch.complex128, (n_delta, 3, 3), "sigma"), _dev(rho, torch.float64, (n_delta, 3, 3), "rho"),
         _stream(stream)))
     return sigma, sigma_tilde, rho

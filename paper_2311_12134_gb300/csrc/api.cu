@@ -61,15 +61,15 @@ void timer_end(cudaStream_t st) {
 // kernels in kubo.cu
 int kubo_forward(const int64_t* offsets, const int32_t* site_atom, const int32_t* species, int n_species,
                  const double2* J, int64_t J_dstride, const double2* tau, int64_t S_total, int K, int n_atoms, int n_delta,
-                 double volume, double2* partial, double2* S, double2* sigma_tilde, double2* sigma, double* rho,
-                 cudaStream_t st);
+                 double volume, bool df, double2* partial, double2* S, double2* sigma_tilde, double2* sigma,
+                 double* rho, cudaStream_t st);
 int adj_abar(const int32_t* species, int n_species, const double2* J, int64_t J_dstride, const double2* w, int K,
              double volume, int n_atoms, int n_delta, double2* abar, cudaStream_t st);
 int adj_rhs(const Unit* d_units, int n_units, int S_max, const int32_t* site_atom, const int32_t* species,
             int n_species, const double2* J, int64_t J_dstride, const double2* tau, int64_t S_total,
             const double2* abar, int n_delta, int K, char* ws, bool df, cudaStream_t st);
 int adj_site(const Unit* d_units, int n_units, int S_max, const double2* tau, int64_t S_total, int K, const char* ws,
-             double2* G, cudaStream_t st);
+             double2* G, bool df, cudaStream_t st);
 int adj_reduce(const int64_t* inv_off, const int64_t* inv_sites, const double2* G, int64_t S_total, int K,
                int n_atoms, int n_energy, double2* grad, cudaStream_t st);
 int adj_species(const int32_t* species, const double2* grad, int K, int n_atoms, int n_species, int n_energy,
@@ -173,7 +173,7 @@ static UnitBytes unit_bytes(int n, int precision, int nrhs, bool backward) {
   UnitBytes ub{};
   const size_t nn = (size_t)n * n;
   ub.fac = align_up(nn * (precision == LSMS_FP64 ? 16 : 8));
-  ub.piv = align_up((size_t)n * 4 * 3);  // pivots, perm, iperm
+  ub.piv = align_up((size_t)n * 4);  // pivots (row interchanged with row i at step i)
   ub.m64 = precision == LSMS_FP64 ? 0 : align_up(nn * 16);
   ub.x = align_up((size_t)n * nrhs * 16);
   ub.b = backward ? align_up((size_t)n * nrhs * 16) : 0;
@@ -184,7 +184,8 @@ static UnitBytes unit_bytes(int n, int precision, int nrhs, bool backward) {
 }
 
 static size_t ws_unit_bytes(const UnitBytes& ub, bool store) {
-  return (store ? 0 : ub.fac + ub.piv) + ub.m64 + ub.x + ub.b + ub.x32 + ub.probe;
+  // with a factor store, the factors, pivots and (mixed form) the double-float copy of M live there
+  return (store ? 0 : ub.fac + ub.piv + ub.m64) + ub.x + ub.b + ub.x32 + ub.probe;
 }
 
 // Atoms sorted by LIZ size (largest first, then atom index); every energy of an atom is adjacent.
@@ -266,14 +267,14 @@ static int get_plan(lsms_liz* liz, DeviceData* dd, int lmax, int n_energy, int p
       if (store) {
         u.fac_off = (int64_t)store_off;
         u.piv_off = (int64_t)(store_off + ub.fac);
-        store_off += ub.fac + ub.piv;
+        u.m64_off = (int64_t)(store_off + ub.fac + ub.piv);
+        store_off += ub.fac + ub.piv + ub.m64;
       } else {
         u.fac_off = (int64_t)cur;
         u.piv_off = (int64_t)(cur + ub.fac);
-        cur += ub.fac + ub.piv;
+        u.m64_off = (int64_t)(cur + ub.fac + ub.piv);
+        cur += ub.fac + ub.piv + ub.m64;
       }
-      u.m64_off = (int64_t)cur;
-      cur += ub.m64;
       u.x_off = (int64_t)cur;
       cur += ub.x;
       u.r_off = (int64_t)cur;
@@ -432,7 +433,7 @@ __device__ void hankel6_df(double d, double2 kap, double2 mpref, bool adv, float
 // FP64 form: FP64 sums, M (complex128) written into the factor array.
 // Mixed form: the sums in double-float arithmetic on the FP32 pipes (FP64
 // accuracy); writes M as (hi, lo) float pairs (float4 per element, at
-// ws + m64_off) for the refinement residual and, if write_fac, the hi part
+// fac_base + m64_off) for the refinement residual and, if write_fac, the hi part
 // (complex64) as the matrix to factor.
 template <bool MIXED>
 __global__ void __launch_bounds__(256, 2) k_assemble(const Unit* __restrict__ units, int nE,
@@ -561,7 +562,7 @@ __global__ void __launch_bounds__(256, 2) k_assemble(const Unit* __restrict__ un
               v4 = df_value(acc);
             }
             if (!(isfinite(v4.x) && isfinite(v4.z))) flags[ee] |= LSMS_UNIT_NONFINITE;
-            reinterpret_cast<float4*>(ws + u.m64_off)[idx] = make_float4(v4.x, v4.z, v4.y, v4.w);
+            reinterpret_cast<float4*>(fac_base + u.m64_off)[idx] = make_float4(v4.x, v4.z, v4.y, v4.w);
             if (write_fac) reinterpret_cast<float2*>(fac_base + u.fac_off)[idx] = make_float2(v4.x, v4.z);
           } else {
             double2 v;
@@ -589,34 +590,30 @@ __global__ void __launch_bounds__(256, 2) k_assemble(const Unit* __restrict__ un
 }
 
 // ------------------------------------------------------------------ RHS / refinement kernels
-// Right-hand sides enter the solves already permuted by P (P M = L U):
-// row position i holds original row perm[i].
+// Right-hand sides enter the solves in the original row order: the forward
+// sweep of the solve applies the factor's row swaps panel by panel.
 
-// X = P E0 (E0 = first K columns of the identity), complex<R>.
+// X = E0 (the first K columns of the identity), complex<R>.
 template <typename C>
-__global__ void k_rhs_identity(const Unit* __restrict__ units, const char* fac_base, char* ws, int which, int K,
-                               int nrhs) {
+__global__ void k_rhs_identity(const Unit* __restrict__ units, char* ws, int which, int K, int nrhs) {
   const Unit u = units[blockIdx.y];
   const int n = u.n;
-  const int32_t* perm = reinterpret_cast<const int32_t*>(fac_base + u.piv_off) + n;
   C* X = reinterpret_cast<C*>(ws + (which == RHS_X ? u.x_off : u.x32_off));
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)n * nrhs;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(idx % n), c = (int)(idx / n);
-    X[idx] = (perm[i] == c && c < K) ? cvt<C>(make_double2(1.0, 0.0)) : cvt<C>(make_double2(0.0, 0.0));
+    X[idx] = (i == c && c < K) ? cvt<C>(make_double2(1.0, 0.0)) : cvt<C>(make_double2(0.0, 0.0));
   }
 }
 
-// X32 = P B rounded (mixed form) or X = P B (FP64 form); B complex128 at r_off.
-__global__ void k_copy_b(const Unit* __restrict__ units, const char* fac_base, char* ws, int nrhs, bool to_x32) {
+// X32 = B rounded (mixed form) or X = B (FP64 form); B complex128 at r_off.
+__global__ void k_copy_b(const Unit* __restrict__ units, char* ws, int nrhs, bool to_x32) {
   const Unit u = units[blockIdx.y];
   const int n = u.n;
-  const int32_t* perm = reinterpret_cast<const int32_t*>(fac_base + u.piv_off) + n;
   const double2* B = reinterpret_cast<const double2*>(ws + u.r_off);
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)n * nrhs;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(idx % n), c = (int)(idx / n);
-    const double2 b = B[(size_t)c * n + perm[i]];
+    const double2 b = B[idx];
     if (to_x32) reinterpret_cast<float2*>(ws + u.x32_off)[idx] = to32(b);
     else reinterpret_cast<double2*>(ws + u.x_off)[idx] = b;
   }
@@ -649,9 +646,8 @@ __global__ void __launch_bounds__(256, 3) k_residual(const Unit* __restrict__ un
   const int n = u.n;
   const int row0 = blockIdx.x * 64;
   if (row0 >= n) return;
-  const float4* M = reinterpret_cast<const float4*>(ws + u.m64_off);
+  const float4* M = reinterpret_cast<const float4*>(fac_base + u.m64_off);
   const double2* X = reinterpret_cast<const double2*>(ws + u.x_off);
-  const int32_t* iperm = reinterpret_cast<const int32_t*>(fac_base + u.piv_off) + 2 * n;
   float2* X32 = reinterpret_cast<float2*>(ws + u.x32_off);
   __shared__ float4 sX[32][NCOL + 1];
   const int tid = threadIdx.x;
@@ -704,7 +700,6 @@ __global__ void __launch_bounds__(256, 3) k_residual(const Unit* __restrict__ un
   }
   if (live) {
     const double2* B = reinterpret_cast<const double2*>(ws + u.r_off);
-    const int pos = iperm[row];
 #pragma unroll
     for (int c = 0; c < CPG; ++c) {
       const int col = cg * CPG + c;
@@ -714,7 +709,7 @@ __global__ void __launch_bounds__(256, 3) k_residual(const Unit* __restrict__ un
       else b = (row == col && col < K) ? mk(1.0, 0.0) : mk(0.0, 0.0);
       const double re = b.x - ((double)sr[c] + (double)tr[c]);
       const double im = b.y - ((double)si[c] + (double)ti[c]);
-      X32[(size_t)col * n + pos] = make_float2((float)re, (float)im);
+      X32[(size_t)col * n + row] = make_float2((float)re, (float)im);
     }
   }
 }
@@ -814,10 +809,9 @@ __global__ void __launch_bounds__(256, 3) k_probe_residual(const Unit* __restric
   const int n = u.n;
   const int row0 = blockIdx.x * 64;
   if (row0 >= n) return;
-  const float4* M = reinterpret_cast<const float4*>(ws + u.m64_off);
+  const float4* M = reinterpret_cast<const float4*>(fac_base + u.m64_off);
   const double2* Y = reinterpret_cast<const double2*>(ws + u.p_off);
   const double2* BW = Y + (size_t)kProbe * n;
-  const int32_t* iperm = reinterpret_cast<const int32_t*>(fac_base + u.piv_off) + 2 * n;
   float2* X32 = reinterpret_cast<float2*>(ws + u.x32_off);
   __shared__ float4 sY[128][kProbe];
   __shared__ float4 sPart[3][kProbe][64];
@@ -873,7 +867,6 @@ __global__ void __launch_bounds__(256, 3) k_probe_residual(const Unit* __restric
   }
   __syncthreads();
   if (grp == 0 && live) {
-    const int pos = iperm[row];
 #pragma unroll
     for (int q = 0; q < kProbe; ++q) {
 #pragma unroll
@@ -887,7 +880,7 @@ __global__ void __launch_bounds__(256, 3) k_probe_residual(const Unit* __restric
       const double2 b = BW[(size_t)q * n + row];
       const double re = b.x - ((double)sr[q] + (double)tr[q]);
       const double im = b.y - ((double)si[q] + (double)ti[q]);
-      X32[(size_t)q * n + pos] = make_float2((float)re, (float)im);
+      X32[(size_t)q * n + row] = make_float2((float)re, (float)im);
     }
   }
 }
@@ -1019,12 +1012,12 @@ static int solve_refine(const Call& c, const Plan& p, const Chunk& ch, const cha
   const dim3 g1((ch.n_max * nrhs + 255) / 256, nu);
   int rc;
   if (c.precision == LSMS_FP64) {
-    if (explicit_b) LSMS_LAUNCH(k_copy_b, g1, dim3(256), 0, c.st, du, fac_base, ws, nrhs, false);
-    else LSMS_LAUNCH(k_rhs_identity<double2>, g1, dim3(256), 0, c.st, du, fac_base, ws, (int)RHS_X, c.K, nrhs);
+    if (explicit_b) LSMS_LAUNCH(k_copy_b, g1, dim3(256), 0, c.st, du, ws, nrhs, false);
+    else LSMS_LAUNCH(k_rhs_identity<double2>, g1, dim3(256), 0, c.st, du, ws, (int)RHS_X, c.K, nrhs);
     return lu_solve_chunk<double>(du, nu, fac_base, ws, RHS_X, nrhs, nullptr, c.st);
   }
-  if (explicit_b) LSMS_LAUNCH(k_copy_b, g1, dim3(256), 0, c.st, du, fac_base, ws, nrhs, true);
-  else LSMS_LAUNCH(k_rhs_identity<float2>, g1, dim3(256), 0, c.st, du, fac_base, ws, (int)RHS_X32, c.K, nrhs);
+  if (explicit_b) LSMS_LAUNCH(k_copy_b, g1, dim3(256), 0, c.st, du, ws, nrhs, true);
+  else LSMS_LAUNCH(k_rhs_identity<float2>, g1, dim3(256), 0, c.st, du, ws, (int)RHS_X32, c.K, nrhs);
   if ((rc = lu_solve_chunk<float>(du, nu, fac_base, ws, RHS_X32, nrhs, nullptr, c.st))) return rc;
   LSMS_LAUNCH(k_widen, g1, dim3(256), 0, c.st, du, ws, nrhs);
   // done flags of this chunk's units start cleared (memset by the caller)
@@ -1170,7 +1163,7 @@ extern "C" int lsms_lu_store_bytes(const lsms_liz* liz, int lmax, int n_energy, 
   for (int m = 0; m < liz->n_atoms; ++m) {
     const int n = K * (int)(liz->offsets[m + 1] - liz->offsets[m]);
     const UnitBytes ub = unit_bytes(n, precision, K, false);
-    s += (ub.fac + ub.piv) * n_energy;
+    s += (ub.fac + ub.piv + ub.m64) * n_energy;
   }
   *bytes = s;
   return LSMS_OK;
@@ -1249,11 +1242,11 @@ extern "C" int lsms_tau_blocks(const lsms_liz* liz_c, int lmax, const int32_t* s
 
 extern "C" int lsms_kubo_sigma(const lsms_liz* liz_c, int lmax, const int32_t* species, int n_species,
                                const lsms_complex* J, int64_t J_delta_stride, const lsms_complex* tau, int n_delta,
-                               double volume, lsms_complex* sigma_tilde, lsms_complex* sigma, double* rho,
-                               void* stream) {
+                               double volume, int precision, lsms_complex* sigma_tilde, lsms_complex* sigma,
+                               double* rho, void* stream) {
   clear_error();
   lsms_liz* liz = const_cast<lsms_liz*>(liz_c);
-  int rc = check_common(liz, lmax, species, n_species, 2 * std::max(n_delta, 1), LSMS_FP64);
+  int rc = check_common(liz, lmax, species, n_species, 2 * std::max(n_delta, 1), precision);
   if (rc) return rc;
   if (n_delta < 1 || !J || !tau || !sigma) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma: J, tau, sigma required, n_delta >= 1");
   if (!(volume > 0.0) || !std::isfinite(volume)) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma: volume must be > 0");
@@ -1268,7 +1261,7 @@ extern "C" int lsms_kubo_sigma(const lsms_liz* liz_c, int lmax, const int32_t* s
   LSMS_CUDA_TRY(cudaMallocAsync((void**)&scratch, part_bytes + s_bytes, st));
   rc = kubo_forward(dd->offsets, dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J), J_delta_stride,
                     reinterpret_cast<const double2*>(tau), liz->total_sites, K, liz->n_atoms, n_delta, volume,
-                    reinterpret_cast<double2*>(scratch), reinterpret_cast<double2*>(scratch + part_bytes),
+                    precision == LSMS_MIXED, reinterpret_cast<double2*>(scratch), reinterpret_cast<double2*>(scratch + part_bytes),
                     reinterpret_cast<double2*>(sigma_tilde), reinterpret_cast<double2*>(sigma), rho, st);
   cudaFreeAsync(scratch, st);
   return rc;
@@ -1342,13 +1335,15 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
       const Unit* du = p->d_units + ch.u0;
       const int nu = ch.u1 - ch.u0;
       const int S_max = ch.n_max / c.K;
-      if ((r2 = assemble_factor(c, *p, ch, fac_base, chunk, stat, !store))) return r2;
+      // stored factors come with the double-float copy of M (mixed form): nothing to rebuild
+      if (!store && (r2 = assemble_factor(c, *p, ch, fac_base, chunk, stat, true))) return r2;
       if ((r2 = adj_rhs(du, nu, S_max, c.dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J), J_delta_stride,
                         reinterpret_cast<const double2*>(tau), liz->total_sites, abar, n_delta, c.K, chunk,
                         precision == LSMS_MIXED, c.st)))
         return r2;
       if ((r2 = solve_refine(c, *p, ch, fac_base, chunk, stat, done, true))) return r2;
-      if ((r2 = adj_site(du, nu, S_max, reinterpret_cast<const double2*>(tau), liz->total_sites, c.K, chunk, G, c.st)))
+      if ((r2 = adj_site(du, nu, S_max, reinterpret_cast<const double2*>(tau), liz->total_sites, c.K, chunk, G,
+                         precision == LSMS_MIXED, c.st)))
         return r2;
     }
     if ((r2 = adj_reduce(c.dd->inv_off, c.dd->inv_sites, G, liz->total_sites, c.K, liz->n_atoms, n_energy,

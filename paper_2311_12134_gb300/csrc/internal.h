@@ -31,7 +31,7 @@ struct Unit {
   int32_t S;         // LIZ size S_m
   int64_t site_off;  // first site of LIZ_m in the global site arrays
   int64_t fac_off;   // byte offset of the factor matrix (from fac base)
-  int64_t m64_off;   // byte offset of the FP64 matrix copy (mixed form), from workspace
+  int64_t m64_off;   // byte offset of the double-float copy of M (mixed form), from fac base
   int64_t piv_off;   // byte offset of the pivots (from fac base)
   int64_t x_off;     // byte offset of the n x RHS complex128 solution block (workspace)
   int64_t r_off;     // byte offset of the n x RHS complex128 residual block (workspace)

@@ -6,7 +6,8 @@
 //   S_c[mu][nu](m) = sum_{n in LIZ_m} Tr[ J^{m mu}(z2,z1) tau^{0n}(z1) J^{n nu}(z1,z2) tau^{n0}(z2) ]
 // with tau^{0n} = (tau^{n0})^T (complex-symmetric M).  Eq.
 // (sigma-tilde-consolidation) then combines the four pairs at finite delta.
-// All arithmetic here is FP64; sums over atoms and sites run in a fixed order.
+// FP64 arithmetic, except the mixed form's K x K products (double-float on the
+// FP32 pipes, FP64-class accuracy); sums over atoms and sites run in a fixed order.
 #include <cmath>
 #include <mutex>
 #include <type_traits>
@@ -20,12 +21,18 @@ __device__ __forceinline__ int swap_combo(int c) { return ((c & 1) << 1) | (c >>
 
 // ------------------------------------------------------------------ forward traces
 // grid (n_atoms, n_delta * 4), block 256 = 16 x 16 element threads.
+// DF = false: FP64 arithmetic (FP64 form).  DF = true (mixed form): the K x K
+// products and the site sum in double-float arithmetic on the FP32 pipes
+// (unit roundoff about 2^-48; the last trace and everything after it in FP64).
+template <bool DF>
 __global__ void __launch_bounds__(256) k_kubo_partial(const int64_t* __restrict__ offsets,
                                                       const int32_t* __restrict__ site_atom,
                                                       const int32_t* __restrict__ species,
                                                       const double2* __restrict__ J, int64_t J_dstride,
                                                       const double2* __restrict__ tau, int64_t S_total, int K,
                                                       int n_atoms, int n_species, double2* __restrict__ partial) {
+  using V = typename std::conditional<DF, float4, double2>::type;
+  using Acc = typename std::conditional<DF, DfAcc, double2>::type;
   const int m = blockIdx.x;
   const int d = blockIdx.y >> 2, c = blockIdx.y & 3;
   const int a = c >> 1, b = c & 1;
@@ -33,60 +40,77 @@ __global__ void __launch_bounds__(256) k_kubo_partial(const int64_t* __restrict_
   const int cb = swap_combo(c);
   const int KK = K * K;
   const double2* Jd = J + (size_t)d * J_dstride;
-  __shared__ double2 sT1[16][17], sT2[16][17];
-  __shared__ double2 sB[3][16][17];
-  __shared__ double2 sP[3][16][17];
+  __shared__ V sT1[16][17], sT2[16][17];
+  __shared__ V sB[3][16][17];
+  __shared__ V sP[3][16][17];
+  auto ld = [](double2 x) -> V {
+    if constexpr (DF) return df_split(x);
+    else return x;
+  };
+  auto zero = []() -> Acc {
+    if constexpr (DF) return df_zero();
+    else return mk(0.0, 0.0);
+  };
+  auto mac = [](Acc& acc, V x, V y) {
+    if constexpr (DF) dfc_mac(acc, x, y);
+    else acc = cfma(x, y, acc);
+  };
+  auto val = [](const Acc& acc) -> V {
+    if constexpr (DF) return df_value(acc);
+    else return acc;
+  };
+  auto wide = [](V x) -> double2 {
+    if constexpr (DF) return df_join(x);
+    else return x;
+  };
   const int tid = threadIdx.x;
   const int i = tid >> 4, j = tid & 15;
   const bool act = (i < K) && (j < K);
-  double2 Y[3];
+  Acc Y[3];
 #pragma unroll
-  for (int v = 0; v < 3; ++v) Y[v] = mk(0.0, 0.0);
+  for (int v = 0; v < 3; ++v) Y[v] = zero();
   const int64_t s0 = offsets[m], s1 = offsets[m + 1];
   for (int64_t s = s0; s < s1; ++s) {
     const int sp = min(max(0, species[site_atom[s]]), n_species - 1);  // out-of-range ids never index J
     if (act) {
-      sT1[i][j] = tau[((size_t)e1 * S_total + s) * KK + i * K + j];
-      sT2[i][j] = tau[((size_t)e2 * S_total + s) * KK + i * K + j];
+      sT1[i][j] = ld(tau[((size_t)e1 * S_total + s) * KK + i * K + j]);
+      sT2[i][j] = ld(tau[((size_t)e2 * S_total + s) * KK + i * K + j]);
 #pragma unroll
-      for (int v = 0; v < 3; ++v) sB[v][i][j] = Jd[(((size_t)sp * 4 + c) * 3 + v) * KK + i * K + j];
+      for (int v = 0; v < 3; ++v) sB[v][i][j] = ld(Jd[(((size_t)sp * 4 + c) * 3 + v) * KK + i * K + j]);
     }
     __syncthreads();
     if (act) {
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
-        double2 acc = mk(0.0, 0.0);
-        for (int q = 0; q < K; ++q) acc = cfma(sB[v][i][q], sT2[q][j], acc);  // J^nu tau^{n0}(z2)
-        sP[v][i][j] = acc;
+        Acc acc = zero();
+        for (int q = 0; q < K; ++q) mac(acc, sB[v][i][q], sT2[q][j]);  // J^nu tau^{n0}(z2)
+        sP[v][i][j] = val(acc);
       }
     }
     __syncthreads();
     if (act) {
 #pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        double2 acc = Y[v];
-        for (int q = 0; q < K; ++q) acc = cfma(sT1[q][i], sP[v][q][j], acc);  // tau^{0n}(z1) = tau^{n0}(z1)^T
-        Y[v] = acc;
-      }
+      for (int v = 0; v < 3; ++v)
+        for (int q = 0; q < K; ++q) mac(Y[v], sT1[q][i], sP[v][q][j]);  // tau^{0n}(z1) = tau^{n0}(z1)^T
     }
     __syncthreads();
   }
   // S[mu][nu] = Tr[J^{m mu} Y^nu] = sum_ij Jm[i][j] Y[j][i]
   if (act) {
 #pragma unroll
-    for (int v = 0; v < 3; ++v) sP[v][i][j] = Y[v];
+    for (int v = 0; v < 3; ++v) sP[v][i][j] = val(Y[v]);
   }
   const int spm = min(max(0, species[m]), n_species - 1);
   if (act) {
 #pragma unroll
-    for (int u = 0; u < 3; ++u) sB[u][i][j] = Jd[(((size_t)spm * 4 + cb) * 3 + u) * KK + i * K + j];
+    for (int u = 0; u < 3; ++u) sB[u][i][j] = ld(Jd[(((size_t)spm * 4 + cb) * 3 + u) * KK + i * K + j]);
   }
   __syncthreads();
   __shared__ double2 red[9][8];
   const int lane = tid & 31, warp = tid >> 5;
   for (int u = 0; u < 3; ++u)
     for (int v = 0; v < 3; ++v) {
-      double2 t = act ? cmul(sB[u][i][j], sP[v][j][i]) : mk(0.0, 0.0);
+      double2 t = act ? cmul(wide(sB[u][i][j]), wide(sP[v][j][i])) : mk(0.0, 0.0);
 #pragma unroll
       for (int off = 16; off; off >>= 1) {
         t.x += __shfl_xor_sync(0xffffffffu, t.x, off);
@@ -279,9 +303,12 @@ __global__ void __launch_bounds__(256) k_adj_rhs(const Unit* __restrict__ units,
 
 // Per-site gradient contribution for unit (m, e), site p (one CTA each):
 //   D_p = - tau^{p0} (X1_p)^T - X2_p (tau^{p0})^T,  X = M^{-1} B  (n x 2K at ws + unit.x_off)
-// written to G[e][s] (K x K row-major).  grid (S_max, n_units).
+// written to G[e][s] (K x K row-major).  grid (S_max, n_units).  DF: the products
+// in double-float arithmetic on the FP32 pipes (mixed form), else FP64.
+template <bool DF>
 __global__ void __launch_bounds__(256) k_adj_site(const Unit* __restrict__ units, const double2* __restrict__ tau,
                                                   int64_t S_total, int K, const char* ws, double2* __restrict__ G) {
+  using V = typename std::conditional<DF, float4, double2>::type;
   const Unit u = units[blockIdx.y];
   const int p = blockIdx.x;
   if (p >= u.S) return;
@@ -289,22 +316,37 @@ __global__ void __launch_bounds__(256) k_adj_site(const Unit* __restrict__ units
   const int e = u.energy, n = u.n;
   const int64_t s = u.site_off + p;
   const double2* X = reinterpret_cast<const double2*>(ws + u.x_off);
-  __shared__ double2 sT[16][17], sX1[16][17], sX2[16][17];
+  __shared__ V sT[16][17], sX1[16][17], sX2[16][17];
+  auto ld = [](double2 x) -> V {
+    if constexpr (DF) return df_split(x);
+    else return x;
+  };
   const int tid = threadIdx.x, i = tid >> 4, j = tid & 15;
   const bool act = (i < K) && (j < K);
   if (act) {
-    sT[i][j] = tau[((size_t)e * S_total + s) * KK + i * K + j];
-    sX1[i][j] = X[(size_t)j * n + K * p + i];
-    sX2[i][j] = X[(size_t)(K + j) * n + K * p + i];
+    sT[i][j] = ld(tau[((size_t)e * S_total + s) * KK + i * K + j]);
+    sX1[i][j] = ld(X[(size_t)j * n + K * p + i]);
+    sX2[i][j] = ld(X[(size_t)(K + j) * n + K * p + i]);
   }
   __syncthreads();
   if (act) {
-    double2 acc = mk(0.0, 0.0);
-    for (int t = 0; t < K; ++t) {
-      acc = cfma(sT[i][t], sX1[j][t], acc);   // tau^{p0} X1^T
-      acc = cfma(sX2[i][t], sT[j][t], acc);   // X2 tau^{p0 T}
+    double2 r;
+    if constexpr (DF) {
+      DfAcc acc = df_zero();
+      for (int t = 0; t < K; ++t) {
+        dfc_mac(acc, sT[i][t], sX1[j][t]);   // tau^{p0} X1^T
+        dfc_mac(acc, sX2[i][t], sT[j][t]);   // X2 tau^{p0 T}
+      }
+      r = df_join(df_value(acc));
+    } else {
+      double2 acc = mk(0.0, 0.0);
+      for (int t = 0; t < K; ++t) {
+        acc = cfma(sT[i][t], sX1[j][t], acc);
+        acc = cfma(sX2[i][t], sT[j][t], acc);
+      }
+      r = acc;
     }
-    G[((size_t)e * S_total + s) * KK + i * K + j] = mk(-acc.x, -acc.y);
+    G[((size_t)e * S_total + s) * KK + i * K + j] = mk(-r.x, -r.y);
   }
 }
 
@@ -340,10 +382,14 @@ __global__ void __launch_bounds__(256) k_adj_species(const int32_t* __restrict__
 // ------------------------------------------------------------------ wrappers
 int kubo_forward(const int64_t* offsets, const int32_t* site_atom, const int32_t* species, int n_species,
                  const double2* J, int64_t J_dstride, const double2* tau, int64_t S_total, int K, int n_atoms, int n_delta,
-                 double volume, double2* partial, double2* S, double2* sigma_tilde, double2* sigma, double* rho,
-                 cudaStream_t st) {
-  LSMS_LAUNCH(k_kubo_partial, dim3(n_atoms, n_delta * 4), dim3(256), 0, st, offsets, site_atom, species, J,
-              J_dstride, tau, S_total, K, n_atoms, n_species, partial);
+                 double volume, bool df, double2* partial, double2* S, double2* sigma_tilde, double2* sigma,
+                 double* rho, cudaStream_t st) {
+  if (df)
+    LSMS_LAUNCH(k_kubo_partial<true>, dim3(n_atoms, n_delta * 4), dim3(256), 0, st, offsets, site_atom, species, J,
+                J_dstride, tau, S_total, K, n_atoms, n_species, partial);
+  else
+    LSMS_LAUNCH(k_kubo_partial<false>, dim3(n_atoms, n_delta * 4), dim3(256), 0, st, offsets, site_atom, species, J,
+                J_dstride, tau, S_total, K, n_atoms, n_species, partial);
   LSMS_LAUNCH(k_kubo_reduce, dim3(n_delta * 4 * 9), dim3(256), 0, st, partial, n_atoms, S);
   LSMS_LAUNCH(k_kubo_finish, dim3(1), dim3(32), 0, st, S, n_delta, volume, sigma_tilde, sigma, rho);
   return LSMS_OK;
@@ -369,8 +415,9 @@ int adj_rhs(const Unit* d_units, int n_units, int S_max, const int32_t* site_ato
 }
 
 int adj_site(const Unit* d_units, int n_units, int S_max, const double2* tau, int64_t S_total, int K, const char* ws,
-             double2* G, cudaStream_t st) {
-  LSMS_LAUNCH(k_adj_site, dim3(S_max, n_units), dim3(256), 0, st, d_units, tau, S_total, K, ws, G);
+             double2* G, bool df, cudaStream_t st) {
+  if (df) LSMS_LAUNCH(k_adj_site<true>, dim3(S_max, n_units), dim3(256), 0, st, d_units, tau, S_total, K, ws, G);
+  else LSMS_LAUNCH(k_adj_site<false>, dim3(S_max, n_units), dim3(256), 0, st, d_units, tau, S_total, K, ws, G);
   return LSMS_OK;
 }
 
@@ -426,8 +473,8 @@ using namespace lsms;
 
 extern "C" int lsms_kubo_sigma_noalloc(const lsms_liz* liz_c, int lmax, const int32_t* species, int n_species,
                                        const lsms_complex* J, int64_t J_delta_stride, const lsms_complex* tau,
-                                       int n_delta, double volume, lsms_complex* sigma_tilde, lsms_complex* sigma,
-                                       double* rho, void* stream) {
+                                       int n_delta, double volume, int precision, lsms_complex* sigma_tilde,
+                                       lsms_complex* sigma, double* rho, void* stream) {
   clear_error();
   lsms_liz* liz = const_cast<lsms_liz*>(liz_c);
   if (!liz) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_noalloc: NULL liz");
@@ -437,6 +484,8 @@ extern "C" int lsms_kubo_sigma_noalloc(const lsms_liz* liz_c, int lmax, const in
     return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_noalloc: J, tau, sigma required, 1 <= n_delta <= %d", kMaxEnergies / 2);
   if (!(volume > 0.0) || !std::isfinite(volume)) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_noalloc: volume must be > 0");
   if (J_delta_stride < 0) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_noalloc: negative J stride");
+  if (precision != LSMS_FP64 && precision != LSMS_MIXED)
+    return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_noalloc: unknown precision %d", precision);
   const size_t part_bytes = round256((size_t)n_delta * 4 * liz->n_atoms * 9 * sizeof(double2));
   const size_t s_bytes = round256((size_t)n_delta * 36 * sizeof(double2));
   if (part_bytes + s_bytes > kNoAllocScratchBytes)
@@ -456,7 +505,8 @@ extern "C" int lsms_kubo_sigma_noalloc(const lsms_liz* liz_c, int lmax, const in
   // previous call's contents need no clearing.
   return kubo_forward(dd->offsets, dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J),
                       J_delta_stride, reinterpret_cast<const double2*>(tau), liz->total_sites, K, liz->n_atoms,
-                      n_delta, volume, reinterpret_cast<double2*>(base), reinterpret_cast<double2*>(base + part_bytes),
+                      n_delta, volume, precision == LSMS_MIXED, reinterpret_cast<double2*>(base),
+                      reinterpret_cast<double2*>(base + part_bytes),
                       reinterpret_cast<double2*>(sigma_tilde), reinterpret_cast<double2*>(sigma), rho,
                       reinterpret_cast<cudaStream_t>(stream));
 }

@@ -6,17 +6,18 @@
 // Pivoting: the row with the largest |Re| + |Im| in the column, the lowest row
 // on ties.  Right-looking, panel width NB:
 //   k_panel      factor the n-k x NB panel (pivot search by warp shuffles),
-//   k_swap_trsm  apply the panel's row swaps to every other column (left ones
-//                too, so L ends up in the final row order) and form
-//                U12 = L11^{-1} A12 (one warp per column),
+//   k_swap_trsm  apply the panel's row swaps to the columns right of it and
+//                form U12 = L11^{-1} A12 (one warp per column); columns left
+//                of the panel are not swapped (L is kept as computed, LINPACK
+//                style),
 //   k_gemm       A22 -= L21 U12: register-tiled complex GEMM on the FP64 pipe
 //                (FP64 form); the complex64 form uses k_gemm_tc (tc_gemm.cu),
-//                the same update on the tensor cores,
-//   k_perm       the permutation P as perm[i] (original row at position i) and
-//                its inverse iperm.
+//                the same update on the tensor cores.
 // Units of a chunk are sorted by n (largest first); each launch covers every
-// unit and units already finished return at once.  k_solve then runs plain
-// forward/backward substitution on right-hand sides already permuted by P.
+// unit and units already finished return at once.  k_solve (FP64) and
+// k_solve_c64 (complex64) then run blocked forward/backward substitution; the
+// forward sweep applies each panel's row swaps to the right-hand sides just
+// before that panel's block of L, so the right-hand sides come in unpermuted.
 #include <algorithm>
 #include <type_traits>
 
@@ -31,6 +32,63 @@ __device__ __forceinline__ double2 shfl2(double2 v, int src) {
 }
 __device__ __forceinline__ float2 shfl2(float2 v, int src) {
   return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// The row interchanges of one factor panel (rows k + j <-> sp[j], j = 0..31 in
+// order; sp[j] = k + j for no interchange) applied to one column by one warp.
+// Lane j holds row k + j of the column in x on entry and exit; rows below the
+// panel that the interchanges reach are read and written in place.  When those
+// rows are all distinct (the usual case) each is read once up front and written
+// once at the end and the sequence runs in registers; repeated targets take the
+// sequential path through memory.
+template <typename C>
+__device__ __forceinline__ C panel_swaps(C x, C* col, const int* sp, int k, int lane) {
+  constexpr int NB = 32;
+  const int pj = sp[lane];
+  const bool outj = pj >= k + NB;
+  const unsigned same = __match_any_sync(0xffffffffu, outj ? pj : -1 - lane);
+  const bool fast = !__any_sync(0xffffffffu, outj && __popc(same) > 1);
+  if (fast) {
+    C y = outj ? col[pj] : x;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int p = sp[j];
+      if (p == k + j) continue;
+      if (p < k + NB) {
+        const int b = p - k;
+        const C va = shfl2(x, j);
+        const C vb = shfl2(x, b);
+        if (lane == j) x = vb;
+        if (lane == b) x = va;
+      } else if (lane == j) {
+        const C t = y;
+        y = x;
+        x = t;
+      }
+    }
+    if (outj) col[pj] = y;
+  } else {
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int p = sp[j];
+      if (p == k + j) continue;
+      if (p < k + NB) {
+        const int b = p - k;
+        const C va = shfl2(x, j);
+        const C vb = shfl2(x, b);
+        if (lane == j) x = vb;
+        if (lane == b) x = va;
+      } else {
+        if (lane == j) {
+          const C t = col[p];
+          col[p] = x;
+          x = t;
+        }
+        __syncwarp();
+      }
+    }
+  }
+  return x;
 }
 
 // ------------------------------------------------------------------ panel
@@ -113,231 +171,157 @@ __global__ void __launch_bounds__(256) k_panel(const Unit* __restrict__ units, c
 }
 
 // Panel factorization held in shared memory: the m = n - k rows x NB columns of
-// the panel are read once, factored column by column in shared memory (pivot
-// search by warp shuffles), and written back once.  Units whose panel does not
-// fit (m > max_rows) are left to k_panel, which works in global memory.
+// the panel are read once, factored column by column in shared memory, and
+// written back once.  Units whose panel does not fit (m > max_rows) are left to
+// k_panel, which works in global memory.
+// Rows never move inside shared memory: thread t owns the physical rows t,
+// t + 512, ... and keeps their logical (pivoted) row numbers in registers, so a
+// row interchange is two register updates.  The pivot search for column j + 1
+// runs inside the update of column j (on the values just written), which leaves
+// one block barrier per column.  Same arithmetic and pivot choices as the
+// row-swapping form (largest |Re| + |Im|, lowest logical row on ties).
 template <typename R, int NB>
 __global__ void __launch_bounds__(512) k_panel_smem(const Unit* __restrict__ units, char* fac_base, int k,
                                                     int32_t* stat, int max_rows) {
   using C = Cx<R>;
+  constexpr int NT = 512, MAXR = 4;  // threads; rows per thread (m <= 2048)
   const Unit u = units[blockIdx.x];
   const int n = u.n;
   if (k >= n) return;
   const int m = n - k;
-  if (m > max_rows) return;
+  if (m > max_rows || m > NT * MAXR) return;
   extern __shared__ __align__(16) unsigned char panel_raw[];
-  C* sP = reinterpret_cast<C*>(panel_raw);  // [NB][m], column-major
+  C* sP = reinterpret_cast<C*>(panel_raw);  // [NB][m], column-major, physical rows
   C* A = reinterpret_cast<C*>(fac_base + u.fac_off);
   int32_t* piv = reinterpret_cast<int32_t*>(fac_base + u.piv_off);
   const int nbp = min(NB, m);
-  __shared__ R s_val[16];
-  __shared__ int s_idx[16];
-  __shared__ int s_piv;
+  __shared__ R s_val[2][16];
+  __shared__ int s_lg[2][16], s_ph[2][16];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nthr = blockDim.x, nwarps = nthr >> 5;
   for (int c = 0; c < nbp; ++c)
-    for (int r = tid; r < m; r += nthr) sP[c * m + r] = A[(size_t)(k + c) * n + k + r];
-  __syncthreads();
-  int flags = 0;
-  for (int j = 0; j < nbp; ++j) {
-    C* Pj = sP + j * m;
-    R best = R(-1);
-    int bidx = m;
-    for (int i = j + tid; i < m; i += nthr) {
-      const R v = cabs1(Pj[i]);
-      if (v > best) { best = v; bidx = i; }  // strict: lowest row kept; NaN never wins
-    }
+    for (int r = tid; r < m; r += NT) sP[c * m + r] = A[(size_t)(k + c) * n + k + r];
+  int lg[MAXR];  // logical row of physical row tid + NT r
+#pragma unroll
+  for (int r = 0; r < MAXR; ++r) lg[r] = tid + NT * r;
+  // warp-level best (value, logical row, physical row); lowest logical row on ties
+  auto warp_best = [&](R& best, int& bl, int& bp) {
 #pragma unroll
     for (int off = 16; off; off >>= 1) {
       const R ov = __shfl_xor_sync(0xffffffffu, best, off);
-      const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
-      if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
+      const int ol = __shfl_xor_sync(0xffffffffu, bl, off);
+      const int op = __shfl_xor_sync(0xffffffffu, bp, off);
+      if (ov > best || (ov == best && ol < bl)) { best = ov; bl = ol; bp = op; }
     }
-    if (lane == 0) { s_val[warp] = best; s_idx[warp] = bidx; }
-    __syncthreads();
-    if (warp == 0) {
-      best = lane < nwarps ? s_val[lane] : R(-1);
-      bidx = lane < nwarps ? s_idx[lane] : m;
+  };
+  // pivot candidates of column 0
+  {
+    R best = R(-1);
+    int bl = m, bp = 0;
 #pragma unroll
-      for (int off = 16; off; off >>= 1) {
-        const R ov = __shfl_xor_sync(0xffffffffu, best, off);
-        const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
-        if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
-      }
-      if (lane == 0) {
-        const int p = (bidx < m) ? bidx : j;
-        s_piv = p;
-        piv[k + j] = k + p;
+    for (int r = 0; r < MAXR; ++r) {
+      const int ph = tid + NT * r;
+      if (ph < m) {
+        R v = cabs1(sP[ph]);
+        if (!(v >= R(0))) v = R(-0.5);  // NaN: below every number, so it wins only an all-NaN column (row j)
+        if (v > best || (v == best && lg[r] < bl)) { best = v; bl = lg[r]; bp = ph; }
       }
     }
-    __syncthreads();
-    const int p = s_piv;
-    if (p != j && tid < nbp) {
-      C* col = sP + tid * m;
-      const C t = col[j];
-      col[j] = col[p];
-      col[p] = t;
-    }
-    __syncthreads();
-    const C pv = Pj[j];
+    warp_best(best, bl, bp);
+    if (lane == 0) { s_val[0][warp] = best; s_lg[0][warp] = bl; s_ph[0][warp] = bp; }
+  }
+  __syncthreads();
+  int flags = 0;
+  for (int j = 0; j < nbp; ++j) {
+    const int par = j & 1;
+    // every warp reduces the 16 warp results itself: no second barrier
+    R best = lane < 16 ? s_val[par][lane] : R(-1);
+    int bl = lane < 16 ? s_lg[par][lane] : m;
+    int bp = lane < 16 ? s_ph[par][lane] : 0;
+    warp_best(best, bl, bp);
+    const int p = bl, pph = bp;
+    if (tid == 0) piv[k + j] = k + p;
+    // interchange logical rows j and p
+#pragma unroll
+    for (int r = 0; r < MAXR; ++r) lg[r] = lg[r] == j ? p : (lg[r] == p ? j : lg[r]);
+    const C pv = sP[j * m + pph];
     const bool zero = (pv.x == R(0) && pv.y == R(0));
     if (zero) flags |= LSMS_UNIT_ZERO_PIVOT;
     if (!finite2(pv)) flags |= LSMS_UNIT_NONFINITE;
-    const C r = zero ? mk(R(0), R(0)) : crcp(pv);
-    for (int i = j + 1 + tid; i < m; i += nthr) {
-      const C l = cmul(Pj[i], r);
-      if (!zero) Pj[i] = l;
-      for (int c = j + 1; c < nbp; ++c) sP[c * m + i] = cfms(l, sP[c * m + j], sP[c * m + i]);
+    const C rcp = zero ? mk(R(0), R(0)) : crcp(pv);
+    best = R(-1);
+    bl = m;
+    bp = 0;
+#pragma unroll
+    for (int r = 0; r < MAXR; ++r) {
+      const int ph = tid + NT * r;
+      if (ph < m && lg[r] > j) {
+        const C l = cmul(sP[j * m + ph], rcp);
+        if (!zero) sP[j * m + ph] = l;
+        for (int c = j + 1; c < nbp; ++c) {
+          const C v = cfms(l, sP[c * m + pph], sP[c * m + ph]);
+          sP[c * m + ph] = v;
+          if (c == j + 1) {
+            R a = cabs1(v);
+            if (!(a >= R(0))) a = R(-0.5);
+            if (a > best || (a == best && lg[r] < bl)) { best = a; bl = lg[r]; bp = ph; }
+          }
+        }
+      }
+    }
+    if (j + 1 < nbp) {
+      warp_best(best, bl, bp);
+      if (lane == 0) { s_val[par ^ 1][warp] = best; s_lg[par ^ 1][warp] = bl; s_ph[par ^ 1][warp] = bp; }
     }
     __syncthreads();
   }
-  for (int c = 0; c < nbp; ++c)
-    for (int r = tid; r < m; r += nthr) A[(size_t)(k + c) * n + k + r] = sP[c * m + r];
+  // write back in logical order
+#pragma unroll
+  for (int r = 0; r < MAXR; ++r) {
+    const int ph = tid + NT * r;
+    if (ph < m)
+      for (int c = 0; c < nbp; ++c) A[(size_t)(k + c) * n + k + lg[r]] = sP[c * m + ph];
+  }
   if (tid == 0 && flags) atomicOr(&stat[u.stat_off], flags);
 }
 
 // ------------------------------------------------------------------ swap + trsm
-// One warp per column outside the panel; lane i holds rows k+i (+32 r).
-// Columns left of the panel only take the row swaps; columns to its right also
-// get U12 = L11^{-1} A12.
+// One warp per column right of the panel (lane i holds row k + i): the panel's
+// row interchanges, then U12 = L11^{-1} A12.  Columns left of the panel keep
+// their row order (L is stored as computed, LINPACK style): the forward solve
+// applies each panel's interchanges to the right-hand sides before that panel's
+// columns of L are used.
 constexpr int kSwapCols = 64;  // columns per CTA of k_swap_trsm (8 warps x 8)
 
 template <typename R, int NB>
 __global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ units, char* fac_base, int k) {
   using C = Cx<R>;
-  constexpr int RPL = NB / 32;
+  static_assert(NB == 32, "one lane per panel row");
   const Unit u = units[blockIdx.y];
   const int n = u.n;
-  if (k >= n) return;
-  const int nbp = min(NB, n - k);
-  const int v0 = blockIdx.x * kSwapCols;           // virtual columns: [0, k) left, then right
-  const int n_virtual = n - nbp;
-  if (v0 >= n_virtual) return;
+  const int c0 = k + NB + blockIdx.x * kSwapCols;
+  if (c0 >= n) return;  // columns right of the panel exist only when the panel is full
   C* A = reinterpret_cast<C*>(fac_base + u.fac_off);
   const int32_t* piv = reinterpret_cast<const int32_t*>(fac_base + u.piv_off);
   __shared__ C sL[NB][NB + 1];
   __shared__ int sp[NB];
-  const bool any_right = (k + NB < n) && (v0 + kSwapCols > k);
-  if (any_right) {
-    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
-      const int i = idx % NB, j = idx / NB;
-      sL[i][j] = A[(size_t)(k + j) * n + k + i];
-    }
+  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+    const int i = idx % NB, j = idx / NB;
+    sL[i][j] = A[(size_t)(k + j) * n + k + i];
   }
-  for (int j = threadIdx.x; j < NB; j += blockDim.x) sp[j] = j < nbp ? piv[k + j] : k + j;
+  for (int j = threadIdx.x; j < NB; j += blockDim.x) sp[j] = piv[k + j];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int v = v0 + warp; v < min(v0 + kSwapCols, n_virtual); v += blockDim.x >> 5) {
-  int c;
-  bool right;
-  if (v < k) {
-    c = v;
-    right = false;
-  } else {
-    c = v - k + k + NB;
-    right = true;
-  }
-  C* Ac = A + (size_t)c * n;
-  C x[RPL];
-#pragma unroll
-  for (int r = 0; r < RPL; ++r) {
-    const int i = lane + 32 * r;
-    x[r] = i < nbp ? Ac[k + i] : mk(R(0), R(0));
-  }
-  // Rows below the panel that the swaps touch: when all of them are distinct
-  // (the usual case) each is read once up front and written once at the end;
-  // the swap sequence then runs in registers.  Repeated targets take the
-  // sequential path through memory.
-  bool fast = false;
-  C y = mk(R(0), R(0));
-  int pj = k + lane;
-  if (RPL == 1) {
-    pj = sp[lane];
-    const bool outj = pj >= k + NB;
-    const unsigned same = __match_any_sync(0xffffffffu, outj ? pj : -1 - lane);
-    fast = !__any_sync(0xffffffffu, outj && __popc(same) > 1);
-    if (fast && outj) y = Ac[pj];
-  }
-  if (fast) {
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      const int p = sp[j];
-      if (p == k + j) continue;
-      if (p < k + NB) {
-        const int b = p - k;
-        const C va = shfl2(x[0], j);
-        const C vb = shfl2(x[0], b);
-        if (lane == j) x[0] = vb;
-        if (lane == b) x[0] = va;
-      } else if (lane == j) {
-        const C t = y;
-        y = x[0];
-        x[0] = t;
-      }
-    }
-    if (pj >= k + NB) Ac[pj] = y;
-  } else {
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      const int p = sp[j];
-      if (p == k + j) continue;
-      if (p < k + NB) {
-        const int b = p - k;
-        const C va = shfl2(x[j / 32], j % 32);
-        C vb = x[0];
-#pragma unroll
-        for (int r = 0; r < RPL; ++r)
-          if (b / 32 == r) vb = shfl2(x[r], b % 32);
-        if (lane == j % 32) x[j / 32] = vb;
-#pragma unroll
-        for (int r = 0; r < RPL; ++r)
-          if (b / 32 == r && lane == b % 32) x[r] = va;
-      } else {
-        if (lane == j % 32) {
-          const C t = Ac[p];
-          Ac[p] = x[j / 32];
-          x[j / 32] = t;
-        }
-        __syncwarp();
-      }
-    }
-  }
-  if (right) {
+  const int c1 = min(c0 + kSwapCols, n);
+  for (int c = c0 + warp; c < c1; c += blockDim.x >> 5) {
+    C* Ac = A + (size_t)c * n;
+    C x = panel_swaps(Ac[k + lane], Ac, sp, k, lane);
 #pragma unroll
     for (int j = 0; j < NB - 1; ++j) {
-      const C xj = shfl2(x[j / 32], j % 32);
-#pragma unroll
-      for (int r = 0; r < RPL; ++r) {
-        const int i = lane + 32 * r;
-        if (i > j) x[r] = cfms(sL[i][j], xj, x[r]);
-      }
+      const C xj = shfl2(x, j);
+      if (lane > j) x = cfms(sL[lane][j], xj, x);
     }
+    Ac[k + lane] = x;
   }
-#pragma unroll
-  for (int r = 0; r < RPL; ++r) {
-    const int i = lane + 32 * r;
-    if (i < nbp) Ac[k + i] = x[r];
-  }
-  }  // column loop
-}
-
-// perm[i] = original row now at position i, iperm[perm[i]] = i.  One thread per unit.
-__global__ void k_perm(const Unit* __restrict__ units, int n_units, char* fac_base) {
-  const int ui = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ui >= n_units) return;
-  const Unit u = units[ui];
-  const int n = u.n;
-  int32_t* piv = reinterpret_cast<int32_t*>(fac_base + u.piv_off);
-  int32_t* perm = piv + n;
-  int32_t* iperm = piv + 2 * n;
-  for (int i = 0; i < n; ++i) perm[i] = i;
-  for (int i = 0; i < n; ++i) {
-    const int p = piv[i];
-    const int t = perm[i];
-    perm[i] = perm[p];
-    perm[p] = t;
-  }
-  for (int i = 0; i < n; ++i) iperm[perm[i]] = i;
 }
 
 // ------------------------------------------------------------------ trailing GEMM (SIMT)
@@ -435,9 +419,9 @@ __device__ __forceinline__ void update_rows(const Cx<R>* __restrict__ A, Cx<R>* 
   }
 }
 
-// One CTA of 512 threads per unit: L y = b (unit lower), then U x = y,
-// for the n x nrhs column-major block X whose rows are already permuted by P.
-// The NB x NB triangles are solved by warps taking columns in turn (lane = row, values
+// One CTA of 512 threads per unit: L y = P b (unit lower, each panel's swaps
+// applied just before its block), then U x = y, on the n x nrhs column-major
+// block X.  The NB x NB triangles are solved by warps taking columns in turn (lane = row, values
 // passed by shuffles); the rows below/above are updated by the whole CTA.
 template <typename R, int NB>
 __global__ void __launch_bounds__(512, 2) k_solve(const Unit* __restrict__ units, const char* fac_base, char* ws,
@@ -449,8 +433,10 @@ __global__ void __launch_bounds__(512, 2) k_solve(const Unit* __restrict__ units
   const int n = u.n;
   const C* A = reinterpret_cast<const C*>(fac_base + u.fac_off);
   C* X = reinterpret_cast<C*>(ws + (which == RHS_X ? u.x_off : u.x32_off));
+  const int32_t* piv = reinterpret_cast<const int32_t*>(fac_base + u.piv_off);
   __shared__ C sT[NB][NB + 1];
   __shared__ C sX[NB][33];
+  __shared__ int sp[NB];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nthr = blockDim.x;
   // forward
@@ -460,9 +446,11 @@ __global__ void __launch_bounds__(512, 2) k_solve(const Unit* __restrict__ units
       const int i = idx % NB, j = idx / NB;
       sT[i][j] = (i < nbp && j < nbp) ? A[(size_t)(k + j) * n + k + i] : mk(R(0), R(0));
     }
+    if (tid < NB) sp[tid] = tid < nbp ? piv[k + tid] : k + tid;
     __syncthreads();
     for (int col = warp; col < nrhs; col += nthr >> 5) {
       C x = lane < nbp ? X[(size_t)col * n + k + lane] : mk(R(0), R(0));
+      x = panel_swaps(x, X + (size_t)col * n, sp, k, lane);
       for (int j = 0; j < nbp - 1; ++j) {
         const C xj = shfl2(x, j);
         if (lane > j) x = cfms(sT[lane][j], xj, x);
@@ -503,6 +491,132 @@ __global__ void __launch_bounds__(512, 2) k_solve(const Unit* __restrict__ units
   }
 }
 
+// ------------------------------------------------------------------ complex64 solve
+// The complex64 solve of the mixed form, specialised on the padded right-hand-side
+// count NCOL (columns >= nrhs are zero and never stored).  The update of the rows
+// below (forward) or above (backward) a solved block gives each thread one row
+// and G = min(NCOL, 8) columns: per step j one coalesced 8-byte load of the
+// factor, G/2 16-byte shared-memory loads of the solved block and 4 G FMAs.
+template <int NCOL>
+__device__ __forceinline__ void update_rows_c64(const float2* __restrict__ A, float2* X, const float2 (*sX)[NCOL],
+                                                int n, int k, int nbp, int r0, int r1, int nrhs, int tid) {
+  constexpr int G = NCOL < 8 ? NCOL : 8;
+  constexpr int NG = NCOL / G;
+  constexpr int NB = 32;
+  const int rows = r1 - r0;
+  if (rows <= 0) return;
+  for (int idx = tid; idx < rows * NG; idx += 512) {
+    const int gi = idx / rows;
+    const int i = r0 + (idx - gi * rows);
+    const int g = gi * G;
+    float2 acc[G];
+#pragma unroll
+    for (int c = 0; c < G; ++c) acc[c] = (g + c < nrhs) ? X[(size_t)(g + c) * n + i] : make_float2(0.f, 0.f);
+    const float2* Ai = A + (size_t)k * n + i;
+    if (nbp == NB) {
+#pragma unroll 1
+      for (int j0 = 0; j0 < NB; j0 += 8) {
+        float2 l[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) l[jj] = Ai[(size_t)(j0 + jj) * n];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+#pragma unroll
+          for (int c = 0; c < G; c += 2) {
+            const float4 xx = *reinterpret_cast<const float4*>(&sX[j0 + jj][g + c]);
+            acc[c] = cfms(l[jj], make_float2(xx.x, xx.y), acc[c]);
+            acc[c + 1] = cfms(l[jj], make_float2(xx.z, xx.w), acc[c + 1]);
+          }
+        }
+      }
+    } else {
+      for (int j = 0; j < nbp; ++j) {
+        const float2 l = Ai[(size_t)j * n];
+#pragma unroll
+        for (int c = 0; c < G; c += 2) {
+          const float4 xx = *reinterpret_cast<const float4*>(&sX[j][g + c]);
+          acc[c] = cfms(l, make_float2(xx.x, xx.y), acc[c]);
+          acc[c + 1] = cfms(l, make_float2(xx.z, xx.w), acc[c + 1]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < G; ++c)
+      if (g + c < nrhs) X[(size_t)(g + c) * n + i] = acc[c];
+  }
+}
+
+// One CTA of 512 threads per unit: L y = P b (unit lower, each panel's swaps
+// applied just before its block), then U x = y on the n x nrhs column-major
+// block X.  The 32 x 32
+// triangles are solved by warps taking columns in turn (lane = row, values
+// passed by shuffles, reciprocals of U's diagonal formed before the sweep).
+template <int NCOL>
+__global__ void __launch_bounds__(512, 2) k_solve_c64(const Unit* __restrict__ units, const char* fac_base,
+                                                     char* ws, int which, int nrhs, const int32_t* done) {
+  static_assert(NCOL >= 2 && NCOL % 2 == 0 && NCOL <= 32, "padded column count");
+  constexpr int NB = 32;
+  const Unit u = units[blockIdx.x];
+  if (done && done[u.stat_off]) return;
+  const int n = u.n;
+  const float2* A = reinterpret_cast<const float2*>(fac_base + u.fac_off);
+  float2* X = reinterpret_cast<float2*>(ws + (which == RHS_X ? u.x_off : u.x32_off));
+  const int32_t* piv = reinterpret_cast<const int32_t*>(fac_base + u.piv_off);
+  __shared__ float2 sT[NB][NB + 1];
+  __shared__ __align__(16) float2 sX[NB][NCOL];
+  __shared__ int sp[NB];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // forward
+  for (int k = 0; k < n; k += NB) {
+    const int nbp = min(NB, n - k);
+    for (int idx = tid; idx < NB * NB; idx += 512) {
+      const int i = idx % NB, j = idx / NB;
+      sT[i][j] = (i < nbp && j < nbp) ? A[(size_t)(k + j) * n + k + i] : make_float2(0.f, 0.f);
+    }
+    if (tid < NB) sp[tid] = tid < nbp ? piv[k + tid] : k + tid;
+    __syncthreads();
+    for (int col = warp; col < NCOL; col += 16) {
+      const bool live = col < nrhs && lane < nbp;
+      float2 x = live ? X[(size_t)col * n + k + lane] : make_float2(0.f, 0.f);
+      if (col < nrhs) x = panel_swaps(x, X + (size_t)col * n, sp, k, lane);
+      for (int j = 0; j < nbp - 1; ++j) {
+        const float2 xj = shfl2(x, j);
+        if (lane > j) x = cfms(sT[lane][j], xj, x);
+      }
+      if (live) X[(size_t)col * n + k + lane] = x;
+      sX[lane][col] = x;
+    }
+    __syncthreads();
+    update_rows_c64<NCOL>(A, X, sX, n, k, nbp, k + nbp, n, nrhs, tid);
+    __syncthreads();
+  }
+  // backward
+  const int last = ((n - 1) / NB) * NB;
+  for (int k = last; k >= 0; k -= NB) {
+    const int nbp = min(NB, n - k);
+    for (int idx = tid; idx < NB * NB; idx += 512) {
+      const int i = idx % NB, j = idx / NB;
+      sT[i][j] = (i < nbp && j < nbp) ? A[(size_t)(k + j) * n + k + i] : make_float2(i == j ? 1.f : 0.f, 0.f);
+    }
+    __syncthreads();
+    for (int col = warp; col < NCOL; col += 16) {
+      const bool live = col < nrhs && lane < nbp;
+      const float2 dinv = crcp(sT[lane][lane]);
+      float2 x = live ? X[(size_t)col * n + k + lane] : make_float2(0.f, 0.f);
+      for (int j = nbp - 1; j >= 0; --j) {
+        if (lane == j) x = cmul(x, dinv);
+        const float2 xj = shfl2(x, j);
+        if (lane < j) x = cfms(sT[lane][j], xj, x);
+      }
+      if (live) X[(size_t)col * n + k + lane] = x;
+      sX[lane][col] = x;
+    }
+    __syncthreads();
+    update_rows_c64<NCOL>(A, X, sX, n, k, nbp, 0, k, nrhs, tid);
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ wrappers
 template <typename R>
 int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base, int32_t* stat,
@@ -524,11 +638,11 @@ int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
     const int rows_smem = std::min(m_max, max_rows);
     LSMS_LAUNCH((k_panel_smem<R, NB>), dim3(n_units), dim3(512), (size_t)rows_smem * NB * sizeof(Cx<R>), st,
                 d_units, fac_base, k, stat, max_rows);
-    // one warp per column outside the panel: left ones [0, k), right ones [k + NB, n)
-    LSMS_LAUNCH((k_swap_trsm<R, NB>), dim3((n_max + kSwapCols - 1) / kSwapCols, n_units), dim3(256), 0, st, d_units,
-                fac_base, k);
     const int trail = n_max - k - NB;
     if (trail <= 0) continue;
+    // one warp per column right of the panel
+    LSMS_LAUNCH((k_swap_trsm<R, NB>), dim3((trail + kSwapCols - 1) / kSwapCols, n_units), dim3(256), 0, st, d_units,
+                fac_base, k);
     if constexpr (std::is_same<R, float>::value) {
       // complex64: the trailing update runs on the tensor cores (3xTF32, tc_gemm.cu)
       const int rc = gemm_tc_chunk(d_units, n_units, n_max, k, fac_base, stat, st);
@@ -538,7 +652,6 @@ int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
       LSMS_LAUNCH((k_gemm<R, NB>), dim3(tiles * tiles, n_units), dim3(256), 0, st, d_units, fac_base, k, tiles);
     }
   }
-  LSMS_LAUNCH(k_perm, dim3((n_units + 127) / 128), dim3(128), 0, st, d_units, n_units, fac_base);
   return LSMS_OK;
 }
 
@@ -547,7 +660,16 @@ int lu_solve_chunk(const Unit* d_units, int n_units, const char* fac_base, char*
                    const int32_t* done, cudaStream_t st) {
   if (nrhs < 1 || nrhs > 32) return fail(LSMS_ERR_ARG, "internal: nrhs %d out of range", nrhs);
   constexpr int NB = LuCfg<R>::NB;
-  LSMS_LAUNCH((k_solve<R, NB>), dim3(n_units), dim3(512), 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
+  if constexpr (std::is_same<R, float>::value) {
+    const dim3 g(n_units), b(512);
+    if (nrhs <= 2) LSMS_LAUNCH(k_solve_c64<2>, g, b, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
+    else if (nrhs <= 4) LSMS_LAUNCH(k_solve_c64<4>, g, b, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
+    else if (nrhs <= 8) LSMS_LAUNCH(k_solve_c64<8>, g, b, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
+    else if (nrhs <= 16) LSMS_LAUNCH(k_solve_c64<16>, g, b, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
+    else LSMS_LAUNCH(k_solve_c64<32>, g, b, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
+  } else {
+    LSMS_LAUNCH((k_solve<R, NB>), dim3(n_units), dim3(512), 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
+  }
   return LSMS_OK;
 }
 

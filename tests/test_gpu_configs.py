@@ -40,7 +40,7 @@ def _run(B, w, precision, ws_gib=16, J=None):
     sp = torch.as_tensor(w.species).cuda()
     tau, st = B.tau_blocks(lz, w.lmax, sp, torch.as_tensor(w.tinv).cuda(), w.z, precision, workspace=ws)
     Jd = torch.as_tensor(B.dipole_current(w.lmax, w.r_ll) if J is None else J).cuda()
-    sig, _, rho = B.kubo_sigma(lz, w.lmax, sp, Jd, tau, w.n_delta, w.volume)
+    sig, _, rho = B.kubo_sigma(lz, w.lmax, sp, Jd, tau, w.n_delta, w.volume, precision=precision)
     torch.cuda.synchronize()
     del ws
     return lz, tau, st.cpu().numpy(), sig.cpu().numpy()

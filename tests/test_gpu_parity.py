@@ -167,7 +167,8 @@ def gpu_sigma(w, precision, J=None):
     lz, tau, st, _ = gpu_tau(w, precision)
     Jh = B.dipole_current(w.lmax, w.r_ll) if J is None else J
     sp = torch.as_tensor(w.species).cuda()
-    sig, sigt, rho = B.kubo_sigma(lz, w.lmax, sp, torch.as_tensor(Jh).cuda(), tau, w.n_delta, w.volume)
+    sig, sigt, rho = B.kubo_sigma(lz, w.lmax, sp, torch.as_tensor(Jh).cuda(), tau, w.n_delta, w.volume,
+                                  precision=precision)
     torch.cuda.synchronize()
     return sig.cpu().numpy(), sigt.cpu().numpy(), rho.cpu().numpy()
 

@@ -59,6 +59,16 @@ def test_noalloc_matches_allocating_entry_point_twice(B):
         assert np.abs(ref[0].cpu().numpy()).max() > 0
 
 
+def test_noalloc_matches_in_the_mixed_form(B):
+    """The double-float trace variant through both entry points."""
+    w, lz, sp, tau, J = _case(B, 34)
+    ref = B.kubo_sigma(lz, w.lmax, sp, J, tau, w.n_delta, w.volume, precision="mixed")
+    got = B.kubo_sigma_noalloc(lz, w.lmax, sp, J, tau, w.n_delta, w.volume, precision="mixed")
+    torch.cuda.synchronize()
+    for g, r in zip(got, ref):
+        assert _close(g, r)
+
+
 def test_noalloc_back_to_back_on_one_problem(B):
     """Two consecutive calls on the same inputs (the second reuses the array the
     first left behind) give the allocating entry point's result both times."""
@@ -81,7 +91,7 @@ def test_noalloc_rejects_oversized_problems_on_the_host(B):
     import ctypes
     rc = B.lib().lsms_kubo_sigma_noalloc(lz.handle, 3, ctypes.c_void_p(sp.data_ptr()), 1,
                                          ctypes.c_void_p(dummy.data_ptr()), 0, ctypes.c_void_p(dummy.data_ptr()),
-                                         32, 1000.0, None, ctypes.c_void_p(dummy.data_ptr()), None, None)
+                                         32, 1000.0, 0, None, ctypes.c_void_p(dummy.data_ptr()), None, None)
     assert rc == -1
     msg = B.lib().lsms_last_error().decode()
     assert "static buffer" in msg and "lsms_kubo_sigma" in msg
