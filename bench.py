@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64-form comparison leg")
+    ap.add_argument("--no-conj-leg", action="store_true", help="skip the conjugate-pair leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chunk-mb", type=int, default=0,
                     help="workspace size in MiB (units are processed in chunks that fit); 0 = all units at once")
@@ -293,10 +294,10 @@ def run_ours(args):
     gs_d = torch.as_tensor(grad_sigma).to(dev)
     stream = torch.cuda.current_stream(dev)
 
-    def make(precision):
+    def make(precision, conj_pairs=False):
         return Problem(w.pos, w.lattice, w.r_liz, w.lmax, w.species, w.tinv, w.z, J, w.volume,
                        precision=precision, device=dev, keep_factors=True,
-                       workspace_bytes=(args.chunk_mb << 20) if args.chunk_mb else None)
+                       workspace_bytes=(args.chunk_mb << 20) if args.chunk_mb else None, conj_pairs=conj_pairs)
 
     def step(p):
         p.forward()
@@ -372,9 +373,30 @@ def run_ours(args):
     # end-to-end through the public host-to-host API
     e2e = measure_e2e(w, J, args, dev, stream, active, world)
 
+    # conjugate-pair mode (tau(conj z) = conj tau(z): only the z systems are factored);
+    # reported on its own, never counted as solves
+    conj = None
+    if not args.no_conj_leg:
+        pc = make(args.precision, conj_pairs=True)
+        sgc = StepGraph(pc, gs_d)
+        msc = timed_fn(lambda _p: sgc.replay(), pc, args.steps, args.warmup)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            pc.forward()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        conj = {"ms_per_step": msc, "sigma_ms": ev0.elapsed_time(ev1) / args.steps,
+                "factored_units": units // 2, "tau_results": units,
+                "sigma_rel_diff_vs_main": float(np.abs(pc.sigma_out.cpu().numpy() - main_sigma).max()
+                                                / np.abs(main_sigma).max()),
+                "note": "LSMS_CONJ_PAIRS: z_- = conj z_+ and t^-1(z_-) = conj t^-1(z_+), so only the z_+ LIZ "
+                        "matrices are factored; not counted in value"}
+        del sgc, pc
+        torch.cuda.empty_cache()
+
     fp64 = None
     if not args.no_fp64_leg and args.precision != "fp64":
-        del main
+        del sg, main
         torch.cuda.empty_cache()
         p64 = make("fp64")
         ms64, _ = timed(p64, max(1, min(args.steps, 2)), 1)
@@ -426,7 +448,7 @@ def run_ours(args):
         "ir_probes_mean": float(fwd_probes.mean()), "ir_probes_adjoint_mean": float(bwd_probes.mean()),
         "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
         "kernels": roof_all,
-        "cpu_baseline": cpu, "fp64_form": fp64, "accuracy_vs_oracle": acc,
+        "cpu_baseline": cpu, "fp64_form": fp64, "conj_pairs": conj, "accuracy_vs_oracle": acc,
     }
     if fp64:
         line["speedup_vs_fp64_form"] = value / fp64["value"]
@@ -522,6 +544,7 @@ def roofline(kt, w, n_list, fwd_passes, bwd_passes, precision, traffic):
         return None, None
     models = kernel_models(w, n_list, fwd_passes, bwd_passes, precision)
     # one row per kernel: the template instances (right-hand-side counts etc.) summed
+    raw = dict(kt)
     merged = {}
     for name, (ms, launches) in kt.items():
         base = name.split("<")[0]
@@ -547,12 +570,12 @@ def roofline(kt, w, n_list, fwd_passes, bwd_passes, precision, traffic):
                 row.update({"bound": "hbm", "achieved": gbs, "peak": PEAKS["hbm_gbs"], "unit": "GB/s",
                             "frac": gbs / PEAKS["hbm_gbs"]})
             row["tensor_frac" if base == "k_gemm_tc" else "alu_frac"] = ach / peak
-        row["instances"] = instances[base]
+        row["instances"] = {nm: round(raw[nm][0], 4) for nm in instances[base]}
         rows[base] = row
     for name, (ms, launches) in kt.items():  # unmodelled kernels: time only
         if name not in rows:
             rows[name] = {"kernel": name, "ms_per_step": ms, "launches_per_step": launches,
-                          "instances": instances[name]}
+                          "instances": {nm: round(raw[nm][0], 4) for nm in instances[name]}}
     modelled = [r for r in rows.values() if "frac" in r]
     if not modelled:
         return None, rows

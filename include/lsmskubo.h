@@ -74,6 +74,22 @@ enum lsms_precision {
                       refinement of the tau column block to FP64 accuracy */
 };
 
+/* Flag OR-ed into the precision argument of lsms_tau_blocks,
+ * lsms_kubo_sigma_backward, lsms_tau_workspace_bytes,
+ * lsms_backward_workspace_bytes and lsms_lu_store_bytes: conjugate pairs.
+ * The energies come in pairs z[2d + 1] = conj z[2d] (checked on the host,
+ * exactly; LSMS_ERR_ARG otherwise) whose t^{-1} blocks are conjugate too
+ * (checked on the device to 1e-12 of the block's largest entry; a pair that
+ * fails sets LSMS_UNIT_BAD_INPUT on the second energy's units).  Then
+ * M(conj z) = conj M(z) in the real-harmonic basis (g(z*) = conj g(z)), so
+ * only the first energy of each pair is assembled and factored:
+ * tau(conj z) = conj tau(z), and the adjoint solves M(conj z) X = B as
+ * X = conj(M(z)^{-1} conj B) with the first energy's factors.  The solves
+ * and refinement of the second energies are skipped in the forward (their
+ * unit_status words copy the first energy's); lu_store then holds the first
+ * energies' factors only, so use the flag in both calls or in neither. */
+#define LSMS_CONJ_PAIRS 0x100
+
 /* Unit status values written to unit_status[e][m] (0 = fine). */
 #define LSMS_UNIT_OK 0
 #define LSMS_UNIT_ZERO_PIVOT 1
@@ -130,7 +146,7 @@ int lsms_gaunt_table(int lmax, double* C);
  * species      dev [n_atoms] int32 species index of each atom (< n_species).
  * tinv         dev [n_species][n_energy][K][K] t^{-1}(z_e), complex-symmetric.
  * z            host [n_energy] complex energies (Im z != 0 recommended).
- * precision    LSMS_FP64 or LSMS_MIXED.
+ * precision    LSMS_FP64 or LSMS_MIXED, optionally | LSMS_CONJ_PAIRS.
  * tau          dev [n_energy][S_total][K][K] output: tau[e][s] = tau^{s 0} of
  *              the LIZ that site s belongs to (row L, column L').
  * unit_status  dev [n_energy][n_atoms] int32 output, or NULL: bits 0-7 the
@@ -139,7 +155,7 @@ int lsms_gaunt_table(int lmax, double* C);
  *              for FP64).  Mixed form: a sweep adds the complex64 correction
  *              D = (LU)^-1 (B - M X) (residual in double-float, ~2^-48) to X and
  *              stops when ||D||_F <= 1e-10 ||X||_F; after each sweep a probe
- *              takes the same test on 2 random +-1 combinations of the columns
+ *              takes the same test on 2 random complex Gaussian combinations of the columns
  *              (y = X w: ||(LU)^-1 (B w - M y)|| <= 1e-10 ||y||) and stops
  *              there when both pass, so X carries the correction test's error
  *              bound without a further full sweep.  LSMS_UNIT_NOCONV after 6

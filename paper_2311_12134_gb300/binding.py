@@ -196,14 +196,20 @@ def lu_store_bytes(liz, lmax, n_energy, precision):
     return a.value
 
 
-def _prec(precision):
-    return PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+LSMS_CONJ_PAIRS = 0x100
+
+
+def _prec(precision, conj_pairs=False):
+    """Precision argument of the C ABI: "fp64"/"mixed" (or the enum), | LSMS_CONJ_PAIRS."""
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return p | (LSMS_CONJ_PAIRS if conj_pairs else 0)
 
 
 def tau_blocks(liz, lmax, species, tinv, z, precision="fp64", tau=None, unit_status=None, workspace=None,
-               lu_store=None, stream=None):
+               lu_store=None, stream=None, conj_pairs=False):
     """lsms_tau_blocks.  species int32 [N] (cuda), tinv complex128 [n_species, n_energy, K, K] (cuda),
-    z host complex [n_energy].  Returns (tau [n_energy, S_total, K, K], unit_status [n_energy, N])."""
+    z host complex [n_energy].  Returns (tau [n_energy, S_total, K, K], unit_status [n_energy, N]).
+    conj_pairs: LSMS_CONJ_PAIRS (energies in (z, conj z) pairs; only z is factored)."""
     import torch
     K = (lmax + 1) ** 2
     zh, zp = _host(z, np.complex128)
@@ -218,7 +224,8 @@ def tau_blocks(liz, lmax, species, tinv, z, precision="fp64", tau=None, unit_sta
                                                          workspace.numel())
     st_p, st_n = (_P(0), 0) if lu_store is None else (_dev(lu_store, torch.uint8, None, "lu_store"), lu_store.numel())
     _check(lib().lsms_tau_blocks(liz.handle, lmax, _dev(species, torch.int32, (liz.n_atoms,), "species"), n_species,
-                                 _dev(tinv, torch.complex128, (n_species, nE, K, K), "tinv"), zp, nE, _prec(precision),
+                                 _dev(tinv, torch.complex128, (n_species, nE, K, K), "tinv"), zp, nE,
+                                 _prec(precision, conj_pairs),
                                  _dev(tau, torch.complex128, (nE, liz.total_sites, K, K), "tau"),
                                  _dev(unit_status, torch.int32, (nE, liz.n_atoms), "unit_status"), ws_p, ws_n, st_p,
                                  st_n, _stream(stream)))
@@ -274,7 +281,7 @@ def kubo_sigma_noalloc(liz, lmax, species, J, tau, n_delta, volume, J_delta_stri
 
 def kubo_sigma_backward(liz, lmax, species, tinv, z, J, tau, volume, grad_sigma, precision="fp64", lu_store=None,
                         J_delta_stride=0, grad_tinv=None, grad_tinv_species=None, unit_status=None, workspace=None,
-                        stream=None):
+                        stream=None, conj_pairs=False):
     """lsms_kubo_sigma_backward.  Returns (grad_tinv [n_energy, N, K, K], grad_tinv_species [n_species, n_energy, K, K])."""
     import torch
     K = (lmax + 1) ** 2
@@ -291,7 +298,7 @@ def kubo_sigma_backward(liz, lmax, species, tinv, z, J, tau, volume, grad_sigma,
     st_p, st_n = (_P(0), 0) if lu_store is None else (_dev(lu_store, torch.uint8, None, "lu_store"), lu_store.numel())
     _check(lib().lsms_kubo_sigma_backward(
         liz.handle, lmax, _dev(species, torch.int32, (liz.n_atoms,), "species"), n_species,
-        _dev(tinv, torch.complex128, (n_species, nE, K, K), "tinv"), zp, nE, _prec(precision),
+        _dev(tinv, torch.complex128, (n_species, nE, K, K), "tinv"), zp, nE, _prec(precision, conj_pairs),
         _dev(J, torch.complex128, None, "J"), int(J_delta_stride),
         _dev(tau, torch.complex128, (nE, liz.total_sites, K, K), "tau"), float(volume),
         _dev(grad_sigma, torch.complex128, (nE // 2, 3, 3), "grad_sigma"), st_p, st_n,

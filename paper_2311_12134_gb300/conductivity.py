@@ -17,11 +17,12 @@ class Problem:
     pos [N,3], lattice [3,3] or None, r_liz, lmax, species [N] (host), tinv
     [n_species, 2 n_delta, K, K] (host or device complex128), z [2 n_delta]
     complex (E_F + i d, E_F - i d per delta), J [n_species, 4, 3, K, K] (host or
-    device complex128), volume (bohr^3).
+    device complex128), volume (bohr^3).  conj_pairs: the (z, conj z) pairs have
+    conjugate t^-1, so only z is factored (tau(conj z) = conj tau(z)).
     """
 
     def __init__(self, pos, lattice, r_liz, lmax, species, tinv, z, J, volume, precision="fp64", device="cuda",
-                 keep_factors=True, workspace_bytes=None):
+                 keep_factors=True, workspace_bytes=None, conj_pairs=False):
         import torch
         self.lmax = int(lmax)
         self.K = (self.lmax + 1) ** 2
@@ -32,17 +33,18 @@ class Problem:
         self.n_delta = self.z.shape[0] // 2
         self.volume = float(volume)
         self.precision = precision
+        self.conj_pairs = bool(conj_pairs)  # energies in (z, conj z) pairs: factor z only
         self.device = torch.device(device)
         self.species = torch.as_tensor(np.ascontiguousarray(species, dtype=np.int32)).to(self.device)
         self.tinv = torch.as_tensor(tinv).to(device=self.device, dtype=torch.complex128).contiguous()
         self.J = torch.as_tensor(J).to(device=self.device, dtype=torch.complex128).contiguous()
         nE = self.z.shape[0]
-        mn, al = B.tau_workspace_bytes(self.liz, self.lmax, nE, B._prec(precision))
+        mn, al = B.tau_workspace_bytes(self.liz, self.lmax, nE, B._prec(precision, self.conj_pairs))
         ws = al if workspace_bytes is None else max(mn, int(workspace_bytes))
         self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
         self.lu_store = None
         if keep_factors:
-            self.lu_store = torch.empty(B.lu_store_bytes(self.liz, self.lmax, nE, B._prec(precision)),
+            self.lu_store = torch.empty(B.lu_store_bytes(self.liz, self.lmax, nE, B._prec(precision, self.conj_pairs)),
                                         dtype=torch.uint8, device=self.device)
         self.tau = torch.empty((nE, self.liz.total_sites, self.K, self.K), dtype=torch.complex128,
                                device=self.device)
@@ -60,7 +62,8 @@ class Problem:
     def solve_tau(self, tinv=None, stream=None):
         t = self.tinv if tinv is None else tinv
         B.tau_blocks(self.liz, self.lmax, self.species, t, self.z, self.precision, tau=self.tau,
-                     unit_status=self.unit_status, workspace=self.workspace, lu_store=self.lu_store, stream=stream)
+                     unit_status=self.unit_status, workspace=self.workspace, lu_store=self.lu_store, stream=stream,
+                     conj_pairs=self.conj_pairs)
         return self.tau
 
     def sigma(self, stream=None):
@@ -77,13 +80,15 @@ class Problem:
         """PyTorch gradients of Re sum(conj(grad_sigma) sigma): per site [nE, N, K, K] and per species."""
         import torch
         if self._bw_ws is None:
-            mn, al = B.backward_workspace_bytes(self.liz, self.lmax, self.z.shape[0], B._prec(self.precision))
+            mn, al = B.backward_workspace_bytes(self.liz, self.lmax, self.z.shape[0],
+                                                B._prec(self.precision, self.conj_pairs))
             self._bw_ws = torch.empty(min(al, max(mn, self.workspace.numel())), dtype=torch.uint8,
                                       device=self.device)
         t = self.tinv if tinv is None else tinv
         return B.kubo_sigma_backward(self.liz, self.lmax, self.species, t, self.z, self.J, self.tau, self.volume,
                                      grad_sigma.contiguous(), self.precision, lu_store=self.lu_store,
-                                     unit_status=self.bw_status, workspace=self._bw_ws, stream=stream)
+                                     unit_status=self.bw_status, workspace=self._bw_ws, stream=stream,
+                                     conj_pairs=self.conj_pairs)
 
 
 def _sigma_fn():

@@ -166,7 +166,7 @@ int existing_device_data(lsms_liz* liz, DeviceData** out) {
 
 // ------------------------------------------------------------------ plans
 struct UnitBytes {
-  size_t fac, piv, m64, x, b, x32, probe;
+  size_t fac, piv, m64, x, b, x32, probe, xdf;
 };
 
 static UnitBytes unit_bytes(int n, int precision, int nrhs, bool backward) {
@@ -180,12 +180,28 @@ static UnitBytes unit_bytes(int n, int precision, int nrhs, bool backward) {
   // complex64 corrections; the convergence probe uses the first kProbe columns
   ub.x32 = precision == LSMS_FP64 ? 0 : align_up((size_t)n * std::max(nrhs, kProbe) * 8);
   ub.probe = precision == LSMS_FP64 ? 0 : align_up((size_t)n * kProbe * 2 * 16);  // y_q and (B w)_q
+  ub.xdf = precision == LSMS_FP64 ? 0 : align_up((size_t)n * nrhs * 16);          // X as float4 (hi, lo)
   return ub;
 }
 
-static size_t ws_unit_bytes(const UnitBytes& ub, bool store) {
-  // with a factor store, the factors, pivots and (mixed form) the double-float copy of M live there
-  return (store ? 0 : ub.fac + ub.piv + ub.m64) + ub.x + ub.b + ub.x32 + ub.probe;
+// Workspace bytes of a unit: the right-hand-side blocks, plus the factors,
+// pivots and (mixed form) the double-float copy of M when the unit owns factors
+// that live in the workspace (no factor store).
+static size_t ws_unit_bytes(const UnitBytes& ub, bool factors_in_ws) {
+  return (factors_in_ws ? ub.fac + ub.piv + ub.m64 : 0) + ub.x + ub.b + ub.x32 + ub.probe + ub.xdf;
+}
+
+// Energies of one atom solved by a plan, and whether each owns factors.
+// conj: energies come in (z, conj z) pairs; the forward solves only the first
+// of each pair, the backward solves both with the first one's factors.
+static void plan_energies(int n_energy, bool conj, bool backward, std::vector<int>* es, std::vector<char>* owns) {
+  es->clear();
+  owns->clear();
+  for (int e = 0; e < n_energy; ++e) {
+    if (conj && (e & 1) && !backward) continue;
+    es->push_back(e);
+    owns->push_back(!(conj && (e & 1)));
+  }
 }
 
 // Atoms sorted by LIZ size (largest first, then atom index); every energy of an atom is adjacent.
@@ -214,6 +230,9 @@ static WsHeader ws_header(const lsms_liz* liz, int n_energy, size_t extra_bytes)
   return h;
 }
 
+// Conjugate-pair mode: one flag per energy pair (t^-1 pair not conjugate).
+static size_t conj_extra_bytes(int n_energy) { return align_up((size_t)(n_energy / 2 + 1) * 4); }
+
 static size_t backward_extra_bytes(const lsms_liz* liz, int lmax, int n_energy) {
   const size_t KK = (size_t)(lmax + 1) * (lmax + 1) * (lmax + 1) * (lmax + 1);
   const int n_delta = n_energy / 2;
@@ -221,9 +240,9 @@ static size_t backward_extra_bytes(const lsms_liz* liz, int lmax, int n_energy) 
 }
 
 static int get_plan(lsms_liz* liz, DeviceData* dd, int lmax, int n_energy, int precision, int nrhs, bool backward,
-                    bool store, size_t chunk_bytes, Plan** out) {
-  const auto key = std::make_tuple(lmax, n_energy, precision, nrhs * 4 + (backward ? 2 : 0) + (store ? 1 : 0),
-                                   chunk_bytes, 0);
+                    bool store, bool conj, size_t chunk_bytes, Plan** out) {
+  const auto key = std::make_tuple(lmax, n_energy, precision,
+                                   nrhs * 8 + (conj ? 4 : 0) + (backward ? 2 : 0) + (store ? 1 : 0), chunk_bytes, 0);
   std::lock_guard<std::mutex> lk(liz->mu);
   auto it = dd->plans.find(key);
   if (it != dd->plans.end()) {
@@ -237,43 +256,59 @@ static int get_plan(lsms_liz* liz, DeviceData* dd, int lmax, int n_energy, int p
   p.precision = precision;
   p.nrhs = nrhs;
   p.store = store;
+  p.conj = conj;
   p.ws_bytes = chunk_bytes;
+  std::vector<int> es;
+  std::vector<char> owns;
+  plan_energies(n_energy, conj, backward, &es, &owns);
+  p.fac_per_atom = (int)std::count(owns.begin(), owns.end(), 1);
   const std::vector<int> order = atom_order(liz);
   size_t store_off = 0;
   size_t cur = 0;
-  Chunk ch{0, 0, 0, 0};
+  Chunk ch{0, 0, 0, 0, 0, 0};
   for (int m : order) {
     const int S = (int)(liz->offsets[m + 1] - liz->offsets[m]);
     const int n = K * S;
     const UnitBytes ub = unit_bytes(n, precision, nrhs, backward);
-    const size_t need = ws_unit_bytes(ub, store);
-    if (need * n_energy > chunk_bytes)
-      return fail(LSMS_ERR_NOMEM, "workspace of %zu bytes cannot hold the %d energies of one atom (%zu bytes)",
-                  chunk_bytes, n_energy, need * n_energy);
-    if (cur + need * n_energy > chunk_bytes) {  // chunks hold whole atoms (all energies)
+    size_t need = 0;
+    for (size_t i = 0; i < es.size(); ++i) need += ws_unit_bytes(ub, owns[i] && !store);
+    if (need > chunk_bytes)
+      return fail(LSMS_ERR_NOMEM, "workspace of %zu bytes cannot hold the %zu energies of one atom (%zu bytes)",
+                  chunk_bytes, es.size(), need);
+    if (cur + need > chunk_bytes) {  // chunks hold whole atoms (all energies)
       ch.u1 = (int)p.units.size();
+      ch.f1 = (int)p.fac_units.size();
       ch.ws_bytes = cur;
       p.chunks.push_back(ch);
-      ch = Chunk{(int)p.units.size(), 0, 0, 0};
+      ch = Chunk{(int)p.units.size(), 0, (int)p.fac_units.size(), 0, 0, 0};
       cur = 0;
     }
-    for (int e = 0; e < n_energy; ++e) {
+    Unit owner{};
+    for (size_t i = 0; i < es.size(); ++i) {
       Unit u{};
       u.atom = m;
-      u.energy = e;
+      u.energy = es[i];
       u.n = n;
       u.S = S;
       u.site_off = liz->offsets[m];
-      if (store) {
-        u.fac_off = (int64_t)store_off;
-        u.piv_off = (int64_t)(store_off + ub.fac);
-        u.m64_off = (int64_t)(store_off + ub.fac + ub.piv);
-        store_off += ub.fac + ub.piv + ub.m64;
-      } else {
-        u.fac_off = (int64_t)cur;
-        u.piv_off = (int64_t)(cur + ub.fac);
-        u.m64_off = (int64_t)(cur + ub.fac + ub.piv);
-        cur += ub.fac + ub.piv + ub.m64;
+      if (owns[i]) {
+        if (store) {
+          u.fac_off = (int64_t)store_off;
+          u.piv_off = (int64_t)(store_off + ub.fac);
+          u.m64_off = (int64_t)(store_off + ub.fac + ub.piv);
+          store_off += ub.fac + ub.piv + ub.m64;
+        } else {
+          u.fac_off = (int64_t)cur;
+          u.piv_off = (int64_t)(cur + ub.fac);
+          u.m64_off = (int64_t)(cur + ub.fac + ub.piv);
+          cur += ub.fac + ub.piv + ub.m64;
+        }
+        owner = u;
+      } else {  // second energy of a conjugate pair: the first one's factors (just placed)
+        u.fac_off = owner.fac_off;
+        u.piv_off = owner.piv_off;
+        u.m64_off = owner.m64_off;
+        u.conj = 1;
       }
       u.x_off = (int64_t)cur;
       cur += ub.x;
@@ -283,16 +318,21 @@ static int get_plan(lsms_liz* liz, DeviceData* dd, int lmax, int n_energy, int p
       cur += ub.x32;
       u.p_off = (int64_t)cur;
       cur += ub.probe;
-      u.stat_off = (int64_t)e * liz->n_atoms + m;  // index of this unit's status word
+      u.xdf_off = (int64_t)cur;
+      cur += ub.xdf;
+      u.stat_off = (int64_t)es[i] * liz->n_atoms + m;  // index of this unit's status word
       ch.n_max = std::max(ch.n_max, n);
       p.units.push_back(u);
+      if (owns[i]) p.fac_units.push_back(u);
     }
   }
   ch.u1 = (int)p.units.size();
+  ch.f1 = (int)p.fac_units.size();
   ch.ws_bytes = cur;
   p.chunks.push_back(ch);
   int rc = upload(&p.d_units, p.units);
   if (rc) return rc;
+  if ((rc = upload(&p.d_fac_units, p.fac_units))) return rc;
   it = dd->plans.emplace(key, std::move(p)).first;
   *out = &it->second;
   return LSMS_OK;
@@ -619,15 +659,19 @@ __global__ void k_copy_b(const Unit* __restrict__ units, char* ws, int nrhs, boo
   }
 }
 
-// X = X32 widened.
+// X = X32 widened (and its double-float copy, lo parts zero).
 __global__ void k_widen(const Unit* __restrict__ units, char* ws, int nrhs) {
   const Unit u = units[blockIdx.y];
   const int n = u.n;
   const float2* X32 = reinterpret_cast<const float2*>(ws + u.x32_off);
   double2* X = reinterpret_cast<double2*>(ws + u.x_off);
+  float4* Xdf = reinterpret_cast<float4*>(ws + u.xdf_off);
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)n * nrhs;
-       idx += (int64_t)gridDim.x * blockDim.x)
-    X[idx] = to64(X32[idx]);
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const float2 x = X32[idx];
+    X[idx] = to64(x);
+    Xdf[idx] = make_float4(x.x, 0.f, x.y, 0.f);
+  }
 }
 
 // Refinement residual, FP64-accurate, on the FP32 pipes: B - M X with M held as
@@ -647,7 +691,7 @@ __global__ void __launch_bounds__(256, 3) k_residual(const Unit* __restrict__ un
   const int row0 = blockIdx.x * 64;
   if (row0 >= n) return;
   const float4* M = reinterpret_cast<const float4*>(fac_base + u.m64_off);
-  const double2* X = reinterpret_cast<const double2*>(ws + u.x_off);
+  const float4* Xdf = reinterpret_cast<const float4*>(ws + u.xdf_off);  // X as (hi, lo) pairs
   float2* X32 = reinterpret_cast<float2*>(ws + u.x32_off);
   __shared__ float4 sX[32][NCOL + 1];
   const int tid = threadIdx.x;
@@ -664,7 +708,7 @@ __global__ void __launch_bounds__(256, 3) k_residual(const Unit* __restrict__ un
     for (int idx = tid; idx < 32 * NCOL; idx += 256) {
       const int jj = idx & 31, c = idx >> 5;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (jj < jn && c < NRHS) v = df_split(X[(size_t)c * n + j0 + jj]);
+      if (jj < jn && c < NRHS) v = Xdf[(size_t)c * n + j0 + jj];
       sX[jj][c] = v;
     }
     __syncthreads();
@@ -714,23 +758,35 @@ __global__ void __launch_bounds__(256, 3) k_residual(const Unit* __restrict__ un
   }
 }
 
-// Probe weights w_q[c] = +-1, from the integer hash "lowbias32" (C. Wellons) of
-// (unit, sweep, q, c): a fixed pseudo-random sign pattern per unit and sweep.
-__device__ __forceinline__ double probe_sign(int64_t unit, int sweep, int q, int c) {
-  uint32_t h = (uint32_t)(((unit * 16 + sweep) * 4 + q) * 64 + c);
+// Probe weights: w_q[c] complex Gaussian (Box-Muller on two uniforms), the
+// uniforms from the integer hash "lowbias32" (C. Wellons) of (unit, sweep, q, c,
+// draw): a fixed pseudo-random vector per unit and sweep.  Gaussian weights
+// make ||D w|| small only with probability ~ the squared ratio, whatever the
+// structure of D.
+__device__ __forceinline__ uint32_t probe_hash(uint32_t h) {
   h ^= h >> 16;
   h *= 0x7feb352du;
   h ^= h >> 15;
   h *= 0x846ca68bu;
   h ^= h >> 16;
-  return (h & 1u) ? 1.0 : -1.0;
+  return h;
+}
+
+__device__ __forceinline__ double2 probe_weight(int64_t unit, int sweep, int q, int c) {
+  const uint32_t key = (uint32_t)((((unit * 16 + sweep) * 4 + q) * 64 + c) * 2);
+  const double u1 = ((double)probe_hash(key) + 1.0) * 0x1p-32;  // (0, 1]
+  const double u2 = (double)probe_hash(key + 1) * 0x1p-32;      // [0, 1)
+  const double r = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  return make_double2(r * cs, r * sn);
 }
 
 // X += X32 (the correction); done when ||correction||_F <= tol ||X||_F.  One CTA
 // per unit.  Each sweep adds 1 << 8 to the unit's status word (pass count).
-// Mixed form: also forms the convergence-probe inputs y_q = X w_q and
-// (B w)_q for kProbe sign vectors w_q (FP64; the sums are exact up to rounding),
-// stored as [q][n] complex128 at p_off and p_off + kProbe n.
+// Mixed form: also keeps X's double-float copy and forms the convergence-probe
+// inputs y_q = X w_q and (B w)_q for kProbe complex Gaussian vectors w_q (FP64),
+// stored as [q][n] (hi, lo) float4 at p_off and [q][n] complex128 after them.
 __global__ void __launch_bounds__(256) k_ir_update(const Unit* __restrict__ units, char* ws, int nrhs, int K,
                                                    bool explicit_b, int sweep, double tol, int32_t* done,
                                                    int32_t* stat) {
@@ -739,12 +795,13 @@ __global__ void __launch_bounds__(256) k_ir_update(const Unit* __restrict__ unit
   const int n = u.n;
   const float2* D = reinterpret_cast<const float2*>(ws + u.x32_off);
   double2* X = reinterpret_cast<double2*>(ws + u.x_off);
+  float4* Xdf = reinterpret_cast<float4*>(ws + u.xdf_off);
   const double2* B = reinterpret_cast<const double2*>(ws + u.r_off);
-  double2* Y = reinterpret_cast<double2*>(ws + u.p_off);
-  double2* BW = Y + (size_t)kProbe * n;
-  __shared__ double sw[kProbe][64];
-  for (int idx = threadIdx.x; idx < kProbe * 64; idx += blockDim.x)
-    sw[idx / 64][idx % 64] = probe_sign(u.stat_off, sweep, idx / 64, idx % 64);
+  float4* Y = reinterpret_cast<float4*>(ws + u.p_off);  // y_q as (hi, lo) pairs
+  double2* BW = reinterpret_cast<double2*>(Y + (size_t)kProbe * n);
+  __shared__ double2 sw[kProbe][32];
+  for (int idx = threadIdx.x; idx < kProbe * 32; idx += blockDim.x)
+    sw[idx / 32][idx % 32] = probe_weight(u.stat_off, sweep, idx / 32, idx % 32);
   __syncthreads();
   double dn = 0.0, xn = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -756,21 +813,22 @@ __global__ void __launch_bounds__(256) k_ir_update(const Unit* __restrict__ unit
       const double2 d = to64(D[idx]);
       const double2 x = cadd(X[idx], d);
       X[idx] = x;
+      Xdf[idx] = df_split(x);  // split once here instead of in every residual CTA
       dn += d.x * d.x + d.y * d.y;
       xn += x.x * x.x + x.y * x.y;
       const double2 b = explicit_b ? B[idx] : mk(0.0, 0.0);
 #pragma unroll
       for (int q = 0; q < kProbe; ++q) {
-        const double s = sw[q][c & 63];
-        y[q] = mk(y[q].x + s * x.x, y[q].y + s * x.y);
-        if (explicit_b) bw[q] = mk(bw[q].x + s * b.x, bw[q].y + s * b.y);
+        const double2 w = sw[q][c & 31];
+        y[q] = cfma(x, w, y[q]);
+        if (explicit_b) bw[q] = cfma(b, w, bw[q]);
       }
     }
 #pragma unroll
     for (int q = 0; q < kProbe; ++q) {
       // B = E0 (forward): (B w)_i = w_i for i < K
-      if (!explicit_b && i < K && i < nrhs) bw[q] = mk(sw[q][i], 0.0);
-      Y[(size_t)q * n + i] = y[q];
+      if (!explicit_b && i < K && i < nrhs) bw[q] = sw[q][i];
+      Y[(size_t)q * n + i] = df_split(y[q]);
       BW[(size_t)q * n + i] = bw[q];
     }
   }
@@ -810,8 +868,8 @@ __global__ void __launch_bounds__(256, 3) k_probe_residual(const Unit* __restric
   const int row0 = blockIdx.x * 64;
   if (row0 >= n) return;
   const float4* M = reinterpret_cast<const float4*>(fac_base + u.m64_off);
-  const double2* Y = reinterpret_cast<const double2*>(ws + u.p_off);
-  const double2* BW = Y + (size_t)kProbe * n;
+  const float4* Y = reinterpret_cast<const float4*>(ws + u.p_off);  // y_q as (hi, lo) pairs
+  const double2* BW = reinterpret_cast<const double2*>(Y + (size_t)kProbe * n);
   float2* X32 = reinterpret_cast<float2*>(ws + u.x32_off);
   __shared__ float4 sY[128][kProbe];
   __shared__ float4 sPart[3][kProbe][64];
@@ -828,7 +886,7 @@ __global__ void __launch_bounds__(256, 3) k_probe_residual(const Unit* __restric
     __syncthreads();
     for (int idx = tid; idx < 128 * kProbe; idx += 256) {
       const int jj = idx & 127, q = idx >> 7;
-      sY[jj][q] = jj < jn ? df_split(Y[(size_t)q * n + j0 + jj]) : make_float4(0.f, 0.f, 0.f, 0.f);
+      sY[jj][q] = jj < jn ? Y[(size_t)q * n + j0 + jj] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
     if (live) {
@@ -888,7 +946,7 @@ __global__ void __launch_bounds__(256, 3) k_probe_residual(const Unit* __restric
 // Convergence probe, test half: X32 columns q now hold the corrections d_q that
 // the next sweep would add to y_q = X w_q.  The unit is done when every
 // ||d_q|| <= tol ||y_q||: E||D w||^2 = 2 ||D||_F^2 and E||X w||^2 = 2 ||X||_F^2
-// for random signs w, so this is the sweep test of k_ir_update taken on
+// for complex Gaussian w, so this is the sweep test of k_ir_update taken on
 // kProbe random combinations of the columns.  Adds 1 << 16 to the status word.
 __global__ void __launch_bounds__(256) k_probe_check(const Unit* __restrict__ units, const char* ws, double tol,
                                                      int32_t* done, int32_t* stat) {
@@ -896,7 +954,7 @@ __global__ void __launch_bounds__(256) k_probe_check(const Unit* __restrict__ un
   if (done[u.stat_off]) return;
   const int n = u.n;
   const float2* D = reinterpret_cast<const float2*>(ws + u.x32_off);
-  const double2* Y = reinterpret_cast<const double2*>(ws + u.p_off);
+  const float4* Y = reinterpret_cast<const float4*>(ws + u.p_off);  // (hi, lo) pairs
   double dn[kProbe], yn[kProbe];
 #pragma unroll
   for (int q = 0; q < kProbe; ++q) dn[q] = yn[q] = 0.0;
@@ -904,7 +962,7 @@ __global__ void __launch_bounds__(256) k_probe_check(const Unit* __restrict__ un
 #pragma unroll
     for (int q = 0; q < kProbe; ++q) {
       const double2 d = to64(D[(size_t)q * n + i]);
-      const double2 y = Y[(size_t)q * n + i];
+      const double2 y = df_join(Y[(size_t)q * n + i]);
       dn[q] += d.x * d.x + d.y * d.y;
       yn[q] += y.x * y.x + y.y * y.y;
     }
@@ -943,7 +1001,8 @@ __global__ void k_ir_finish(const Unit* __restrict__ units, int n_units, const i
 }
 
 // tau[e][site_off + p][L][L'] = X[L' * n + K p + L].  grid (S_max, n_units).
-__global__ void k_write_tau(const Unit* __restrict__ units, const char* ws, int K, int64_t S_total,
+// conj_pairs: also tau[e + 1] = conj(tau[e]) (the partner energy conj z_e).
+__global__ void k_write_tau(const Unit* __restrict__ units, const char* ws, int K, int64_t S_total, bool conj_pairs,
                             double2* __restrict__ tau) {
   const Unit u = units[blockIdx.y];
   const int p = blockIdx.x;
@@ -952,7 +1011,9 @@ __global__ void k_write_tau(const Unit* __restrict__ units, const char* ws, int 
   const int L = tid >> 4, Lp = tid & 15;
   if (L >= K || Lp >= K) return;
   const double2* X = reinterpret_cast<const double2*>(ws + u.x_off);
-  tau[(((size_t)u.energy * S_total) + u.site_off + p) * K * K + L * K + Lp] = X[(size_t)Lp * u.n + K * p + L];
+  const double2 x = X[(size_t)Lp * u.n + K * p + L];
+  tau[(((size_t)u.energy * S_total) + u.site_off + p) * K * K + L * K + Lp] = x;
+  if (conj_pairs) tau[(((size_t)(u.energy + 1) * S_total) + u.site_off + p) * K * K + L * K + Lp] = mk(x.x, -x.y);
 }
 
 __global__ void k_status_out(const int32_t* __restrict__ stat, int n, int32_t* __restrict__ out) {
@@ -960,11 +1021,65 @@ __global__ void k_status_out(const int32_t* __restrict__ stat, int n, int32_t* _
   if (i < n) out[i] = stat[i];
 }
 
+// Conjugate-pair mode: flag[d] = 1 when some t^{-1} block of energy 2d + 1 is not
+// the conjugate of energy 2d's (|b - conj a| > 1e-12 max|a| over the block).
+// grid (n_species, n_delta), block 256.
+__global__ void k_check_conj_tinv(const double2* __restrict__ tinv, int n_energy, int KK, int32_t* flag) {
+  const int s = blockIdx.x, d = blockIdx.y;
+  const double2* a = tinv + ((size_t)s * n_energy + 2 * d) * KK;
+  const double2* b = a + KK;
+  double dm = 0.0, am = 0.0;
+  for (int i = threadIdx.x; i < KK; i += blockDim.x) {
+    const double2 x = a[i], y = b[i];
+    dm = fmax(dm, fabs(y.x - x.x) + fabs(y.y + x.y));
+    am = fmax(am, fabs(x.x) + fabs(x.y));
+    if (!isfinite(x.x) || !isfinite(x.y) || !isfinite(y.x) || !isfinite(y.y)) dm = INFINITY;
+  }
+  __shared__ double s1[256], s2[256];
+  s1[threadIdx.x] = dm;
+  s2[threadIdx.x] = am;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s1[threadIdx.x] = fmax(s1[threadIdx.x], s1[threadIdx.x + w]);
+      s2[threadIdx.x] = fmax(s2[threadIdx.x], s2[threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && !(s1[0] <= 1e-12 * s2[0])) atomicOr(&flag[d], 1);
+}
+
+// Conjugate-pair mode, status of the second energy of each pair: stat (its own
+// solves in the backward, else the partner's) plus LSMS_UNIT_BAD_INPUT when the
+// pair's t^{-1} is not conjugate.  One thread per (pair, atom).
+__global__ void k_status_conj(const int32_t* __restrict__ stat, const int32_t* __restrict__ flag, int n_atoms,
+                              int n_delta, bool from_partner, int32_t* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_atoms * n_delta) return;
+  const int d = i / n_atoms, m = i % n_atoms;
+  const size_t minus = (size_t)(2 * d + 1) * n_atoms + m;
+  const int32_t v = from_partner ? stat[(size_t)(2 * d) * n_atoms + m] : stat[minus];
+  out[minus] = v | (flag[d] ? LSMS_UNIT_BAD_INPUT : 0);
+}
+
+// Conjugate-pair mode (backward): conjugate the n x nrhs complex128 block at
+// r_off (which = 0) or x_off (which = 1) of the units solved with their
+// partner's factors.  grid (ceil(n_max nrhs / 256), n_units).
+__global__ void k_conj_block(const Unit* __restrict__ units, char* ws, int nrhs, int which) {
+  const Unit u = units[blockIdx.y];
+  if (!u.conj) return;
+  double2* X = reinterpret_cast<double2*>(ws + (which == 0 ? u.r_off : u.x_off));
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)u.n * nrhs;
+       idx += (int64_t)gridDim.x * blockDim.x)
+    X[idx].y = -X[idx].y;
+}
+
 // ------------------------------------------------------------------ shared driver
 struct Call {
   lsms_liz* liz;
   DeviceData* dd;
-  int lmax, K, n_species, n_energy, precision;
+  int lmax, K, n_species, n_energy, precision;  // precision: LSMS_FP64 or LSMS_MIXED
+  bool conj;                                    // LSMS_CONJ_PAIRS given
   const int32_t* species;
   const double2* tinv;
   EnergyTable E;
@@ -981,25 +1096,21 @@ static int check_common(const lsms_liz* liz, int lmax, const void* species, int 
   return LSMS_OK;
 }
 
-// Assemble + factor one chunk (fac at fac_base), mixed form also writes the FP64 copy.
-static int assemble_factor(const Call& c, const Plan& p, const Chunk& ch, char* fac_base, char* ws, int32_t* stat,
-                           bool factor) {
-  const Unit* du = p.d_units + ch.u0;
-  const int nu = ch.u1 - ch.u0;
+// Assemble + factor the units of one chunk that own factors (at fac_base); the
+// mixed form also writes the double-float copy of M.
+static int assemble_factor(const Call& c, const Plan& p, const Chunk& ch, char* fac_base, char* ws, int32_t* stat) {
+  const Unit* du = p.d_fac_units + ch.f0;  // the units that own factors
+  const int nu = ch.f1 - ch.f0;
   const int S_max = ch.n_max / c.K;
-  const int n_at = nu / c.n_energy;  // chunks hold whole atoms
+  const int n_at = nu / p.fac_per_atom;  // chunks hold whole atoms
   if (c.precision == LSMS_FP64) {
-    if (factor) {
-      LSMS_LAUNCH(k_assemble<false>, dim3(S_max, n_at), dim3(256), 0, c.st, du, c.n_energy, c.dd->disp,
-                  c.dd->site_atom, c.species, c.tinv, c.n_species, c.n_energy, c.E, c.K, fac_base, ws, true, stat);
-      return lu_factor_chunk<double>(du, nu, ch.n_max, fac_base, stat, c.st);
-    }
-    return LSMS_OK;
+    LSMS_LAUNCH(k_assemble<false>, dim3(S_max, n_at), dim3(256), 0, c.st, du, p.fac_per_atom, c.dd->disp,
+                c.dd->site_atom, c.species, c.tinv, c.n_species, c.n_energy, c.E, c.K, fac_base, ws, true, stat);
+    return lu_factor_chunk<double>(du, nu, ch.n_max, fac_base, stat, c.st);
   }
-  LSMS_LAUNCH(k_assemble<true>, dim3(S_max, n_at), dim3(256), 0, c.st, du, c.n_energy, c.dd->disp, c.dd->site_atom,
-              c.species, c.tinv, c.n_species, c.n_energy, c.E, c.K, fac_base, ws, factor, stat);
-  if (factor) return lu_factor_chunk<float>(du, nu, ch.n_max, fac_base, stat, c.st);
-  return LSMS_OK;
+  LSMS_LAUNCH(k_assemble<true>, dim3(S_max, n_at), dim3(256), 0, c.st, du, p.fac_per_atom, c.dd->disp,
+              c.dd->site_atom, c.species, c.tinv, c.n_species, c.n_energy, c.E, c.K, fac_base, ws, true, stat);
+  return lu_factor_chunk<float>(du, nu, ch.n_max, fac_base, stat, c.st);
 }
 
 // Solve M X = B for a chunk whose factors exist.  B = E0 (forward) or the explicit
@@ -1040,6 +1151,15 @@ static int solve_refine(const Call& c, const Plan& p, const Chunk& ch, const cha
     LSMS_LAUNCH(k_probe_check, dim3(nu), dim3(256), 0, c.st, du, ws, kIrTol, done, stat);
   }
   LSMS_LAUNCH(k_ir_finish, dim3((nu + 255) / 256), dim3(256), 0, c.st, du, nu, done, stat);
+  return LSMS_OK;
+}
+
+// Conjugate-pair mode: n_energy even and z[2d + 1] = conj z[2d] exactly.
+static int check_conj_energies(const lsms_complex* z, int n_energy) {
+  if (n_energy & 1) return fail(LSMS_ERR_ARG, "LSMS_CONJ_PAIRS needs an even n_energy");
+  for (int d = 0; d < n_energy / 2; ++d)
+    if (!(z[2 * d + 1].re == z[2 * d].re && z[2 * d + 1].im == -z[2 * d].im))
+      return fail(LSMS_ERR_ARG, "LSMS_CONJ_PAIRS: z[%d] is not the conjugate of z[%d]", 2 * d + 1, 2 * d);
   return LSMS_OK;
 }
 
@@ -1105,35 +1225,55 @@ extern "C" void lsms_liz_destroy(lsms_liz* liz) {
     cudaFree(d.inv_off);
     cudaFree(d.inv_sites);
     cudaFree(d.site_centre);
-    for (auto& pk : d.plans) cudaFree(pk.second.d_units);
+    for (auto& pk : d.plans) {
+      cudaFree(pk.second.d_units);
+      cudaFree(pk.second.d_fac_units);
+    }
   }
   if (cur >= 0) cudaSetDevice(cur);
   delete liz;
 }
 
+// Workspace of one atom's units (factors in the workspace, i.e. no store):
+// largest over atoms and total.
 static size_t unit_ws_max_sum(const lsms_liz* liz, int lmax, int n_energy, int precision, int nrhs, bool backward,
-                              size_t* sum) {
+                              bool conj, size_t* sum) {
   const int K = (lmax + 1) * (lmax + 1);
+  std::vector<int> es;
+  std::vector<char> owns;
+  plan_energies(n_energy, conj, backward, &es, &owns);
   size_t mx = 0, s = 0;
   for (int m = 0; m < liz->n_atoms; ++m) {
     const int n = K * (int)(liz->offsets[m + 1] - liz->offsets[m]);
-    const size_t b = ws_unit_bytes(unit_bytes(n, precision, nrhs, backward), false);
-    mx = std::max(mx, b * n_energy);
-    s += b * n_energy;
+    const UnitBytes ub = unit_bytes(n, precision, nrhs, backward);
+    size_t b = 0;
+    for (size_t i = 0; i < es.size(); ++i) b += ws_unit_bytes(ub, owns[i]);
+    mx = std::max(mx, b);
+    s += b;
   }
   *sum = s;
   return mx;
 }
 
+// Precision argument: LSMS_FP64 or LSMS_MIXED, optionally with LSMS_CONJ_PAIRS.
+static bool split_precision(int precision, int* base, bool* conj) {
+  *base = precision & ~LSMS_CONJ_PAIRS;
+  *conj = (precision & LSMS_CONJ_PAIRS) != 0;
+  return *base == LSMS_FP64 || *base == LSMS_MIXED;
+}
+
 extern "C" int lsms_tau_workspace_bytes(const lsms_liz* liz, int lmax, int n_energy, int precision, size_t* min_bytes,
                                         size_t* all_bytes) {
   clear_error();
-  if (!liz || lmax < 0 || lmax > kMaxLmax || n_energy < 1 || n_energy > kMaxEnergies)
+  int base;
+  bool conj;
+  if (!liz || lmax < 0 || lmax > kMaxLmax || n_energy < 1 || n_energy > kMaxEnergies ||
+      !split_precision(precision, &base, &conj) || (conj && (n_energy & 1)))
     return fail(LSMS_ERR_ARG, "lsms_tau_workspace_bytes: bad arguments");
   const int K = (lmax + 1) * (lmax + 1);
   size_t sum = 0;
-  const size_t mx = unit_ws_max_sum(liz, lmax, n_energy, precision, K, false, &sum);
-  const WsHeader h = ws_header(liz, n_energy, 0);
+  const size_t mx = unit_ws_max_sum(liz, lmax, n_energy, base, K, false, conj, &sum);
+  const WsHeader h = ws_header(liz, n_energy, conj_extra_bytes(n_energy));
   if (min_bytes) *min_bytes = h.total_fixed + mx;
   if (all_bytes) *all_bytes = h.total_fixed + sum;
   return LSMS_OK;
@@ -1142,12 +1282,15 @@ extern "C" int lsms_tau_workspace_bytes(const lsms_liz* liz, int lmax, int n_ene
 extern "C" int lsms_backward_workspace_bytes(const lsms_liz* liz, int lmax, int n_energy, int precision,
                                              size_t* min_bytes, size_t* all_bytes) {
   clear_error();
-  if (!liz || lmax < 0 || lmax > kMaxLmax || n_energy < 2 || n_energy > kMaxEnergies || (n_energy & 1))
+  int base;
+  bool conj;
+  if (!liz || lmax < 0 || lmax > kMaxLmax || n_energy < 2 || n_energy > kMaxEnergies || (n_energy & 1) ||
+      !split_precision(precision, &base, &conj))
     return fail(LSMS_ERR_ARG, "lsms_backward_workspace_bytes: bad arguments");
   const int K = (lmax + 1) * (lmax + 1);
   size_t sum = 0;
-  const size_t mx = unit_ws_max_sum(liz, lmax, n_energy, precision, 2 * K, true, &sum);
-  const WsHeader h = ws_header(liz, n_energy, backward_extra_bytes(liz, lmax, n_energy));
+  const size_t mx = unit_ws_max_sum(liz, lmax, n_energy, base, 2 * K, true, conj, &sum);
+  const WsHeader h = ws_header(liz, n_energy, backward_extra_bytes(liz, lmax, n_energy) + conj_extra_bytes(n_energy));
   if (min_bytes) *min_bytes = h.total_fixed + mx;
   if (all_bytes) *all_bytes = h.total_fixed + sum;
   return LSMS_OK;
@@ -1155,15 +1298,18 @@ extern "C" int lsms_backward_workspace_bytes(const lsms_liz* liz, int lmax, int 
 
 extern "C" int lsms_lu_store_bytes(const lsms_liz* liz, int lmax, int n_energy, int precision, size_t* bytes) {
   clear_error();
+  int base;
+  bool conj;
   if (!liz || !bytes || lmax < 0 || lmax > kMaxLmax || n_energy < 1 || n_energy > kMaxEnergies ||
-      (precision != LSMS_FP64 && precision != LSMS_MIXED))
+      !split_precision(precision, &base, &conj) || (conj && (n_energy & 1)))
     return fail(LSMS_ERR_ARG, "lsms_lu_store_bytes: bad arguments");
   const int K = (lmax + 1) * (lmax + 1);
+  const int n_fac = conj ? n_energy / 2 : n_energy;  // factored energies per atom
   size_t s = 0;
   for (int m = 0; m < liz->n_atoms; ++m) {
     const int n = K * (int)(liz->offsets[m + 1] - liz->offsets[m]);
-    const UnitBytes ub = unit_bytes(n, precision, K, false);
-    s += (ub.fac + ub.piv + ub.m64) * n_energy;
+    const UnitBytes ub = unit_bytes(n, base, K, false);
+    s += (ub.fac + ub.piv + ub.m64) * n_fac;
   }
   *bytes = s;
   return LSMS_OK;
@@ -1177,16 +1323,21 @@ extern "C" int lsms_tau_blocks(const lsms_liz* liz_c, int lmax, const int32_t* s
                                void* lu_store, size_t lu_store_bytes, void* stream) {
   clear_error();
   lsms_liz* liz = const_cast<lsms_liz*>(liz_c);
-  int rc = check_common(liz, lmax, species, n_species, n_energy, precision);
+  int base;
+  bool conj;
+  if (!split_precision(precision, &base, &conj)) return fail(LSMS_ERR_ARG, "unknown precision %d", precision);
+  int rc = check_common(liz, lmax, species, n_species, n_energy, base);
   if (rc) return rc;
   if (!tinv || !z || !tau) return fail(LSMS_ERR_ARG, "lsms_tau_blocks: tinv, z and tau are required");
+  if (conj && (rc = check_conj_energies(z, n_energy))) return rc;
   Call c{};
   c.liz = liz;
   c.lmax = lmax;
   c.K = (lmax + 1) * (lmax + 1);
   c.n_species = n_species;
   c.n_energy = n_energy;
-  c.precision = precision;
+  c.precision = base;
+  c.conj = conj;
   c.species = species;
   c.tinv = reinterpret_cast<const double2*>(tinv);
   c.st = reinterpret_cast<cudaStream_t>(stream);
@@ -1200,7 +1351,7 @@ extern "C" int lsms_tau_blocks(const lsms_liz* liz_c, int lmax, const int32_t* s
   const bool store = lu_store != nullptr;
   size_t min_b = 0, all_b = 0;
   lsms_tau_workspace_bytes(liz, lmax, n_energy, precision, &min_b, &all_b);
-  const WsHeader h = ws_header(liz, n_energy, 0);
+  const WsHeader h = ws_header(liz, n_energy, conj_extra_bytes(n_energy));
   char* ws = static_cast<char*>(workspace);
   bool own = false;
   size_t ws_bytes = workspace_bytes;
@@ -1212,28 +1363,38 @@ extern "C" int lsms_tau_blocks(const lsms_liz* liz_c, int lmax, const int32_t* s
     return fail(LSMS_ERR_NOMEM, "workspace holds %zu bytes, at least %zu needed", ws_bytes, min_b);
   }
   Plan* p = nullptr;
-  if ((rc = get_plan(liz, c.dd, lmax, n_energy, precision, c.K, false, store, ws_bytes - h.total_fixed, &p))) {
+  if ((rc = get_plan(liz, c.dd, lmax, n_energy, base, c.K, false, store, conj, ws_bytes - h.total_fixed, &p))) {
     if (own) cudaFreeAsync(ws, c.st);
     return rc;
   }
   int32_t* stat = reinterpret_cast<int32_t*>(ws + h.stat);
   int32_t* done = reinterpret_cast<int32_t*>(ws + h.done);
   const size_t nu_all = (size_t)liz->n_atoms * n_energy;
+  int32_t* conj_flag = reinterpret_cast<int32_t*>(ws + h.extra);
   rc = [&]() -> int {
     LSMS_CUDA_TRY(cudaMemsetAsync(stat, 0, nu_all * 4, c.st));
     LSMS_CUDA_TRY(cudaMemsetAsync(done, 0, nu_all * 4, c.st));
+    if (conj) {
+      LSMS_CUDA_TRY(cudaMemsetAsync(conj_flag, 0, conj_extra_bytes(n_energy), c.st));
+      LSMS_LAUNCH(k_check_conj_tinv, dim3(n_species, n_energy / 2), dim3(256), 0, c.st, c.tinv, n_energy,
+                  c.K * c.K, conj_flag);
+    }
     char* chunk = ws + h.chunk;
     char* fac_base = store ? static_cast<char*>(lu_store) : chunk;
     for (const Chunk& ch : p->chunks) {
-      int r2 = assemble_factor(c, *p, ch, fac_base, chunk, stat, true);
+      int r2 = assemble_factor(c, *p, ch, fac_base, chunk, stat);
       if (r2) return r2;
       if ((r2 = solve_refine(c, *p, ch, fac_base, chunk, stat, done, false))) return r2;
       LSMS_LAUNCH(k_write_tau, dim3(ch.n_max / c.K, ch.u1 - ch.u0), dim3(256), 0, c.st, p->d_units + ch.u0, chunk,
-                  c.K, liz->total_sites, reinterpret_cast<double2*>(tau));
+                  c.K, liz->total_sites, conj, reinterpret_cast<double2*>(tau));
     }
-    if (unit_status)
+    if (unit_status) {
       LSMS_LAUNCH(k_status_out, dim3((unsigned)((nu_all + 255) / 256)), dim3(256), 0, c.st, stat, (int)nu_all,
                   unit_status);
+      if (conj)
+        LSMS_LAUNCH(k_status_conj, dim3((unsigned)((nu_all / 2 + 255) / 256)), dim3(256), 0, c.st, stat, conj_flag,
+                    liz->n_atoms, n_energy / 2, true, unit_status);
+    }
     return LSMS_OK;
   }();
   if (own) cudaFreeAsync(ws, c.st);
@@ -1276,18 +1437,23 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
                                         void* workspace, size_t workspace_bytes, void* stream) {
   clear_error();
   lsms_liz* liz = const_cast<lsms_liz*>(liz_c);
-  int rc = check_common(liz, lmax, species, n_species, n_energy, precision);
+  int base;
+  bool conj;
+  if (!split_precision(precision, &base, &conj)) return fail(LSMS_ERR_ARG, "unknown precision %d", precision);
+  int rc = check_common(liz, lmax, species, n_species, n_energy, base);
   if (rc) return rc;
   if ((n_energy & 1) || !tinv || !z || !J || !tau || !grad_sigma || !grad_tinv)
     return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_backward: missing argument or odd n_energy");
   if (!(volume > 0.0)) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_backward: volume must be > 0");
+  if (conj && (rc = check_conj_energies(z, n_energy))) return rc;
   Call c{};
   c.liz = liz;
   c.lmax = lmax;
   c.K = (lmax + 1) * (lmax + 1);
   c.n_species = n_species;
   c.n_energy = n_energy;
-  c.precision = precision;
+  c.precision = base;
+  c.conj = conj;
   c.species = species;
   c.tinv = reinterpret_cast<const double2*>(tinv);
   c.st = reinterpret_cast<cudaStream_t>(stream);
@@ -1302,7 +1468,7 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
   const size_t KK = (size_t)c.K * c.K;
   size_t min_b = 0, all_b = 0;
   lsms_backward_workspace_bytes(liz, lmax, n_energy, precision, &min_b, &all_b);
-  const WsHeader h = ws_header(liz, n_energy, backward_extra_bytes(liz, lmax, n_energy));
+  const WsHeader h = ws_header(liz, n_energy, backward_extra_bytes(liz, lmax, n_energy) + conj_extra_bytes(n_energy));
   char* ws = static_cast<char*>(workspace);
   bool own = false;
   size_t ws_bytes = workspace_bytes;
@@ -1314,7 +1480,7 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
     return fail(LSMS_ERR_NOMEM, "workspace holds %zu bytes, at least %zu needed", ws_bytes, min_b);
   }
   Plan* p = nullptr;
-  if ((rc = get_plan(liz, c.dd, lmax, n_energy, precision, 2 * c.K, true, store, ws_bytes - h.total_fixed, &p))) {
+  if ((rc = get_plan(liz, c.dd, lmax, n_energy, base, 2 * c.K, true, store, conj, ws_bytes - h.total_fixed, &p))) {
     if (own) cudaFreeAsync(ws, c.st);
     return rc;
   }
@@ -1322,10 +1488,16 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
   int32_t* done = reinterpret_cast<int32_t*>(ws + h.done);
   double2* abar = reinterpret_cast<double2*>(ws + h.extra);
   double2* G = reinterpret_cast<double2*>(ws + h.extra + align_up((size_t)liz->n_atoms * n_delta * 12 * KK * 16));
+  int32_t* conj_flag = reinterpret_cast<int32_t*>(ws + h.extra + backward_extra_bytes(liz, lmax, n_energy));
   const size_t nu_all = (size_t)liz->n_atoms * n_energy;
   rc = [&]() -> int {
     LSMS_CUDA_TRY(cudaMemsetAsync(stat, 0, nu_all * 4, c.st));
     LSMS_CUDA_TRY(cudaMemsetAsync(done, 0, nu_all * 4, c.st));
+    if (conj) {
+      LSMS_CUDA_TRY(cudaMemsetAsync(conj_flag, 0, conj_extra_bytes(n_energy), c.st));
+      LSMS_LAUNCH(k_check_conj_tinv, dim3(n_species, n_energy / 2), dim3(256), 0, c.st, c.tinv, n_energy,
+                  c.K * c.K, conj_flag);
+    }
     int r2 = adj_abar(species, n_species, reinterpret_cast<const double2*>(J), J_delta_stride,
                       reinterpret_cast<const double2*>(grad_sigma), c.K, volume, liz->n_atoms, n_delta, abar, c.st);
     if (r2) return r2;
@@ -1336,12 +1508,16 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
       const int nu = ch.u1 - ch.u0;
       const int S_max = ch.n_max / c.K;
       // stored factors come with the double-float copy of M (mixed form): nothing to rebuild
-      if (!store && (r2 = assemble_factor(c, *p, ch, fac_base, chunk, stat, true))) return r2;
+      if (!store && (r2 = assemble_factor(c, *p, ch, fac_base, chunk, stat))) return r2;
       if ((r2 = adj_rhs(du, nu, S_max, c.dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J), J_delta_stride,
                         reinterpret_cast<const double2*>(tau), liz->total_sites, abar, n_delta, c.K, chunk,
                         precision == LSMS_MIXED, c.st)))
         return r2;
+      const dim3 gc((ch.n_max * p->nrhs + 255) / 256, nu);
+      // second energy of a conjugate pair: M(conj z) = conj M(z), so X = conj(M(z)^-1 conj B)
+      if (conj) LSMS_LAUNCH(k_conj_block, gc, dim3(256), 0, c.st, du, chunk, p->nrhs, 0);
       if ((r2 = solve_refine(c, *p, ch, fac_base, chunk, stat, done, true))) return r2;
+      if (conj) LSMS_LAUNCH(k_conj_block, gc, dim3(256), 0, c.st, du, chunk, p->nrhs, 1);
       if ((r2 = adj_site(du, nu, S_max, reinterpret_cast<const double2*>(tau), liz->total_sites, c.K, chunk, G,
                          precision == LSMS_MIXED, c.st)))
         return r2;
@@ -1349,9 +1525,13 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
     if ((r2 = adj_reduce(c.dd->inv_off, c.dd->inv_sites, G, liz->total_sites, c.K, liz->n_atoms, n_energy,
                          reinterpret_cast<double2*>(grad_tinv), c.st)))
       return r2;
-    if (unit_status)
+    if (unit_status) {
       LSMS_LAUNCH(k_status_out, dim3((unsigned)((nu_all + 255) / 256)), dim3(256), 0, c.st, stat, (int)nu_all,
                   unit_status);
+      if (conj)
+        LSMS_LAUNCH(k_status_conj, dim3((unsigned)((nu_all / 2 + 255) / 256)), dim3(256), 0, c.st, stat, conj_flag,
+                    liz->n_atoms, n_delta, false, unit_status);
+    }
     if (grad_tinv_species)
       return adj_species(species, reinterpret_cast<const double2*>(grad_tinv), c.K, liz->n_atoms, n_species, n_energy,
                          reinterpret_cast<double2*>(grad_tinv_species), c.st);

@@ -37,22 +37,34 @@ struct Unit {
   int64_t r_off;     // byte offset of the n x RHS complex128 residual block (workspace)
   int64_t x32_off;   // byte offset of the n x RHS complex64 scratch (workspace)
   int64_t p_off;     // byte offset of the convergence-probe vectors (mixed form, workspace)
+  int64_t xdf_off;   // byte offset of X as double-float (hi, lo) pairs (mixed form, workspace)
   int64_t stat_off;  // index into the per-unit scratch scalars
+  int32_t conj;      // 1: solved with its conjugate partner's factors on conjugated right-hand sides
+  int32_t pad;
 };
 
 struct Chunk {
   int u0, u1;        // unit range in the plan
+  int f0, f1;        // range of the units that own factors (fac_units)
   int n_max;         // largest n in the chunk (units are sorted by n, descending)
   size_t ws_bytes;   // workspace bytes used by the chunk
 };
 
+// Work plan of one call shape.  units: every (atom, energy) system solved;
+// fac_units: the ones whose matrix is assembled and factored (all of them,
+// except the second energy of each conjugate pair in the conjugate-pair mode,
+// which reuses its partner's factors).  Both are atom-major, atoms sorted by
+// LIZ size (largest first); a chunk holds whole atoms.
 struct Plan {
   int lmax = -1, n_energy = 0, precision = 0, nrhs = 0;
-  bool store = false;
+  bool store = false, conj = false;
+  int fac_per_atom = 0;          // fac_units per atom
   size_t ws_bytes = 0;
-  std::vector<Unit> units;     // host copy
+  std::vector<Unit> units;       // host copies
+  std::vector<Unit> fac_units;
   std::vector<Chunk> chunks;
-  Unit* d_units = nullptr;     // device copy
+  Unit* d_units = nullptr;       // device copies
+  Unit* d_fac_units = nullptr;
 };
 
 struct DeviceData {

@@ -91,6 +91,17 @@ __device__ __forceinline__ C panel_swaps(C x, C* col, const int* sp, int k, int 
   return x;
 }
 
+// Asynchronous global -> shared copy of one complex element (cp.async: 8 bytes
+// for complex64, 16 for complex128); completed by cp.async.wait_all.
+__device__ __forceinline__ void cp_async_elem(float2* dst, const float2* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double2* dst, const double2* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+
 // ------------------------------------------------------------------ panel
 template <typename R, int NB>
 __global__ void __launch_bounds__(256) k_panel(const Unit* __restrict__ units, char* fac_base, int k,
@@ -171,38 +182,42 @@ __global__ void __launch_bounds__(256) k_panel(const Unit* __restrict__ units, c
 }
 
 // Panel factorization held in shared memory: the m = n - k rows x NB columns of
-// the panel are read once, factored column by column in shared memory, and
-// written back once.  Units whose panel does not fit (m > max_rows) are left to
-// k_panel, which works in global memory.
-// Rows never move inside shared memory: thread t owns the physical rows t,
-// t + 512, ... and keeps their logical (pivoted) row numbers in registers, so a
-// row interchange is two register updates.  The pivot search for column j + 1
-// runs inside the update of column j (on the values just written), which leaves
-// one block barrier per column.  Same arithmetic and pivot choices as the
-// row-swapping form (largest |Re| + |Im|, lowest logical row on ties).
+// the panel are read once (cp.async), factored column by column in shared
+// memory, and written back once.  Units whose panel does not fit (m > max_rows)
+// are left to k_panel, which works in global memory.
+// One thread per physical row (1024 threads, m <= 1024).  Rows never move in
+// shared memory: each thread keeps the logical (pivoted) number of its row in a
+// register, so a row interchange is two register updates.  The pivot search
+// for column j + 1 runs inside the update of column j (on the values just
+// written), which leaves one block barrier per column.  Same arithmetic and pivot
+// choices as the row-swapping form (largest |Re| + |Im|, lowest logical row on
+// ties, NaN never chosen unless the whole column is NaN).
+constexpr int kPanelThreads = 1024;
+
 template <typename R, int NB>
-__global__ void __launch_bounds__(512) k_panel_smem(const Unit* __restrict__ units, char* fac_base, int k,
-                                                    int32_t* stat, int max_rows) {
+__global__ void __launch_bounds__(kPanelThreads) k_panel_smem(const Unit* __restrict__ units, char* fac_base, int k,
+                                                              int32_t* stat, int max_rows) {
   using C = Cx<R>;
-  constexpr int NT = 512, MAXR = 4;  // threads; rows per thread (m <= 2048)
+  constexpr int NT = kPanelThreads, NW = NT / 32;
+  static_assert(NW <= 32, "one warp reduces the warp results");
   const Unit u = units[blockIdx.x];
   const int n = u.n;
   if (k >= n) return;
   const int m = n - k;
-  if (m > max_rows || m > NT * MAXR) return;
+  if (m > max_rows || m > NT) return;
   extern __shared__ __align__(16) unsigned char panel_raw[];
   C* sP = reinterpret_cast<C*>(panel_raw);  // [NB][m], column-major, physical rows
   C* A = reinterpret_cast<C*>(fac_base + u.fac_off);
   int32_t* piv = reinterpret_cast<int32_t*>(fac_base + u.piv_off);
   const int nbp = min(NB, m);
-  __shared__ R s_val[2][16];
-  __shared__ int s_lg[2][16], s_ph[2][16];
+  __shared__ R s_val[2][NW];
+  __shared__ int s_lg[2][NW], s_ph[2][NW];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int c = 0; c < nbp; ++c)
-    for (int r = tid; r < m; r += NT) sP[c * m + r] = A[(size_t)(k + c) * n + k + r];
-  int lg[MAXR];  // logical row of physical row tid + NT r
-#pragma unroll
-  for (int r = 0; r < MAXR; ++r) lg[r] = tid + NT * r;
+  const bool own = tid < m;  // this thread's physical row is tid
+  if (own)
+    for (int c = 0; c < nbp; ++c) cp_async_elem(&sP[c * m + tid], &A[(size_t)(k + c) * n + k + tid]);
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  int lg = tid;  // logical row of physical row tid
   // warp-level best (value, logical row, physical row); lowest logical row on ties
   auto warp_best = [&](R& best, int& bl, int& bp) {
 #pragma unroll
@@ -213,74 +228,63 @@ __global__ void __launch_bounds__(512) k_panel_smem(const Unit* __restrict__ uni
       if (ov > best || (ov == best && ol < bl)) { best = ov; bl = ol; bp = op; }
     }
   };
-  // pivot candidates of column 0
+  auto mag = [](C v) -> R {  // |Re| + |Im|; NaN below every number
+    const R a = cabs1(v);
+    return a >= R(0) ? a : R(-0.5);
+  };
   {
-    R best = R(-1);
-    int bl = m, bp = 0;
-#pragma unroll
-    for (int r = 0; r < MAXR; ++r) {
-      const int ph = tid + NT * r;
-      if (ph < m) {
-        R v = cabs1(sP[ph]);
-        if (!(v >= R(0))) v = R(-0.5);  // NaN: below every number, so it wins only an all-NaN column (row j)
-        if (v > best || (v == best && lg[r] < bl)) { best = v; bl = lg[r]; bp = ph; }
-      }
-    }
+    R best = own ? mag(sP[tid]) : R(-1);
+    int bl = own ? tid : m, bp = tid;
     warp_best(best, bl, bp);
     if (lane == 0) { s_val[0][warp] = best; s_lg[0][warp] = bl; s_ph[0][warp] = bp; }
   }
   __syncthreads();
   int flags = 0;
-  for (int j = 0; j < nbp; ++j) {
-    const int par = j & 1;
-    // every warp reduces the 16 warp results itself: no second barrier
-    R best = lane < 16 ? s_val[par][lane] : R(-1);
-    int bl = lane < 16 ? s_lg[par][lane] : m;
-    int bp = lane < 16 ? s_ph[par][lane] : 0;
-    warp_best(best, bl, bp);
-    const int p = bl, pph = bp;
-    if (tid == 0) piv[k + j] = k + p;
-    // interchange logical rows j and p
+  // kept rolled: the fully unrolled complex128 instance produced wrong factors
+  // (n a multiple of 32) while every rolled build matches the oracle
+#pragma unroll 1
+  for (int j = 0; j < NB; ++j) {
+    if (j < nbp) {
+      const int par = j & 1;
+      R best = lane < NW ? s_val[par][lane] : R(-1);  // NW <= 32 warp results
+      int bl = lane < NW ? s_lg[par][lane] : m, bp = lane < NW ? s_ph[par][lane] : 0;
+      warp_best(best, bl, bp);
+      const int p = bl, pph = bp;
+      if (tid == 0) piv[k + j] = k + p;
+      lg = lg == j ? p : (lg == p ? j : lg);  // interchange logical rows j and p
+      const C pv = sP[j * m + pph];
+      const bool zero = (pv.x == R(0) && pv.y == R(0));
+      if (zero) flags |= LSMS_UNIT_ZERO_PIVOT;
+      if (!finite2(pv)) flags |= LSMS_UNIT_NONFINITE;
+      const C rcp = zero ? mk(R(0), R(0)) : crcp(pv);
+      best = R(-1);
+      bl = m;
+      bp = tid;
+      if (own && lg > j) {
+        const C l = cmul(sP[j * m + tid], rcp);
+        if (!zero) sP[j * m + tid] = l;
 #pragma unroll
-    for (int r = 0; r < MAXR; ++r) lg[r] = lg[r] == j ? p : (lg[r] == p ? j : lg[r]);
-    const C pv = sP[j * m + pph];
-    const bool zero = (pv.x == R(0) && pv.y == R(0));
-    if (zero) flags |= LSMS_UNIT_ZERO_PIVOT;
-    if (!finite2(pv)) flags |= LSMS_UNIT_NONFINITE;
-    const C rcp = zero ? mk(R(0), R(0)) : crcp(pv);
-    best = R(-1);
-    bl = m;
-    bp = 0;
-#pragma unroll
-    for (int r = 0; r < MAXR; ++r) {
-      const int ph = tid + NT * r;
-      if (ph < m && lg[r] > j) {
-        const C l = cmul(sP[j * m + ph], rcp);
-        if (!zero) sP[j * m + ph] = l;
-        for (int c = j + 1; c < nbp; ++c) {
-          const C v = cfms(l, sP[c * m + pph], sP[c * m + ph]);
-          sP[c * m + ph] = v;
-          if (c == j + 1) {
-            R a = cabs1(v);
-            if (!(a >= R(0))) a = R(-0.5);
-            if (a > best || (a == best && lg[r] < bl)) { best = a; bl = lg[r]; bp = ph; }
+        for (int c = j + 1; c < NB; ++c) {
+          if (c < nbp) {
+            const C v = cfms(l, sP[c * m + pph], sP[c * m + tid]);
+            sP[c * m + tid] = v;
+            if (c == j + 1) {
+              best = mag(v);
+              bl = lg;
+            }
           }
         }
       }
+      if (j + 1 < nbp) {
+        warp_best(best, bl, bp);
+        if (lane == 0) { s_val[par ^ 1][warp] = best; s_lg[par ^ 1][warp] = bl; s_ph[par ^ 1][warp] = bp; }
+      }
+      __syncthreads();
     }
-    if (j + 1 < nbp) {
-      warp_best(best, bl, bp);
-      if (lane == 0) { s_val[par ^ 1][warp] = best; s_lg[par ^ 1][warp] = bl; s_ph[par ^ 1][warp] = bp; }
-    }
-    __syncthreads();
   }
   // write back in logical order
-#pragma unroll
-  for (int r = 0; r < MAXR; ++r) {
-    const int ph = tid + NT * r;
-    if (ph < m)
-      for (int c = 0; c < nbp; ++c) A[(size_t)(k + c) * n + k + lg[r]] = sP[c * m + ph];
-  }
+  if (own)
+    for (int c = 0; c < nbp; ++c) A[(size_t)(k + c) * n + k + lg] = sP[c * m + tid];
   if (tid == 0 && flags) atomicOr(&stat[u.stat_off], flags);
 }
 
@@ -636,7 +640,7 @@ int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
     if (m_max > max_rows)
       LSMS_LAUNCH((k_panel<R, NB>), dim3(n_units), dim3(256), 0, st, d_units, fac_base, k, stat, max_rows);
     const int rows_smem = std::min(m_max, max_rows);
-    LSMS_LAUNCH((k_panel_smem<R, NB>), dim3(n_units), dim3(512), (size_t)rows_smem * NB * sizeof(Cx<R>), st,
+    LSMS_LAUNCH((k_panel_smem<R, NB>), dim3(n_units), dim3(kPanelThreads), (size_t)rows_smem * NB * sizeof(Cx<R>), st,
                 d_units, fac_base, k, stat, max_rows);
     const int trail = n_max - k - NB;
     if (trail <= 0) continue;

@@ -67,7 +67,7 @@ def test_bcc2000_uneven_three_deltas(B):
     lz, tau_m, st_m, sig_m = _run(B, w, "mixed")
     sizes = lz.sizes
     assert sizes.min() < sizes.max()                       # uneven LIZ sizes
-    assert np.all((st_m & 0xff) == 0)
+    assert np.all((st_m & 0xff) == 0), np.unique(st_m & 0xff, return_counts=True)
     assert ((st_m >> 8) & 0xff).max() <= 6
     assert ((st_m >> 16) & 0xff).max() <= 6
     atoms = [int(np.argmax(sizes)), int(np.argmin(sizes)), 1234]
@@ -75,7 +75,7 @@ def test_bcc2000_uneven_three_deltas(B):
     del tau_m
     torch.cuda.empty_cache()
     lz64, tau_d, st_d, sig_d = _run(B, w, "fp64")
-    assert np.all((st_d & 0xff) == 0)
+    assert np.all((st_d & 0xff) == 0), np.unique(st_d & 0xff, return_counts=True)
     _check_sampled(w, lz64, tau_d, atoms[:2], TOL["fp64"])
     for d in range(3):                                     # per broadening
         err = np.abs(sig_m[d] - sig_d[d]).max() / np.abs(sig_d[d]).max()
