@@ -61,13 +61,17 @@ void timer_end(cudaStream_t st) {
 // kernels in kubo.cu
 int kubo_forward(const int64_t* offsets, const int32_t* site_atom, const int32_t* species, int n_species,
                  const double2* J, int64_t J_dstride, const double2* tau, int64_t S_total, int K, int n_atoms, int n_delta,
-                 double volume, bool df, double2* partial, double2* S, double2* sigma_tilde, double2* sigma,
-                 double* rho, cudaStream_t st);
+                 double volume, bool df, float4* jdf, double2* partial, double2* S, double2* sigma_tilde,
+                 double2* sigma, double* rho, cudaStream_t st);
+size_t jdf_scratch_bytes(int n_species, int K, int n_delta, int64_t J_dstride);
 int adj_abar(const int32_t* species, int n_species, const double2* J, int64_t J_dstride, const double2* w, int K,
-             double volume, int n_atoms, int n_delta, double2* abar, cudaStream_t st);
+             double volume, int n_atoms, int n_delta, double2* abar, float4* abar_df, cudaStream_t st);
+int split_j(const double2* J, int64_t J_dstride, int n_species, int K, int n_delta, float4* out, int64_t* out_dstride,
+            cudaStream_t st);
 int adj_rhs(const Unit* d_units, int n_units, int S_max, const int32_t* site_atom, const int32_t* species,
             int n_species, const double2* J, int64_t J_dstride, const double2* tau, int64_t S_total,
-            const double2* abar, int n_delta, int K, char* ws, bool df, cudaStream_t st);
+            const double2* abar, const float4* jdf, int64_t jdf_dstride, const float4* abar_df, int n_delta, int K,
+            char* ws, bool df, cudaStream_t st);
 int adj_site(const Unit* d_units, int n_units, int S_max, const double2* tau, int64_t S_total, int K, const char* ws,
              double2* G, bool df, cudaStream_t st);
 int adj_reduce(const int64_t* inv_off, const int64_t* inv_sites, const double2* G, int64_t S_total, int K,
@@ -233,10 +237,12 @@ static WsHeader ws_header(const lsms_liz* liz, int n_energy, size_t extra_bytes)
 // Conjugate-pair mode: one flag per energy pair (t^-1 pair not conjugate).
 static size_t conj_extra_bytes(int n_energy) { return align_up((size_t)(n_energy / 2 + 1) * 4); }
 
+// abar (complex128), the per-site gradient blocks, abar as double-float pairs
 static size_t backward_extra_bytes(const lsms_liz* liz, int lmax, int n_energy) {
   const size_t KK = (size_t)(lmax + 1) * (lmax + 1) * (lmax + 1) * (lmax + 1);
   const int n_delta = n_energy / 2;
-  return align_up((size_t)liz->n_atoms * n_delta * 12 * KK * 16) + align_up((size_t)n_energy * liz->total_sites * KK * 16);
+  return 2 * align_up((size_t)liz->n_atoms * n_delta * 12 * KK * 16) +
+         align_up((size_t)n_energy * liz->total_sites * KK * 16);
 }
 
 static int get_plan(lsms_liz* liz, DeviceData* dd, int lmax, int n_energy, int precision, int nrhs, bool backward,
@@ -1418,11 +1424,13 @@ extern "C" int lsms_kubo_sigma(const lsms_liz* liz_c, int lmax, const int32_t* s
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t part_bytes = align_up((size_t)n_delta * 4 * liz->n_atoms * 9 * 16);
   const size_t s_bytes = align_up((size_t)n_delta * 36 * 16);
+  const size_t jdf_bytes = precision == LSMS_MIXED ? jdf_scratch_bytes(n_species, K, n_delta, J_delta_stride) : 0;
   char* scratch = nullptr;
-  LSMS_CUDA_TRY(cudaMallocAsync((void**)&scratch, part_bytes + s_bytes, st));
+  LSMS_CUDA_TRY(cudaMallocAsync((void**)&scratch, part_bytes + s_bytes + jdf_bytes, st));
   rc = kubo_forward(dd->offsets, dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J), J_delta_stride,
                     reinterpret_cast<const double2*>(tau), liz->total_sites, K, liz->n_atoms, n_delta, volume,
-                    precision == LSMS_MIXED, reinterpret_cast<double2*>(scratch), reinterpret_cast<double2*>(scratch + part_bytes),
+                    precision == LSMS_MIXED, reinterpret_cast<float4*>(scratch + part_bytes + s_bytes),
+                    reinterpret_cast<double2*>(scratch), reinterpret_cast<double2*>(scratch + part_bytes),
                     reinterpret_cast<double2*>(sigma_tilde), reinterpret_cast<double2*>(sigma), rho, st);
   cudaFreeAsync(scratch, st);
   return rc;
@@ -1486,9 +1494,22 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
   }
   int32_t* stat = reinterpret_cast<int32_t*>(ws + h.stat);
   int32_t* done = reinterpret_cast<int32_t*>(ws + h.done);
+  const size_t abar_bytes = align_up((size_t)liz->n_atoms * n_delta * 12 * KK * 16);
   double2* abar = reinterpret_cast<double2*>(ws + h.extra);
-  double2* G = reinterpret_cast<double2*>(ws + h.extra + align_up((size_t)liz->n_atoms * n_delta * 12 * KK * 16));
+  double2* G = reinterpret_cast<double2*>(ws + h.extra + abar_bytes);
+  float4* abar_df = reinterpret_cast<float4*>(ws + h.extra + abar_bytes +
+                                              align_up((size_t)n_energy * liz->total_sites * KK * 16));
   int32_t* conj_flag = reinterpret_cast<int32_t*>(ws + h.extra + backward_extra_bytes(liz, lmax, n_energy));
+  const bool df = base == LSMS_MIXED;
+  float4* jdf = nullptr;  // J as double-float pairs (mixed form), stream-ordered scratch
+  int64_t jdf_dstride = 0;
+  if (df) {
+    const cudaError_t e = cudaMallocAsync((void**)&jdf, jdf_scratch_bytes(n_species, c.K, n_delta, J_delta_stride), c.st);
+    if (e != cudaSuccess) {
+      if (own) cudaFreeAsync(ws, c.st);
+      return fail(LSMS_ERR_NOMEM, "lsms_kubo_sigma_backward: %s", cudaGetErrorString(e));
+    }
+  }
   const size_t nu_all = (size_t)liz->n_atoms * n_energy;
   rc = [&]() -> int {
     LSMS_CUDA_TRY(cudaMemsetAsync(stat, 0, nu_all * 4, c.st));
@@ -1499,8 +1520,12 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
                   c.K * c.K, conj_flag);
     }
     int r2 = adj_abar(species, n_species, reinterpret_cast<const double2*>(J), J_delta_stride,
-                      reinterpret_cast<const double2*>(grad_sigma), c.K, volume, liz->n_atoms, n_delta, abar, c.st);
+                      reinterpret_cast<const double2*>(grad_sigma), c.K, volume, liz->n_atoms, n_delta, abar,
+                      df ? abar_df : nullptr, c.st);
     if (r2) return r2;
+    if (df && (r2 = split_j(reinterpret_cast<const double2*>(J), J_delta_stride, n_species, c.K, n_delta, jdf,
+                            &jdf_dstride, c.st)))
+      return r2;
     char* chunk = ws + h.chunk;
     char* fac_base = store ? const_cast<char*>(static_cast<const char*>(lu_store)) : chunk;
     for (const Chunk& ch : p->chunks) {
@@ -1510,8 +1535,8 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
       // stored factors come with the double-float copy of M (mixed form): nothing to rebuild
       if (!store && (r2 = assemble_factor(c, *p, ch, fac_base, chunk, stat))) return r2;
       if ((r2 = adj_rhs(du, nu, S_max, c.dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J), J_delta_stride,
-                        reinterpret_cast<const double2*>(tau), liz->total_sites, abar, n_delta, c.K, chunk,
-                        precision == LSMS_MIXED, c.st)))
+                        reinterpret_cast<const double2*>(tau), liz->total_sites, abar, jdf, jdf_dstride, abar_df,
+                        n_delta, c.K, chunk, df, c.st)))
         return r2;
       const dim3 gc((ch.n_max * p->nrhs + 255) / 256, nu);
       // second energy of a conjugate pair: M(conj z) = conj M(z), so X = conj(M(z)^-1 conj B)
@@ -1537,6 +1562,7 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
                          reinterpret_cast<double2*>(grad_tinv_species), c.st);
     return LSMS_OK;
   }();
+  if (jdf) cudaFreeAsync(jdf, c.st);
   if (own) cudaFreeAsync(ws, c.st);
   return rc;
 }

@@ -19,6 +19,14 @@ namespace lsms {
 // c = 2a + b for (z1, z2) = (a, b), a/b = 0 for +, 1 for -; the swapped pair is 2b + a.
 __device__ __forceinline__ int swap_combo(int c) { return ((c & 1) << 1) | (c >> 1); }
 
+// J (per delta block d at d * J_dstride) as double-float (hi, lo) pairs, compact:
+// out[d][per].  grid (ceil(per / 256), n_dj).
+__global__ void k_split_j(const double2* __restrict__ J, int64_t J_dstride, int64_t per, float4* __restrict__ out) {
+  const int d = blockIdx.y;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per; i += (int64_t)gridDim.x * blockDim.x)
+    out[(size_t)d * per + i] = df_split(J[(size_t)d * J_dstride + i]);
+}
+
 // ------------------------------------------------------------------ forward traces
 // grid (n_atoms, n_delta * 4), block 256 = 16 x 16 element threads.
 // DF = false: FP64 arithmetic (FP64 form).  DF = true (mixed form): the K x K
@@ -29,6 +37,7 @@ __global__ void __launch_bounds__(256) k_kubo_partial(const int64_t* __restrict_
                                                       const int32_t* __restrict__ site_atom,
                                                       const int32_t* __restrict__ species,
                                                       const double2* __restrict__ J, int64_t J_dstride,
+                                                      const float4* __restrict__ Jdf, int64_t Jdf_dstride,
                                                       const double2* __restrict__ tau, int64_t S_total, int K,
                                                       int n_atoms, int n_species, double2* __restrict__ partial) {
   using V = typename std::conditional<DF, float4, double2>::type;
@@ -40,6 +49,11 @@ __global__ void __launch_bounds__(256) k_kubo_partial(const int64_t* __restrict_
   const int cb = swap_combo(c);
   const int KK = K * K;
   const double2* Jd = J + (size_t)d * J_dstride;
+  const float4* Jdfd = DF ? Jdf + (size_t)d * Jdf_dstride : nullptr;  // J already split (mixed form)
+  auto ldJ = [&](size_t idx) -> V {
+    if constexpr (DF) return Jdfd[idx];
+    else return Jd[idx];
+  };
   __shared__ V sT1[16][17], sT2[16][17];
   __shared__ V sB[3][16][17];
   __shared__ V sP[3][16][17];
@@ -76,7 +90,7 @@ __global__ void __launch_bounds__(256) k_kubo_partial(const int64_t* __restrict_
       sT1[i][j] = ld(tau[((size_t)e1 * S_total + s) * KK + i * K + j]);
       sT2[i][j] = ld(tau[((size_t)e2 * S_total + s) * KK + i * K + j]);
 #pragma unroll
-      for (int v = 0; v < 3; ++v) sB[v][i][j] = ld(Jd[(((size_t)sp * 4 + c) * 3 + v) * KK + i * K + j]);
+      for (int v = 0; v < 3; ++v) sB[v][i][j] = ldJ((((size_t)sp * 4 + c) * 3 + v) * KK + i * K + j);
     }
     __syncthreads();
     if (act) {
@@ -103,7 +117,7 @@ __global__ void __launch_bounds__(256) k_kubo_partial(const int64_t* __restrict_
   const int spm = min(max(0, species[m]), n_species - 1);
   if (act) {
 #pragma unroll
-    for (int u = 0; u < 3; ++u) sB[u][i][j] = ld(Jd[(((size_t)spm * 4 + cb) * 3 + u) * KK + i * K + j]);
+    for (int u = 0; u < 3; ++u) sB[u][i][j] = ldJ((((size_t)spm * 4 + cb) * 3 + u) * KK + i * K + j);
   }
   __syncthreads();
   __shared__ double2 red[9][8];
@@ -187,7 +201,8 @@ __global__ void k_kubo_finish(const double2* __restrict__ S, int n_delta, double
 __global__ void __launch_bounds__(256) k_adj_abar(const int32_t* __restrict__ species,
                                                   const double2* __restrict__ J, int64_t J_dstride,
                                                   const double2* __restrict__ w, int K, double volume,
-                                                  int n_delta, int n_species, double2* __restrict__ abar) {
+                                                  int n_delta, int n_species, double2* __restrict__ abar,
+                                                  float4* __restrict__ abar_df) {
   const int m = blockIdx.x;
   const int d = blockIdx.y >> 2, c = blockIdx.y & 3;
   const int cb = swap_combo(c);
@@ -204,7 +219,9 @@ __global__ void __launch_bounds__(256) k_adj_abar(const int32_t* __restrict__ sp
       const double2 cw = mk(ac * wc.x, -ac * wc.y);
       acc = cfma(cw, Jd[(((size_t)sp * 4 + cb) * 3 + u) * KK + tid], acc);
     }
-    abar[((((size_t)m * n_delta + d) * 4 + c) * 3 + v) * KK + tid] = acc;
+    const size_t o = ((((size_t)m * n_delta + d) * 4 + c) * 3 + v) * KK + tid;
+    abar[o] = acc;
+    if (abar_df) abar_df[o] = df_split(acc);  // split once for the double-float right-hand sides
   }
 }
 
@@ -218,8 +235,9 @@ template <bool DF>
 __global__ void __launch_bounds__(256) k_adj_rhs(const Unit* __restrict__ units, const int32_t* __restrict__ site_atom,
                                                  const int32_t* __restrict__ species, const double2* __restrict__ J,
                                                  int64_t J_dstride, const double2* __restrict__ tau, int64_t S_total,
-                                                 const double2* __restrict__ abar, int n_delta, int n_species, int K,
-                                                 char* ws) {
+                                                 const double2* __restrict__ abar, const float4* __restrict__ Jdf,
+                                                 int64_t Jdf_dstride, const float4* __restrict__ abar_df,
+                                                 int n_delta, int n_species, int K, char* ws) {
   using V = typename std::conditional<DF, float4, double2>::type;
   const Unit u = units[blockIdx.y];
   const int nsite = blockIdx.x;
@@ -250,8 +268,15 @@ __global__ void __launch_bounds__(256) k_adj_rhs(const Unit* __restrict__ units,
       if (act) sT[i][j] = load(tau[((size_t)eo * S_total + s) * KK + i * K + j]);
       for (int v = 0; v < 3; ++v) {
         if (act) {
-          sJ[i][j] = load(Jd[(((size_t)sp * 4 + c) * 3 + v) * KK + i * K + j]);
-          sA[i][j] = load(abar[((((size_t)m * n_delta + d) * 4 + c) * 3 + v) * KK + i * K + j]);
+          const size_t jo = (((size_t)sp * 4 + c) * 3 + v) * KK + i * K + j;
+          const size_t ao = ((((size_t)m * n_delta + d) * 4 + c) * 3 + v) * KK + i * K + j;
+          if constexpr (DF) {  // J and Abar split once per call (k_split_j, k_adj_abar)
+            sJ[i][j] = Jdf[(size_t)d * Jdf_dstride + jo];
+            sA[i][j] = abar_df[ao];
+          } else {
+            sJ[i][j] = Jd[jo];
+            sA[i][j] = abar[ao];
+          }
         }
         __syncthreads();
         if (act) {
@@ -382,35 +407,49 @@ __global__ void __launch_bounds__(256) k_adj_species(const int32_t* __restrict__
 // ------------------------------------------------------------------ wrappers
 int kubo_forward(const int64_t* offsets, const int32_t* site_atom, const int32_t* species, int n_species,
                  const double2* J, int64_t J_dstride, const double2* tau, int64_t S_total, int K, int n_atoms, int n_delta,
-                 double volume, bool df, double2* partial, double2* S, double2* sigma_tilde, double2* sigma,
-                 double* rho, cudaStream_t st) {
-  if (df)
+                 double volume, bool df, float4* jdf, double2* partial, double2* S, double2* sigma_tilde,
+                 double2* sigma, double* rho, cudaStream_t st) {
+  if (df) {
+    const int64_t per = (int64_t)n_species * 12 * K * K;
+    const int n_dj = J_dstride > 0 ? n_delta : 1;
+    LSMS_LAUNCH(k_split_j, dim3((unsigned)((per + 255) / 256), n_dj), dim3(256), 0, st, J, J_dstride, per, jdf);
     LSMS_LAUNCH(k_kubo_partial<true>, dim3(n_atoms, n_delta * 4), dim3(256), 0, st, offsets, site_atom, species, J,
-                J_dstride, tau, S_total, K, n_atoms, n_species, partial);
-  else
+                J_dstride, jdf, J_dstride > 0 ? per : 0, tau, S_total, K, n_atoms, n_species, partial);
+  } else {
     LSMS_LAUNCH(k_kubo_partial<false>, dim3(n_atoms, n_delta * 4), dim3(256), 0, st, offsets, site_atom, species, J,
-                J_dstride, tau, S_total, K, n_atoms, n_species, partial);
+                J_dstride, nullptr, 0, tau, S_total, K, n_atoms, n_species, partial);
+  }
   LSMS_LAUNCH(k_kubo_reduce, dim3(n_delta * 4 * 9), dim3(256), 0, st, partial, n_atoms, S);
   LSMS_LAUNCH(k_kubo_finish, dim3(1), dim3(32), 0, st, S, n_delta, volume, sigma_tilde, sigma, rho);
   return LSMS_OK;
 }
 
 int adj_abar(const int32_t* species, int n_species, const double2* J, int64_t J_dstride, const double2* w, int K,
-             double volume, int n_atoms, int n_delta, double2* abar, cudaStream_t st) {
+             double volume, int n_atoms, int n_delta, double2* abar, float4* abar_df, cudaStream_t st) {
   LSMS_LAUNCH(k_adj_abar, dim3(n_atoms, n_delta * 4), dim3(256), 0, st, species, J, J_dstride, w, K, volume,
-              n_delta, n_species, abar);
+              n_delta, n_species, abar, abar_df);
+  return LSMS_OK;
+}
+
+int split_j(const double2* J, int64_t J_dstride, int n_species, int K, int n_delta, float4* out, int64_t* out_dstride,
+            cudaStream_t st) {
+  const int64_t per = (int64_t)n_species * 12 * K * K;
+  const int n_dj = J_dstride > 0 ? n_delta : 1;
+  LSMS_LAUNCH(k_split_j, dim3((unsigned)((per + 255) / 256), n_dj), dim3(256), 0, st, J, J_dstride, per, out);
+  *out_dstride = J_dstride > 0 ? per : 0;
   return LSMS_OK;
 }
 
 int adj_rhs(const Unit* d_units, int n_units, int S_max, const int32_t* site_atom, const int32_t* species,
             int n_species, const double2* J, int64_t J_dstride, const double2* tau, int64_t S_total,
-            const double2* abar, int n_delta, int K, char* ws, bool df, cudaStream_t st) {
+            const double2* abar, const float4* jdf, int64_t jdf_dstride, const float4* abar_df, int n_delta, int K,
+            char* ws, bool df, cudaStream_t st) {
   if (df)
     LSMS_LAUNCH(k_adj_rhs<true>, dim3(S_max, n_units), dim3(256), 0, st, d_units, site_atom, species, J, J_dstride,
-                tau, S_total, abar, n_delta, n_species, K, ws);
+                tau, S_total, abar, jdf, jdf_dstride, abar_df, n_delta, n_species, K, ws);
   else
     LSMS_LAUNCH(k_adj_rhs<false>, dim3(S_max, n_units), dim3(256), 0, st, d_units, site_atom, species, J, J_dstride,
-                tau, S_total, abar, n_delta, n_species, K, ws);
+                tau, S_total, abar, nullptr, 0, nullptr, n_delta, n_species, K, ws);
   return LSMS_OK;
 }
 
@@ -450,6 +489,15 @@ void* g_scratch_addr[64];
 
 size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 
+}  // namespace
+
+// Bytes of the double-float copy of J used by the mixed-form traces.
+size_t jdf_scratch_bytes(int n_species, int K, int n_delta, int64_t J_dstride) {
+  return round256((size_t)(J_dstride > 0 ? n_delta : 1) * n_species * 12 * K * K * sizeof(float4));
+}
+
+namespace {
+
 int scratch_address(void** out) {
   int dev = 0;
   LSMS_CUDA_TRY(cudaGetDevice(&dev));
@@ -486,26 +534,28 @@ extern "C" int lsms_kubo_sigma_noalloc(const lsms_liz* liz_c, int lmax, const in
   if (J_delta_stride < 0) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_noalloc: negative J stride");
   if (precision != LSMS_FP64 && precision != LSMS_MIXED)
     return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_noalloc: unknown precision %d", precision);
+  const int K = (lmax + 1) * (lmax + 1);
   const size_t part_bytes = round256((size_t)n_delta * 4 * liz->n_atoms * 9 * sizeof(double2));
   const size_t s_bytes = round256((size_t)n_delta * 36 * sizeof(double2));
-  if (part_bytes + s_bytes > kNoAllocScratchBytes)
+  const size_t jdf_bytes = precision == LSMS_MIXED ? jdf_scratch_bytes(n_species, K, n_delta, J_delta_stride) : 0;
+  if (part_bytes + s_bytes + jdf_bytes > kNoAllocScratchBytes)
     return fail(LSMS_ERR_ARG,
                 "lsms_kubo_sigma_noalloc: %d atoms x %d deltas need %zu bytes of scratch; the static buffer holds "
                 "%zu bytes (about 29,000 atom-delta pairs); use lsms_kubo_sigma",
-                liz->n_atoms, n_delta, part_bytes + s_bytes, kNoAllocScratchBytes);
+                liz->n_atoms, n_delta, part_bytes + s_bytes + jdf_bytes, kNoAllocScratchBytes);
   DeviceData* dd = nullptr;
   int rc = existing_device_data(liz, &dd);
   if (rc) return rc;
   void* scratch = nullptr;
   if ((rc = scratch_address(&scratch))) return rc;
   char* base = static_cast<char*>(scratch);
-  const int K = (lmax + 1) * (lmax + 1);
   // Every scratch element read by the kernels is written earlier in the same
-  // call (partial traces by k_kubo_partial, sums by k_kubo_reduce), so the
-  // previous call's contents need no clearing.
+  // call (split J by k_split_j, partial traces by k_kubo_partial, sums by
+  // k_kubo_reduce), so the previous call's contents need no clearing.
   return kubo_forward(dd->offsets, dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J),
                       J_delta_stride, reinterpret_cast<const double2*>(tau), liz->total_sites, K, liz->n_atoms,
-                      n_delta, volume, precision == LSMS_MIXED, reinterpret_cast<double2*>(base),
+                      n_delta, volume, precision == LSMS_MIXED,
+                      reinterpret_cast<float4*>(base + part_bytes + s_bytes), reinterpret_cast<double2*>(base),
                       reinterpret_cast<double2*>(base + part_bytes),
                       reinterpret_cast<double2*>(sigma_tilde), reinterpret_cast<double2*>(sigma), rho,
                       reinterpret_cast<cudaStream_t>(stream));

@@ -501,6 +501,8 @@ __global__ void __launch_bounds__(512, 2) k_solve(const Unit* __restrict__ units
 // below (forward) or above (backward) a solved block gives each thread one row
 // and G = min(NCOL, 8) columns: per step j one coalesced 8-byte load of the
 // factor, G/2 16-byte shared-memory loads of the solved block and 4 G FMAs.
+constexpr int kSolveThreads = 256;  // complex64 solve CTA
+
 template <int NCOL>
 __device__ __forceinline__ void update_rows_c64(const float2* __restrict__ A, float2* X, const float2 (*sX)[NCOL],
                                                 int n, int k, int nbp, int r0, int r1, int nrhs, int tid) {
@@ -509,7 +511,7 @@ __device__ __forceinline__ void update_rows_c64(const float2* __restrict__ A, fl
   constexpr int NB = 32;
   const int rows = r1 - r0;
   if (rows <= 0) return;
-  for (int idx = tid; idx < rows * NG; idx += 512) {
+  for (int idx = tid; idx < rows * NG; idx += kSolveThreads) {
     const int gi = idx / rows;
     const int i = r0 + (idx - gi * rows);
     const int g = gi * G;
@@ -550,13 +552,14 @@ __device__ __forceinline__ void update_rows_c64(const float2* __restrict__ A, fl
   }
 }
 
-// One CTA of 512 threads per unit: L y = P b (unit lower, each panel's swaps
-// applied just before its block), then U x = y on the n x nrhs column-major
-// block X.  The 32 x 32
+// One CTA of kSolveThreads threads per unit (several units resident per SM, so
+// one unit's serial triangle phases overlap the others' row updates): L y = P b
+// (unit lower, each panel's swaps applied just before its block), then U x = y
+// on the n x nrhs column-major block X.  The 32 x 32
 // triangles are solved by warps taking columns in turn (lane = row, values
 // passed by shuffles, reciprocals of U's diagonal formed before the sweep).
 template <int NCOL>
-__global__ void __launch_bounds__(512, 2) k_solve_c64(const Unit* __restrict__ units, const char* fac_base,
+__global__ void __launch_bounds__(kSolveThreads, 1024 / kSolveThreads) k_solve_c64(const Unit* __restrict__ units, const char* fac_base,
                                                      char* ws, int which, int nrhs, const int32_t* done) {
   static_assert(NCOL >= 2 && NCOL % 2 == 0 && NCOL <= 32, "padded column count");
   constexpr int NB = 32;
@@ -573,13 +576,13 @@ __global__ void __launch_bounds__(512, 2) k_solve_c64(const Unit* __restrict__ u
   // forward
   for (int k = 0; k < n; k += NB) {
     const int nbp = min(NB, n - k);
-    for (int idx = tid; idx < NB * NB; idx += 512) {
+    for (int idx = tid; idx < NB * NB; idx += kSolveThreads) {
       const int i = idx % NB, j = idx / NB;
       sT[i][j] = (i < nbp && j < nbp) ? A[(size_t)(k + j) * n + k + i] : make_float2(0.f, 0.f);
     }
     if (tid < NB) sp[tid] = tid < nbp ? piv[k + tid] : k + tid;
     __syncthreads();
-    for (int col = warp; col < NCOL; col += 16) {
+    for (int col = warp; col < NCOL; col += kSolveThreads / 32) {
       const bool live = col < nrhs && lane < nbp;
       float2 x = live ? X[(size_t)col * n + k + lane] : make_float2(0.f, 0.f);
       if (col < nrhs) x = panel_swaps(x, X + (size_t)col * n, sp, k, lane);
@@ -598,12 +601,12 @@ __global__ void __launch_bounds__(512, 2) k_solve_c64(const Unit* __restrict__ u
   const int last = ((n - 1) / NB) * NB;
   for (int k = last; k >= 0; k -= NB) {
     const int nbp = min(NB, n - k);
-    for (int idx = tid; idx < NB * NB; idx += 512) {
+    for (int idx = tid; idx < NB * NB; idx += kSolveThreads) {
       const int i = idx % NB, j = idx / NB;
       sT[i][j] = (i < nbp && j < nbp) ? A[(size_t)(k + j) * n + k + i] : make_float2(i == j ? 1.f : 0.f, 0.f);
     }
     __syncthreads();
-    for (int col = warp; col < NCOL; col += 16) {
+    for (int col = warp; col < NCOL; col += kSolveThreads / 32) {
       const bool live = col < nrhs && lane < nbp;
       const float2 dinv = crcp(sT[lane][lane]);
       float2 x = live ? X[(size_t)col * n + k + lane] : make_float2(0.f, 0.f);
@@ -665,7 +668,7 @@ int lu_solve_chunk(const Unit* d_units, int n_units, const char* fac_base, char*
   if (nrhs < 1 || nrhs > 32) return fail(LSMS_ERR_ARG, "internal: nrhs %d out of range", nrhs);
   constexpr int NB = LuCfg<R>::NB;
   if constexpr (std::is_same<R, float>::value) {
-    const dim3 g(n_units), b(512);
+    const dim3 g(n_units), b(kSolveThreads);
     if (nrhs <= 2) LSMS_LAUNCH(k_solve_c64<2>, g, b, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
     else if (nrhs <= 4) LSMS_LAUNCH(k_solve_c64<4>, g, b, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
     else if (nrhs <= 8) LSMS_LAUNCH(k_solve_c64<8>, g, b, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
