@@ -16,6 +16,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblsmskubo.so")
 
 LSMS_FP64 = 0
 LSMS_MIXED = 1
+LSMS_OK = 0
+LSMS_ERR_ARG = -1  # status codes of the C ABI (include/lsmskubo.h)
 PRECISIONS = {"fp64": LSMS_FP64, "mixed": LSMS_MIXED}
 
 UNIT_ZERO_PIVOT = 1

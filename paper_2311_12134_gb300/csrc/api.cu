@@ -482,7 +482,7 @@ __device__ void hankel6_df(double d, double2 kap, double2 mpref, bool adv, float
 // fac_base + m64_off) for the refinement residual and, if write_fac, the hi part
 // (complex64) as the matrix to factor.
 template <bool MIXED>
-__global__ void __launch_bounds__(256, 2) k_assemble(const Unit* __restrict__ units, int nE,
+__global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ units, int nE,
                                                   const double* __restrict__ disp,
                                                   const int32_t* __restrict__ site_atom,
                                                   const int32_t* __restrict__ species,

@@ -220,12 +220,27 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_smem(const Unit* __rest
   int lg = tid;  // logical row of physical row tid
   // warp-level best (value, logical row, physical row); lowest logical row on ties
   auto warp_best = [&](R& best, int& bl, int& bp) {
+    if constexpr (std::is_same<R, float>::value) {
+      // single-instruction warp reductions: the magnitude as an order-preserving
+      // key (non-negative floats order like their bit patterns; NaN and
+      // non-candidates (best < 0) get key 0), then the lowest logical row among
+      // the lanes holding the largest key
+      const unsigned key = best >= 0.f ? __float_as_uint(best) + 1u : 0u;
+      const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+      const unsigned lmin = __reduce_min_sync(0xffffffffu, key == kmax ? (unsigned)bl : 0xffffffffu);
+      const unsigned win = __ballot_sync(0xffffffffu, key == kmax && (unsigned)bl == lmin);
+      const int src = __ffs(win) - 1;
+      best = __shfl_sync(0xffffffffu, best, src);
+      bp = __shfl_sync(0xffffffffu, bp, src);
+      bl = (int)lmin;
+    } else {
 #pragma unroll
-    for (int off = 16; off; off >>= 1) {
-      const R ov = __shfl_xor_sync(0xffffffffu, best, off);
-      const int ol = __shfl_xor_sync(0xffffffffu, bl, off);
-      const int op = __shfl_xor_sync(0xffffffffu, bp, off);
-      if (ov > best || (ov == best && ol < bl)) { best = ov; bl = ol; bp = op; }
+      for (int off = 16; off; off >>= 1) {
+        const R ov = __shfl_xor_sync(0xffffffffu, best, off);
+        const int ol = __shfl_xor_sync(0xffffffffu, bl, off);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, off);
+        if (ov > best || (ov == best && ol < bl)) { best = ov; bl = ol; bp = op; }
+      }
     }
   };
   auto mag = [](C v) -> R {  // |Re| + |Im|; NaN below every number

@@ -92,3 +92,56 @@ def test_dipole_current_matches_oracle(L):
         J = B.dipole_current(lmax, r)
         ref = okubo.dipole_current(lmax, r)
         assert np.abs(J - ref).max() < 1e-15
+
+
+def test_argument_errors_are_reported_before_any_device_work(L):
+    """Bad arguments come back as LSMS_ERR_ARG with a message, checked on the host
+    before the library touches a device (so this runs without a GPU)."""
+    import ctypes
+    from paper_2311_12134_gb300 import binding as B
+    lib = B.lib()
+    w = wl.fcc_pure_32()
+    lz = B.build_liz(w.pos, w.lattice, w.r_liz)
+    z = np.ascontiguousarray(w.z, dtype=np.complex128)
+    zp = z.ctypes.data_as(ctypes.c_void_p)
+    dummy = ctypes.c_void_p(16)  # never dereferenced: every call below fails its checks first
+    sz_a, sz_b = ctypes.c_size_t(), ctypes.c_size_t()
+
+    def tau(lmax=3, n_species=1, n_energy=2, precision=0, z_ptr=zp, tinv=dummy):
+        return lib.lsms_tau_blocks(lz.handle, lmax, dummy, n_species, tinv, z_ptr, n_energy, precision, dummy,
+                                   None, None, 0, None, 0, None)
+
+    cases = {
+        "lmax": tau(lmax=4),
+        "species": tau(n_species=0),
+        "n_energy": tau(n_energy=0),
+        "too many energies": tau(n_energy=65),
+        "precision": tau(precision=7),
+        "tinv": tau(tinv=None),
+        "conj odd": tau(n_energy=1, precision=B._prec("mixed", True)),
+        "sizes lmax": lib.lsms_tau_workspace_bytes(lz.handle, 5, 2, 0, ctypes.byref(sz_a), ctypes.byref(sz_b)),
+        "sizes conj odd": lib.lsms_tau_workspace_bytes(lz.handle, 3, 3, B._prec("fp64", True), ctypes.byref(sz_a),
+                                                       ctypes.byref(sz_b)),
+        "store precision": lib.lsms_lu_store_bytes(lz.handle, 3, 2, 9, ctypes.byref(sz_a)),
+        "backward odd n_energy": lib.lsms_backward_workspace_bytes(lz.handle, 3, 3, 0, ctypes.byref(sz_a),
+                                                                   ctypes.byref(sz_b)),
+        "sigma volume": lib.lsms_kubo_sigma(lz.handle, 3, dummy, 1, dummy, 0, dummy, 1, -1.0, 0, None, dummy, None,
+                                            None),
+        "sigma precision": lib.lsms_kubo_sigma(lz.handle, 3, dummy, 1, dummy, 0, dummy, 1, 1.0, 5, None, dummy, None,
+                                               None),
+        "sigma stride": lib.lsms_kubo_sigma(lz.handle, 3, dummy, 1, dummy, -1, dummy, 1, 1.0, 0, None, dummy, None,
+                                            None),
+    }
+    for what, rc in cases.items():
+        assert rc == B.LSMS_ERR_ARG, (what, rc)
+        assert lib.lsms_last_error().decode(), what
+    # conjugate pairs need z[2d+1] = conj z[2d] exactly
+    zb = z.copy()
+    zb[1] += 1e-12
+    assert tau(precision=B._prec("mixed", True), z_ptr=zb.ctypes.data_as(ctypes.c_void_p)) == B.LSMS_ERR_ARG
+    assert "conjugate" in lib.lsms_last_error().decode()
+    # the sizing calls succeed and are consistent: the store halves with conjugate pairs
+    full, half = ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.lsms_lu_store_bytes(lz.handle, 3, 2, 1, ctypes.byref(full)) == 0
+    assert lib.lsms_lu_store_bytes(lz.handle, 3, 2, B._prec("mixed", True), ctypes.byref(half)) == 0
+    assert full.value == 2 * half.value > 0
