@@ -304,17 +304,24 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_smem(const Unit* __rest
 }
 
 // ------------------------------------------------------------------ swap + trsm
-// One warp per column right of the panel (lane i holds row k + i): the panel's
-// row interchanges, then U12 = L11^{-1} A12.  Columns left of the panel keep
-// their row order (L is stored as computed, LINPACK style): the forward solve
-// applies each panel's interchanges to the right-hand sides before that panel's
-// columns of L are used.
-constexpr int kSwapCols = 64;  // columns per CTA of k_swap_trsm (8 warps x 8)
+// Columns right of the panel, one thread per column (256 columns per CTA): the
+// panel's row interchanges, then U12 = L11^{-1} A12.  The 32 interchanges are
+// the same for every column, so the CTA composes them once into a permutation
+// of the panel rows and the rows below the panel they reach: each thread then
+// loads its column's 32 panel rows already permuted (gathers), writes the rows
+// below the panel (their new values always come from panel rows), solves the
+// unit-lower triangle in registers with L11 read as shared-memory broadcasts,
+// and stores the 32 rows.  One broadcast of L11 serves 32 columns, where a
+// warp per column needed a shuffle or shared-memory access per step and
+// column.  Columns left of the panel keep their row order (L is stored as
+// computed, LINPACK style): the forward solve applies each panel's
+// interchanges to the right-hand sides before that panel's columns of L are used.
+constexpr int kSwapCols = 256;  // columns per CTA of k_swap_trsm
 
 template <typename R, int NB>
 __global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ units, char* fac_base, int k) {
   using C = Cx<R>;
-  static_assert(NB == 32, "one lane per panel row");
+  static_assert(NB == 32, "one warp of interchanges");
   const Unit u = units[blockIdx.y];
   const int n = u.n;
   const int c0 = k + NB + blockIdx.x * kSwapCols;
@@ -322,25 +329,74 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ unit
   C* A = reinterpret_cast<C*>(fac_base + u.fac_off);
   const int32_t* piv = reinterpret_cast<const int32_t*>(fac_base + u.piv_off);
   __shared__ C sL[NB][NB + 1];
-  __shared__ int sp[NB];
-  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+  __shared__ int sStep[NB];       // slot exchanged with slot j at interchange j (-1: none)
+  __shared__ int sTgtRow[NB];     // row of target slot 32 + t
+  __shared__ int sSrcRow[NB];     // panel row i takes the value of row sSrcRow[i]
+  __shared__ int sTgtSrc[NB];     // target row t takes the value of (panel) row sTgtSrc[t]
+  __shared__ int sNt;             // number of distinct rows below the panel
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
     const int i = idx % NB, j = idx / NB;
     sL[i][j] = A[(size_t)(k + j) * n + k + i];
   }
-  for (int j = threadIdx.x; j < NB; j += blockDim.x) sp[j] = piv[k + j];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c1 = min(c0 + kSwapCols, n);
-  for (int c = c0 + warp; c < c1; c += blockDim.x >> 5) {
-    C* Ac = A + (size_t)c * n;
-    C x = panel_swaps(Ac[k + lane], Ac, sp, k, lane);
-#pragma unroll
-    for (int j = 0; j < NB - 1; ++j) {
-      const C xj = shfl2(x, j);
-      if (lane > j) x = cfms(sL[lane][j], xj, x);
+  if (tid < 32) {
+    const int lane = tid;
+    const int p = piv[k + lane];
+    const bool out = p >= k + NB;
+    // distinct rows below the panel: each gets a slot 32 + t, t = rank of its first occurrence
+    const unsigned same = __match_any_sync(0xffffffffu, out ? p : -1 - lane);
+    const int first = __ffs(same) - 1;
+    const unsigned firsts = __ballot_sync(0xffffffffu, out && first == lane);
+    const int t = __popc(firsts & ((1u << first) - 1u));
+    sStep[lane] = p == k + lane ? -1 : (out ? NB + t : p - k);
+    if (out && first == lane) sTgtRow[t] = p;
+    if (lane == 0) sNt = __popc(firsts);
+    __syncwarp();
+    if (lane == 0) {
+      int cur[2 * NB];  // slot s now holds the value that started in slot cur[s]
+      for (int s = 0; s < 2 * NB; ++s) cur[s] = s;
+      for (int j = 0; j < NB; ++j) {
+        const int o = sStep[j];
+        if (o < 0) continue;
+        const int tmp = cur[j];
+        cur[j] = cur[o];
+        cur[o] = tmp;
+      }
+      auto row_of = [&](int s) { return s < NB ? k + s : sTgtRow[s - NB]; };
+      for (int i = 0; i < NB; ++i) sSrcRow[i] = row_of(cur[i]);
+      for (int q = 0; q < sNt; ++q) sTgtSrc[q] = row_of(cur[NB + q]);
     }
-    Ac[k + lane] = x;
   }
+  __syncthreads();
+  const int c = c0 + tid;
+  if (c >= n) return;
+  C* Ac = A + (size_t)c * n;
+  C x[NB];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) x[i] = Ac[sSrcRow[i]];  // gathered: the interchanged panel rows
+  // rows below the panel: new values from panel rows, which are written only at the end
+  const int nt = sNt;
+  for (int q0 = 0; q0 < nt; q0 += 8) {
+    C tv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) tv[q] = q0 + q < nt ? Ac[sTgtSrc[q0 + q]] : mk(R(0), R(0));
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (q0 + q < nt) Ac[sTgtRow[q0 + q]] = tv[q];
+  }
+  // U12 = L11^{-1} A12 (unit lower), by rows
+#pragma unroll
+  for (int i = 1; i < NB; ++i) {
+    C a0 = x[i], a1 = mk(R(0), R(0));
+#pragma unroll
+    for (int j = 0; j < i; j += 2) {
+      a0 = cfms(sL[i][j], x[j], a0);
+      if (j + 1 < i) a1 = cfms(sL[i][j + 1], x[j + 1], a1);
+    }
+    x[i] = mk(a0.x + a1.x, a0.y + a1.y);
+  }
+#pragma unroll
+  for (int i = 0; i < NB; ++i) Ac[k + i] = x[i];
 }
 
 // ------------------------------------------------------------------ trailing GEMM (SIMT)
