@@ -535,7 +535,11 @@ def kernel_models(w, n_list, fwd_passes, bwd_passes, precision, nb=32):
                           "16x16 complex products in double-float FP32 arithmetic")
     else:
         m["k_adj_rhs"] = (len(w.z) * sites * 24 * 16 ** 3 * 8.0, FP64_PEAK_TFLOPS, "FP64 16x16 products")
-    m["k_kubo_partial"] = (w.n_delta * 4 * sites * 6 * 16 ** 3 * 8.0, FP64_PEAK_TFLOPS, "FP64 16x16 products")
+    if mixed:
+        m["k_kubo_partial"] = (w.n_delta * 4 * sites * 6 * 16 ** 3 * 8.0, 8.0 * FP32_OPS / DF_OPS_PER_CMAC / 1e12,
+                               "16x16 complex products in double-float FP32 arithmetic")
+    else:
+        m["k_kubo_partial"] = (w.n_delta * 4 * sites * 6 * 16 ** 3 * 8.0, FP64_PEAK_TFLOPS, "FP64 16x16 products")
     return m
 
 

@@ -682,10 +682,12 @@ __global__ void k_widen(const Unit* __restrict__ units, char* ws, int nrhs) {
 
 // Refinement residual, FP64-accurate, on the FP32 pipes: B - M X with M held as
 // (hi, lo) float pairs and X split the same way, products by the FMA two-product
-// and sums by two-sum (double-float arithmetic, unit roundoff about 2^-48).
-// Output rounded to complex64 and permuted by P into X32 for the correction
-// solve.  grid (ceil(n_max / 64), n_units), block 256: 64 rows x NRHS columns,
-// 4 column groups of CPG = NRHS / 4 columns per thread.
+// and sums by two-sum (double-float arithmetic, unit roundoff about 2^-48), in
+// paired FP32 instructions (real and imaginary lanes).  Output rounded to
+// complex64 into X32 for the correction solve.  grid (ceil(n_max / 64),
+// n_units), block 256: 64 rows x NRHS columns, 4 column groups of CPG = NRHS / 4
+// columns per thread.  The X tile is staged in shared memory as the two pairs
+// each product needs, (x.re, x.im) and (-x.im, x.re), high and low parts.
 template <int NRHS>
 __global__ void __launch_bounds__(256, 3) k_residual(const Unit* __restrict__ units, const char* fac_base, char* ws,
                                                      int K, bool explicit_b, const int32_t* __restrict__ done) {
@@ -696,18 +698,28 @@ __global__ void __launch_bounds__(256, 3) k_residual(const Unit* __restrict__ un
   const int n = u.n;
   const int row0 = blockIdx.x * 64;
   if (row0 >= n) return;
-  const float4* M = reinterpret_cast<const float4*>(fac_base + u.m64_off);
-  const float4* Xdf = reinterpret_cast<const float4*>(ws + u.xdf_off);  // X as (hi, lo) pairs
+  const float4* M = reinterpret_cast<const float4*>(fac_base + u.m64_off);  // (re.hi, im.hi, re.lo, im.lo)
+  const float4* Xdf = reinterpret_cast<const float4*>(ws + u.xdf_off);       // (re.hi, re.lo, im.hi, im.lo)
   float2* X32 = reinterpret_cast<float2*>(ws + u.x32_off);
-  __shared__ float4 sX[32][NCOL + 1];
+  __shared__ float4 sP[32][NCOL + 1], sQ[32][NCOL + 1];  // (x.re, x.im | hi, lo), (-x.im, x.re | hi, lo)
   const int tid = threadIdx.x;
   const int r = tid & 63, cg = tid >> 6;
   const int row = row0 + r;
   const bool live = row < n;
   const float4* Mrow = M + (live ? row : 0);
-  float sr[CPG], tr[CPG], si[CPG], ti[CPG];
+  float2 s[CPG], t[CPG];
 #pragma unroll
-  for (int c = 0; c < CPG; ++c) sr[c] = tr[c] = si[c] = ti[c] = 0.f;
+  for (int c = 0; c < CPG; ++c) s[c] = t[c] = make_float2(0.f, 0.f);
+  auto mac = [&](const float4 m, int jj) {
+    const float2 mrh = make_float2(m.x, m.x), mrl = make_float2(m.z, m.z);
+    const float2 mih = make_float2(m.y, m.y), mil = make_float2(m.w, m.w);
+#pragma unroll
+    for (int c = 0; c < CPG; ++c) {
+      const float4 P = sP[jj][cg * CPG + c], Q = sQ[jj][cg * CPG + c];
+      df2_mac(s[c], t[c], mrh, mrl, make_float2(P.x, P.y), make_float2(P.z, P.w));
+      df2_mac(s[c], t[c], mih, mil, make_float2(Q.x, Q.y), make_float2(Q.z, Q.w));
+    }
+  };
   for (int j0 = 0; j0 < n; j0 += 32) {
     const int jn = min(32, n - j0);
     __syncthreads();
@@ -715,36 +727,16 @@ __global__ void __launch_bounds__(256, 3) k_residual(const Unit* __restrict__ un
       const int jj = idx & 31, c = idx >> 5;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (jj < jn && c < NRHS) v = Xdf[(size_t)c * n + j0 + jj];
-      sX[jj][c] = v;
+      sP[jj][c] = make_float4(v.x, v.z, v.y, v.w);
+      sQ[jj][c] = make_float4(-v.z, v.x, -v.w, v.y);
     }
     __syncthreads();
     if (live) {
       if (jn == 32) {
 #pragma unroll 4
-        for (int jj = 0; jj < 32; ++jj) {
-          const float4 m = Mrow[(size_t)(j0 + jj) * n];
-#pragma unroll
-          for (int c = 0; c < CPG; ++c) {
-            const float4 x = sX[jj][cg * CPG + c];
-            // Re += m.re x.re - m.im x.im ; Im += m.re x.im + m.im x.re
-            df_mac(sr[c], tr[c], m.x, m.z, x.x, x.y);
-            df_mac(sr[c], tr[c], -m.y, -m.w, x.z, x.w);
-            df_mac(si[c], ti[c], m.x, m.z, x.z, x.w);
-            df_mac(si[c], ti[c], m.y, m.w, x.x, x.y);
-          }
-        }
+        for (int jj = 0; jj < 32; ++jj) mac(Mrow[(size_t)(j0 + jj) * n], jj);
       } else {
-        for (int jj = 0; jj < jn; ++jj) {
-          const float4 m = Mrow[(size_t)(j0 + jj) * n];
-#pragma unroll
-          for (int c = 0; c < CPG; ++c) {
-            const float4 x = sX[jj][cg * CPG + c];
-            df_mac(sr[c], tr[c], m.x, m.z, x.x, x.y);
-            df_mac(sr[c], tr[c], -m.y, -m.w, x.z, x.w);
-            df_mac(si[c], ti[c], m.x, m.z, x.z, x.w);
-            df_mac(si[c], ti[c], m.y, m.w, x.x, x.y);
-          }
-        }
+        for (int jj = 0; jj < jn; ++jj) mac(Mrow[(size_t)(j0 + jj) * n], jj);
       }
     }
   }
@@ -757,8 +749,8 @@ __global__ void __launch_bounds__(256, 3) k_residual(const Unit* __restrict__ un
       double2 b;
       if (explicit_b) b = B[(size_t)col * n + row];
       else b = (row == col && col < K) ? mk(1.0, 0.0) : mk(0.0, 0.0);
-      const double re = b.x - ((double)sr[c] + (double)tr[c]);
-      const double im = b.y - ((double)si[c] + (double)ti[c]);
+      const double re = b.x - ((double)s[c].x + (double)t[c].x);
+      const double im = b.y - ((double)s[c].y + (double)t[c].y);
       X32[(size_t)col * n + row] = make_float2((float)re, (float)im);
     }
   }
@@ -1169,6 +1161,68 @@ static int check_conj_energies(const lsms_complex* z, int n_energy) {
   return LSMS_OK;
 }
 
+// Two halves of a chunk run on two streams: the caller's and a side stream
+// (one per host thread and device), forked and joined by events, which a
+// CUDA-graph capture records as edges.  The step is a chain of batched launches
+// whose latency-bound phases (panels, interchanges, solves) leave the GPU partly
+// idle; the other half's bandwidth- and compute-bound launches fill it.  The
+// halves hold whole atoms and disjoint workspace.  With the kernel timers on,
+// everything stays on the caller's stream so that each launch is timed alone.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+static int side_stream(SideStream** out) {
+  static thread_local SideStream side[64];  // per host thread: a stream is captured into one graph at a time
+  int dev = 0;
+  LSMS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(LSMS_ERR_CUDA, "device index %d unsupported", dev);
+  SideStream& ss = side[dev];
+  if (!ss.s) {
+    LSMS_CUDA_TRY(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
+    LSMS_CUDA_TRY(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming));
+    LSMS_CUDA_TRY(cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming));
+  }
+  *out = &ss;
+  return LSMS_OK;
+}
+
+// Split ch at an atom boundary (units and factor units are atom-major, with the
+// same number per atom).  False if ch holds fewer than 2 atoms.
+static bool split_chunk(const Plan& p, const Chunk& ch, Chunk* a, Chunk* b) {
+  const int n_at = (ch.f1 - ch.f0) / p.fac_per_atom;
+  if (n_at < 2) return false;
+  const int upa = (ch.u1 - ch.u0) / n_at;
+  const int h = n_at / 2;
+  *a = ch;
+  *b = ch;
+  a->u1 = b->u0 = ch.u0 + h * upa;
+  a->f1 = b->f0 = ch.f0 + h * p.fac_per_atom;
+  a->n_max = b->n_max = 0;
+  for (int u = a->u0; u < a->u1; ++u) a->n_max = std::max(a->n_max, p.units[u].n);
+  for (int u = b->u0; u < b->u1; ++u) b->n_max = std::max(b->n_max, p.units[u].n);
+  return true;
+}
+
+// run(chunk, stream) for the two halves of ch on two streams, or for ch on c.st.
+template <typename F>
+static int run_split(const Call& c, const Plan& p, const Chunk& ch, F run) {
+  Chunk a, b;
+  SideStream* ss = nullptr;
+  if (g_timer_on.load(std::memory_order_relaxed) || !split_chunk(p, ch, &a, &b)) return run(ch, c.st);
+  int rc = side_stream(&ss);
+  if (rc) return rc;
+  LSMS_CUDA_TRY(cudaEventRecord(ss->fork, c.st));
+  LSMS_CUDA_TRY(cudaStreamWaitEvent(ss->s, ss->fork, 0));
+  rc = run(a, c.st);
+  if (!rc) rc = run(b, ss->s);
+  // joined even after an error: no work stays forked from the caller's stream
+  LSMS_CUDA_TRY(cudaEventRecord(ss->join, ss->s));
+  LSMS_CUDA_TRY(cudaStreamWaitEvent(c.st, ss->join, 0));
+  return rc;
+}
+
 static int begin_call(lsms_liz* liz, const lsms_complex* z, int n_energy, Call* c) {
   for (int e = 0; e < n_energy; ++e) {
     if (!std::isfinite(z[e].re) || !std::isfinite(z[e].im)) return fail(LSMS_ERR_ARG, "energy %d is not finite", e);
@@ -1387,12 +1441,18 @@ extern "C" int lsms_tau_blocks(const lsms_liz* liz_c, int lmax, const int32_t* s
     }
     char* chunk = ws + h.chunk;
     char* fac_base = store ? static_cast<char*>(lu_store) : chunk;
-    for (const Chunk& ch : p->chunks) {
-      int r2 = assemble_factor(c, *p, ch, fac_base, chunk, stat);
+    for (const Chunk& whole : p->chunks) {
+      int r2 = run_split(c, *p, whole, [&](const Chunk& ch, cudaStream_t st) -> int {
+        Call cs = c;
+        cs.st = st;
+        int r3 = assemble_factor(cs, *p, ch, fac_base, chunk, stat);
+        if (r3) return r3;
+        if ((r3 = solve_refine(cs, *p, ch, fac_base, chunk, stat, done, false))) return r3;
+        LSMS_LAUNCH(k_write_tau, dim3(ch.n_max / c.K, ch.u1 - ch.u0), dim3(256), 0, st, p->d_units + ch.u0, chunk,
+                    c.K, liz->total_sites, conj, reinterpret_cast<double2*>(tau));
+        return LSMS_OK;
+      });
       if (r2) return r2;
-      if ((r2 = solve_refine(c, *p, ch, fac_base, chunk, stat, done, false))) return r2;
-      LSMS_LAUNCH(k_write_tau, dim3(ch.n_max / c.K, ch.u1 - ch.u0), dim3(256), 0, c.st, p->d_units + ch.u0, chunk,
-                  c.K, liz->total_sites, conj, reinterpret_cast<double2*>(tau));
     }
     if (unit_status) {
       LSMS_LAUNCH(k_status_out, dim3((unsigned)((nu_all + 255) / 256)), dim3(256), 0, c.st, stat, (int)nu_all,
@@ -1528,24 +1588,29 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
       return r2;
     char* chunk = ws + h.chunk;
     char* fac_base = store ? const_cast<char*>(static_cast<const char*>(lu_store)) : chunk;
-    for (const Chunk& ch : p->chunks) {
-      const Unit* du = p->d_units + ch.u0;
-      const int nu = ch.u1 - ch.u0;
-      const int S_max = ch.n_max / c.K;
-      // stored factors come with the double-float copy of M (mixed form): nothing to rebuild
-      if (!store && (r2 = assemble_factor(c, *p, ch, fac_base, chunk, stat))) return r2;
-      if ((r2 = adj_rhs(du, nu, S_max, c.dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J), J_delta_stride,
-                        reinterpret_cast<const double2*>(tau), liz->total_sites, abar, jdf, jdf_dstride, abar_df,
-                        n_delta, c.K, chunk, df, c.st)))
-        return r2;
-      const dim3 gc((ch.n_max * p->nrhs + 255) / 256, nu);
-      // second energy of a conjugate pair: M(conj z) = conj M(z), so X = conj(M(z)^-1 conj B)
-      if (conj) LSMS_LAUNCH(k_conj_block, gc, dim3(256), 0, c.st, du, chunk, p->nrhs, 0);
-      if ((r2 = solve_refine(c, *p, ch, fac_base, chunk, stat, done, true))) return r2;
-      if (conj) LSMS_LAUNCH(k_conj_block, gc, dim3(256), 0, c.st, du, chunk, p->nrhs, 1);
-      if ((r2 = adj_site(du, nu, S_max, reinterpret_cast<const double2*>(tau), liz->total_sites, c.K, chunk, G,
-                         precision == LSMS_MIXED, c.st)))
-        return r2;
+    for (const Chunk& whole : p->chunks) {
+      r2 = run_split(c, *p, whole, [&](const Chunk& ch, cudaStream_t st) -> int {
+        Call cs = c;
+        cs.st = st;
+        const Unit* du = p->d_units + ch.u0;
+        const int nu = ch.u1 - ch.u0;
+        const int S_max = ch.n_max / c.K;
+        int r3;
+        // stored factors come with the double-float copy of M (mixed form): nothing to rebuild
+        if (!store && (r3 = assemble_factor(cs, *p, ch, fac_base, chunk, stat))) return r3;
+        if ((r3 = adj_rhs(du, nu, S_max, c.dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J),
+                          J_delta_stride, reinterpret_cast<const double2*>(tau), liz->total_sites, abar, jdf,
+                          jdf_dstride, abar_df, n_delta, c.K, chunk, df, st)))
+          return r3;
+        const dim3 gc((ch.n_max * p->nrhs + 255) / 256, nu);
+        // second energy of a conjugate pair: M(conj z) = conj M(z), so X = conj(M(z)^-1 conj B)
+        if (conj) LSMS_LAUNCH(k_conj_block, gc, dim3(256), 0, st, du, chunk, p->nrhs, 0);
+        if ((r3 = solve_refine(cs, *p, ch, fac_base, chunk, stat, done, true))) return r3;
+        if (conj) LSMS_LAUNCH(k_conj_block, gc, dim3(256), 0, st, du, chunk, p->nrhs, 1);
+        return adj_site(du, nu, S_max, reinterpret_cast<const double2*>(tau), liz->total_sites, c.K, chunk, G,
+                        precision == LSMS_MIXED, st);
+      });
+      if (r2) return r2;
     }
     if ((r2 = adj_reduce(c.dd->inv_off, c.dd->inv_sites, G, liz->total_sites, c.K, liz->n_atoms, n_energy,
                          reinterpret_cast<double2*>(grad_tinv), c.st)))

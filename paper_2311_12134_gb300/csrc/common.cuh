@@ -146,6 +146,26 @@ __device__ __forceinline__ void dfc_mac(DfAcc& acc, float4 a, float4 b) {
   df_mac(acc.si, acc.ti, a.z, a.w, b.x, b.y);
 }
 
+// Packed forms on float2 (the paired FP32 instructions of sm_100 and later: two
+// lanes of arithmetic per instruction).  A complex accumulator is s = (re, im)
+// high parts and t = (re, im) low parts; a complex product m x splits as
+// m.re (x.re, x.im) + m.im (-x.im, x.re), each a real value times a pair.
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// (s, t) += (ah + al)(bh + bl) lane-wise: exact ah bh (two-product), the cross
+// terms, and the two-sum's rounding error into t.
+__device__ __forceinline__ void df2_mac(float2& s, float2& t, float2 ah, float2 al, float2 bh, float2 bl) {
+  const float2 p = __fmul2_rn(ah, bh);
+  float2 e = __ffma2_rn(ah, bh, f2neg(p));
+  e = __ffma2_rn(ah, bl, e);
+  e = __ffma2_rn(al, bh, e);
+  const float2 a = __fadd2_rn(s, p);
+  const float2 bb = __fadd2_rn(a, f2neg(s));
+  const float2 err = __fadd2_rn(__fadd2_rn(s, f2neg(__fadd2_rn(a, f2neg(bb)))), __fadd2_rn(p, f2neg(bb)));
+  t = __fadd2_rn(t, __fadd2_rn(err, e));
+  s = a;
+}
+
 // normalised (hi, lo) pairs of an accumulator
 __device__ __forceinline__ float4 df_value(const DfAcc& a) {
   const float rh = a.sr + a.tr, ih = a.si + a.ti;

@@ -150,6 +150,35 @@ def test_chunking_is_invisible(alloy32):
     assert torch.equal(t_all, t_few)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_two_stream_split_is_invisible(precision):
+    """Each chunk runs as two halves on two streams; with the kernel timers on it
+    runs on one stream.  Both give bit-identical tau, sigma and gradient."""
+    from paper_2311_12134_gb300 import binding as B
+    from paper_2311_12134_gb300.conductivity import Problem
+    w = _alloy32(seed=23)
+    J = B.dipole_current(w.lmax, w.r_ll)
+    p = Problem(w.pos, w.lattice, w.r_liz, w.lmax, w.species, w.tinv, w.z, J, w.volume, precision=precision)
+    gs = torch.zeros((1, 3, 3), dtype=torch.complex128, device="cuda")
+    gs[0, 1, 1] = 1.0
+
+    def step():
+        p.forward()
+        g = [t.clone() for t in p.backward(gs)]
+        torch.cuda.synchronize()
+        return p.tau.clone(), p.sigma_out.clone(), g
+
+    tau2, sig2, g2 = step()
+    B.kernel_timer_start()
+    try:
+        tau1, sig1, g1 = step()
+    finally:
+        B.kernel_timer_stop()
+    assert torch.equal(tau1, tau2)
+    assert torch.equal(sig1, sig2)
+    assert torch.equal(g1[0], g2[0]) and torch.equal(g1[1], g2[1])
+
+
 def test_nonfinite_input_flags_units():
     w = _alloy32()
     w.tinv = w.tinv.copy()
