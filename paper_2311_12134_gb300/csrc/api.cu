@@ -11,6 +11,7 @@
 //                below 1e-10 of X (at most kIrMaxIter sweeps)
 //   k_write_tau  scatter X into tau[e][site]
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -1161,65 +1162,85 @@ static int check_conj_energies(const lsms_complex* z, int n_energy) {
   return LSMS_OK;
 }
 
-// Two halves of a chunk run on two streams: the caller's and a side stream
-// (one per host thread and device), forked and joined by events, which a
-// CUDA-graph capture records as edges.  The step is a chain of batched launches
-// whose latency-bound phases (panels, interchanges, solves) leave the GPU partly
-// idle; the other half's bandwidth- and compute-bound launches fill it.  The
-// halves hold whole atoms and disjoint workspace.  With the kernel timers on,
-// everything stays on the caller's stream so that each launch is timed alone.
-struct SideStream {
-  cudaStream_t s = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+// The parts of a chunk run on concurrent streams: the caller's and side streams
+// (per host thread and device), forked and joined by events, which a CUDA-graph
+// capture records as edges.  The step is a chain of batched launches whose
+// latency-bound phases (panels, interchanges, solves) leave the GPU partly idle;
+// the other parts' bandwidth- and compute-bound launches fill it.  Parts hold
+// whole atoms and disjoint workspace.  With the kernel timers on, everything
+// stays on the caller's stream so that each launch is timed alone.
+constexpr int kMaxParts = 4;
+struct SideStreams {
+  cudaStream_t s[kMaxParts - 1] = {};
+  cudaEvent_t fork = nullptr, join[kMaxParts - 1] = {};
 };
 
-static int side_stream(SideStream** out) {
-  static thread_local SideStream side[64];  // per host thread: a stream is captured into one graph at a time
+// Number of concurrent parts per chunk (environment LSMS_STREAMS, 1..4; default 4).
+static int stream_parts() {
+  static const int parts = [] {
+    const char* e = std::getenv("LSMS_STREAMS");
+    const int v = e ? std::atoi(e) : 4;
+    return std::min(std::max(v, 1), kMaxParts);
+  }();
+  return parts;
+}
+
+static int side_streams(SideStreams** out) {
+  static thread_local SideStreams side[64];  // per host thread: a stream is captured into one graph at a time
   int dev = 0;
   LSMS_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return fail(LSMS_ERR_CUDA, "device index %d unsupported", dev);
-  SideStream& ss = side[dev];
-  if (!ss.s) {
-    LSMS_CUDA_TRY(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
+  SideStreams& ss = side[dev];
+  if (!ss.fork) {
+    for (int i = 0; i < kMaxParts - 1; ++i) {
+      LSMS_CUDA_TRY(cudaStreamCreateWithFlags(&ss.s[i], cudaStreamNonBlocking));
+      LSMS_CUDA_TRY(cudaEventCreateWithFlags(&ss.join[i], cudaEventDisableTiming));
+    }
     LSMS_CUDA_TRY(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming));
-    LSMS_CUDA_TRY(cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming));
   }
   *out = &ss;
   return LSMS_OK;
 }
 
-// Split ch at an atom boundary (units and factor units are atom-major, with the
-// same number per atom).  False if ch holds fewer than 2 atoms.
-static bool split_chunk(const Plan& p, const Chunk& ch, Chunk* a, Chunk* b) {
+// Split ch at atom boundaries into up to `want` parts (units and factor units
+// are atom-major, with the same number per atom).  Returns the number of parts.
+static int split_chunk(const Plan& p, const Chunk& ch, int want, Chunk* part) {
   const int n_at = (ch.f1 - ch.f0) / p.fac_per_atom;
-  if (n_at < 2) return false;
-  const int upa = (ch.u1 - ch.u0) / n_at;
-  const int h = n_at / 2;
-  *a = ch;
-  *b = ch;
-  a->u1 = b->u0 = ch.u0 + h * upa;
-  a->f1 = b->f0 = ch.f0 + h * p.fac_per_atom;
-  a->n_max = b->n_max = 0;
-  for (int u = a->u0; u < a->u1; ++u) a->n_max = std::max(a->n_max, p.units[u].n);
-  for (int u = b->u0; u < b->u1; ++u) b->n_max = std::max(b->n_max, p.units[u].n);
-  return true;
+  const int np = std::max(1, std::min(want, n_at));
+  const int upa = (ch.u1 - ch.u0) / std::max(n_at, 1);
+  for (int i = 0; i < np; ++i) {
+    const int a0 = (int)((int64_t)n_at * i / np), a1 = (int)((int64_t)n_at * (i + 1) / np);
+    Chunk& c = part[i];
+    c = ch;
+    c.u0 = ch.u0 + a0 * upa;
+    c.u1 = ch.u0 + a1 * upa;
+    c.f0 = ch.f0 + a0 * p.fac_per_atom;
+    c.f1 = ch.f0 + a1 * p.fac_per_atom;
+    c.n_max = 0;
+    for (int u = c.u0; u < c.u1; ++u) c.n_max = std::max(c.n_max, p.units[u].n);
+  }
+  if (np == 1) part[0] = ch;
+  return np;
 }
 
-// run(chunk, stream) for the two halves of ch on two streams, or for ch on c.st.
+// run(chunk, stream) for the parts of ch on concurrent streams, or for ch on c.st.
 template <typename F>
 static int run_split(const Call& c, const Plan& p, const Chunk& ch, F run) {
-  Chunk a, b;
-  SideStream* ss = nullptr;
-  if (g_timer_on.load(std::memory_order_relaxed) || !split_chunk(p, ch, &a, &b)) return run(ch, c.st);
-  int rc = side_stream(&ss);
+  Chunk part[kMaxParts];
+  const int np = g_timer_on.load(std::memory_order_relaxed) ? 1 : split_chunk(p, ch, stream_parts(), part);
+  if (np == 1) return run(ch, c.st);
+  SideStreams* ss = nullptr;
+  int rc = side_streams(&ss);
   if (rc) return rc;
   LSMS_CUDA_TRY(cudaEventRecord(ss->fork, c.st));
-  LSMS_CUDA_TRY(cudaStreamWaitEvent(ss->s, ss->fork, 0));
-  rc = run(a, c.st);
-  if (!rc) rc = run(b, ss->s);
+  for (int i = 1; i < np; ++i) LSMS_CUDA_TRY(cudaStreamWaitEvent(ss->s[i - 1], ss->fork, 0));
+  rc = run(part[0], c.st);
+  for (int i = 1; i < np && !rc; ++i) rc = run(part[i], ss->s[i - 1]);
   // joined even after an error: no work stays forked from the caller's stream
-  LSMS_CUDA_TRY(cudaEventRecord(ss->join, ss->s));
-  LSMS_CUDA_TRY(cudaStreamWaitEvent(c.st, ss->join, 0));
+  for (int i = 1; i < np; ++i) {
+    LSMS_CUDA_TRY(cudaEventRecord(ss->join[i - 1], ss->s[i - 1]));
+    LSMS_CUDA_TRY(cudaStreamWaitEvent(c.st, ss->join[i - 1], 0));
+  }
   return rc;
 }
 
