@@ -161,11 +161,12 @@ int lsms_gaunt_table(int lmax, double* C);
  *              bound without a further full sweep.  LSMS_UNIT_NOCONV after 6
  *              sweeps.
  * workspace    dev scratch of workspace_bytes (>= lsms_tau_workspace_bytes for
- *              one unit); the units are processed in chunks that fit it.  NULL
- *              = the library allocates (stream-ordered) and frees it.
- * lu_store     dev buffer of lu_store_bytes (lsms_lu_store_bytes) that keeps the
- *              factors and pivots (mixed form: also M as double-float pairs) for
- *              lsms_kubo_sigma_backward, or NULL.
+ *              one unit), 256-byte aligned (else LSMS_ERR_ARG); the units are
+ *              processed in chunks that fit it.  NULL = the library allocates
+ *              (stream-ordered) and frees it.
+ * lu_store     dev buffer of lu_store_bytes (lsms_lu_store_bytes), 256-byte
+ *              aligned, that keeps the factors and pivots (mixed form: also M as
+ *              double-float pairs) for lsms_kubo_sigma_backward, or NULL.
  * stream       cudaStream_t (NULL = legacy default stream).
  */
 int lsms_tau_workspace_bytes(const lsms_liz* liz, int lmax, int n_energy, int precision,
@@ -242,7 +243,8 @@ int lsms_kubo_sigma_noalloc(const lsms_liz* liz, int lmax, const int32_t* specie
  * unit_status  dev [n_energy][n_atoms] int32 output of the adjoint solves (as
  *              for lsms_tau_blocks), or NULL.
  * workspace    dev scratch of workspace_bytes (>= lsms_backward_workspace_bytes
- *              minimum), or NULL for a stream-ordered allocation.
+ *              minimum, 256-byte aligned, else LSMS_ERR_ARG), or NULL for a
+ *              stream-ordered allocation.
  * n_energy must be even (energies in (+, -) pairs per delta). */
 int lsms_backward_workspace_bytes(const lsms_liz* liz, int lmax, int n_energy, int precision,
                                   size_t* min_bytes, size_t* all_bytes);

@@ -1426,6 +1426,8 @@ extern "C" int lsms_tau_blocks(const lsms_liz* liz_c, int lmax, const int32_t* s
   size_t need_store = 0;
   if (lu_store) {
     if ((rc = lsms_lu_store_bytes(liz, lmax, n_energy, precision, &need_store))) return rc;
+    if (reinterpret_cast<uintptr_t>(lu_store) % kAlign)
+      return fail(LSMS_ERR_ARG, "lu_store must be %d-byte aligned", (int)kAlign);
     if (lu_store_bytes < need_store)
       return fail(LSMS_ERR_NOMEM, "lu_store holds %zu bytes, %zu needed", lu_store_bytes, need_store);
   }
@@ -1442,6 +1444,8 @@ extern "C" int lsms_tau_blocks(const lsms_liz* liz_c, int lmax, const int32_t* s
     own = true;
   } else if (ws_bytes < min_b) {
     return fail(LSMS_ERR_NOMEM, "workspace holds %zu bytes, at least %zu needed", ws_bytes, min_b);
+  } else if (reinterpret_cast<uintptr_t>(ws) % kAlign) {
+    return fail(LSMS_ERR_ARG, "workspace must be %d-byte aligned", (int)kAlign);
   }
   Plan* p = nullptr;
   if ((rc = get_plan(liz, c.dd, lmax, n_energy, base, c.K, false, store, conj, ws_bytes - h.total_fixed, &p))) {
@@ -1551,6 +1555,8 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
   if (store) {
     size_t need = 0;
     if ((rc = lsms_lu_store_bytes(liz, lmax, n_energy, precision, &need))) return rc;
+    if (reinterpret_cast<uintptr_t>(lu_store) % kAlign)
+      return fail(LSMS_ERR_ARG, "lu_store must be %d-byte aligned", (int)kAlign);
     if (lu_store_bytes < need) return fail(LSMS_ERR_NOMEM, "lu_store holds %zu bytes, %zu needed", lu_store_bytes, need);
   }
   const int n_delta = n_energy / 2;
@@ -1567,6 +1573,8 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
     own = true;
   } else if (ws_bytes < min_b) {
     return fail(LSMS_ERR_NOMEM, "workspace holds %zu bytes, at least %zu needed", ws_bytes, min_b);
+  } else if (reinterpret_cast<uintptr_t>(ws) % kAlign) {
+    return fail(LSMS_ERR_ARG, "workspace must be %d-byte aligned", (int)kAlign);
   }
   Plan* p = nullptr;
   if ((rc = get_plan(liz, c.dd, lmax, n_energy, base, 2 * c.K, true, store, conj, ws_bytes - h.total_fixed, &p))) {

@@ -149,59 +149,59 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const Unit* __restrict__ units,
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
 
-  // A^ row r: [L_re(r, 0..31) | L_im(r, 0..31)], hi and lo parts.  All global
-  // loads of a thread are issued before any shared-memory store so they overlap.
+  // Operand loads, all issued before any conversion so that they overlap:
+  // A^ row r = [L_re(r, 0..31) | L_im(r, 0..31)] (thread r: one coalesced 8-byte
+  // load per column of L21), and the 32 x 32 block U12, read as 64 contiguous
+  // bytes per thread (column c = tid / 4, rows j0 = 8 (tid % 4) .. j0 + 7).
+  const int r = tid;
+  const int row = row0 + r;
+  const bool a_ok = row < n;
+  float2 v[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) v[j] = a_ok ? __ldg(&A[(size_t)(k + j) * n + row]) : make_float2(0.f, 0.f);
+  const int bc = tid >> 2, j0 = (tid & 3) * 8;
+  const bool b_ok = col0 + bc < n;
+  float2 w[8];
   {
-    const int r = tid;
-    const int row = row0 + r;
-    const bool ok = row < n;
-    float2 v[NB];
+    const float2* src = A + (size_t)(col0 + bc) * n + k + j0;
+    if (!b_ok) {
 #pragma unroll
-    for (int j = 0; j < NB; ++j) v[j] = ok ? __ldg(&A[(size_t)(k + j) * n + row]) : make_float2(0.f, 0.f);
+      for (int q = 0; q < 8; ++q) w[q] = make_float2(0.f, 0.f);
+    } else if ((n & 1) == 0) {  // (col n + k + j0) even: 16-byte aligned
 #pragma unroll
-    for (int q = 0; q < NB / 4; ++q) {
-      float4 h, l;
-      h.x = tf32_hi(v[4 * q].x); h.y = tf32_hi(v[4 * q + 1].x); h.z = tf32_hi(v[4 * q + 2].x); h.w = tf32_hi(v[4 * q + 3].x);
-      l.x = v[4 * q].x - h.x; l.y = v[4 * q + 1].x - h.y; l.z = v[4 * q + 2].x - h.z; l.w = v[4 * q + 3].x - h.w;
-      *reinterpret_cast<float4*>(sAh + swz(r, 4 * q, CHUNK_A)) = h;
-      *reinterpret_cast<float4*>(sAl + swz(r, 4 * q, CHUNK_A)) = l;
-      h.x = tf32_hi(v[4 * q].y); h.y = tf32_hi(v[4 * q + 1].y); h.z = tf32_hi(v[4 * q + 2].y); h.w = tf32_hi(v[4 * q + 3].y);
-      l.x = v[4 * q].y - h.x; l.y = v[4 * q + 1].y - h.y; l.z = v[4 * q + 2].y - h.z; l.w = v[4 * q + 3].y - h.w;
-      *reinterpret_cast<float4*>(sAh + swz(r, NB + 4 * q, CHUNK_A)) = h;
-      *reinterpret_cast<float4*>(sAl + swz(r, NB + 4 * q, CHUNK_A)) = l;
+      for (int q = 0; q < 4; ++q) {
+        const float4 t4 = __ldg(reinterpret_cast<const float4*>(src) + q);
+        w[2 * q] = make_float2(t4.x, t4.y);
+        w[2 * q + 1] = make_float2(t4.z, t4.w);
+      }
+    } else {  // n odd (lmax = 0 or 2): 8-byte loads
+#pragma unroll
+      for (int q = 0; q < 8; ++q) w[q] = __ldg(src + q);
     }
   }
-  // B^ row nn (output column): nn < 32: [U_re(., c) | -U_im(., c)]; nn >= 32: [U_im(., c) | U_re(., c)].
-  // Threads 0..63 build one row each; the column's 32 entries are 256 contiguous bytes.
-  if (tid < TN) {
-    const int nn = tid;
-    const int c = nn & (TNC - 1), part = nn >> 5;
-    const int col = col0 + c;
-    const bool ok = col < n;
-    float2 w[NB];  // 8-byte loads: n may be odd when lmax = 0, so 16-byte alignment is not given
-    const float2* src = A + (size_t)col * n + k;
+  // hi (TF32-rounded) and lo parts of four values, stored at K offset kk of row rr
+  auto put = [](uint8_t* sh, uint8_t* sl, int rr, int kk, int chunk, float a0, float a1, float a2, float a3) {
+    float4 h, l;
+    h.x = tf32_hi(a0); h.y = tf32_hi(a1); h.z = tf32_hi(a2); h.w = tf32_hi(a3);
+    l.x = a0 - h.x; l.y = a1 - h.y; l.z = a2 - h.z; l.w = a3 - h.w;
+    *reinterpret_cast<float4*>(sh + swz(rr, kk, chunk)) = h;
+    *reinterpret_cast<float4*>(sl + swz(rr, kk, chunk)) = l;
+  };
 #pragma unroll
-    for (int q = 0; q < NB; ++q) w[q] = ok ? __ldg(src + q) : make_float2(0.f, 0.f);
+  for (int q = 0; q < NB / 4; ++q) {
+    put(sAh, sAl, r, 4 * q, CHUNK_A, v[4 * q].x, v[4 * q + 1].x, v[4 * q + 2].x, v[4 * q + 3].x);
+    put(sAh, sAl, r, NB + 4 * q, CHUNK_A, v[4 * q].y, v[4 * q + 1].y, v[4 * q + 2].y, v[4 * q + 3].y);
+  }
+  // B^ row bc (output column bc, real part):      [U_re(., bc) | -U_im(., bc)]
+  // B^ row bc + 32 (output column bc, imaginary): [U_im(., bc) |  U_re(., bc)]
 #pragma unroll
-    for (int q = 0; q < NB / 4; ++q) {
-      const float re[4] = {w[4 * q].x, w[4 * q + 1].x, w[4 * q + 2].x, w[4 * q + 3].x};
-      const float im[4] = {w[4 * q].y, w[4 * q + 1].y, w[4 * q + 2].y, w[4 * q + 3].y};
-      float first[4], second[4];
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        first[jj] = part == 0 ? re[jj] : im[jj];
-        second[jj] = part == 0 ? -im[jj] : re[jj];
-      }
-      float4 h, l;
-      h.x = tf32_hi(first[0]); h.y = tf32_hi(first[1]); h.z = tf32_hi(first[2]); h.w = tf32_hi(first[3]);
-      l.x = first[0] - h.x; l.y = first[1] - h.y; l.z = first[2] - h.z; l.w = first[3] - h.w;
-      *reinterpret_cast<float4*>(sBh + swz(nn, 4 * q, CHUNK_B)) = h;
-      *reinterpret_cast<float4*>(sBl + swz(nn, 4 * q, CHUNK_B)) = l;
-      h.x = tf32_hi(second[0]); h.y = tf32_hi(second[1]); h.z = tf32_hi(second[2]); h.w = tf32_hi(second[3]);
-      l.x = second[0] - h.x; l.y = second[1] - h.y; l.z = second[2] - h.z; l.w = second[3] - h.w;
-      *reinterpret_cast<float4*>(sBh + swz(nn, NB + 4 * q, CHUNK_B)) = h;
-      *reinterpret_cast<float4*>(sBl + swz(nn, NB + 4 * q, CHUNK_B)) = l;
-    }
+  for (int h = 0; h < 2; ++h) {
+    const float2* x = w + 4 * h;
+    const int kk = j0 + 4 * h;
+    put(sBh, sBl, bc, kk, CHUNK_B, x[0].x, x[1].x, x[2].x, x[3].x);
+    put(sBh, sBl, bc, NB + kk, CHUNK_B, -x[0].y, -x[1].y, -x[2].y, -x[3].y);
+    put(sBh, sBl, bc + TNC, kk, CHUNK_B, x[0].y, x[1].y, x[2].y, x[3].y);
+    put(sBh, sBl, bc + TNC, NB + kk, CHUNK_B, x[0].x, x[1].x, x[2].x, x[3].x);
   }
   // make the generic-proxy stores visible to the tensor core (async proxy)
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

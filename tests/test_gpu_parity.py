@@ -150,6 +150,26 @@ def test_chunking_is_invisible(alloy32):
     assert torch.equal(t_all, t_few)
 
 
+def test_misaligned_buffers_are_rejected(alloy32):
+    """Caller-provided workspace and lu_store must be 256-byte aligned (the
+    kernels read them with 16-byte vector loads); otherwise LSMS_ERR_ARG."""
+    w = alloy32[0]
+    B = _B()
+    lz = B.build_liz(w.pos, w.lattice, w.r_liz)
+    mn, _ = B.tau_workspace_bytes(lz, w.lmax, len(w.z), B.LSMS_MIXED)
+    ws = torch.empty(mn + 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.LsmsError) as e:
+        B.tau_blocks(lz, w.lmax, torch.as_tensor(w.species).cuda(), torch.as_tensor(w.tinv).cuda(), w.z, "mixed",
+                     workspace=ws[16:16 + mn])
+    assert e.value.code == B.LSMS_ERR_ARG and "aligned" in str(e.value)
+    need = B.lu_store_bytes(lz, w.lmax, len(w.z), B.LSMS_MIXED)
+    store = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.LsmsError) as e:
+        B.tau_blocks(lz, w.lmax, torch.as_tensor(w.species).cuda(), torch.as_tensor(w.tinv).cuda(), w.z, "mixed",
+                     lu_store=store[16:16 + need])
+    assert e.value.code == B.LSMS_ERR_ARG and "aligned" in str(e.value)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_two_stream_split_is_invisible(precision):
     """Each chunk runs as two halves on two streams; with the kernel timers on it
