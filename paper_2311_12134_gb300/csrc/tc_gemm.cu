@@ -114,18 +114,27 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 
 }  // namespace tc
 
-// grid (tiles_m_max * tiles_n_max, n_units), block 128, dynamic smem tc::SMEM_BYTES.
+// grid (row tiles, n_units), block 128, dynamic smem tc::SMEM_BYTES.  One CTA
+// per 128-row block of a unit's trailing matrix, walking the block's 32-column
+// tiles: L21's hi/lo split is staged once, and for tile j the CTA overlaps
+//   the tensor-core product of tile j (TMEM accumulator j % 2),
+//   the loads of U12 for tile j + 1 and of C for tile j (into registers),
+//   the epilogue of tile j - 1 (tcgen05.ld, C - product, store).
+// Every wait on the tensor core is bounded; on a timeout the unit is flagged
+// LSMS_UNIT_TIMEOUT, the walk stops, and the CTA waits (bounded) for its last
+// issued product before freeing the accumulators.
 __global__ void __launch_bounds__(128) k_gemm_tc(const Unit* __restrict__ units, char* fac_base, int k,
-                                                 int tiles_n_max, int32_t* stat) {
+                                                 int32_t* stat) {
   using namespace tc;
   const Unit u = units[blockIdx.y];
   const int n = u.n;
   const int t0 = k + NB;
   const int mt = n - t0;
   if (mt <= 0) return;
-  const int ti = blockIdx.x / tiles_n_max, tj = blockIdx.x % tiles_n_max;
-  if (ti * TM >= mt || tj * TNC >= mt) return;
-  const int row0 = t0 + ti * TM, col0 = t0 + tj * TNC;
+  const int ti = blockIdx.x;
+  if (ti * TM >= mt) return;
+  const int tn = (mt + TNC - 1) / TNC;
+  const int row0 = t0 + ti * TM;
   float2* A = reinterpret_cast<float2*>(fac_base + u.fac_off);
 
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -133,52 +142,23 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const Unit* __restrict__ units,
   uint8_t* sAl = smem + OP_A;
   uint8_t* sBh = smem + 2 * OP_A;
   uint8_t* sBl = smem + 2 * OP_A + OP_B;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * OP_A + 2 * OP_B);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * OP_A + 2 * OP_B);  // [2], one per accumulator
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 2 * OP_A + 2 * OP_B + 16);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // TMEM accumulator (warp 0 allocates; the address lands in shared memory)
+  // two TMEM accumulators of 64 columns (warp 0 allocates; the address lands in shared memory)
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(TMEM_COLS));
+                 "r"(2 * TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + 1)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
 
-  // Operand loads, all issued before any conversion so that they overlap:
-  // A^ row r = [L_re(r, 0..31) | L_im(r, 0..31)] (thread r: one coalesced 8-byte
-  // load per column of L21), and the 32 x 32 block U12, read as 64 contiguous
-  // bytes per thread (column c = tid / 4, rows j0 = 8 (tid % 4) .. j0 + 7).
-  const int r = tid;
-  const int row = row0 + r;
-  const bool a_ok = row < n;
-  float2 v[NB];
-#pragma unroll
-  for (int j = 0; j < NB; ++j) v[j] = a_ok ? __ldg(&A[(size_t)(k + j) * n + row]) : make_float2(0.f, 0.f);
-  const int bc = tid >> 2, j0 = (tid & 3) * 8;
-  const bool b_ok = col0 + bc < n;
-  float2 w[8];
-  {
-    const float2* src = A + (size_t)(col0 + bc) * n + k + j0;
-    if (!b_ok) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) w[q] = make_float2(0.f, 0.f);
-    } else if ((n & 1) == 0) {  // (col n + k + j0) even: 16-byte aligned
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float4 t4 = __ldg(reinterpret_cast<const float4*>(src) + q);
-        w[2 * q] = make_float2(t4.x, t4.y);
-        w[2 * q + 1] = make_float2(t4.z, t4.w);
-      }
-    } else {  // n odd (lmax = 0 or 2): 8-byte loads
-#pragma unroll
-      for (int q = 0; q < 8; ++q) w[q] = __ldg(src + q);
-    }
-  }
   // hi (TF32-rounded) and lo parts of four values, stored at K offset kk of row rr
   auto put = [](uint8_t* sh, uint8_t* sl, int rr, int kk, int chunk, float a0, float a1, float a2, float a3) {
     float4 h, l;
@@ -187,88 +167,149 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const Unit* __restrict__ units,
     *reinterpret_cast<float4*>(sh + swz(rr, kk, chunk)) = h;
     *reinterpret_cast<float4*>(sl + swz(rr, kk, chunk)) = l;
   };
+
+  // U12 columns of tile j: thread loads column bc = tid / 4, rows j0 .. j0 + 7
+  // (64 contiguous bytes; 16-byte loads when n is even)
+  const int bc = tid >> 2, j0 = (tid & 3) * 8;
+  float2 w[8];
+  auto load_b = [&](int j) {
+    const int col = t0 + j * TNC + bc;
+    const float2* src = A + (size_t)col * n + k + j0;
+    if (col >= n) {
 #pragma unroll
-  for (int q = 0; q < NB / 4; ++q) {
-    put(sAh, sAl, r, 4 * q, CHUNK_A, v[4 * q].x, v[4 * q + 1].x, v[4 * q + 2].x, v[4 * q + 3].x);
-    put(sAh, sAl, r, NB + 4 * q, CHUNK_A, v[4 * q].y, v[4 * q + 1].y, v[4 * q + 2].y, v[4 * q + 3].y);
-  }
+      for (int q = 0; q < 8; ++q) w[q] = make_float2(0.f, 0.f);
+    } else if ((n & 1) == 0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 t4 = __ldg(reinterpret_cast<const float4*>(src) + q);
+        w[2 * q] = make_float2(t4.x, t4.y);
+        w[2 * q + 1] = make_float2(t4.z, t4.w);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) w[q] = __ldg(src + q);
+    }
+  };
   // B^ row bc (output column bc, real part):      [U_re(., bc) | -U_im(., bc)]
   // B^ row bc + 32 (output column bc, imaginary): [U_im(., bc) |  U_re(., bc)]
+  auto store_b = [&]() {
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const float2* x = w + 4 * h;
-    const int kk = j0 + 4 * h;
-    put(sBh, sBl, bc, kk, CHUNK_B, x[0].x, x[1].x, x[2].x, x[3].x);
-    put(sBh, sBl, bc, NB + kk, CHUNK_B, -x[0].y, -x[1].y, -x[2].y, -x[3].y);
-    put(sBh, sBl, bc + TNC, kk, CHUNK_B, x[0].y, x[1].y, x[2].y, x[3].y);
-    put(sBh, sBl, bc + TNC, NB + kk, CHUNK_B, x[0].x, x[1].x, x[2].x, x[3].x);
-  }
-  // make the generic-proxy stores visible to the tensor core (async proxy)
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tslot;
-
-  if (tid == 0) {
-    const uint32_t idesc = make_idesc(TM, TN);
-    const uint32_t a_hi = smem_u32(sAh), a_lo = smem_u32(sAl), b_hi = smem_u32(sBh), b_lo = smem_u32(sBl);
-    uint32_t acc = 0;
-    // hi*hi, hi*lo, lo*hi
-    for (int s = 0; s < 3; ++s) {
-      const uint32_t ab = (s == 2) ? a_lo : a_hi;
-      const uint32_t bb = (s == 1) ? b_lo : b_hi;
-#pragma unroll
-      for (int kc = 0; kc < 2; ++kc)
-#pragma unroll
-        for (int k4 = 0; k4 < 4; ++k4) {
-          const uint64_t da = make_desc(ab + kc * CHUNK_A + k4 * 32);
-          const uint64_t db = make_desc(bb + kc * CHUNK_B + k4 * 32);
-          mma_tf32(tmem, da, db, idesc, acc);
-          acc = 1;
-        }
+    for (int h = 0; h < 2; ++h) {
+      const float2* x = w + 4 * h;
+      const int kk = j0 + 4 * h;
+      put(sBh, sBl, bc, kk, CHUNK_B, x[0].x, x[1].x, x[2].x, x[3].x);
+      put(sBh, sBl, bc, NB + kk, CHUNK_B, -x[0].y, -x[1].y, -x[2].y, -x[3].y);
+      put(sBh, sBl, bc + TNC, kk, CHUNK_B, x[0].y, x[1].y, x[2].y, x[3].y);
+      put(sBh, sBl, bc + TNC, NB + kk, CHUNK_B, x[0].x, x[1].x, x[2].x, x[3].x);
     }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
-                 : "memory");
-  }
-  // C tile of this thread's row, fetched while the tensor core works
+  };
+  // C tile j, this thread's row (32 complex entries)
   const int crow = row0 + warp * 32 + lane;
   float2 cv[TNC];
+  auto load_c = [&](int j) {
+    const int c0 = t0 + j * TNC;
 #pragma unroll
-  for (int c = 0; c < TNC; ++c)
-    cv[c] = (crow < n && col0 + c < n) ? A[(size_t)(col0 + c) * n + crow] : make_float2(0.f, 0.f);
-  // bounded wait for the accumulator; the outcome is made CTA-uniform because
-  // tcgen05.ld below is a warp-collective instruction
-  bool ready = false;
-  for (long long it = 0; it < kWaitLimit; ++it) {
-    if (tc::mbar_try_wait(smem_u32(mbar), 0)) {
-      ready = true;
-      break;
+    for (int c = 0; c < TNC; ++c)
+      cv[c] = (crow < n && c0 + c < n) ? A[(size_t)(c0 + c) * n + crow] : make_float2(0.f, 0.f);
+  };
+
+  // A^ row r = [L_re(r, 0..31) | L_im(r, 0..31)]: thread r, one coalesced load per column
+  {
+    const int row = row0 + tid;
+    const bool ok = row < n;
+    float2 v[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) v[j] = ok ? __ldg(&A[(size_t)(k + j) * n + row]) : make_float2(0.f, 0.f);
+    load_b(0);
+#pragma unroll
+    for (int q = 0; q < NB / 4; ++q) {
+      put(sAh, sAl, tid, 4 * q, CHUNK_A, v[4 * q].x, v[4 * q + 1].x, v[4 * q + 2].x, v[4 * q + 3].x);
+      put(sAh, sAl, tid, NB + 4 * q, CHUNK_A, v[4 * q].y, v[4 * q + 1].y, v[4 * q + 2].y, v[4 * q + 3].y);
     }
   }
-  ready = __syncthreads_and(ready);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ready) {
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+
+  // bounded wait, CTA-uniform outcome (tcgen05.ld is warp-collective)
+  auto wait_mma = [&](int j) -> bool {
+    bool ok = false;
+    const uint32_t mb = smem_u32(mbar + (j & 1));
+    const uint32_t parity = (uint32_t)((j >> 1) & 1);
+    for (long long it = 0; it < kWaitLimit; ++it)
+      if (tc::mbar_try_wait(mb, parity)) {
+        ok = true;
+        break;
+      }
+    ok = __syncthreads_and(ok);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return ok;
+  };
+  auto epilogue = [&](int j, uint32_t tmem) {
+    const uint32_t lane_base = tmem + (uint32_t)((j & 1) * TMEM_COLS) + ((uint32_t)(warp * 32) << 16);
     float dre[32], dim[32];
-    tc::tmem_ld32(lane_base + 0, dre);     // columns 0..31: real parts
-    tc::tmem_ld32(lane_base + 32, dim);    // columns 32..63: imaginary parts
+    tc::tmem_ld32(lane_base + 0, dre);   // columns 0..31: real parts
+    tc::tmem_ld32(lane_base + 32, dim);  // columns 32..63: imaginary parts
+    const int c0 = t0 + j * TNC;
     if (crow < n) {
 #pragma unroll
       for (int c = 0; c < TNC; ++c)
-        if (col0 + c < n) A[(size_t)(col0 + c) * n + crow] = make_float2(cv[c].x - dre[c], cv[c].y - dim[c]);
+        if (c0 + c < n) A[(size_t)(c0 + c) * n + crow] = make_float2(cv[c].x - dre[c], cv[c].y - dim[c]);
     }
-  } else if (tid == 0) {
-    atomicOr(&stat[u.stat_off], LSMS_UNIT_TIMEOUT);
-    // give the tensor core a second bounded window before the accumulator is freed
-    for (long long it = 0; it < kWaitLimit; ++it)
-      if (tc::mbar_try_wait(smem_u32(mbar), 0)) break;
+  };
+
+  uint32_t tmem = 0;
+  int issued = -1;  // last tile whose product was issued
+  bool ok = true;
+  for (int j = 0; j < tn; ++j) {
+    if (j > 0 && !(ok = wait_mma(j - 1))) break;  // product j - 1 done: B stage free, accumulator ready
+    store_b();
+    // make the generic-proxy stores visible to the tensor core (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tmem = *tslot;
+    if (tid == 0) {
+      const uint32_t idesc = make_idesc(TM, TN);
+      const uint32_t d = tmem + (uint32_t)((j & 1) * TMEM_COLS);
+      const uint32_t a_hi = smem_u32(sAh), a_lo = smem_u32(sAl), b_hi = smem_u32(sBh), b_lo = smem_u32(sBl);
+      uint32_t acc = 0;
+      // hi*hi, hi*lo, lo*hi
+      for (int s = 0; s < 3; ++s) {
+        const uint32_t ab = (s == 2) ? a_lo : a_hi;
+        const uint32_t bb = (s == 1) ? b_lo : b_hi;
+#pragma unroll
+        for (int kc = 0; kc < 2; ++kc)
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4) {
+            mma_tf32(d, make_desc(ab + kc * CHUNK_A + k4 * 32), make_desc(bb + kc * CHUNK_B + k4 * 32), idesc, acc);
+            acc = 1;
+          }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(mbar + (j & 1)))
+                   : "memory");
+    }
+    issued = j;
+    if (j + 1 < tn) load_b(j + 1);
+    if (j > 0) epilogue(j - 1, tmem);
+    load_c(j);
+  }
+  if (ok && issued >= 0) {
+    if ((ok = wait_mma(issued))) epilogue(issued, tmem);
+  }
+  if (!ok) {
+    if (tid == 0) {
+      atomicOr(&stat[u.stat_off], LSMS_UNIT_TIMEOUT);
+      // give the tensor core a second bounded window before the accumulators are freed
+      const uint32_t mb = smem_u32(mbar + (issued & 1));
+      for (long long it = 0; it < kWaitLimit; ++it)
+        if (tc::mbar_try_wait(mb, (uint32_t)((issued >> 1) & 1))) break;
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(2 * TMEM_COLS));
   }
 }
 
@@ -281,8 +322,8 @@ int gemm_tc_chunk(const Unit* d_units, int n_units, int n_max, int k, char* fac_
   }
   const int mt = n_max - k - tc::NB;
   if (mt <= 0) return LSMS_OK;
-  const int tm = (mt + tc::TM - 1) / tc::TM, tn = (mt + tc::TNC - 1) / tc::TNC;
-  LSMS_LAUNCH(k_gemm_tc, dim3(tm * tn, n_units), dim3(128), tc::SMEM_BYTES, st, d_units, fac_base, k, tn, stat);
+  const int tm = (mt + tc::TM - 1) / tc::TM;
+  LSMS_LAUNCH(k_gemm_tc, dim3(tm, n_units), dim3(128), tc::SMEM_BYTES, st, d_units, fac_base, k, stat);
   return LSMS_OK;
 }
 
