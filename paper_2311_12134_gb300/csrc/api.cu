@@ -179,7 +179,7 @@ static UnitBytes unit_bytes(int n, int precision, int nrhs, bool backward) {
   const size_t nn = (size_t)n * n;
   ub.fac = align_up(nn * (precision == LSMS_FP64 ? 16 : 8));
   ub.piv = align_up((size_t)n * 4);  // pivots (row interchanged with row i at step i)
-  ub.m64 = precision == LSMS_FP64 ? 0 : align_up(nn * 16);
+  ub.m64 = precision == LSMS_FP64 ? 0 : (size_t)(diag_inv_rel_off(n) + diag_inv_bytes(n));  // + diagonal-block inverses
   ub.x = align_up((size_t)n * nrhs * 16);
   ub.b = backward ? align_up((size_t)n * nrhs * 16) : 0;
   // complex64 corrections; the convergence probe uses the first kProbe columns

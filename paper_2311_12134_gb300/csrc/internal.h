@@ -23,6 +23,20 @@ constexpr int kMaxK3 = (kMaxL3 + 1) * (kMaxL3 + 1);
 int fail(int code, const char* fmt, ...);
 void clear_error();
 
+// Mixed form: the region at m64_off holds the double-float copy of M (n x n
+// float4) and, after it, the inverses of the 32 x 32 diagonal blocks of L and U
+// (complex64, column-major, block b at 2 b 1024 entries: L^-1 then U^-1).
+#ifdef __CUDACC__
+#define LSMS_HD __host__ __device__
+#else
+#define LSMS_HD
+#endif
+constexpr int kDiagNB = 32;
+LSMS_HD inline int64_t diag_inv_rel_off(int n) { return ((int64_t)n * n * 16 + 255) / 256 * 256; }
+LSMS_HD inline int64_t diag_inv_bytes(int n) {
+  return ((int64_t)((n + kDiagNB - 1) / kDiagNB) * 2 * kDiagNB * kDiagNB * 8 + 255) / 256 * 256;
+}
+
 // One (atom, energy) LIZ problem inside a chunk of the batched solve.
 struct Unit {
   int32_t atom;      // centre atom m
@@ -31,7 +45,7 @@ struct Unit {
   int32_t S;         // LIZ size S_m
   int64_t site_off;  // first site of LIZ_m in the global site arrays
   int64_t fac_off;   // byte offset of the factor matrix (from fac base)
-  int64_t m64_off;   // byte offset of the double-float copy of M (mixed form), from fac base
+  int64_t m64_off;   // byte offset of the double-float copy of M and the diagonal-block inverses (mixed form)
   int64_t piv_off;   // byte offset of the pivots (from fac base)
   int64_t x_off;     // byte offset of the n x RHS complex128 solution block (workspace)
   int64_t r_off;     // byte offset of the n x RHS complex128 residual block (workspace)

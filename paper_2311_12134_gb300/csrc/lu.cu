@@ -316,6 +316,42 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_smem(const Unit* __rest
 // column.  Columns left of the panel keep their row order (L is stored as
 // computed, LINPACK style): the forward solve applies each panel's
 // interchanges to the right-hand sides before that panel's columns of L are used.
+// The 32 interchanges of panel k (row k + j with row piv[k + j], j = 0..nbp-1,
+// applied in order) composed into one gather, by one warp: panel row k + i takes
+// the value of row src[i]; the distinct rows below the panel that the
+// interchanges reach, tgt[q] (q < *nt), take the value of row tgt_src[q] (always
+// a panel row).  Read every source before writing any target.
+__device__ __noinline__ void compose_panel_swaps(const int32_t* piv, int k, int nbp, int lane, int* step,
+                                                    int* tgt, int* src, int* tgt_src, int* nt) {
+  constexpr int NB = 32;
+  const int p = lane < nbp ? piv[k + lane] : k + lane;
+  const bool out = p >= k + NB;
+  // distinct rows below the panel: each gets a slot 32 + t, t = rank of its first occurrence
+  const unsigned same = __match_any_sync(0xffffffffu, out ? p : -1 - lane);
+  const int first = __ffs(same) - 1;
+  const unsigned firsts = __ballot_sync(0xffffffffu, out && first == lane);
+  const int t = __popc(firsts & ((1u << first) - 1u));
+  step[lane] = p == k + lane ? -1 : (out ? NB + t : p - k);  // slot exchanged with slot lane
+  if (out && first == lane) tgt[t] = p;
+  const int n_tgt = __popc(firsts);
+  if (lane == 0) *nt = n_tgt;
+  __syncwarp();
+  // the slot whose starting value ends in slot s: the interchanges undone in reverse order
+  auto origin = [&](int s) {
+    for (int j = NB - 1; j >= 0; --j) {
+      const int o = step[j];
+      if (o < 0) continue;
+      if (s == j) s = o;
+      else if (s == o) s = j;
+    }
+    return s;
+  };
+  auto row_of = [&](int s) { return s < NB ? k + s : tgt[s - NB]; };
+  src[lane] = row_of(origin(lane));
+  if (lane < n_tgt) tgt_src[lane] = row_of(origin(NB + lane));
+  __syncwarp();
+}
+
 constexpr int kSwapCols = 256;  // columns per CTA of k_swap_trsm
 
 template <typename R, int NB>
@@ -339,34 +375,7 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ unit
     const int i = idx % NB, j = idx / NB;
     sL[i][j] = A[(size_t)(k + j) * n + k + i];
   }
-  if (tid < 32) {
-    const int lane = tid;
-    const int p = piv[k + lane];
-    const bool out = p >= k + NB;
-    // distinct rows below the panel: each gets a slot 32 + t, t = rank of its first occurrence
-    const unsigned same = __match_any_sync(0xffffffffu, out ? p : -1 - lane);
-    const int first = __ffs(same) - 1;
-    const unsigned firsts = __ballot_sync(0xffffffffu, out && first == lane);
-    const int t = __popc(firsts & ((1u << first) - 1u));
-    sStep[lane] = p == k + lane ? -1 : (out ? NB + t : p - k);
-    if (out && first == lane) sTgtRow[t] = p;
-    if (lane == 0) sNt = __popc(firsts);
-    __syncwarp();
-    if (lane == 0) {
-      int cur[2 * NB];  // slot s now holds the value that started in slot cur[s]
-      for (int s = 0; s < 2 * NB; ++s) cur[s] = s;
-      for (int j = 0; j < NB; ++j) {
-        const int o = sStep[j];
-        if (o < 0) continue;
-        const int tmp = cur[j];
-        cur[j] = cur[o];
-        cur[o] = tmp;
-      }
-      auto row_of = [&](int s) { return s < NB ? k + s : sTgtRow[s - NB]; };
-      for (int i = 0; i < NB; ++i) sSrcRow[i] = row_of(cur[i]);
-      for (int q = 0; q < sNt; ++q) sTgtSrc[q] = row_of(cur[NB + q]);
-    }
-  }
+  if (tid < 32) compose_panel_swaps(piv, k, NB, tid, sStep, sTgtRow, sSrcRow, sTgtSrc, &sNt);
   __syncthreads();
   const int c = c0 + tid;
   if (c >= n) return;
@@ -623,47 +632,111 @@ __device__ __forceinline__ void update_rows_c64(const float2* __restrict__ A, fl
   }
 }
 
+// Inverses of the 32 x 32 diagonal blocks of the complex64 factors, L_bb (unit
+// lower) and U_bb (upper), stored after the double-float copy of M for the
+// solves.  grid (ceil(n_max / 32), n_units), block 64: warp 0 inverts L_bb,
+// warp 1 U_bb, lane j forming column j by substitution; a partial last block is
+// padded with the identity.
+__global__ void __launch_bounds__(64) k_diag_inv(const Unit* __restrict__ units, char* fac_base) {
+  constexpr int NB = kDiagNB;
+  const Unit u = units[blockIdx.y];
+  const int n = u.n, k = blockIdx.x * NB;
+  if (k >= n) return;
+  const int nbp = min(NB, n - k);
+  const float2* A = reinterpret_cast<const float2*>(fac_base + u.fac_off);
+  float2* D = reinterpret_cast<float2*>(fac_base + u.m64_off + diag_inv_rel_off(n)) + (size_t)blockIdx.x * 2 * NB * NB;
+  __shared__ float2 sB[NB][NB + 1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int idx = tid; idx < NB * NB; idx += 64) {
+    const int i = idx % NB, j = idx / NB;
+    sB[i][j] = (i < nbp && j < nbp) ? A[(size_t)(k + j) * n + k + i] : make_float2(i == j ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  float2 y[NB];
+  if (warp == 0) {  // L y = e_lane, L unit lower
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      float2 a = make_float2(i == lane ? 1.f : 0.f, 0.f);
+#pragma unroll
+      for (int m = 0; m < i; ++m) a = cfms(sB[i][m], y[m], a);
+      y[i] = a;
+    }
+  } else {  // U y = e_lane, U upper
+#pragma unroll
+    for (int i = NB - 1; i >= 0; --i) {
+      float2 a = make_float2(i == lane ? 1.f : 0.f, 0.f);
+#pragma unroll
+      for (int m = i + 1; m < NB; ++m) a = cfms(sB[i][m], y[m], a);
+      y[i] = cmul(a, crcp(sB[i][i]));
+    }
+  }
+  float2* out = D + (size_t)warp * NB * NB + (size_t)lane * NB;  // column lane
+#pragma unroll
+  for (int i = 0; i < NB; ++i) out[i] = y[i];
+}
+
 // One CTA of kSolveThreads threads per unit (several units resident per SM, so
-// one unit's serial triangle phases overlap the others' row updates): L y = P b
-// (unit lower, each panel's swaps applied just before its block), then U x = y
-// on the n x nrhs column-major block X.  The 32 x 32
-// triangles are solved by warps taking columns in turn (lane = row, values
-// passed by shuffles, reciprocals of U's diagonal formed before the sweep).
+// one unit's block phases overlap the others' row updates): L y = P b (unit
+// lower, each panel's interchanges applied just before its block, LINPACK
+// order), then U x = y, on the n x nrhs column-major block X.  Each 32-row block
+// step gathers its rows (the panel's interchanges composed once into a gather),
+// multiplies them by the stored inverse of the diagonal block (all threads, no
+// serial chain), and updates the rows below (above, going back) with the block's
+// 32 columns of L (U).
 template <int NCOL>
 __global__ void __launch_bounds__(kSolveThreads, 1024 / kSolveThreads) k_solve_c64(const Unit* __restrict__ units, const char* fac_base,
                                                      char* ws, int which, int nrhs, const int32_t* done) {
   static_assert(NCOL >= 2 && NCOL % 2 == 0 && NCOL <= 32, "padded column count");
-  constexpr int NB = 32;
+  constexpr int NB = kDiagNB;
   const Unit u = units[blockIdx.x];
   if (done && done[u.stat_off]) return;
   const int n = u.n;
   const float2* A = reinterpret_cast<const float2*>(fac_base + u.fac_off);
+  const float2* D = reinterpret_cast<const float2*>(fac_base + u.m64_off + diag_inv_rel_off(n));
   float2* X = reinterpret_cast<float2*>(ws + (which == RHS_X ? u.x_off : u.x32_off));
   const int32_t* piv = reinterpret_cast<const int32_t*>(fac_base + u.piv_off);
-  __shared__ float2 sT[NB][NB + 1];
-  __shared__ __align__(16) float2 sX[NB][NCOL];
-  __shared__ int sp[NB];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ float2 sT[NB][NB + 1];                 // inverse of the diagonal block
+  __shared__ __align__(16) float2 sX[NB][NCOL];     // the block's solved rows
+  __shared__ float2 sIn[NB][NCOL + 1];              // the block's rows before the inverse
+  __shared__ float2 sTv[NB][NCOL + 1];              // new values of the rows below reached by interchanges
+  __shared__ int sStep[NB], sTgt[NB], sSrc[NB], sTgtSrc[NB], sNt;
+  const int tid = threadIdx.x;
+  // y = T^-1 (block rows) for every (row, column) pair of the block
+  auto apply_inverse = [&](int k, int nbp) {
+#pragma unroll 1
+    for (int idx = tid; idx < NB * NCOL; idx += kSolveThreads) {
+      const int i = idx % NB, c = idx / NB;
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < NB; j += 2) {
+        a0 = cfma(sT[i][j], sIn[j][c], a0);
+        a1 = cfma(sT[i][j + 1], sIn[j + 1][c], a1);
+      }
+      const float2 y = make_float2(a0.x + a1.x, a0.y + a1.y);
+      sX[i][c] = y;
+      if (i < nbp && c < nrhs) X[(size_t)c * n + k + i] = y;
+    }
+  };
   // forward
   for (int k = 0; k < n; k += NB) {
     const int nbp = min(NB, n - k);
-    for (int idx = tid; idx < NB * NB; idx += kSolveThreads) {
-      const int i = idx % NB, j = idx / NB;
-      sT[i][j] = (i < nbp && j < nbp) ? A[(size_t)(k + j) * n + k + i] : make_float2(0.f, 0.f);
-    }
-    if (tid < NB) sp[tid] = tid < nbp ? piv[k + tid] : k + tid;
+    const float2* Dk = D + (size_t)(k / NB) * 2 * NB * NB;  // L^-1 block
+    for (int idx = tid; idx < NB * NB; idx += kSolveThreads) sT[idx % NB][idx / NB] = Dk[idx];
+    if (tid < 32) compose_panel_swaps(piv, k, nbp, tid, sStep, sTgt, sSrc, sTgtSrc, &sNt);
     __syncthreads();
-    for (int col = warp; col < NCOL; col += kSolveThreads / 32) {
-      const bool live = col < nrhs && lane < nbp;
-      float2 x = live ? X[(size_t)col * n + k + lane] : make_float2(0.f, 0.f);
-      if (col < nrhs) x = panel_swaps(x, X + (size_t)col * n, sp, k, lane);
-      for (int j = 0; j < nbp - 1; ++j) {
-        const float2 xj = shfl2(x, j);
-        if (lane > j) x = cfms(sT[lane][j], xj, x);
-      }
-      if (live) X[(size_t)col * n + k + lane] = x;
-      sX[lane][col] = x;
+    const int nt = sNt;
+    for (int idx = tid; idx < NB * NCOL; idx += kSolveThreads) {
+      const int i = idx % NB, c = idx / NB;
+      const bool live = c < nrhs;
+      sIn[i][c] = (live && i < nbp) ? X[(size_t)c * n + sSrc[i]] : make_float2(0.f, 0.f);
+      if (live && i < nt) sTv[i][c] = X[(size_t)c * n + sTgtSrc[i]];
     }
+    __syncthreads();
+    for (int idx = tid; idx < NB * NCOL; idx += kSolveThreads) {
+      const int q = idx % NB, c = idx / NB;
+      if (c < nrhs && q < nt) X[(size_t)c * n + sTgt[q]] = sTv[q][c];
+    }
+    apply_inverse(k, nbp);
     __syncthreads();
     update_rows_c64<NCOL>(A, X, sX, n, k, nbp, k + nbp, n, nrhs, tid);
     __syncthreads();
@@ -672,23 +745,14 @@ __global__ void __launch_bounds__(kSolveThreads, 1024 / kSolveThreads) k_solve_c
   const int last = ((n - 1) / NB) * NB;
   for (int k = last; k >= 0; k -= NB) {
     const int nbp = min(NB, n - k);
-    for (int idx = tid; idx < NB * NB; idx += kSolveThreads) {
-      const int i = idx % NB, j = idx / NB;
-      sT[i][j] = (i < nbp && j < nbp) ? A[(size_t)(k + j) * n + k + i] : make_float2(i == j ? 1.f : 0.f, 0.f);
+    const float2* Dk = D + (size_t)(k / NB) * 2 * NB * NB + NB * NB;  // U^-1 block
+    for (int idx = tid; idx < NB * NB; idx += kSolveThreads) sT[idx % NB][idx / NB] = Dk[idx];
+    for (int idx = tid; idx < NB * NCOL; idx += kSolveThreads) {
+      const int i = idx % NB, c = idx / NB;
+      sIn[i][c] = (c < nrhs && i < nbp) ? X[(size_t)c * n + k + i] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    for (int col = warp; col < NCOL; col += kSolveThreads / 32) {
-      const bool live = col < nrhs && lane < nbp;
-      const float2 dinv = crcp(sT[lane][lane]);
-      float2 x = live ? X[(size_t)col * n + k + lane] : make_float2(0.f, 0.f);
-      for (int j = nbp - 1; j >= 0; --j) {
-        if (lane == j) x = cmul(x, dinv);
-        const float2 xj = shfl2(x, j);
-        if (lane < j) x = cfms(sT[lane][j], xj, x);
-      }
-      if (live) X[(size_t)col * n + k + lane] = x;
-      sX[lane][col] = x;
-    }
+    apply_inverse(k, nbp);
     __syncthreads();
     update_rows_c64<NCOL>(A, X, sX, n, k, nbp, 0, k, nrhs, tid);
     __syncthreads();
@@ -730,6 +794,9 @@ int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
       LSMS_LAUNCH((k_gemm<R, NB>), dim3(tiles * tiles, n_units), dim3(256), 0, st, d_units, fac_base, k, tiles);
     }
   }
+  // complex64: inverses of the diagonal blocks for the solves
+  if constexpr (std::is_same<R, float>::value)
+    LSMS_LAUNCH(k_diag_inv, dim3((n_max + kDiagNB - 1) / kDiagNB, n_units), dim3(64), 0, st, d_units, fac_base);
   return LSMS_OK;
 }
 
