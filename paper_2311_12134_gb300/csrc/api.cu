@@ -689,7 +689,9 @@ __global__ void k_widen(const Unit* __restrict__ units, char* ws, int nrhs) {
 // n_units), block 256: 64 rows x NRHS columns, 4 column groups of CPG = NRHS / 4
 // columns per thread.  The X tile is staged in shared memory as the two pairs
 // each product needs, (x.re, x.im) and (-x.im, x.re), high and low parts.
-template <int NRHS>
+// XLO = false: X is the widened complex64 first solution (its low parts are
+// zero), so the products M.hi X.lo are left out.
+template <int NRHS, bool XLO>
 __global__ void __launch_bounds__(256, 3) k_residual(const Unit* __restrict__ units, const char* fac_base, char* ws,
                                                      int K, bool explicit_b, const int32_t* __restrict__ done) {
   constexpr int CPG = (NRHS + 3) / 4;
@@ -717,8 +719,8 @@ __global__ void __launch_bounds__(256, 3) k_residual(const Unit* __restrict__ un
 #pragma unroll
     for (int c = 0; c < CPG; ++c) {
       const float4 P = sP[jj][cg * CPG + c], Q = sQ[jj][cg * CPG + c];
-      df2_mac(s[c], t[c], mrh, mrl, make_float2(P.x, P.y), make_float2(P.z, P.w));
-      df2_mac(s[c], t[c], mih, mil, make_float2(Q.x, Q.y), make_float2(Q.z, Q.w));
+      df2_mac<XLO>(s[c], t[c], mrh, mrl, make_float2(P.x, P.y), make_float2(P.z, P.w));
+      df2_mac<XLO>(s[c], t[c], mih, mil, make_float2(Q.x, Q.y), make_float2(Q.z, Q.w));
     }
   };
   for (int j0 = 0; j0 < n; j0 += 32) {
@@ -1134,8 +1136,11 @@ static int solve_refine(const Call& c, const Plan& p, const Chunk& ch, const cha
   for (int it = 0; it < kIrMaxIter; ++it) {
     const dim3 gr((ch.n_max + 63) / 64, nu);
     switch (nrhs) {  // K or 2K for lmax = 0..3
-#define LSMS_RESID(NR) \
-  case NR: LSMS_LAUNCH(k_residual<NR>, gr, dim3(256), 0, c.st, du, fac_base, ws, c.K, explicit_b, done); break;
+#define LSMS_RESID(NR)                                                                                 \
+  case NR:                                                                                             \
+    if (it == 0) LSMS_LAUNCH((k_residual<NR, false>), gr, dim3(256), 0, c.st, du, fac_base, ws, c.K, explicit_b, done); \
+    else LSMS_LAUNCH((k_residual<NR, true>), gr, dim3(256), 0, c.st, du, fac_base, ws, c.K, explicit_b, done);          \
+    break;
       LSMS_RESID(1) LSMS_RESID(2) LSMS_RESID(4) LSMS_RESID(8) LSMS_RESID(9) LSMS_RESID(18) LSMS_RESID(16)
       LSMS_RESID(32)
 #undef LSMS_RESID

@@ -153,11 +153,13 @@ __device__ __forceinline__ void dfc_mac(DfAcc& acc, float4 a, float4 b) {
 __device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
 
 // (s, t) += (ah + al)(bh + bl) lane-wise: exact ah bh (two-product), the cross
-// terms, and the two-sum's rounding error into t.
+// terms, and the two-sum's rounding error into t.  BLO = false: bl is zero (b is
+// a float) and its cross term is left out.
+template <bool BLO = true>
 __device__ __forceinline__ void df2_mac(float2& s, float2& t, float2 ah, float2 al, float2 bh, float2 bl) {
   const float2 p = __fmul2_rn(ah, bh);
   float2 e = __ffma2_rn(ah, bh, f2neg(p));
-  e = __ffma2_rn(ah, bl, e);
+  if constexpr (BLO) e = __ffma2_rn(ah, bl, e);
   e = __ffma2_rn(al, bh, e);
   const float2 a = __fadd2_rn(s, p);
   const float2 bb = __fadd2_rn(a, f2neg(s));
