@@ -156,9 +156,9 @@ int lsms_gaunt_table(int lmax, double* C);
  *              D = (LU)^-1 (B - M X) (residual in double-float, ~2^-48) to X and
  *              stops when ||D||_F <= 1e-10 ||X||_F; after each sweep a probe
  *              takes the same test on 2 random complex Gaussian combinations of the columns
- *              (y = X w: ||(LU)^-1 (B w - M y)|| <= 1e-10 ||y||) and stops
- *              there when both pass, so X carries the correction test's error
- *              bound without a further full sweep.  LSMS_UNIT_NOCONV after 6
+ *              (y_q = X w_q: sum_q ||(LU)^-1 (B w_q - M y_q)||^2 <= 1e-20
+ *              sum_q ||y_q||^2) and stops there when it passes, so X carries
+ *              the correction test's error bound without a further full sweep.  LSMS_UNIT_NOCONV after 6
  *              sweeps.
  * workspace    dev scratch of workspace_bytes (>= lsms_tau_workspace_bytes for
  *              one unit), 256-byte aligned (else LSMS_ERR_ARG); the units are

@@ -603,8 +603,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
               for (int t = t0; t < t1; ++t) {
                 const float2 c = s_coef2[t];
                 const float4 w = Vq[s_lpp[t]];
-                df_mac(acc.sr, acc.tr, c.x, c.y, w.x, w.y);
-                df_mac(acc.si, acc.ti, c.x, c.y, w.z, w.w);
+                dfr_mac(acc, c, w);
               }
               v4 = df_value(acc);
             }
@@ -800,42 +799,54 @@ __global__ void __launch_bounds__(256) k_ir_update(const Unit* __restrict__ unit
   const double2* B = reinterpret_cast<const double2*>(ws + u.r_off);
   float4* Y = reinterpret_cast<float4*>(ws + u.p_off);  // y_q as (hi, lo) pairs
   double2* BW = reinterpret_cast<double2*>(Y + (size_t)kProbe * n);
-  __shared__ double2 sw[kProbe][32];
+  // probe weights rounded to complex64 (exact in both products below)
+  __shared__ float2 sw[kProbe][32];
   for (int idx = threadIdx.x; idx < kProbe * 32; idx += blockDim.x)
-    sw[idx / 32][idx % 32] = probe_weight(u.stat_off, sweep, idx / 32, idx % 32);
+    sw[idx / 32][idx % 32] = to32(probe_weight(u.stat_off, sweep, idx / 32, idx % 32));
   __syncthreads();
-  double dn = 0.0, xn = 0.0;
+  // the update in FP64 (X is the complex128 solution) and its double-float split;
+  // the norms in FP32 (a ratio test), y = X w in double-float on the FP32 pipes,
+  // (B w) in FP64
+  float dn = 0.f, xn = 0.f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double2 y[kProbe], bw[kProbe];
+    DfAcc y[kProbe];
+    double2 bw[kProbe];
 #pragma unroll
-    for (int q = 0; q < kProbe; ++q) y[q] = bw[q] = mk(0.0, 0.0);
+    for (int q = 0; q < kProbe; ++q) {
+      y[q] = df_zero();
+      bw[q] = mk(0.0, 0.0);
+    }
     for (int c = 0; c < nrhs; ++c) {
       const size_t idx = (size_t)c * n + i;
-      const double2 d = to64(D[idx]);
-      const double2 x = cadd(X[idx], d);
+      const float2 d32 = D[idx];
+      const double2 x = cadd(X[idx], to64(d32));
       X[idx] = x;
-      Xdf[idx] = df_split(x);  // split once here instead of in every residual CTA
-      dn += d.x * d.x + d.y * d.y;
-      xn += x.x * x.x + x.y * x.y;
-      const double2 b = explicit_b ? B[idx] : mk(0.0, 0.0);
+      const float4 xs = df_split(x);  // split once here instead of in every residual CTA
+      Xdf[idx] = xs;
+      dn = fmaf(d32.x, d32.x, fmaf(d32.y, d32.y, dn));
+      xn = fmaf(xs.x, xs.x, fmaf(xs.z, xs.z, xn));
 #pragma unroll
       for (int q = 0; q < kProbe; ++q) {
-        const double2 w = sw[q][c & 31];
-        y[q] = cfma(x, w, y[q]);
-        if (explicit_b) bw[q] = cfma(b, w, bw[q]);
+        const float2 w = sw[q][c & 31];
+        dfc_mac(y[q], xs, make_float4(w.x, 0.f, w.y, 0.f));
+      }
+      if (explicit_b) {
+        const double2 b = B[idx];
+#pragma unroll
+        for (int q = 0; q < kProbe; ++q) bw[q] = cfma(b, to64(sw[q][c & 31]), bw[q]);
       }
     }
 #pragma unroll
     for (int q = 0; q < kProbe; ++q) {
       // B = E0 (forward): (B w)_i = w_i for i < K
-      if (!explicit_b && i < K && i < nrhs) bw[q] = sw[q][i];
-      Y[(size_t)q * n + i] = df_split(y[q]);
+      if (!explicit_b && i < K && i < nrhs) bw[q] = to64(sw[q][i]);
+      Y[(size_t)q * n + i] = df_value(y[q]);
       BW[(size_t)q * n + i] = bw[q];
     }
   }
   __shared__ double s1[256], s2[256];
-  s1[threadIdx.x] = dn;
-  s2[threadIdx.x] = xn;
+  s1[threadIdx.x] = (double)dn;
+  s2[threadIdx.x] = (double)xn;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if (threadIdx.x < w) {
@@ -868,57 +879,58 @@ __global__ void __launch_bounds__(256, 3) k_probe_residual(const Unit* __restric
   const int n = u.n;
   const int row0 = blockIdx.x * 64;
   if (row0 >= n) return;
-  const float4* M = reinterpret_cast<const float4*>(fac_base + u.m64_off);
-  const float4* Y = reinterpret_cast<const float4*>(ws + u.p_off);  // y_q as (hi, lo) pairs
+  const float4* M = reinterpret_cast<const float4*>(fac_base + u.m64_off);  // (re.hi, im.hi, re.lo, im.lo)
+  const float4* Y = reinterpret_cast<const float4*>(ws + u.p_off);  // y_q as (re.hi, re.lo, im.hi, im.lo)
   const double2* BW = reinterpret_cast<const double2*>(Y + (size_t)kProbe * n);
   float2* X32 = reinterpret_cast<float2*>(ws + u.x32_off);
-  __shared__ float4 sY[128][kProbe];
+  // y staged as the pairs each product needs: (y.re, y.im) and (-y.im, y.re), hi and lo
+  __shared__ float4 sP[128][kProbe], sQ[128][kProbe];
   __shared__ float4 sPart[3][kProbe][64];
   const int tid = threadIdx.x;
   const int r = tid & 63, grp = tid >> 6;
   const int row = row0 + r;
   const bool live = row < n;
   const float4* Mrow = M + (live ? row : 0);
-  float sr[kProbe], tr[kProbe], si[kProbe], ti[kProbe];
+  float2 s2[kProbe], t2[kProbe];
 #pragma unroll
-  for (int q = 0; q < kProbe; ++q) sr[q] = tr[q] = si[q] = ti[q] = 0.f;
+  for (int q = 0; q < kProbe; ++q) s2[q] = t2[q] = make_float2(0.f, 0.f);
+  auto mac = [&](const float4 m, int jj) {
+    const float2 mrh = make_float2(m.x, m.x), mrl = make_float2(m.z, m.z);
+    const float2 mih = make_float2(m.y, m.y), mil = make_float2(m.w, m.w);
+#pragma unroll
+    for (int q = 0; q < kProbe; ++q) {
+      const float4 P = sP[jj][q], Q = sQ[jj][q];
+      df2_mac(s2[q], t2[q], mrh, mrl, make_float2(P.x, P.y), make_float2(P.z, P.w));
+      df2_mac(s2[q], t2[q], mih, mil, make_float2(Q.x, Q.y), make_float2(Q.z, Q.w));
+    }
+  };
   for (int j0 = 0; j0 < n; j0 += 128) {
     const int jn = min(128, n - j0);
     __syncthreads();
     for (int idx = tid; idx < 128 * kProbe; idx += 256) {
       const int jj = idx & 127, q = idx >> 7;
-      sY[jj][q] = jj < jn ? Y[(size_t)q * n + j0 + jj] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 v = jj < jn ? Y[(size_t)q * n + j0 + jj] : make_float4(0.f, 0.f, 0.f, 0.f);
+      sP[jj][q] = make_float4(v.x, v.z, v.y, v.w);
+      sQ[jj][q] = make_float4(-v.z, v.x, -v.w, v.y);
     }
     __syncthreads();
     if (live) {
       const int ja = grp * 32, jb = min(ja + 32, jn);
       if (jb - ja == 32) {
 #pragma unroll 4
-        for (int jj = ja; jj < ja + 32; ++jj) {
-          const float4 m = Mrow[(size_t)(j0 + jj) * n];
-#pragma unroll
-          for (int q = 0; q < kProbe; ++q) {
-            const float4 x = sY[jj][q];
-            df_mac(sr[q], tr[q], m.x, m.z, x.x, x.y);
-            df_mac(sr[q], tr[q], -m.y, -m.w, x.z, x.w);
-            df_mac(si[q], ti[q], m.x, m.z, x.z, x.w);
-            df_mac(si[q], ti[q], m.y, m.w, x.x, x.y);
-          }
-        }
+        for (int jj = ja; jj < ja + 32; ++jj) mac(Mrow[(size_t)(j0 + jj) * n], jj);
       } else {
-        for (int jj = ja; jj < jb; ++jj) {
-          const float4 m = Mrow[(size_t)(j0 + jj) * n];
-#pragma unroll
-          for (int q = 0; q < kProbe; ++q) {
-            const float4 x = sY[jj][q];
-            df_mac(sr[q], tr[q], m.x, m.z, x.x, x.y);
-            df_mac(sr[q], tr[q], -m.y, -m.w, x.z, x.w);
-            df_mac(si[q], ti[q], m.x, m.z, x.z, x.w);
-            df_mac(si[q], ti[q], m.y, m.w, x.x, x.y);
-          }
-        }
+        for (int jj = ja; jj < jb; ++jj) mac(Mrow[(size_t)(j0 + jj) * n], jj);
       }
     }
+  }
+  float sr[kProbe], tr[kProbe], si[kProbe], ti[kProbe];
+#pragma unroll
+  for (int q = 0; q < kProbe; ++q) {
+    sr[q] = s2[q].x;
+    si[q] = s2[q].y;
+    tr[q] = t2[q].x;
+    ti[q] = t2[q].y;
   }
   if (grp > 0) {
 #pragma unroll
@@ -945,10 +957,13 @@ __global__ void __launch_bounds__(256, 3) k_probe_residual(const Unit* __restric
 }
 
 // Convergence probe, test half: X32 columns q now hold the corrections d_q that
-// the next sweep would add to y_q = X w_q.  The unit is done when every
-// ||d_q|| <= tol ||y_q||: E||D w||^2 = 2 ||D||_F^2 and E||X w||^2 = 2 ||X||_F^2
-// for complex Gaussian w, so this is the sweep test of k_ir_update taken on
-// kProbe random combinations of the columns.  Adds 1 << 16 to the status word.
+// the next sweep would add to y_q = X w_q.  The unit is done when
+// sum_q ||d_q||^2 <= tol^2 sum_q ||y_q||^2: E||D w||^2 = 2 ||D||_F^2 and
+// E||X w||^2 = 2 ||X||_F^2 for complex Gaussian w, so this is the sweep test of
+// k_ir_update taken on kProbe random combinations of the columns, pooled (a
+// lower-variance estimate than requiring each probe to pass, with about the
+// same chance, ~2e-8, of passing a rank-one correction 100x above tol).  Adds
+// 1 << 16 to the status word.
 __global__ void __launch_bounds__(256) k_probe_check(const Unit* __restrict__ units, const char* ws, double tol,
                                                      int32_t* done, int32_t* stat) {
   const Unit u = units[blockIdx.x];
@@ -984,13 +999,13 @@ __global__ void __launch_bounds__(256) k_probe_check(const Unit* __restrict__ un
   }
   if (threadIdx.x == 0) {
     atomicAdd(&stat[u.stat_off], 1 << 16);
-    bool pass = true;
+    double a = 0.0, b = 0.0;
 #pragma unroll
     for (int q = 0; q < kProbe; ++q) {
-      const double a = s[2 * q][0], b = s[2 * q + 1][0];
-      if (!isfinite(a) || !isfinite(b) || a > tol * tol * b) pass = false;
+      a += s[2 * q][0];
+      b += s[2 * q + 1][0];
     }
-    if (pass) done[u.stat_off] = 1;
+    if (isfinite(a) && isfinite(b) && a <= tol * tol * b) done[u.stat_off] = 1;
   }
 }
 

@@ -132,20 +132,6 @@ __device__ __forceinline__ double2 df_join(float4 a) {
   return make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
 }
 
-// complex accumulator: re = sr + tr, im = si + ti
-struct DfAcc {
-  float sr, tr, si, ti;
-};
-__device__ __forceinline__ DfAcc df_zero() { return DfAcc{0.f, 0.f, 0.f, 0.f}; }
-
-// acc += a * b (complex, double-float)
-__device__ __forceinline__ void dfc_mac(DfAcc& acc, float4 a, float4 b) {
-  df_mac(acc.sr, acc.tr, a.x, a.y, b.x, b.y);
-  df_mac(acc.sr, acc.tr, -a.z, -a.w, b.z, b.w);
-  df_mac(acc.si, acc.ti, a.x, a.y, b.z, b.w);
-  df_mac(acc.si, acc.ti, a.z, a.w, b.x, b.y);
-}
-
 // Packed forms on float2 (the paired FP32 instructions of sm_100 and later: two
 // lanes of arithmetic per instruction).  A complex accumulator is s = (re, im)
 // high parts and t = (re, im) low parts; a complex product m x splits as
@@ -168,10 +154,31 @@ __device__ __forceinline__ void df2_mac(float2& s, float2& t, float2 ah, float2 
   s = a;
 }
 
+// complex accumulator: re = s.x + t.x, im = s.y + t.y
+struct DfAcc {
+  float2 s, t;
+};
+__device__ __forceinline__ DfAcc df_zero() { return DfAcc{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+
+// acc += a * b (complex, double-float; a, b as (re.hi, re.lo, im.hi, im.lo)).
+// Scalar instructions: in the 16 x 16 products that use it, pairing the operands
+// for the paired instructions cost more than it saved.
+__device__ __forceinline__ void dfc_mac(DfAcc& acc, float4 a, float4 b) {
+  df_mac(acc.s.x, acc.t.x, a.x, a.y, b.x, b.y);
+  df_mac(acc.s.x, acc.t.x, -a.z, -a.w, b.z, b.w);
+  df_mac(acc.s.y, acc.t.y, a.x, a.y, b.z, b.w);
+  df_mac(acc.s.y, acc.t.y, a.z, a.w, b.x, b.y);
+}
+
+// acc += c * w, c real (hi, lo), w complex (re.hi, re.lo, im.hi, im.lo)
+__device__ __forceinline__ void dfr_mac(DfAcc& acc, float2 c, float4 w) {
+  df2_mac(acc.s, acc.t, make_float2(c.x, c.x), make_float2(c.y, c.y), make_float2(w.x, w.z), make_float2(w.y, w.w));
+}
+
 // normalised (hi, lo) pairs of an accumulator
 __device__ __forceinline__ float4 df_value(const DfAcc& a) {
-  const float rh = a.sr + a.tr, ih = a.si + a.ti;
-  return make_float4(rh, a.tr - (rh - a.sr), ih, a.ti - (ih - a.si));
+  const float rh = a.s.x + a.t.x, ih = a.s.y + a.t.y;
+  return make_float4(rh, a.t.x - (rh - a.s.x), ih, a.t.y - (ih - a.s.y));
 }
 
 // Real double-float values (hi, lo) as float2, normalised (|lo| <= ulp(hi) / 2).

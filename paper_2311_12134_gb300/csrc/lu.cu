@@ -591,10 +591,27 @@ __device__ __forceinline__ void update_rows_c64(const float2* __restrict__ A, fl
   constexpr int NB = 32;
   const int rows = r1 - r0;
   if (rows <= 0) return;
-  for (int idx = tid; idx < rows * NG; idx += kSolveThreads) {
-    const int gi = idx / rows;
-    const int i = r0 + (idx - gi * rows);
+  // work item = (row, group of G columns); a warp takes 32 consecutive rows of one
+  // group and the NG groups of the same rows go to consecutive warps, so the
+  // factor's 32-row segments are fetched once and reused from L1 by the others
+  const int chunks = (rows + 31) / 32;
+  for (int idx = tid; idx < chunks * 32 * NG; idx += kSolveThreads) {
+    const int gi = (idx >> 5) % NG;
+    const int i = r0 + ((idx >> 5) / NG) * 32 + (idx & 31);
+    if (i >= r1) continue;
     const int g = gi * G;
+    // the factor entries of this thread's next item (read once from DRAM) are
+    // requested into L2 now, by the warps of the first column group only (with
+    // 32 columns the extra L2 traffic cost more than the latency it hid)
+    if constexpr (NCOL <= 16) {
+      const int nidx = idx + kSolveThreads;
+      const int ni = r0 + ((nidx >> 5) / NG) * 32 + (nidx & 31);
+      if (gi == 0 && ni < r1 && (nidx >> 5) % NG == 0) {
+        const float2* An = A + (size_t)k * n + ni;
+#pragma unroll 4
+        for (int j = 0; j < nbp; ++j) asm volatile("prefetch.global.L2 [%0];" ::"l"(An + (size_t)j * n));
+      }
+    }
     float2 acc[G];
 #pragma unroll
     for (int c = 0; c < G; ++c) acc[c] = (g + c < nrhs) ? X[(size_t)(g + c) * n + i] : make_float2(0.f, 0.f);
