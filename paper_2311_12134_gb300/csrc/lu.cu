@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(512, 2) k_solve(const Unit* __restrict__ units
 // factor, G/2 16-byte shared-memory loads of the solved block and 4 G FMAs.
 constexpr int kSolveThreads = 256;  // complex64 solve CTA
 
-template <int NCOL>
+template <int NCOL, int NT>
 __device__ __forceinline__ void update_rows_c64(const float2* __restrict__ A, float2* X, const float2 (*sX)[NCOL],
                                                 int n, int k, int nbp, int r0, int r1, int nrhs, int tid) {
   constexpr int G = NCOL < 8 ? NCOL : 8;
@@ -595,7 +595,7 @@ __device__ __forceinline__ void update_rows_c64(const float2* __restrict__ A, fl
   // group and the NG groups of the same rows go to consecutive warps, so the
   // factor's 32-row segments are fetched once and reused from L1 by the others
   const int chunks = (rows + 31) / 32;
-  for (int idx = tid; idx < chunks * 32 * NG; idx += kSolveThreads) {
+  for (int idx = tid; idx < chunks * 32 * NG; idx += NT) {
     const int gi = (idx >> 5) % NG;
     const int i = r0 + ((idx >> 5) / NG) * 32 + (idx & 31);
     if (i >= r1) continue;
@@ -604,7 +604,7 @@ __device__ __forceinline__ void update_rows_c64(const float2* __restrict__ A, fl
     // requested into L2 now, by the warps of the first column group only (with
     // 32 columns the extra L2 traffic cost more than the latency it hid)
     if constexpr (NCOL <= 16) {
-      const int nidx = idx + kSolveThreads;
+      const int nidx = idx + NT;
       const int ni = r0 + ((nidx >> 5) / NG) * 32 + (nidx & 31);
       if (gi == 0 && ni < r1 && (nidx >> 5) % NG == 0) {
         const float2* An = A + (size_t)k * n + ni;
@@ -700,17 +700,21 @@ __global__ void __launch_bounds__(64) k_diag_inv(const Unit* __restrict__ units,
 // multiplies them by the stored inverse of the diagonal block (all threads, no
 // serial chain), and updates the rows below (above, going back) with the block's
 // 32 columns of L (U).
-template <int NCOL>
-__global__ void __launch_bounds__(kSolveThreads, 1024 / kSolveThreads) k_solve_c64(const Unit* __restrict__ units, const char* fac_base,
+template <int NCOL, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_solve_c64(const Unit* __restrict__ units, const char* fac_base,
                                                      char* ws, int which, int nrhs, const int32_t* done) {
   static_assert(NCOL >= 2 && NCOL % 2 == 0 && NCOL <= 32, "padded column count");
   constexpr int NB = kDiagNB;
   const Unit u = units[blockIdx.x];
   if (done && done[u.stat_off]) return;
   const int n = u.n;
+  // columns [NCOL y, NCOL y + NCOL) of the right-hand sides (slice y = blockIdx.y)
+  const int c_off = blockIdx.y * NCOL;
+  nrhs = min(NCOL, nrhs - c_off);
+  if (nrhs <= 0) return;
   const float2* A = reinterpret_cast<const float2*>(fac_base + u.fac_off);
   const float2* D = reinterpret_cast<const float2*>(fac_base + u.m64_off + diag_inv_rel_off(n));
-  float2* X = reinterpret_cast<float2*>(ws + (which == RHS_X ? u.x_off : u.x32_off));
+  float2* X = reinterpret_cast<float2*>(ws + (which == RHS_X ? u.x_off : u.x32_off)) + (size_t)c_off * n;
   const int32_t* piv = reinterpret_cast<const int32_t*>(fac_base + u.piv_off);
   __shared__ float2 sT[NB][NB + 1];                 // inverse of the diagonal block
   __shared__ __align__(16) float2 sX[NB][NCOL];     // the block's solved rows
@@ -721,7 +725,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1024 / kSolveThreads) k_solve_c
   // y = T^-1 (block rows) for every (row, column) pair of the block
   auto apply_inverse = [&](int k, int nbp) {
 #pragma unroll 1
-    for (int idx = tid; idx < NB * NCOL; idx += kSolveThreads) {
+    for (int idx = tid; idx < NB * NCOL; idx += NT) {
       const int i = idx % NB, c = idx / NB;
       float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
@@ -738,24 +742,24 @@ __global__ void __launch_bounds__(kSolveThreads, 1024 / kSolveThreads) k_solve_c
   for (int k = 0; k < n; k += NB) {
     const int nbp = min(NB, n - k);
     const float2* Dk = D + (size_t)(k / NB) * 2 * NB * NB;  // L^-1 block
-    for (int idx = tid; idx < NB * NB; idx += kSolveThreads) sT[idx % NB][idx / NB] = Dk[idx];
+    for (int idx = tid; idx < NB * NB; idx += NT) sT[idx % NB][idx / NB] = Dk[idx];
     if (tid < 32) compose_panel_swaps(piv, k, nbp, tid, sStep, sTgt, sSrc, sTgtSrc, &sNt);
     __syncthreads();
     const int nt = sNt;
-    for (int idx = tid; idx < NB * NCOL; idx += kSolveThreads) {
+    for (int idx = tid; idx < NB * NCOL; idx += NT) {
       const int i = idx % NB, c = idx / NB;
       const bool live = c < nrhs;
       sIn[i][c] = (live && i < nbp) ? X[(size_t)c * n + sSrc[i]] : make_float2(0.f, 0.f);
       if (live && i < nt) sTv[i][c] = X[(size_t)c * n + sTgtSrc[i]];
     }
     __syncthreads();
-    for (int idx = tid; idx < NB * NCOL; idx += kSolveThreads) {
+    for (int idx = tid; idx < NB * NCOL; idx += NT) {
       const int q = idx % NB, c = idx / NB;
       if (c < nrhs && q < nt) X[(size_t)c * n + sTgt[q]] = sTv[q][c];
     }
     apply_inverse(k, nbp);
     __syncthreads();
-    update_rows_c64<NCOL>(A, X, sX, n, k, nbp, k + nbp, n, nrhs, tid);
+    update_rows_c64<NCOL, NT>(A, X, sX, n, k, nbp, k + nbp, n, nrhs, tid);
     __syncthreads();
   }
   // backward
@@ -763,15 +767,15 @@ __global__ void __launch_bounds__(kSolveThreads, 1024 / kSolveThreads) k_solve_c
   for (int k = last; k >= 0; k -= NB) {
     const int nbp = min(NB, n - k);
     const float2* Dk = D + (size_t)(k / NB) * 2 * NB * NB + NB * NB;  // U^-1 block
-    for (int idx = tid; idx < NB * NB; idx += kSolveThreads) sT[idx % NB][idx / NB] = Dk[idx];
-    for (int idx = tid; idx < NB * NCOL; idx += kSolveThreads) {
+    for (int idx = tid; idx < NB * NB; idx += NT) sT[idx % NB][idx / NB] = Dk[idx];
+    for (int idx = tid; idx < NB * NCOL; idx += NT) {
       const int i = idx % NB, c = idx / NB;
       sIn[i][c] = (c < nrhs && i < nbp) ? X[(size_t)c * n + k + i] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     apply_inverse(k, nbp);
     __syncthreads();
-    update_rows_c64<NCOL>(A, X, sX, n, k, nbp, 0, k, nrhs, tid);
+    update_rows_c64<NCOL, NT>(A, X, sX, n, k, nbp, 0, k, nrhs, tid);
     __syncthreads();
   }
 }
@@ -823,12 +827,14 @@ int lu_solve_chunk(const Unit* d_units, int n_units, const char* fac_base, char*
   if (nrhs < 1 || nrhs > 32) return fail(LSMS_ERR_ARG, "internal: nrhs %d out of range", nrhs);
   constexpr int NB = LuCfg<R>::NB;
   if constexpr (std::is_same<R, float>::value) {
-    const dim3 g(n_units), b(kSolveThreads);
-    if (nrhs <= 2) LSMS_LAUNCH(k_solve_c64<2>, g, b, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
-    else if (nrhs <= 4) LSMS_LAUNCH(k_solve_c64<4>, g, b, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
-    else if (nrhs <= 8) LSMS_LAUNCH(k_solve_c64<8>, g, b, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
-    else if (nrhs <= 16) LSMS_LAUNCH(k_solve_c64<16>, g, b, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
-    else LSMS_LAUNCH(k_solve_c64<32>, g, b, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
+    // more than 8 columns: slices of 8 (16 above 16 columns) per 128-thread CTA,
+    // so that each unit's chain of block steps runs as two concurrent chains
+    const dim3 g1(n_units), b256(kSolveThreads);
+    if (nrhs <= 2) LSMS_LAUNCH((k_solve_c64<2, kSolveThreads>), g1, b256, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
+    else if (nrhs <= 4) LSMS_LAUNCH((k_solve_c64<4, kSolveThreads>), g1, b256, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
+    else if (nrhs <= 8) LSMS_LAUNCH((k_solve_c64<8, kSolveThreads>), g1, b256, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
+    else if (nrhs <= 16) LSMS_LAUNCH((k_solve_c64<8, 128>), dim3(n_units, 2), dim3(128), 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
+    else LSMS_LAUNCH((k_solve_c64<16, 128>), dim3(n_units, 2), dim3(128), 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
   } else {
     LSMS_LAUNCH((k_solve<R, NB>), dim3(n_units), dim3(512), 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
   }
