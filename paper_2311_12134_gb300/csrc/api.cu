@@ -126,11 +126,31 @@ static int ensure_device_tables(int dev) {
   return LSMS_OK;
 }
 
+// Several host arrays in one device allocation and one copy (each piece 256-byte
+// aligned): a LIZ set's tables and a plan's unit lists cost one cudaMalloc, one
+// cudaMemcpy and one cudaFree instead of one of each per array.
+class Packed {
+ public:
+  template <typename T>
+  size_t add(const std::vector<T>& v) {
+    const size_t off = host_.size();
+    const size_t bytes = v.size() * sizeof(T);
+    host_.resize(off + align_up(std::max<size_t>(bytes, 1)));
+    if (bytes) std::memcpy(host_.data() + off, v.data(), bytes);
+    return off;
+  }
+  int upload(void** block) {
+    LSMS_CUDA_TRY(cudaMalloc(block, std::max<size_t>(host_.size(), 1)));
+    if (!host_.empty()) LSMS_CUDA_TRY(cudaMemcpy(*block, host_.data(), host_.size(), cudaMemcpyHostToDevice));
+    return LSMS_OK;
+  }
+
+ private:
+  std::vector<char> host_;
+};
 template <typename T>
-static int upload(T** dst, const std::vector<T>& src) {
-  LSMS_CUDA_TRY(cudaMalloc((void**)dst, std::max<size_t>(1, src.size()) * sizeof(T)));
-  if (!src.empty()) LSMS_CUDA_TRY(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
-  return LSMS_OK;
+static T* at(void* block, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(block) + off);
 }
 
 // Device copy of the LIZ arrays (made once per device, synchronous).
@@ -143,13 +163,16 @@ static int device_data(lsms_liz* liz, DeviceData** out) {
   auto it = liz->dev.find(dev);
   if (it == liz->dev.end()) {
     DeviceData dd;
-    std::vector<double> disp(liz->disp);
-    if ((rc = upload(&dd.offsets, liz->offsets))) return rc;
-    if ((rc = upload(&dd.site_atom, liz->site_atom))) return rc;
-    if ((rc = upload(&dd.disp, disp))) return rc;
-    if ((rc = upload(&dd.inv_off, liz->inv_off))) return rc;
-    if ((rc = upload(&dd.inv_sites, liz->inv_sites))) return rc;
-    if ((rc = upload(&dd.site_centre, liz->site_centre))) return rc;
+    Packed pk;
+    const size_t o_off = pk.add(liz->offsets), o_sa = pk.add(liz->site_atom), o_disp = pk.add(liz->disp),
+                 o_ioff = pk.add(liz->inv_off), o_isites = pk.add(liz->inv_sites), o_sc = pk.add(liz->site_centre);
+    if ((rc = pk.upload(&dd.block))) return rc;
+    dd.offsets = at<int64_t>(dd.block, o_off);
+    dd.site_atom = at<int32_t>(dd.block, o_sa);
+    dd.disp = at<double>(dd.block, o_disp);
+    dd.inv_off = at<int64_t>(dd.block, o_ioff);
+    dd.inv_sites = at<int64_t>(dd.block, o_isites);
+    dd.site_centre = at<int32_t>(dd.block, o_sc);
     it = liz->dev.emplace(dev, std::move(dd)).first;
   }
   *out = &it->second;
@@ -337,9 +360,12 @@ static int get_plan(lsms_liz* liz, DeviceData* dd, int lmax, int n_energy, int p
   ch.f1 = (int)p.fac_units.size();
   ch.ws_bytes = cur;
   p.chunks.push_back(ch);
-  int rc = upload(&p.d_units, p.units);
+  Packed pk;
+  const size_t o_u = pk.add(p.units), o_f = pk.add(p.fac_units);
+  int rc = pk.upload(&p.d_block);
   if (rc) return rc;
-  if ((rc = upload(&p.d_fac_units, p.fac_units))) return rc;
+  p.d_units = at<Unit>(p.d_block, o_u);
+  p.d_fac_units = at<Unit>(p.d_block, o_f);
   it = dd->plans.emplace(key, std::move(p)).first;
   *out = &it->second;
   return LSMS_OK;
@@ -1320,16 +1346,8 @@ extern "C" void lsms_liz_destroy(lsms_liz* liz) {
   for (auto& kv : liz->dev) {
     if (cudaSetDevice(kv.first) != cudaSuccess) continue;
     DeviceData& d = kv.second;
-    cudaFree(d.offsets);
-    cudaFree(d.site_atom);
-    cudaFree(d.disp);
-    cudaFree(d.inv_off);
-    cudaFree(d.inv_sites);
-    cudaFree(d.site_centre);
-    for (auto& pk : d.plans) {
-      cudaFree(pk.second.d_units);
-      cudaFree(pk.second.d_fac_units);
-    }
+    cudaFree(d.block);
+    for (auto& pk : d.plans) cudaFree(pk.second.d_block);
   }
   if (cur >= 0) cudaSetDevice(cur);
   delete liz;

@@ -319,10 +319,22 @@ extern "C" int lsms_build_liz(const double* pos, int n_atoms, const double* latt
       }
       cell[((size_t)ci[3 * i] * nc[1] + ci[3 * i + 1]) * nc[2] + ci[3 * i + 2]].push_back(i);
     }
+    // wrapped Cartesian positions, for a cheap pre-test of each candidate
+    std::vector<double> pw((size_t)3 * n_atoms);
+    for (int i = 0; i < n_atoms; ++i)
+      for (int k = 0; k < 3; ++k)
+        pw[3 * i + k] = fw[3 * i] * lattice[0 * 3 + k] + fw[3 * i + 1] * lattice[1 * 3 + k] + fw[3 * i + 2] * lattice[2 * 3 + k];
+    const double pre_cut2 = rcut2 * (1.0 + 1e-9) + 1e-300;
     for (int m = 0; m < n_atoms; ++m) {
       for (int da = -rng[0]; da <= rng[0]; ++da)
         for (int db = -rng[1]; db <= rng[1]; ++db)
           for (int dc = -rng[2]; dc <= rng[2]; ++dc) {
+            // a cell |d| cells away along axis k is at least (|d| - 1) / nc[k] apart in
+            // that fractional coordinate, i.e. (|d| - 1) h[k] / nc[k] in distance
+            const int dd[3] = {da, db, dc};
+            double gap = 0.0;
+            for (int k = 0; k < 3; ++k) gap = std::max(gap, (std::abs(dd[k]) - 1) * h[k] / nc[k]);
+            if (gap > rcut * (1.0 + 1e-9)) continue;
             const int raw[3] = {ci[3 * m] + da, ci[3 * m + 1] + db, ci[3 * m + 2] + dc};
             int cc[3], t[3];
             for (int k = 0; k < 3; ++k) {
@@ -330,7 +342,16 @@ extern "C" int lsms_build_liz(const double* pos, int n_atoms, const double* latt
               t[k] = q;
               cc[k] = raw[k] - q * nc[k];
             }
+            double tw[3];  // t . lattice - wrapped position of m
+            for (int k = 0; k < 3; ++k)
+              tw[k] = t[0] * lattice[0 * 3 + k] + t[1] * lattice[1 * 3 + k] + t[2] * lattice[2 * 3 + k] - pw[3 * m + k];
             for (int j : cell[((size_t)cc[0] * nc[1] + cc[1]) * nc[2] + cc[2]]) {
+              double q2 = 0.0;
+              for (int k = 0; k < 3; ++k) {
+                const double dk = pw[3 * j + k] + tw[k];
+                q2 += dk * dk;
+              }
+              if (q2 > pre_cut2) continue;  // the exact test below decides the rest
               // relative to the wrapped centre: (fw_j + t - fw_m) * lattice == pos_j + T * lattice - pos_m
               // with T = t - floor(f_j) + floor(f_m)
               Cand cd;

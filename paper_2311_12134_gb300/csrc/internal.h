@@ -77,11 +77,13 @@ struct Plan {
   std::vector<Unit> units;       // host copies
   std::vector<Unit> fac_units;
   std::vector<Chunk> chunks;
-  Unit* d_units = nullptr;       // device copies
+  void* d_block = nullptr;       // one device allocation holding the two device copies
+  Unit* d_units = nullptr;
   Unit* d_fac_units = nullptr;
 };
 
 struct DeviceData {
+  void* block = nullptr;         // one device allocation holding the arrays below
   int64_t* offsets = nullptr;    // [N+1]
   int32_t* site_atom = nullptr;  // [S]
   double* disp = nullptr;        // [S][3]

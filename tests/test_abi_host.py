@@ -76,6 +76,21 @@ def test_liz_unwrapped_positions(L):
     _compare_liz(lz, ref)
 
 
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_liz_skewed_cells_and_radii_near_cell_sizes(L, seed):
+    """Skewed random cells, radii from a fraction of a cell to about two cells
+    (the builder skips neighbour cells by a distance bound, so radii close to
+    the cell widths are where a wrong bound would drop sites)."""
+    from paper_2311_12134_gb300 import binding as B
+    rng = np.random.default_rng(seed)
+    lat = np.diag(rng.uniform(5.0, 8.0, 3)) + rng.uniform(-1.5, 1.5, (3, 3)) * (1 - np.eye(3))
+    pos = rng.random((9, 3)) @ lat + rng.normal(0, 0.05, (9, 3))
+    h = 1.0 / np.linalg.norm(np.linalg.inv(lat), axis=0)  # plane spacings
+    for r in sorted({0.4 * h.min(), 0.999 * h.min(), h.min(), 1.001 * h.min(), h.max(), 1.7 * h.max()}):
+        lz = B.build_liz(pos, lat, r)
+        _compare_liz(lz, oliz.build_liz(pos, lat, r))
+
+
 def test_gaunt_table_matches_oracle(L):
     from paper_2311_12134_gb300 import binding as B
     for lmax in range(4):
