@@ -53,7 +53,7 @@ def build(verbose=False, extra_nvcc=()):
                      os.path.join(CSRC, src), "-o", obj])
     for src in CXX_SOURCES:
         obj = os.path.join(BUILD_DIR, src + ".o")
-        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", *inc, "-c",
+        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-ffp-contract=off", *inc, "-c",
                      os.path.join(CSRC, src), "-o", obj])
     with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         outs = list(ex.map(_run, jobs))
@@ -62,7 +62,7 @@ def build(verbose=False, extra_nvcc=()):
             sys.stdout.write(o)
     objs = [os.path.join(BUILD_DIR, s + ".o") for s in CUDA_SOURCES + CXX_SOURCES]
     tmp = LIB + ".tmp"
-    _run([nvcc, ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
+    _run([nvcc, ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lpthread",
           "-Xlinker", "-rpath=" + os.path.join(cuda, "lib64")])
     os.replace(tmp, LIB)
     return LIB

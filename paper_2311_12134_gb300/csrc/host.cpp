@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 
 #include "internal.h"
 
@@ -220,6 +221,26 @@ bool cand_less(const Cand& a, const Cand& b) {
   return false;
 }
 
+// f(m) for m = 0 .. n - 1 on up to 8 host threads (the atoms' neighbour searches
+// are independent); one thread for small n.
+template <typename F>
+void parallel_atoms(int n, F& f) {
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nt = std::min<int>({8, (int)hw, std::max(1, n / 32)});
+  if (nt <= 1) {
+    for (int m = 0; m < n; ++m) f(m);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(nt - 1);
+  auto run = [&](int t) {
+    for (int m = t; m < n; m += nt) f(m);
+  };
+  for (int t = 1; t < nt; ++t) th.emplace_back(run, t);
+  run(0);
+  for (auto& x : th) x.join();
+}
+
 bool inv3(const double a[9], double out[9]) {
   const double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
                      a[2] * (a[3] * a[7] - a[4] * a[6]);
@@ -325,7 +346,8 @@ extern "C" int lsms_build_liz(const double* pos, int n_atoms, const double* latt
       for (int k = 0; k < 3; ++k)
         pw[3 * i + k] = fw[3 * i] * lattice[0 * 3 + k] + fw[3 * i + 1] * lattice[1 * 3 + k] + fw[3 * i + 2] * lattice[2 * 3 + k];
     const double pre_cut2 = rcut2 * (1.0 + 1e-9) + 1e-300;
-    for (int m = 0; m < n_atoms; ++m) {
+    auto search = [&](int m) {
+      per[m].reserve(64);
       for (int da = -rng[0]; da <= rng[0]; ++da)
         for (int db = -rng[1]; db <= rng[1]; ++db)
           for (int dc = -rng[2]; dc <= rng[2]; ++dc) {
@@ -368,12 +390,14 @@ extern "C" int lsms_build_liz(const double* pos, int n_atoms, const double* latt
               per[m].push_back(cd);
             }
           }
-    }
+      std::sort(per[m].begin(), per[m].end(), cand_less);
+    };
+    parallel_atoms(n_atoms, search);
   }
   int64_t total = 0;
   int smax = 0, smin = 1 << 30;
   for (int m = 0; m < n_atoms; ++m) {
-    std::sort(per[m].begin(), per[m].end(), cand_less);
+    if (!lattice) std::sort(per[m].begin(), per[m].end(), cand_less);  // periodic: sorted by the search
     if (per[m].empty() || !per[m][0].centre) { delete z; return fail(LSMS_ERR_ARG, "lsms_build_liz: atom %d missing from its own LIZ", m); }
     const int s = (int)per[m].size();
     smax = std::max(smax, s);
