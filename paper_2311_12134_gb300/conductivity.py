@@ -54,6 +54,7 @@ class Problem:
         self.rho = torch.empty((self.n_delta, 3, 3), dtype=torch.float64, device=self.device)
         self.bw_status = torch.empty((nE, self.liz.n_atoms), dtype=torch.int32, device=self.device)
         self._bw_ws = None
+        self._side = None  # side stream of step()
 
     @property
     def n_units(self):
@@ -76,6 +77,12 @@ class Problem:
         self.solve_tau(tinv, stream)
         return self.sigma(stream)
 
+    def step(self, grad_sigma, tinv=None):
+        """forward() and backward() in one call on the current stream, with sigma's
+        traces overlapping the adjoint solves.  Returns (sigma, (grad_tinv,
+        grad_tinv_species))."""
+        return _step(self, grad_sigma, tinv)
+
     def backward(self, grad_sigma, tinv=None, stream=None):
         """PyTorch gradients of Re sum(conj(grad_sigma) sigma): per site [nE, N, K, K] and per species."""
         import torch
@@ -89,6 +96,25 @@ class Problem:
                                      grad_sigma.contiguous(), self.precision, lu_store=self.lu_store,
                                      unit_status=self.bw_status, workspace=self._bw_ws, stream=stream,
                                      conj_pairs=self.conj_pairs)
+
+
+def _step(problem, grad_sigma, tinv=None):
+    """Forward (tau, sigma) and adjoint in one call: sigma's traces run on a side
+    stream while the adjoint solves run on the current one (the adjoint reads tau
+    and grad_sigma, not sigma), joined before returning.  Same results as
+    forward() then backward()."""
+    import torch
+    cur = torch.cuda.current_stream(problem.device)
+    problem.solve_tau(tinv)
+    if problem._side is None:
+        problem._side = torch.cuda.Stream(device=problem.device)
+    side = problem._side
+    side.wait_stream(cur)
+    with torch.cuda.stream(side):
+        problem.sigma()
+    grads = problem.backward(grad_sigma, tinv)
+    cur.wait_stream(side)
+    return problem.sigma_out, grads
 
 
 def _sigma_fn():
@@ -143,17 +169,19 @@ class StepGraph:
         self.problem = problem
         self.grad_sigma = grad_sigma.contiguous()
         self.with_backward = with_backward
-        problem.forward()
         if with_backward:
-            problem.backward(self.grad_sigma)
+            problem.step(self.grad_sigma)
+        else:
+            problem.forward()
         torch.cuda.synchronize(problem.device)
         self.graph = torch.cuda.CUDAGraph()
         stream = torch.cuda.Stream(device=problem.device)
         stream.wait_stream(torch.cuda.current_stream(problem.device))
         with torch.cuda.graph(self.graph, stream=stream):
-            problem.forward()
             if with_backward:
-                self.grads = problem.backward(self.grad_sigma)
+                _, self.grads = problem.step(self.grad_sigma)
+            else:
+                problem.forward()
         torch.cuda.synchronize(problem.device)
 
     def replay(self):

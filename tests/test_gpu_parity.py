@@ -403,6 +403,28 @@ def test_tau_sizes_multiple_of_the_panel_width(lmax, n_atoms, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_step_overlap_matches_forward_then_backward(precision):
+    """Problem.step runs sigma's traces on a side stream beside the adjoint; the
+    results are bit-identical to forward() followed by backward()."""
+    from paper_2311_12134_gb300 import binding as B
+    from paper_2311_12134_gb300.conductivity import Problem
+    w = _alloy32(seed=29)
+    J = B.dipole_current(w.lmax, w.r_ll)
+    p = Problem(w.pos, w.lattice, w.r_liz, w.lmax, w.species, w.tinv, w.z, J, w.volume, precision=precision)
+    gs = torch.zeros((1, 3, 3), dtype=torch.complex128, device="cuda")
+    gs[0, 2, 0] = 1.0
+    p.forward()
+    g_seq = [t.clone() for t in p.backward(gs)]
+    torch.cuda.synchronize()
+    sig_seq, tau_seq = p.sigma_out.clone(), p.tau.clone()
+    p.sigma_out.zero_()
+    sig, g = p.step(gs)
+    torch.cuda.synchronize()
+    assert torch.equal(sig, sig_seq) and torch.equal(p.tau, tau_seq)
+    assert torch.equal(g[0], g_seq[0]) and torch.equal(g[1], g_seq[1])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_cuda_graph_replay_matches_eager(precision):
     """The whole forward + adjoint step captured in one CUDA graph and replayed gives
     bit-identical tau, sigma and gradient to the eager calls."""
