@@ -20,6 +20,7 @@ import argparse
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -92,7 +93,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # samples go to LSMS_CLOCKS_DIR (default: the system temporary directory)
+        out_dir = os.environ.get("LSMS_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"lsms_clocks_rank{index}_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -590,7 +593,11 @@ def roofline(kt, w, n_list, fwd_passes, bwd_passes, precision, traffic):
     t = traffic.get(top["kernel"].split("<")[0]) if traffic else None
     top = dict(top)
     top["traffic"] = t
-    top["peak_source"] = "derived from unit counts and the 2070 MHz max clock (see DESIGN.md)"
+    if top.get("bound") == "alu":
+        top["peak_source"] = ("derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (max SM clock); double-float "
+                              "kernels at 44 lane ops per complex multiply-add")
+    else:
+        top["peak_source"] = "measured (MEASURED_PEAKS.json)"
     return top, rows
 
 
