@@ -44,6 +44,15 @@
  * uploads tables and builds the work plan (synchronous); later calls with the
  * same sizes allocate nothing when a workspace is passed, so they can be
  * captured into a CUDA graph.
+ *
+ * Concurrency inside a call: lsms_tau_blocks and lsms_kubo_sigma_backward split
+ * each chunk of units at atom boundaries into up to four parts (environment
+ * variable LSMS_STREAMS, 1..4, read once; default 4) that run on the caller's
+ * stream and on side streams, forked from and joined back into the caller's
+ * stream by events (a capture records them as graph edges).  The side streams
+ * are created by the first such call on each host thread and device.  With the
+ * kernel timers on (lsms_kernel_timer_enable) everything runs on the caller's
+ * stream.  Results do not depend on the split.
  */
 #ifndef LSMSKUBO_H
 #define LSMSKUBO_H
