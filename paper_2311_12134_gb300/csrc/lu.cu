@@ -353,6 +353,52 @@ __device__ __noinline__ void compose_panel_swaps(const int32_t* piv, int k, int 
 }
 
 constexpr int kSwapCols = 256;  // columns per CTA of k_swap_trsm
+constexpr int kSwapTileBytes = 32 * (kSwapCols + 1) * 8;  // complex64 panel-row tile of k_swap_trsm
+
+// Complex64 body of k_swap_trsm: the panel rows k .. k + 31 of the CTA's columns
+// move between global and shared memory as coalesced 32-row column segments (a
+// warp per column, lane = row); each thread then gathers its column's
+// interchanged rows from the tile, solves in registers and puts them back.
+// Rows below the panel that the interchanges reach are read and written directly.
+template <int NB>
+__device__ __forceinline__ void k_swap_trsm_staged(float2* A, int n, int k, int c0, const float2 (*sL)[NB + 1],
+                                                   const int* sTgtRow, const int* sSrcRow, const int* sTgtSrc,
+                                                   const int* sNt) {
+  extern __shared__ float2 sTile[];  // [NB][kSwapCols + 1]
+  constexpr int LD = kSwapCols + 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ncols = min(kSwapCols, n - c0);
+  for (int cc = warp; cc < ncols; cc += 8) sTile[lane * LD + cc] = A[(size_t)(c0 + cc) * n + k + lane];
+  __syncthreads();
+  if (tid < ncols) {
+    float2* Ac = A + (size_t)(c0 + tid) * n;
+    float2 x[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {  // gathered: the interchanged panel rows
+      const int r = sSrcRow[i];
+      x[i] = r < k + NB ? sTile[(r - k) * LD + tid] : Ac[r];
+    }
+    // rows below the panel: new values from panel rows (in the tile)
+    const int nt = *sNt;
+    for (int q = 0; q < nt; ++q) Ac[sTgtRow[q]] = sTile[(sTgtSrc[q] - k) * LD + tid];
+    // U12 = L11^{-1} A12 (unit lower), by rows
+#pragma unroll
+    for (int i = 1; i < NB; ++i) {
+      float2 a0 = x[i], a1 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < i; j += 2) {
+        a0 = cfms(sL[i][j], x[j], a0);
+        if (j + 1 < i) a1 = cfms(sL[i][j + 1], x[j + 1], a1);
+      }
+      x[i] = make_float2(a0.x + a1.x, a0.y + a1.y);
+    }
+    // the column's tile entries were read above by this thread only
+#pragma unroll
+    for (int i = 0; i < NB; ++i) sTile[i * LD + tid] = x[i];
+  }
+  __syncthreads();
+  for (int cc = warp; cc < ncols; cc += 8) A[(size_t)(c0 + cc) * n + k + lane] = sTile[lane * LD + cc];
+}
 
 template <typename R, int NB>
 __global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ units, char* fac_base, int k) {
@@ -376,6 +422,10 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ unit
     sL[i][j] = A[(size_t)(k + j) * n + k + i];
   }
   if (tid < 32) compose_panel_swaps(piv, k, NB, tid, sStep, sTgtRow, sSrcRow, sTgtSrc, &sNt);
+  if constexpr (sizeof(C) == 8) {
+    k_swap_trsm_staged<NB>(A, n, k, c0, sL, sTgtRow, sSrcRow, sTgtSrc, &sNt);
+    return;
+  }
   __syncthreads();
   const int c = c0 + tid;
   if (c >= n) return;
@@ -792,6 +842,9 @@ int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
   if (!attr_set) {
     LSMS_CUDA_TRY(cudaFuncSetAttribute(k_panel_smem<R, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kPanelSmemBytes));
+    if (sizeof(Cx<R>) == 8)
+      LSMS_CUDA_TRY(cudaFuncSetAttribute(k_swap_trsm<R, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSwapTileBytes));
     attr_set = true;
   }
   for (int k = 0; k < n_max; k += NB) {
@@ -804,7 +857,8 @@ int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
     const int trail = n_max - k - NB;
     if (trail <= 0) continue;
     // one warp per column right of the panel
-    LSMS_LAUNCH((k_swap_trsm<R, NB>), dim3((trail + kSwapCols - 1) / kSwapCols, n_units), dim3(256), 0, st, d_units,
+    LSMS_LAUNCH((k_swap_trsm<R, NB>), dim3((trail + kSwapCols - 1) / kSwapCols, n_units), dim3(256),
+                sizeof(Cx<R>) == 8 ? kSwapTileBytes : 0, st, d_units,
                 fac_base, k);
     if constexpr (std::is_same<R, float>::value) {
       // complex64: the trailing update runs on the tensor cores (3xTF32, tc_gemm.cu)
