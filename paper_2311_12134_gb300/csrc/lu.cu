@@ -742,10 +742,11 @@ __global__ void __launch_bounds__(64) k_diag_inv(const Unit* __restrict__ units,
   for (int i = 0; i < NB; ++i) out[i] = y[i];
 }
 
-// One CTA of kSolveThreads threads per unit (several units resident per SM, so
-// one unit's block phases overlap the others' row updates): L y = P b (unit
-// lower, each panel's interchanges applied just before its block, LINPACK
-// order), then U x = y, on the n x nrhs column-major block X.  Each 32-row block
+// One CTA of NT threads per unit and slice of NCOL right-hand-side columns
+// (blockIdx.y; several CTAs resident per SM, so one chain's block phases overlap
+// the others' row updates): L y = P b (unit lower, each panel's interchanges
+// applied just before its block, LINPACK order), then U x = y, on the n x nrhs
+// column-major block X.  Each 32-row block
 // step gathers its rows (the panel's interchanges composed once into a gather),
 // multiplies them by the stored inverse of the diagonal block (all threads, no
 // serial chain), and updates the rows below (above, going back) with the block's

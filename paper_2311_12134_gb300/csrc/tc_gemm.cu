@@ -9,13 +9,16 @@
 // as hi*hi + hi*lo + lo*hi ("3xTF32"), accumulated in FP32 in tensor memory,
 // which keeps complex64 accuracy for the refinement that follows.
 //
-// One CTA (4 warps) per 128 x 32 complex output tile:
-//   all threads  load L21 (128 x 32) and U12 (32 x 32), split hi/lo, and store
-//                them K-major into shared memory with the 128-byte swizzle,
+// One CTA (4 warps) per 128-row block, walking its 128 x 32 complex output tiles:
+//   all threads  load L21 (128 x 32, once) and U12 (32 x 32, per tile), split
+//                hi/lo, and store them K-major into shared memory with the
+//                128-byte swizzle,
 //   one thread   issues 24 tcgen05.mma (M = 128, N = 64, K = 8, kind::tf32)
-//                into a 64-column TMEM accumulator and commits to an mbarrier,
+//                into one of two 64-column TMEM accumulators and commits to
+//                that accumulator's mbarrier,
 //   all threads  wait (bounded), read the accumulator with tcgen05.ld
-//                (warp w owns TMEM lanes 32w..32w+31) and update C in place.
+//                (warp w owns TMEM lanes 32w..32w+31) and update C in place,
+//                one tile behind the products.
 #include <cstdint>
 
 #include "common.cuh"
