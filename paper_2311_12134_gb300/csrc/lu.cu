@@ -185,7 +185,9 @@ __global__ void __launch_bounds__(256) k_panel(const Unit* __restrict__ units, c
 // the panel are read once (cp.async), factored column by column in shared
 // memory, and written back once.  Units whose panel does not fit (m > max_rows)
 // are left to k_panel, which works in global memory.
-// One thread per physical row (1024 threads, m <= 1024).  Rows never move in
+// One thread per physical row (the launch takes the tallest panel of its units
+// rounded up to a warp, at most 1024 threads, so short panels leave room for more
+// CTAs per SM).  Rows never move in
 // shared memory: each thread keeps the logical (pivoted) number of its row in a
 // register, so a row interchange is two register updates.  The pivot search
 // for column j + 1 runs inside the update of column j (on the values just
@@ -204,7 +206,8 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_smem(const Unit* __rest
   const int n = u.n;
   if (k >= n) return;
   const int m = n - k;
-  if (m > max_rows || m > NT) return;
+  const int nw = blockDim.x >> 5;  // warps launched: ceil(rows / 32), at most NW
+  if (m > max_rows || m > (int)blockDim.x) return;
   extern __shared__ __align__(16) unsigned char panel_raw[];
   C* sP = reinterpret_cast<C*>(panel_raw);  // [NB][m], column-major, physical rows
   C* A = reinterpret_cast<C*>(fac_base + u.fac_off);
@@ -261,8 +264,8 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_smem(const Unit* __rest
   for (int j = 0; j < NB; ++j) {
     if (j < nbp) {
       const int par = j & 1;
-      R best = lane < NW ? s_val[par][lane] : R(-1);  // NW <= 32 warp results
-      int bl = lane < NW ? s_lg[par][lane] : m, bp = lane < NW ? s_ph[par][lane] : 0;
+      R best = lane < nw ? s_val[par][lane] : R(-1);  // nw <= 32 warp results
+      int bl = lane < nw ? s_lg[par][lane] : m, bp = lane < nw ? s_ph[par][lane] : 0;
       warp_best(best, bl, bp);
       const int p = bl, pph = bp;
       if (tid == 0) piv[k + j] = k + p;
@@ -853,7 +856,9 @@ int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
     if (m_max > max_rows)
       LSMS_LAUNCH((k_panel<R, NB>), dim3(n_units), dim3(256), 0, st, d_units, fac_base, k, stat, max_rows);
     const int rows_smem = std::min(m_max, max_rows);
-    LSMS_LAUNCH((k_panel_smem<R, NB>), dim3(n_units), dim3(kPanelThreads), (size_t)rows_smem * NB * sizeof(Cx<R>), st,
+    // one thread per row: short panels launch fewer threads, so more CTAs fit on an SM
+    const int threads = std::min(kPanelThreads, (rows_smem + 31) / 32 * 32);
+    LSMS_LAUNCH((k_panel_smem<R, NB>), dim3(n_units), dim3(threads), (size_t)rows_smem * NB * sizeof(Cx<R>), st,
                 d_units, fac_base, k, stat, max_rows);
     const int trail = n_max - k - NB;
     if (trail <= 0) continue;
