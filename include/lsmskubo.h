@@ -27,7 +27,10 @@
  *    c = (z1, z2), site m carries J(z2, z1) and site n carries J(z1, z2).
  *  - t^{-1} blocks must be complex-symmetric (true for scatterers with time
  *    reversal symmetry in a real-harmonic basis).  Then M^T = M and the row block
- *    is tau^{0n} = (tau^{n0})^T, which the library uses.
+ *    is tau^{0n} = (tau^{n0})^T, which the library uses.  The assembly checks it:
+ *    a block with max |t - t^T| > 1e-12 max |t| (|.| = |Re| + |Im|) flags every
+ *    unit whose LIZ holds that site LSMS_UNIT_TINV_ASYM, and those units' results
+ *    are not valid.
  *
  * Memory: "dev" = device pointer on the current CUDA device, "host" = host
  * pointer.  The caller owns every buffer it passes; the library owns only the
@@ -46,8 +49,9 @@
  * captured into a CUDA graph.
  *
  * Concurrency inside a call: lsms_tau_blocks and lsms_kubo_sigma_backward split
- * each chunk of units at atom boundaries into up to four parts (environment
- * variable LSMS_STREAMS, 1..4, read once; default 4) that run on the caller's
+ * each chunk of units at atom boundaries into up to four parts (option
+ * "streams", else the environment variable LSMS_STREAMS, 1..4, read once;
+ * default 4) that run on the caller's
  * stream and on side streams, forked from and joined back into the caller's
  * stream by events (a capture records them as graph edges).  The side streams
  * are created by the first such call on each host thread and device.  With the
@@ -99,12 +103,22 @@ enum lsms_precision {
  * energies' factors only, so use the flag in both calls or in neither. */
 #define LSMS_CONJ_PAIRS 0x100
 
-/* Unit status values written to unit_status[e][m] (0 = fine). */
+/* Flag OR-ed into the precision argument of lsms_tau_workspace_bytes and
+ * lsms_backward_workspace_bytes only: the sizes for a call that is given an
+ * lu_store, so the factors (and the mixed form's double-float M) live there
+ * and not in the workspace. */
+#define LSMS_WS_STORE 0x200
+
+/* Unit status values written to unit_status[e][m] (0 = fine).  Every flag
+ * except LSMS_UNIT_FP64_FALLBACK means the unit's results are not valid. */
 #define LSMS_UNIT_OK 0
 #define LSMS_UNIT_ZERO_PIVOT 1
 #define LSMS_UNIT_NOCONV 2
 #define LSMS_UNIT_NONFINITE 4
 #define LSMS_UNIT_BAD_INPUT 8   /* a species index outside 0..n_species-1 */
+#define LSMS_UNIT_TINV_ASYM 16  /* a t^{-1} block of the LIZ is not complex-symmetric */
+#define LSMS_UNIT_GROWTH 32     /* mixed form: pivot growth of the complex64 factors above the limit */
+#define LSMS_UNIT_FP64_FALLBACK 64  /* mixed form: re-solved in the FP64 form on the GPU (valid result) */
 #define LSMS_UNIT_TIMEOUT 128   /* a bounded device wait gave up (results invalid) */
 
 /* ---------------------------------------------------------------- LIZ
@@ -168,11 +182,26 @@ int lsms_gaunt_table(int lmax, double* C);
  *              (y_q = X w_q: sum_q ||(LU)^-1 (B w_q - M y_q)||^2 <= 1e-20
  *              sum_q ||y_q||^2) and stops there when it passes, so X carries
  *              the correction test's error bound without a further full sweep.  LSMS_UNIT_NOCONV after 6
- *              sweeps.
+ *              sweeps (option "ir_max_sweeps").
+ *              Mixed form, pivot growth: the assembly records max |M| and the
+ *              factorization max |U| (|.| = |Re| + |Im|); a unit with
+ *              max |U| > growth_limit * max |M| (option "growth_limit", default
+ *              1e3) is flagged LSMS_UNIT_GROWTH.
+ *              Mixed form, FP64 fallback: after all units, up to
+ *              "fallback_slots" units (default 8, in the library's unit order)
+ *              flagged ZERO_PIVOT, NOCONV, GROWTH or TIMEOUT are assembled,
+ *              factored and solved again in the FP64 form on the GPU within the
+ *              same call; their tau blocks are overwritten, those flags cleared
+ *              and LSMS_UNIT_FP64_FALLBACK set.  Units beyond the slots keep
+ *              their flags.
  * workspace    dev scratch of workspace_bytes (>= lsms_tau_workspace_bytes for
  *              one unit), 256-byte aligned (else LSMS_ERR_ARG); the units are
  *              processed in chunks that fit it.  NULL = the library allocates
- *              (stream-ordered) and frees it.
+ *              (stream-ordered) and frees it.  The sizes include the FP64
+ *              fallback slots (mixed form) at the current "fallback_slots"
+ *              option; change the option before sizing a workspace.
+ *              With LSMS_WS_STORE in the precision argument the sizes assume
+ *              an lu_store (no factors in the workspace).
  * lu_store     dev buffer of lu_store_bytes (lsms_lu_store_bytes), 256-byte
  *              aligned, that keeps the factors and pivots (mixed form: also M as
  *              double-float pairs) for lsms_kubo_sigma_backward, or NULL.
@@ -210,6 +239,17 @@ int lsms_kubo_sigma(const lsms_liz* liz, int lmax, const int32_t* species, int n
                     int n_delta, double volume, int precision, lsms_complex* sigma_tilde,
                     lsms_complex* sigma, double* rho, void* stream);
 
+/* Per-atom terms of the same sum: sigma_tilde_atoms dev [n_delta][4][n_atoms][3][3]
+ * output, entry [d][c][m] = -(1/(pi V)) S_c(m), the term of centre atom m in
+ * Eq. (lsms-conductivity-formula), so that sigma_tilde = sum over m (a local
+ * decomposition of the LSMS conductivity by centre atom).  Other arguments as
+ * for lsms_kubo_sigma.  LSMS_MIXED takes stream-ordered scratch for the
+ * double-float copy of J (as lsms_kubo_sigma does). */
+int lsms_kubo_sigma_atoms(const lsms_liz* liz, int lmax, const int32_t* species, int n_species,
+                          const lsms_complex* J, int64_t J_delta_stride, const lsms_complex* tau,
+                          int n_delta, double volume, int precision, lsms_complex* sigma_tilde_atoms,
+                          void* stream);
+
 /* Same computation and arguments as lsms_kubo_sigma, for callers that cannot
  * allocate device memory during the call: code that must not trigger cudaMalloc
  * or a stream-ordered pool allocation (a serving loop under a fixed memory
@@ -218,14 +258,18 @@ int lsms_kubo_sigma(const lsms_liz* liz, int lmax, const int32_t* species, int n
  * nothing: its scratch (the per-atom partial traces) is a file-scope device
  * array of 16 MiB that every GPU which loads the library holds until the
  * process exits.  The paper has no counterpart; it is a deployment variant.
- *  - Requires n_delta * n_atoms * 576 bytes (each rounded up to 256) plus
- *    n_delta * 576 bytes to fit in 16 MiB, about 29,000 atom-delta pairs;
- *    larger problems are rejected with LSMS_ERR_ARG and a message naming the
- *    limit, before anything is enqueued.
+ *  - Requires n_delta * n_atoms * 576 bytes plus n_delta * 576 bytes plus, for
+ *    LSMS_MIXED, the double-float copy of J (n_species * 12 * K * K * 16 bytes,
+ *    times n_delta when J_delta_stride != 0), each rounded up to 256, to fit in
+ *    16 MiB: about 29,000 atom-delta pairs; larger problems are rejected with
+ *    LSMS_ERR_ARG and a message naming the limit, before anything is enqueued.
  *  - The LIZ set must already have a device copy on the current device (made
  *    by lsms_tau_blocks, which produces tau); otherwise LSMS_ERR_ARG.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    (cudaGetSymbolAddress) and keeps it for the life of the process; make that
+ *    first call before any stream capture.  A cudaDeviceReset (or any teardown
+ *    of the device's primary context) invalidates the kept address: the library
+ *    must not be used across one.
  *  - All calls share the one array: calls that can overlap on the GPU (other
  *    streams, other threads) race and corrupt each other's results; order them
  *    on one stream or synchronise between them.  Each call writes every
@@ -265,6 +309,19 @@ int lsms_kubo_sigma_backward(const lsms_liz* liz, int lmax, const int32_t* speci
                              size_t lu_store_bytes, lsms_complex* grad_tinv,
                              lsms_complex* grad_tinv_species, int32_t* unit_status,
                              void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------- options
+ * Process-wide options (all threads, all devices), read at each call:
+ *   "growth_limit"    pivot-growth limit of the mixed form (default 1e3; > 0)
+ *   "fallback_slots"  FP64 re-solves per mixed-form call (default 8; 0..4096;
+ *                     0 disables the fallback); enters the workspace sizes
+ *   "ir_max_sweeps"   refinement sweeps of the mixed form before
+ *                     LSMS_UNIT_NOCONV (default 6; 0..64)
+ *   "streams"         concurrent parts per chunk (1..4; 0 = the environment
+ *                     variable LSMS_STREAMS, else 4)
+ * LSMS_ERR_ARG for an unknown name or a value out of range. */
+int lsms_set_option(const char* name, double value);
+int lsms_get_option(const char* name, double* value);
 
 /* ---------------------------------------------------------------- misc */
 /* Message of the last error on the calling thread ("" if none). */

@@ -20,8 +20,12 @@ import numpy as np
 LIZ_TOL = 1e-8
 
 
-def build_liz(pos, lattice, r_liz):
-    """Returns dict(offsets [N+1], site_atom [S], disp [S,3], image [S,3])."""
+def build_liz(pos, lattice, r_liz, atoms=None):
+    """Returns dict(offsets [N+1], site_atom [S], disp [S,3], image [S,3]).
+
+    ``atoms``: build only the LIZ of these centre atoms, in the order given
+    (offsets then has len(atoms) + 1 entries; site_atom keeps global atom
+    indices).  The same test is applied to each centre either way."""
     pos = np.asarray(pos, dtype=np.float64)
     N = pos.shape[0]
     if lattice is None:
@@ -38,7 +42,7 @@ def build_liz(pos, lattice, r_liz):
     tvec = shift_arr.astype(np.float64) @ lat                       # [n_shift, 3]
     offsets = [0]
     site_atom, disp, image = [], [], []
-    for m in range(N):
+    for m in (range(N) if atoms is None else atoms):
         d = pos[None, :, :] + tvec[:, None, :] - pos[m][None, None, :]   # [n_shift, N, 3]
         inside = np.linalg.norm(d, axis=-1) <= r_liz + LIZ_TOL
         found = []

@@ -23,6 +23,13 @@ PRECISIONS = {"fp64": LSMS_FP64, "mixed": LSMS_MIXED}
 UNIT_ZERO_PIVOT = 1
 UNIT_NOCONV = 2
 UNIT_NONFINITE = 4
+UNIT_BAD_INPUT = 8
+UNIT_TINV_ASYM = 16
+UNIT_GROWTH = 32
+UNIT_FP64_FALLBACK = 64
+UNIT_TIMEOUT = 128
+# every flag but the fallback marker means the unit's result is not valid
+UNIT_INVALID = 0xff & ~UNIT_FP64_FALLBACK
 
 _lib = None
 
@@ -46,6 +53,9 @@ SIGNATURES = {
     "lsms_tau_blocks": (_I, [_P, _I, _P, _I, _P, _P, _I, _I, _P, _P, _P, _SZ, _P, _SZ, _P]),
     "lsms_kubo_sigma": (_I, [_P, _I, _P, _I, _P, _I64, _P, _I, _D, _I, _P, _P, _P, _P]),
     "lsms_kubo_sigma_noalloc": (_I, [_P, _I, _P, _I, _P, _I64, _P, _I, _D, _I, _P, _P, _P, _P]),
+    "lsms_kubo_sigma_atoms": (_I, [_P, _I, _P, _I, _P, _I64, _P, _I, _D, _I, _P, _P]),
+    "lsms_set_option": (_I, [ctypes.c_char_p, _D]),
+    "lsms_get_option": (_I, [ctypes.c_char_p, ctypes.POINTER(_D)]),
     "lsms_kubo_sigma_backward": (_I, [_P, _I, _P, _I, _P, _P, _I, _I, _P, _I64, _P, _D, _P, _P, _SZ, _P, _P,
                                       _P, _P, _SZ, _P]),
     "lsms_last_error": (ctypes.c_char_p, []),
@@ -199,6 +209,7 @@ def lu_store_bytes(liz, lmax, n_energy, precision):
 
 
 LSMS_CONJ_PAIRS = 0x100
+LSMS_WS_STORE = 0x200  # workspace sizes for a call given an lu_store
 
 
 def _prec(precision, conj_pairs=False):
@@ -254,6 +265,36 @@ def kubo_sigma(liz, lmax, species, J, tau, n_delta, volume, J_delta_stride=0, si
                                  _dev(sigma, torch.complex128, (n_delta, 3, 3), "sigma"),
                                  _dev(rho, torch.float64, (n_delta, 3, 3), "rho"), _stream(stream)))
     return sigma, sigma_tilde, rho
+
+
+def kubo_sigma_atoms(liz, lmax, species, J, tau, n_delta, volume, J_delta_stride=0, out=None, stream=None,
+                     precision="fp64"):
+    """lsms_kubo_sigma_atoms: the per-centre-atom terms of sigma~, [n_delta, 4, n_atoms, 3, 3] complex128
+    (their sum over atoms is sigma~)."""
+    import torch
+    K = (lmax + 1) ** 2
+    dev = tau.device
+    shape = (n_delta, 4, liz.n_atoms, 3, 3)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.complex128, device=dev)
+    n_species = J.shape[-5]
+    _check(lib().lsms_kubo_sigma_atoms(
+        liz.handle, lmax, _dev(species, torch.int32, (liz.n_atoms,), "species"), n_species,
+        _dev(J, torch.complex128, None, "J"), int(J_delta_stride),
+        _dev(tau, torch.complex128, (2 * n_delta, liz.total_sites, K, K), "tau"), n_delta, float(volume),
+        _prec(precision), _dev(out, torch.complex128, shape, "out"), _stream(stream)))
+    return out
+
+
+def set_option(name, value):
+    """lsms_set_option (process-wide): growth_limit, fallback_slots, ir_max_sweeps, streams."""
+    _check(lib().lsms_set_option(name.encode(), float(value)))
+
+
+def get_option(name):
+    v = _D()
+    _check(lib().lsms_get_option(name.encode(), ctypes.byref(v)))
+    return v.value
 
 
 def kubo_sigma_noalloc(liz, lmax, species, J, tau, n_delta, volume, J_delta_stride=0, sigma=None, sigma_tilde=None,

@@ -11,6 +11,26 @@ import numpy as np
 from . import binding as B
 
 
+class UnitStatusError(RuntimeError):
+    """Some (energy, atom) units carry a flag that makes their result invalid."""
+
+    def __init__(self, status):
+        self.status = status
+        bad = (status & B.UNIT_INVALID) != 0
+        flags = np.bitwise_or.reduce((status & B.UNIT_INVALID)[bad]) if bad.any() else 0
+        super().__init__(f"{int(bad.sum())} of {status.size} units flagged invalid (flags 0x{int(flags):02x}); "
+                         "see LSMS_UNIT_* in include/lsmskubo.h")
+
+
+def check_unit_status(status):
+    """Raise UnitStatusError if any unit status word (device or host array) has an invalid flag.
+    LSMS_UNIT_FP64_FALLBACK alone is fine: that unit was re-solved in the FP64 form."""
+    st = status.cpu().numpy() if hasattr(status, "cpu") else np.asarray(status)
+    if np.any(st & B.UNIT_INVALID):
+        raise UnitStatusError(st)
+    return st
+
+
 class Problem:
     """One structure on one CUDA device.
 
@@ -19,11 +39,17 @@ class Problem:
     complex (E_F + i d, E_F - i d per delta), J [n_species, 4, 3, K, K] (host or
     device complex128), volume (bohr^3).  conj_pairs: the (z, conj z) pairs have
     conjugate t^-1, so only z is factored (tau(conj z) = conj tau(z)).
+    check_status: forward() and backward() read the unit status words back and
+    raise UnitStatusError if a unit's result is invalid (a host synchronisation;
+    skipped while a CUDA graph is being captured).  Set it False for timing
+    loops and check with check() afterwards.
     """
 
     def __init__(self, pos, lattice, r_liz, lmax, species, tinv, z, J, volume, precision="fp64", device="cuda",
-                 keep_factors=True, workspace_bytes=None, conj_pairs=False):
+                 keep_factors=True, workspace_bytes=None, conj_pairs=False, check_status=True):
         import torch
+        self.check_status = bool(check_status)
+        self.generation = 0  # number of tau solves so far (the factors in lu_store belong to the latest)
         self.lmax = int(lmax)
         self.K = (self.lmax + 1) ** 2
         self.liz = B.build_liz(pos, lattice, r_liz)
@@ -39,13 +65,15 @@ class Problem:
         self.tinv = torch.as_tensor(tinv).to(device=self.device, dtype=torch.complex128).contiguous()
         self.J = torch.as_tensor(J).to(device=self.device, dtype=torch.complex128).contiguous()
         nE = self.z.shape[0]
-        mn, al = B.tau_workspace_bytes(self.liz, self.lmax, nE, B._prec(precision, self.conj_pairs))
-        ws = al if workspace_bytes is None else max(mn, int(workspace_bytes))
+        self._ws_flags = B.LSMS_WS_STORE if keep_factors else 0
+        prec = B._prec(precision, self.conj_pairs)
+        mn, al = B.tau_workspace_bytes(self.liz, self.lmax, nE, prec | self._ws_flags)
+        ws = al if workspace_bytes is None else min(al, max(mn, int(workspace_bytes)))
         self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
         self.lu_store = None
         if keep_factors:
-            self.lu_store = torch.empty(B.lu_store_bytes(self.liz, self.lmax, nE, B._prec(precision, self.conj_pairs)),
-                                        dtype=torch.uint8, device=self.device)
+            self.lu_store = torch.empty(B.lu_store_bytes(self.liz, self.lmax, nE, prec), dtype=torch.uint8,
+                                        device=self.device)
         self.tau = torch.empty((nE, self.liz.total_sites, self.K, self.K), dtype=torch.complex128,
                                device=self.device)
         self.unit_status = torch.empty((nE, self.liz.n_atoms), dtype=torch.int32, device=self.device)
@@ -65,7 +93,20 @@ class Problem:
         B.tau_blocks(self.liz, self.lmax, self.species, t, self.z, self.precision, tau=self.tau,
                      unit_status=self.unit_status, workspace=self.workspace, lu_store=self.lu_store, stream=stream,
                      conj_pairs=self.conj_pairs)
+        self.generation += 1
+        self._maybe_check(self.unit_status)
         return self.tau
+
+    def _maybe_check(self, status):
+        import torch
+        if self.check_status and not torch.cuda.is_current_stream_capturing():
+            check_unit_status(status)
+
+    def check(self):
+        """Raise UnitStatusError if the last forward or backward left an invalid unit."""
+        check_unit_status(self.unit_status)
+        if self._bw_ws is not None:
+            check_unit_status(self.bw_status)
 
     def sigma(self, stream=None):
         B.kubo_sigma(self.liz, self.lmax, self.species, self.J, self.tau, self.n_delta, self.volume,
@@ -88,14 +129,37 @@ class Problem:
         import torch
         if self._bw_ws is None:
             mn, al = B.backward_workspace_bytes(self.liz, self.lmax, self.z.shape[0],
-                                                B._prec(self.precision, self.conj_pairs))
+                                                B._prec(self.precision, self.conj_pairs) | self._ws_flags)
             self._bw_ws = torch.empty(min(al, max(mn, self.workspace.numel())), dtype=torch.uint8,
                                       device=self.device)
         t = self.tinv if tinv is None else tinv
-        return B.kubo_sigma_backward(self.liz, self.lmax, self.species, t, self.z, self.J, self.tau, self.volume,
-                                     grad_sigma.contiguous(), self.precision, lu_store=self.lu_store,
-                                     unit_status=self.bw_status, workspace=self._bw_ws, stream=stream,
-                                     conj_pairs=self.conj_pairs)
+        out = B.kubo_sigma_backward(self.liz, self.lmax, self.species, t, self.z, self.J, self.tau, self.volume,
+                                    grad_sigma.contiguous(), self.precision, lu_store=self.lu_store,
+                                    unit_status=self.bw_status, workspace=self._bw_ws, stream=stream,
+                                    conj_pairs=self.conj_pairs)
+        self._maybe_check(self.bw_status)
+        return out
+
+    def backward_detached(self, grad_sigma, tinv):
+        """The gradient for an earlier forward whose tau and factors have since been overwritten:
+        tau is solved again for `tinv` into private buffers and the factors are recomputed (no store)."""
+        import torch
+        nE = self.z.shape[0]
+        prec = B._prec(self.precision, self.conj_pairs)
+        mn, al = B.tau_workspace_bytes(self.liz, self.lmax, nE, prec)
+        ws = torch.empty(min(al, max(mn, self.workspace.numel())), dtype=torch.uint8, device=self.device)
+        tau, st = B.tau_blocks(self.liz, self.lmax, self.species, tinv, self.z, self.precision, workspace=ws,
+                               conj_pairs=self.conj_pairs)
+        self._maybe_check(st)
+        del ws
+        mn, al = B.backward_workspace_bytes(self.liz, self.lmax, nE, prec)
+        bws = torch.empty(min(al, max(mn, self.workspace.numel())), dtype=torch.uint8, device=self.device)
+        bst = torch.empty_like(self.bw_status)
+        out = B.kubo_sigma_backward(self.liz, self.lmax, self.species, tinv, self.z, self.J, tau, self.volume,
+                                    grad_sigma.contiguous(), self.precision, lu_store=None, unit_status=bst,
+                                    workspace=bws, conj_pairs=self.conj_pairs)
+        self._maybe_check(bst)
+        return out
 
 
 def _step(problem, grad_sigma, tinv=None):
@@ -125,16 +189,23 @@ def _sigma_fn():
 
         @staticmethod
         def forward(ctx, tinv, problem):
-            s = problem.forward(tinv.detach().contiguous())
+            t = tinv.detach().contiguous()
+            s = problem.forward(t)
             ctx.problem = problem
-            ctx.save_for_backward(tinv)
+            ctx.generation = problem.generation  # the factors and tau of this forward
+            ctx.save_for_backward(t)
             return s.clone()
 
         @staticmethod
         def backward(ctx, grad_sigma):
             (tinv,) = ctx.saved_tensors
-            _, g_species = ctx.problem.backward(grad_sigma.to(torch.complex128), tinv.detach().contiguous())
-            return g_species, None
+            p = ctx.problem
+            gs = grad_sigma.to(torch.complex128).contiguous()
+            if p.generation == ctx.generation:
+                _, g_species = p.backward(gs, tinv)
+            else:  # a later forward overwrote this one's tau and factors: solve again for the saved tinv
+                _, g_species = p.backward_detached(gs, tinv)
+            return g_species.clone(), None
 
     return SigmaFn
 
@@ -152,7 +223,7 @@ def sigma_autograd(tinv, problem):
 def conductivity(pos, lattice, r_liz, lmax, species, tinv, z, J, volume, precision="fp64"):
     """Host-to-host conductivity: returns (sigma [n_delta,3,3] complex128, rho [n_delta,3,3]) as NumPy."""
     p = Problem(pos, lattice, r_liz, lmax, species, tinv, z, J, volume, precision=precision, keep_factors=False)
-    p.forward()
+    p.forward()  # raises UnitStatusError if a unit's result is invalid
     return p.sigma_out.cpu().numpy(), p.rho.cpu().numpy()
 
 

@@ -65,6 +65,9 @@ int kubo_forward(const int64_t* offsets, const int32_t* site_atom, const int32_t
                  double volume, bool df, float4* jdf, double2* partial, double2* S, double2* sigma_tilde,
                  double2* sigma, double* rho, cudaStream_t st);
 size_t jdf_scratch_bytes(int n_species, int K, int n_delta, int64_t J_dstride);
+int kubo_atoms(const int64_t* offsets, const int32_t* site_atom, const int32_t* species, int n_species,
+               const double2* J, int64_t J_dstride, const double2* tau, int64_t S_total, int K, int n_atoms,
+               int n_delta, double volume, bool df, float4* jdf, double2* out, cudaStream_t st);
 int adj_abar(const int32_t* species, int n_species, const double2* J, int64_t J_dstride, const double2* w, int K,
              double volume, int n_atoms, int n_delta, double2* abar, float4* abar_df, cudaStream_t st);
 int split_j(const double2* J, int64_t J_dstride, int n_species, int K, int n_delta, float4* out, int64_t* out_dstride,
@@ -82,6 +85,15 @@ int adj_species(const int32_t* species, const double2* grad, int K, int n_atoms,
 
 constexpr int kIrMaxIter = 6;
 constexpr double kIrTol = 1e-10;
+
+// Process-wide options (lsms_set_option / lsms_get_option).
+static std::atomic<double> g_opt_growth_limit{1e3};
+static std::atomic<int> g_opt_fallback_slots{8};
+static std::atomic<int> g_opt_ir_max_sweeps{kIrMaxIter};
+static std::atomic<int> g_opt_streams{0};  // 0: LSMS_STREAMS or the default
+double opt_growth_limit() { return g_opt_growth_limit.load(); }
+int opt_fallback_slots() { return g_opt_fallback_slots.load(); }
+int opt_ir_max_sweeps() { return g_opt_ir_max_sweeps.load(); }
 constexpr int kProbe = 2;  // random combinations of the right-hand sides in the convergence probe
 constexpr size_t kAlign = 256;
 static inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -202,7 +214,8 @@ static UnitBytes unit_bytes(int n, int precision, int nrhs, bool backward) {
   const size_t nn = (size_t)n * n;
   ub.fac = align_up(nn * (precision == LSMS_FP64 ? 16 : 8));
   ub.piv = align_up((size_t)n * 4);  // pivots (row interchanged with row i at step i)
-  ub.m64 = precision == LSMS_FP64 ? 0 : (size_t)(diag_inv_rel_off(n) + diag_inv_bytes(n));  // + diagonal-block inverses
+  // double-float M + diagonal-block inverses + pivot-growth record
+  ub.m64 = precision == LSMS_FP64 ? 0 : (size_t)(growth_rel_off(n) + kGrowthBytes);
   ub.x = align_up((size_t)n * nrhs * 16);
   ub.b = backward ? align_up((size_t)n * nrhs * 16) : 0;
   // complex64 corrections; the convergence probe uses the first kProbe columns
@@ -242,18 +255,45 @@ static std::vector<int> atom_order(const lsms_liz* liz) {
   return order;
 }
 
+// FP64 fallback of the mixed form: `slots` FP64 re-solves, each sized for the
+// largest LIZ matrix (factors, pivots, solution, and for the adjoint its
+// right-hand sides), plus the slot table and the slot count.
+struct FbLayout {
+  int slots = 0;
+  size_t fac = 0, piv = 0, x = 0, b = 0, slot = 0;
+  size_t units_off = 0, count_off = 0, region_off = 0, total = 0;
+};
+
+static FbLayout fb_layout(const lsms_liz* liz, int lmax, int precision, int nrhs, bool backward) {
+  FbLayout f;
+  f.slots = precision == LSMS_MIXED ? std::max(opt_fallback_slots(), 0) : 0;
+  if (!f.slots) return f;
+  const size_t n = (size_t)(lmax + 1) * (lmax + 1) * liz->max_sites;
+  f.fac = align_up(n * n * 16);
+  f.piv = align_up(n * 4);
+  f.x = align_up(n * nrhs * 16);
+  f.b = backward ? f.x : 0;
+  f.slot = f.fac + f.piv + f.x + f.b;
+  f.units_off = 0;
+  f.count_off = align_up((size_t)f.slots * sizeof(Unit));
+  f.region_off = f.count_off + kAlign;
+  f.total = f.region_off + (size_t)f.slots * f.slot;
+  return f;
+}
+
 struct WsHeader {
-  size_t stat, done, extra, chunk;  // byte offsets
+  size_t stat, done, extra, fb, chunk;  // byte offsets
   size_t total_fixed;
 };
 
-static WsHeader ws_header(const lsms_liz* liz, int n_energy, size_t extra_bytes) {
+static WsHeader ws_header(const lsms_liz* liz, int n_energy, size_t extra_bytes, size_t fb_bytes) {
   WsHeader h{};
   const size_t nu = (size_t)liz->n_atoms * n_energy;
   h.stat = 0;
   h.done = align_up(nu * 4);
   h.extra = h.done + align_up(nu * 4);
-  h.chunk = h.extra + align_up(extra_bytes);
+  h.fb = h.extra + align_up(extra_bytes);
+  h.chunk = h.fb + align_up(fb_bytes);
   h.total_fixed = h.chunk;
   return h;
 }
@@ -498,8 +538,15 @@ __device__ void hankel6_df(double d, double2 kap, double2 mpref, bool adv, float
   }
 }
 
+// Tolerance of the complex-symmetry check of the t^{-1} blocks (relative to the
+// block's largest entry, |.| = |Re| + |Im|).
+constexpr double kSymTol = 1e-12;
+
 // grid (S_max, atoms in the chunk), block 256: one CTA per row site p of one
-// atom's LIZ, for all energies of that atom.  Per round of 16 column sites q:
+// atom's LIZ, for all energies of that atom.  First, the t^{-1} block of site p
+// is checked for complex symmetry at every energy (M^T = M is what makes the
+// row block tau^{0n} = (tau^{n0})^T); a block that is not symmetric to kSymTol
+// flags the unit LSMS_UNIT_TINV_ASYM.  Per round of 16 column sites q:
 // 16 lanes compute Y_L(R^) (shared by the energies), 32 lanes compute
 // V[L''] = mpref h_l''(kappa R) Y_L''(R^) for 2 energies, then thread (L, L')
 // forms sum_L'' s C_{LL'L''} V[L''] for those blocks (diagonal blocks: t^{-1}).
@@ -507,7 +554,8 @@ __device__ void hankel6_df(double d, double2 kap, double2 mpref, bool adv, float
 // Mixed form: the sums in double-float arithmetic on the FP32 pipes (FP64
 // accuracy); writes M as (hi, lo) float pairs (float4 per element, at
 // fac_base + m64_off) for the refinement residual and, if write_fac, the hi part
-// (complex64) as the matrix to factor.
+// (complex64) as the matrix to factor; the largest |M| entry goes into the
+// unit's pivot-growth record.
 template <bool MIXED>
 __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ units, int nE,
                                                   const double* __restrict__ disp,
@@ -550,6 +598,25 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
     bad = LSMS_UNIT_BAD_INPUT;
     spp = 0;
   }
+  // complex symmetry of the t^{-1} block of site p, per energy of this atom
+  __shared__ unsigned int s_dmax[kMaxEnergies], s_amax[kMaxEnergies];
+  for (int i = tid; i < nE; i += blockDim.x) s_dmax[i] = s_amax[i] = 0u;
+  __syncthreads();
+  for (int ee = 0; ee < nE; ++ee) {
+    float dv = 0.f, av = 0.f;
+    if (act) {
+      const double2* tb = tinv + (((size_t)spp * n_energy) + ua[ee].energy) * K * K;
+      const double2 a = tb[L * K + Lp], b = tb[Lp * K + L];
+      dv = (float)(fabs(a.x - b.x) + fabs(a.y - b.y));
+      av = (float)cabs1(a);
+    }
+    dv = warp_max_nonneg(dv);
+    av = warp_max_nonneg(av);
+    if ((tid & 31) == 0) {
+      atomicMax(&s_dmax[ee], __float_as_uint(dv));
+      atomicMax(&s_amax[ee], __float_as_uint(av));
+    }
+  }
   __syncthreads();
   int t0 = 0, t1 = 0;
   if (act) {
@@ -558,9 +625,15 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
   }
   for (int e0 = 0; e0 < nE; e0 += kAsmE) {
     int flags[kAsmE];
-#pragma unroll
-    for (int ee = 0; ee < kAsmE; ++ee) flags[ee] = bad;
+    float mmax[kAsmE];  // mixed form: largest |M| entry written, per energy
     const int ne = min(kAsmE, nE - e0);
+#pragma unroll
+    for (int ee = 0; ee < kAsmE; ++ee) {
+      flags[ee] = bad;
+      mmax[ee] = 0.f;
+      if (ee < ne && !(__uint_as_float(s_dmax[e0 + ee]) <= (float)kSymTol * __uint_as_float(s_amax[e0 + ee])))
+        flags[ee] |= LSMS_UNIT_TINV_ASYM;
+    }
     for (int q0 = 0; q0 < S; q0 += kAsmQ) {
       const int nq = min(kAsmQ, S - q0);
       __syncthreads();
@@ -634,6 +707,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
               v4 = df_value(acc);
             }
             if (!(isfinite(v4.x) && isfinite(v4.z))) flags[ee] |= LSMS_UNIT_NONFINITE;
+            mmax[ee] = fmaxf(mmax[ee], fabsf(v4.x) + fabsf(v4.z));
             reinterpret_cast<float4*>(fac_base + u.m64_off)[idx] = make_float4(v4.x, v4.z, v4.y, v4.w);
             if (write_fac) reinterpret_cast<float2*>(fac_base + u.fac_off)[idx] = make_float2(v4.x, v4.z);
           } else {
@@ -656,9 +730,40 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
         }
       }
     }
-    for (int ee = 0; ee < ne; ++ee)
+    for (int ee = 0; ee < ne; ++ee) {
       if (flags[ee]) atomicOr(&stat[ua[e0 + ee].stat_off], flags[ee]);
+      if (MIXED) {
+        const float wm = warp_max_nonneg(mmax[ee]);
+        const Unit& u = ua[e0 + ee];
+        if ((tid & 31) == 0) atomic_max_nonneg(reinterpret_cast<float*>(fac_base + u.m64_off + growth_rel_off(u.n)), wm);
+      }
+    }
   }
+}
+
+// Zero the pivot-growth records of the units (before k_assemble).  One thread per unit.
+__global__ void k_growth_init(const Unit* __restrict__ units, int n_units, char* fac_base) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_units) return;
+  const Unit u = units[i];
+  float* g = reinterpret_cast<float*>(fac_base + u.m64_off + growth_rel_off(u.n));
+  g[0] = 0.f;
+  g[1] = 0.f;
+}
+
+// Pivot growth of the complex64 factorization: LSMS_UNIT_GROWTH when
+// max |U| > limit * max |M| (|.| = |Re| + |Im|).  With partial pivoting the
+// growth stays near 1 on well-posed LIZ matrices; a large value means the
+// complex64 factors may be too inaccurate for the refinement to recover FP64
+// accuracy, and the unit is re-solved in the FP64 form.  One thread per unit.
+__global__ void k_growth_check(const Unit* __restrict__ units, int n_units, const char* fac_base, float limit,
+                               int32_t* stat) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_units) return;
+  const Unit u = units[i];
+  const float* g = reinterpret_cast<const float*>(fac_base + u.m64_off + growth_rel_off(u.n));
+  // a non-finite M is flagged by the assembly; a finite M with a non-finite factor is growth
+  if (isfinite(g[0]) && !(g[1] <= limit * g[0])) atomicOr(&stat[u.stat_off], LSMS_UNIT_GROWTH);
 }
 
 // ------------------------------------------------------------------ RHS / refinement kernels
@@ -1116,6 +1221,58 @@ __global__ void k_conj_block(const Unit* __restrict__ units, char* ws, int nrhs,
     X[idx].y = -X[idx].y;
 }
 
+// ------------------------------------------------------------------ FP64 fallback (mixed form)
+// Flags after which a mixed-form unit is re-solved in the FP64 form: a zero
+// pivot or pivot growth in the complex64 factors, a refinement that did not
+// converge, or a tensor-core wait that gave up.
+constexpr int32_t kRetryFlags = LSMS_UNIT_ZERO_PIVOT | LSMS_UNIT_NOCONV | LSMS_UNIT_GROWTH | LSMS_UNIT_TIMEOUT;
+
+// One warp: the first `slots` units (plan order) carrying a retry flag get a
+// fallback slot; their retry flags are cleared and LSMS_UNIT_FP64_FALLBACK set
+// (the FP64 kernels then flag whatever they find themselves).  Slot s factors
+// at region + s * slot_bytes; unused slots get n = 0 (every kernel skips them).
+// *count = the number of units that were given a slot; units beyond the slots
+// keep their flags.
+__global__ void __launch_bounds__(32) k_fb_select(const Unit* __restrict__ units, int n_units, int32_t* stat,
+                                                  int slots, int64_t slot_bytes, int64_t off_piv, int64_t off_x,
+                                                  int64_t off_b, Unit* __restrict__ fb, int32_t* count) {
+  const int lane = threadIdx.x;
+  int cnt = 0;
+  for (int i0 = 0; i0 < n_units && cnt < slots; i0 += 32) {
+    const int i = i0 + lane;
+    Unit u{};
+    bool f = false;
+    if (i < n_units) {
+      u = units[i];
+      f = (stat[u.stat_off] & kRetryFlags) != 0;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, f);
+    const int pos = cnt + __popc(b & ((1u << lane) - 1u));
+    if (f && pos < slots) {
+      Unit v{};
+      v.atom = u.atom;
+      v.energy = u.energy;
+      v.n = u.n;
+      v.S = u.S;
+      v.site_off = u.site_off;
+      v.stat_off = u.stat_off;
+      v.fac_off = (int64_t)pos * slot_bytes;
+      v.piv_off = v.fac_off + off_piv;
+      v.x_off = v.fac_off + off_x;
+      v.r_off = v.fac_off + off_b;
+      fb[pos] = v;
+      stat[u.stat_off] = (stat[u.stat_off] & ~kRetryFlags) | LSMS_UNIT_FP64_FALLBACK;
+    }
+    cnt += __popc(b);
+  }
+  const int used = min(cnt, slots);
+  for (int s2 = used + lane; s2 < slots; s2 += 32) {
+    Unit v{};
+    fb[s2] = v;  // n = 0, S = 0: skipped
+  }
+  if (lane == 0) *count = used;
+}
+
 // ------------------------------------------------------------------ shared driver
 struct Call {
   lsms_liz* liz;
@@ -1150,9 +1307,14 @@ static int assemble_factor(const Call& c, const Plan& p, const Chunk& ch, char* 
                 c.dd->site_atom, c.species, c.tinv, c.n_species, c.n_energy, c.E, c.K, fac_base, ws, true, stat);
     return lu_factor_chunk<double>(du, nu, ch.n_max, fac_base, stat, c.st);
   }
+  const dim3 gu((nu + 255) / 256);
+  LSMS_LAUNCH(k_growth_init, gu, dim3(256), 0, c.st, du, nu, fac_base);
   LSMS_LAUNCH(k_assemble<true>, dim3(S_max, n_at), dim3(256), 0, c.st, du, p.fac_per_atom, c.dd->disp,
               c.dd->site_atom, c.species, c.tinv, c.n_species, c.n_energy, c.E, c.K, fac_base, ws, true, stat);
-  return lu_factor_chunk<float>(du, nu, ch.n_max, fac_base, stat, c.st);
+  const int rc = lu_factor_chunk<float>(du, nu, ch.n_max, fac_base, stat, c.st);
+  if (rc) return rc;
+  LSMS_LAUNCH(k_growth_check, gu, dim3(256), 0, c.st, du, nu, fac_base, (float)opt_growth_limit(), stat);
+  return LSMS_OK;
 }
 
 // Solve M X = B for a chunk whose factors exist.  B = E0 (forward) or the explicit
@@ -1174,7 +1336,8 @@ static int solve_refine(const Call& c, const Plan& p, const Chunk& ch, const cha
   if ((rc = lu_solve_chunk<float>(du, nu, fac_base, ws, RHS_X32, nrhs, nullptr, c.st))) return rc;
   LSMS_LAUNCH(k_widen, g1, dim3(256), 0, c.st, du, ws, nrhs);
   // done flags of this chunk's units start cleared (memset by the caller)
-  for (int it = 0; it < kIrMaxIter; ++it) {
+  const int max_sweeps = opt_ir_max_sweeps();
+  for (int it = 0; it < max_sweeps; ++it) {
     const dim3 gr((ch.n_max + 63) / 64, nu);
     switch (nrhs) {  // K or 2K for lmax = 0..3
 #define LSMS_RESID(NR)                                                                                 \
@@ -1199,6 +1362,53 @@ static int solve_refine(const Call& c, const Plan& p, const Chunk& ch, const cha
   return LSMS_OK;
 }
 
+// Arguments of the adjoint right-hand sides and site products (backward only).
+struct AdjArgs {
+  const double2* J;
+  int64_t J_dstride;
+  const double2* tau;
+  const double2* abar;
+  int n_delta;
+  double2* G;
+};
+
+// Re-solve in the FP64 form, on the GPU, the mixed-form units flagged with
+// kRetryFlags (at most f.slots of them, in plan order): assemble M in FP64,
+// factor, solve, and overwrite that unit's tau blocks (forward, adj == NULL) or
+// its per-site gradient blocks (backward).  Runs on c.st after every chunk.
+static int fallback_resolve(const Call& c, const Plan& p, char* ws, const WsHeader& h, const FbLayout& f,
+                            int32_t* stat, double2* tau_out, const AdjArgs* adj) {
+  if (!f.slots || p.units.empty()) return LSMS_OK;
+  Unit* fbu = reinterpret_cast<Unit*>(ws + h.fb + f.units_off);
+  int32_t* cnt = reinterpret_cast<int32_t*>(ws + h.fb + f.count_off);
+  char* region = ws + h.fb + f.region_off;
+  int n_max = 0;
+  for (const Chunk& ch : p.chunks) n_max = std::max(n_max, ch.n_max);
+  const int S_max = n_max / c.K;
+  const int slots = f.slots;
+  const int nrhs = p.nrhs;
+  LSMS_LAUNCH(k_fb_select, dim3(1), dim3(32), 0, c.st, p.d_units, (int)p.units.size(), stat, slots,
+              (int64_t)f.slot, (int64_t)f.fac, (int64_t)(f.fac + f.piv), (int64_t)(f.fac + f.piv + f.x), fbu, cnt);
+  LSMS_LAUNCH(k_assemble<false>, dim3(S_max, slots), dim3(256), 0, c.st, fbu, 1, c.dd->disp, c.dd->site_atom,
+              c.species, c.tinv, c.n_species, c.n_energy, c.E, c.K, region, region, true, stat);
+  int rc = lu_factor_chunk<double>(fbu, slots, n_max, region, stat, c.st);
+  if (rc) return rc;
+  const dim3 g1((n_max * nrhs + 255) / 256, slots);
+  if (!adj) {
+    LSMS_LAUNCH(k_rhs_identity<double2>, g1, dim3(256), 0, c.st, fbu, region, (int)RHS_X, c.K, nrhs);
+    if ((rc = lu_solve_chunk<double>(fbu, slots, region, region, RHS_X, nrhs, nullptr, c.st))) return rc;
+    LSMS_LAUNCH(k_write_tau, dim3(S_max, slots), dim3(256), 0, c.st, fbu, region, c.K, c.liz->total_sites, c.conj,
+                tau_out);
+    return LSMS_OK;
+  }
+  if ((rc = adj_rhs(fbu, slots, S_max, c.dd->site_atom, c.species, c.n_species, adj->J, adj->J_dstride, adj->tau,
+                    c.liz->total_sites, adj->abar, nullptr, 0, nullptr, adj->n_delta, c.K, region, false, c.st)))
+    return rc;
+  LSMS_LAUNCH(k_copy_b, g1, dim3(256), 0, c.st, fbu, region, nrhs, false);
+  if ((rc = lu_solve_chunk<double>(fbu, slots, region, region, RHS_X, nrhs, nullptr, c.st))) return rc;
+  return adj_site(fbu, slots, S_max, adj->tau, c.liz->total_sites, c.K, region, adj->G, false, c.st);
+}
+
 // Conjugate-pair mode: n_energy even and z[2d + 1] = conj z[2d] exactly.
 static int check_conj_energies(const lsms_complex* z, int n_energy) {
   if (n_energy & 1) return fail(LSMS_ERR_ARG, "LSMS_CONJ_PAIRS needs an even n_energy");
@@ -1221,14 +1431,16 @@ struct SideStreams {
   cudaEvent_t fork = nullptr, join[kMaxParts - 1] = {};
 };
 
-// Number of concurrent parts per chunk (environment LSMS_STREAMS, 1..4; default 4).
+// Number of concurrent parts per chunk: the "streams" option if set, else the
+// environment variable LSMS_STREAMS (1..4, read once), else 4.
 static int stream_parts() {
-  static const int parts = [] {
+  static const int env_parts = [] {
     const char* e = std::getenv("LSMS_STREAMS");
     const int v = e ? std::atoi(e) : 4;
     return std::min(std::max(v, 1), kMaxParts);
   }();
-  return parts;
+  const int o = g_opt_streams.load();
+  return o > 0 ? std::min(o, kMaxParts) : env_parts;
 }
 
 static int side_streams(SideStreams** out) {
@@ -1306,6 +1518,41 @@ using namespace lsms;
 // ------------------------------------------------------------------ C ABI
 extern "C" long long lsms_launch_count(void) { return g_launches.load(); }
 
+extern "C" int lsms_set_option(const char* name, double value) {
+  clear_error();
+  if (!name) return fail(LSMS_ERR_ARG, "lsms_set_option: NULL name");
+  const std::string n(name);
+  auto in_int = [&](double lo, double hi) { return value >= lo && value <= hi && value == std::floor(value); };
+  if (n == "growth_limit") {
+    if (!(value > 0.0) || !std::isfinite(value)) return fail(LSMS_ERR_ARG, "growth_limit must be finite and > 0");
+    g_opt_growth_limit.store(value);
+  } else if (n == "fallback_slots") {
+    if (!in_int(0, 4096)) return fail(LSMS_ERR_ARG, "fallback_slots must be an integer in 0..4096");
+    g_opt_fallback_slots.store((int)value);
+  } else if (n == "ir_max_sweeps") {
+    if (!in_int(0, 64)) return fail(LSMS_ERR_ARG, "ir_max_sweeps must be an integer in 0..64");
+    g_opt_ir_max_sweeps.store((int)value);
+  } else if (n == "streams") {
+    if (!in_int(0, kMaxParts)) return fail(LSMS_ERR_ARG, "streams must be an integer in 0..%d", kMaxParts);
+    g_opt_streams.store((int)value);
+  } else {
+    return fail(LSMS_ERR_ARG, "lsms_set_option: unknown option '%s'", name);
+  }
+  return LSMS_OK;
+}
+
+extern "C" int lsms_get_option(const char* name, double* value) {
+  clear_error();
+  if (!name || !value) return fail(LSMS_ERR_ARG, "lsms_get_option: NULL argument");
+  const std::string n(name);
+  if (n == "growth_limit") *value = g_opt_growth_limit.load();
+  else if (n == "fallback_slots") *value = g_opt_fallback_slots.load();
+  else if (n == "ir_max_sweeps") *value = g_opt_ir_max_sweeps.load();
+  else if (n == "streams") *value = stream_parts();
+  else return fail(LSMS_ERR_ARG, "lsms_get_option: unknown option '%s'", name);
+  return LSMS_OK;
+}
+
 extern "C" int lsms_kernel_timer_enable(int on) {
   clear_error();
   std::lock_guard<std::mutex> lk(g_timer_mu);
@@ -1356,7 +1603,7 @@ extern "C" void lsms_liz_destroy(lsms_liz* liz) {
 // Workspace of one atom's units (factors in the workspace, i.e. no store):
 // largest over atoms and total.
 static size_t unit_ws_max_sum(const lsms_liz* liz, int lmax, int n_energy, int precision, int nrhs, bool backward,
-                              bool conj, size_t* sum) {
+                              bool conj, bool store, size_t* sum) {
   const int K = (lmax + 1) * (lmax + 1);
   std::vector<int> es;
   std::vector<char> owns;
@@ -1366,7 +1613,7 @@ static size_t unit_ws_max_sum(const lsms_liz* liz, int lmax, int n_energy, int p
     const int n = K * (int)(liz->offsets[m + 1] - liz->offsets[m]);
     const UnitBytes ub = unit_bytes(n, precision, nrhs, backward);
     size_t b = 0;
-    for (size_t i = 0; i < es.size(); ++i) b += ws_unit_bytes(ub, owns[i]);
+    for (size_t i = 0; i < es.size(); ++i) b += ws_unit_bytes(ub, owns[i] && !store);
     mx = std::max(mx, b);
     s += b;
   }
@@ -1380,19 +1627,25 @@ static bool split_precision(int precision, int* base, bool* conj) {
   *conj = (precision & LSMS_CONJ_PAIRS) != 0;
   return *base == LSMS_FP64 || *base == LSMS_MIXED;
 }
+// The workspace-size functions also take LSMS_WS_STORE (factors kept in lu_store).
+static bool split_precision_ws(int precision, int* base, bool* conj, bool* store) {
+  *store = (precision & LSMS_WS_STORE) != 0;
+  return split_precision(precision & ~LSMS_WS_STORE, base, conj);
+}
 
 extern "C" int lsms_tau_workspace_bytes(const lsms_liz* liz, int lmax, int n_energy, int precision, size_t* min_bytes,
                                         size_t* all_bytes) {
   clear_error();
   int base;
-  bool conj;
+  bool conj, store;
   if (!liz || lmax < 0 || lmax > kMaxLmax || n_energy < 1 || n_energy > kMaxEnergies ||
-      !split_precision(precision, &base, &conj) || (conj && (n_energy & 1)))
+      !split_precision_ws(precision, &base, &conj, &store) || (conj && (n_energy & 1)))
     return fail(LSMS_ERR_ARG, "lsms_tau_workspace_bytes: bad arguments");
   const int K = (lmax + 1) * (lmax + 1);
   size_t sum = 0;
-  const size_t mx = unit_ws_max_sum(liz, lmax, n_energy, base, K, false, conj, &sum);
-  const WsHeader h = ws_header(liz, n_energy, conj_extra_bytes(n_energy));
+  const size_t mx = unit_ws_max_sum(liz, lmax, n_energy, base, K, false, conj, store, &sum);
+  const WsHeader h =
+      ws_header(liz, n_energy, conj_extra_bytes(n_energy), fb_layout(liz, lmax, base, K, false).total);
   if (min_bytes) *min_bytes = h.total_fixed + mx;
   if (all_bytes) *all_bytes = h.total_fixed + sum;
   return LSMS_OK;
@@ -1402,14 +1655,15 @@ extern "C" int lsms_backward_workspace_bytes(const lsms_liz* liz, int lmax, int 
                                              size_t* min_bytes, size_t* all_bytes) {
   clear_error();
   int base;
-  bool conj;
+  bool conj, store;
   if (!liz || lmax < 0 || lmax > kMaxLmax || n_energy < 2 || n_energy > kMaxEnergies || (n_energy & 1) ||
-      !split_precision(precision, &base, &conj))
+      !split_precision_ws(precision, &base, &conj, &store))
     return fail(LSMS_ERR_ARG, "lsms_backward_workspace_bytes: bad arguments");
   const int K = (lmax + 1) * (lmax + 1);
   size_t sum = 0;
-  const size_t mx = unit_ws_max_sum(liz, lmax, n_energy, base, 2 * K, true, conj, &sum);
-  const WsHeader h = ws_header(liz, n_energy, backward_extra_bytes(liz, lmax, n_energy) + conj_extra_bytes(n_energy));
+  const size_t mx = unit_ws_max_sum(liz, lmax, n_energy, base, 2 * K, true, conj, store, &sum);
+  const WsHeader h = ws_header(liz, n_energy, backward_extra_bytes(liz, lmax, n_energy) + conj_extra_bytes(n_energy),
+                               fb_layout(liz, lmax, base, 2 * K, true).total);
   if (min_bytes) *min_bytes = h.total_fixed + mx;
   if (all_bytes) *all_bytes = h.total_fixed + sum;
   return LSMS_OK;
@@ -1471,8 +1725,9 @@ extern "C" int lsms_tau_blocks(const lsms_liz* liz_c, int lmax, const int32_t* s
   }
   const bool store = lu_store != nullptr;
   size_t min_b = 0, all_b = 0;
-  lsms_tau_workspace_bytes(liz, lmax, n_energy, precision, &min_b, &all_b);
-  const WsHeader h = ws_header(liz, n_energy, conj_extra_bytes(n_energy));
+  lsms_tau_workspace_bytes(liz, lmax, n_energy, precision | (store ? LSMS_WS_STORE : 0), &min_b, &all_b);
+  const FbLayout fb = fb_layout(liz, lmax, base, c.K, false);
+  const WsHeader h = ws_header(liz, n_energy, conj_extra_bytes(n_energy), fb.total);
   char* ws = static_cast<char*>(workspace);
   bool own = false;
   size_t ws_bytes = workspace_bytes;
@@ -1517,6 +1772,10 @@ extern "C" int lsms_tau_blocks(const lsms_liz* liz_c, int lmax, const int32_t* s
       });
       if (r2) return r2;
     }
+    if (base == LSMS_MIXED) {
+      const int r2 = fallback_resolve(c, *p, ws, h, fb, stat, reinterpret_cast<double2*>(tau), nullptr);
+      if (r2) return r2;
+    }
     if (unit_status) {
       LSMS_LAUNCH(k_status_out, dim3((unsigned)((nu_all + 255) / 256)), dim3(256), 0, c.st, stat, (int)nu_all,
                   unit_status);
@@ -1556,6 +1815,32 @@ extern "C" int lsms_kubo_sigma(const lsms_liz* liz_c, int lmax, const int32_t* s
                     reinterpret_cast<double2*>(scratch), reinterpret_cast<double2*>(scratch + part_bytes),
                     reinterpret_cast<double2*>(sigma_tilde), reinterpret_cast<double2*>(sigma), rho, st);
   cudaFreeAsync(scratch, st);
+  return rc;
+}
+
+extern "C" int lsms_kubo_sigma_atoms(const lsms_liz* liz_c, int lmax, const int32_t* species, int n_species,
+                                     const lsms_complex* J, int64_t J_delta_stride, const lsms_complex* tau,
+                                     int n_delta, double volume, int precision, lsms_complex* sigma_tilde_atoms,
+                                     void* stream) {
+  clear_error();
+  lsms_liz* liz = const_cast<lsms_liz*>(liz_c);
+  int rc = check_common(liz, lmax, species, n_species, 2 * std::max(n_delta, 1), precision);
+  if (rc) return rc;
+  if (n_delta < 1 || !J || !tau || !sigma_tilde_atoms)
+    return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_atoms: J, tau, sigma_tilde_atoms required, n_delta >= 1");
+  if (!(volume > 0.0) || !std::isfinite(volume)) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_atoms: volume must be > 0");
+  if (J_delta_stride < 0) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma_atoms: negative J stride");
+  DeviceData* dd = nullptr;
+  if ((rc = device_data(liz, &dd))) return rc;
+  const int K = (lmax + 1) * (lmax + 1);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  float4* jdf = nullptr;
+  if (precision == LSMS_MIXED)
+    LSMS_CUDA_TRY(cudaMallocAsync((void**)&jdf, jdf_scratch_bytes(n_species, K, n_delta, J_delta_stride), st));
+  rc = kubo_atoms(dd->offsets, dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J), J_delta_stride,
+                  reinterpret_cast<const double2*>(tau), liz->total_sites, K, liz->n_atoms, n_delta, volume,
+                  precision == LSMS_MIXED, jdf, reinterpret_cast<double2*>(sigma_tilde_atoms), st);
+  if (jdf) cudaFreeAsync(jdf, st);
   return rc;
 }
 
@@ -1600,8 +1885,10 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
   const int n_delta = n_energy / 2;
   const size_t KK = (size_t)c.K * c.K;
   size_t min_b = 0, all_b = 0;
-  lsms_backward_workspace_bytes(liz, lmax, n_energy, precision, &min_b, &all_b);
-  const WsHeader h = ws_header(liz, n_energy, backward_extra_bytes(liz, lmax, n_energy) + conj_extra_bytes(n_energy));
+  lsms_backward_workspace_bytes(liz, lmax, n_energy, precision | (store ? LSMS_WS_STORE : 0), &min_b, &all_b);
+  const FbLayout fb = fb_layout(liz, lmax, base, 2 * c.K, true);
+  const WsHeader h = ws_header(liz, n_energy, backward_extra_bytes(liz, lmax, n_energy) + conj_extra_bytes(n_energy),
+                               fb.total);
   char* ws = static_cast<char*>(workspace);
   bool own = false;
   size_t ws_bytes = workspace_bytes;
@@ -1663,8 +1950,14 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
         const int nu = ch.u1 - ch.u0;
         const int S_max = ch.n_max / c.K;
         int r3;
-        // stored factors come with the double-float copy of M (mixed form): nothing to rebuild
+        // stored factors come with the double-float copy of M (mixed form): nothing to rebuild,
+        // but their pivot-growth record is checked again for this call's status
         if (!store && (r3 = assemble_factor(cs, *p, ch, fac_base, chunk, stat))) return r3;
+        if (store && df) {
+          const int nf = ch.f1 - ch.f0;
+          LSMS_LAUNCH(k_growth_check, dim3((nf + 255) / 256), dim3(256), 0, st, p->d_fac_units + ch.f0, nf, fac_base,
+                      (float)opt_growth_limit(), stat);
+        }
         if ((r3 = adj_rhs(du, nu, S_max, c.dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J),
                           J_delta_stride, reinterpret_cast<const double2*>(tau), liz->total_sites, abar, jdf,
                           jdf_dstride, abar_df, n_delta, c.K, chunk, df, st)))
@@ -1678,6 +1971,11 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
                         precision == LSMS_MIXED, st);
       });
       if (r2) return r2;
+    }
+    if (df) {
+      const AdjArgs aa{reinterpret_cast<const double2*>(J), J_delta_stride, reinterpret_cast<const double2*>(tau),
+                       abar, n_delta, G};
+      if ((r2 = fallback_resolve(c, *p, ws, h, fb, stat, nullptr, &aa))) return r2;
     }
     if ((r2 = adj_reduce(c.dd->inv_off, c.dd->inv_sites, G, liz->total_sites, c.K, liz->n_atoms, n_energy,
                          reinterpret_cast<double2*>(grad_tinv), c.st)))

@@ -247,4 +247,23 @@ int gemm_tc_chunk(const Unit* d_units, int n_units, int n_max, int k, char* fac_
 
 int existing_device_data(lsms_liz* liz, DeviceData** out);
 
+// Process-wide options (lsms_set_option).
+double opt_growth_limit();
+int opt_fallback_slots();
+int opt_ir_max_sweeps();
+
+// Non-negative float maximum into a global word (the bit patterns of
+// non-negative floats order like their values); NaN is stored as +inf.
+__device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
+  v += 0.0f;  // -0 -> +0
+  if (!(v <= 3.4e38f)) v = __int_as_float(0x7f800000);
+  atomicMax(reinterpret_cast<unsigned int*>(addr), __float_as_uint(v));
+}
+// Warp maximum of non-negative floats (NaN as +inf).
+__device__ __forceinline__ float warp_max_nonneg(float v) {
+  v += 0.0f;
+  if (!(v <= 3.4e38f)) v = __int_as_float(0x7f800000);
+  return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(v)));
+}
+
 }  // namespace lsms

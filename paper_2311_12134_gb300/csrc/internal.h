@@ -36,6 +36,11 @@ LSMS_HD inline int64_t diag_inv_rel_off(int n) { return ((int64_t)n * n * 16 + 2
 LSMS_HD inline int64_t diag_inv_bytes(int n) {
   return ((int64_t)((n + kDiagNB - 1) / kDiagNB) * 2 * kDiagNB * kDiagNB * 8 + 255) / 256 * 256;
 }
+// After the diagonal-block inverses: the pivot-growth record of the unit, two
+// floats (max |M| over the assembled matrix, max |U| over the complex64 factor;
+// |.| = |Re| + |Im|), padded to 256 bytes.
+LSMS_HD inline int64_t growth_rel_off(int n) { return diag_inv_rel_off(n) + diag_inv_bytes(n); }
+constexpr int64_t kGrowthBytes = 256;
 
 // One (atom, energy) LIZ problem inside a chunk of the batched solve.
 struct Unit {

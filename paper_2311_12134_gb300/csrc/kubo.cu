@@ -424,6 +424,33 @@ int kubo_forward(const int64_t* offsets, const int32_t* site_atom, const int32_t
   return LSMS_OK;
 }
 
+// x *= a for n complex values.
+__global__ void k_cscale(double2* __restrict__ x, int64_t n, double a) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = mk(a * x[i].x, a * x[i].y);
+}
+
+// The per-atom terms of Eq. (lsms-conductivity-formula) with the -1/(pi V)
+// prefactor: out [n_delta][4][n_atoms][3][3].
+int kubo_atoms(const int64_t* offsets, const int32_t* site_atom, const int32_t* species, int n_species,
+               const double2* J, int64_t J_dstride, const double2* tau, int64_t S_total, int K, int n_atoms,
+               int n_delta, double volume, bool df, float4* jdf, double2* out, cudaStream_t st) {
+  if (df) {
+    const int64_t per = (int64_t)n_species * 12 * K * K;
+    const int n_dj = J_dstride > 0 ? n_delta : 1;
+    LSMS_LAUNCH(k_split_j, dim3((unsigned)((per + 255) / 256), n_dj), dim3(256), 0, st, J, J_dstride, per, jdf);
+    LSMS_LAUNCH(k_kubo_partial<true>, dim3(n_atoms, n_delta * 4), dim3(256), 0, st, offsets, site_atom, species, J,
+                J_dstride, jdf, J_dstride > 0 ? per : 0, tau, S_total, K, n_atoms, n_species, out);
+  } else {
+    LSMS_LAUNCH(k_kubo_partial<false>, dim3(n_atoms, n_delta * 4), dim3(256), 0, st, offsets, site_atom, species, J,
+                J_dstride, nullptr, 0, tau, S_total, K, n_atoms, n_species, out);
+  }
+  const int64_t cnt = (int64_t)n_delta * 4 * n_atoms * 9;
+  LSMS_LAUNCH(k_cscale, dim3((unsigned)std::min<int64_t>((cnt + 255) / 256, 4096)), dim3(256), 0, st, out, cnt,
+              -1.0 / (M_PI * volume));
+  return LSMS_OK;
+}
+
 int adj_abar(const int32_t* species, int n_species, const double2* J, int64_t J_dstride, const double2* w, int K,
              double volume, int n_atoms, int n_delta, double2* abar, float4* abar_df, cudaStream_t st) {
   LSMS_LAUNCH(k_adj_abar, dim3(n_atoms, n_delta * 4), dim3(256), 0, st, species, J, J_dstride, w, K, volume,

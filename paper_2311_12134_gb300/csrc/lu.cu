@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(256) k_panel(const Unit* __restrict__ units, c
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = blockDim.x >> 5;
   int flags = 0;
+  float umax = 0.f;  // complex64: largest |U| entry of the panel rows this thread saw (column k + tid)
   for (int j = 0; j < nbp; ++j) {
     const int col = k + j;
     const C* Ac = A + (size_t)col * n;
@@ -162,6 +163,9 @@ __global__ void __launch_bounds__(256) k_panel(const Unit* __restrict__ units, c
     __syncthreads();
     for (int c = tid; c < nbp; c += blockDim.x) s_row[c] = A[(size_t)(k + c) * n + col];
     __syncthreads();
+    if constexpr (std::is_same<R, float>::value) {
+      if (tid >= j && tid < nbp) umax = fmaxf(umax, cabs1(s_row[tid]));  // row col of U
+    }
     const C pv = s_row[j];
     const bool zero = (pv.x == R(0) && pv.y == R(0));
     if (zero) flags |= LSMS_UNIT_ZERO_PIVOT;
@@ -179,6 +183,12 @@ __global__ void __launch_bounds__(256) k_panel(const Unit* __restrict__ units, c
     __syncthreads();
   }
   if (tid == 0 && flags) atomicOr(&stat[u.stat_off], flags);
+  if constexpr (std::is_same<R, float>::value) {
+    if (warp == 0) {
+      const float wm = warp_max_nonneg(umax);
+      if (lane == 0) atomic_max_nonneg(reinterpret_cast<float*>(fac_base + u.m64_off + growth_rel_off(n)) + 1, wm);
+    }
+  }
 }
 
 // Panel factorization held in shared memory: the m = n - k rows x NB columns of
@@ -304,6 +314,14 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_smem(const Unit* __rest
   if (own)
     for (int c = 0; c < nbp; ++c) A[(size_t)(k + c) * n + k + lg] = sP[c * m + tid];
   if (tid == 0 && flags) atomicOr(&stat[u.stat_off], flags);
+  if constexpr (std::is_same<R, float>::value) {
+    // pivot growth: rows that became rows of U (logical row < nbp), columns right of the diagonal
+    float umax = 0.f;
+    if (own && lg < nbp)
+      for (int c = lg; c < nbp; ++c) umax = fmaxf(umax, cabs1(sP[c * m + tid]));
+    const float wm = warp_max_nonneg(umax);
+    if (lane == 0) atomic_max_nonneg(reinterpret_cast<float*>(fac_base + u.m64_off + growth_rel_off(n)) + 1, wm);
+  }
 }
 
 // ------------------------------------------------------------------ swap + trsm
@@ -366,13 +384,14 @@ constexpr int kSwapTileBytes = 32 * (kSwapCols + 1) * 8;  // complex64 panel-row
 template <int NB>
 __device__ __forceinline__ void k_swap_trsm_staged(float2* A, int n, int k, int c0, const float2 (*sL)[NB + 1],
                                                    const int* sTgtRow, const int* sSrcRow, const int* sTgtSrc,
-                                                   const int* sNt) {
+                                                   const int* sNt, float* growth_u) {
   extern __shared__ float2 sTile[];  // [NB][kSwapCols + 1]
   constexpr int LD = kSwapCols + 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ncols = min(kSwapCols, n - c0);
   for (int cc = warp; cc < ncols; cc += 8) sTile[lane * LD + cc] = A[(size_t)(c0 + cc) * n + k + lane];
   __syncthreads();
+  float umax = 0.f;  // pivot growth: largest |U12| entry of this column
   if (tid < ncols) {
     float2* Ac = A + (size_t)(c0 + tid) * n;
     float2 x[NB];
@@ -397,7 +416,14 @@ __device__ __forceinline__ void k_swap_trsm_staged(float2* A, int n, int k, int 
     }
     // the column's tile entries were read above by this thread only
 #pragma unroll
-    for (int i = 0; i < NB; ++i) sTile[i * LD + tid] = x[i];
+    for (int i = 0; i < NB; ++i) {
+      sTile[i * LD + tid] = x[i];
+      umax = fmaxf(umax, cabs1(x[i]));
+    }
+  }
+  {
+    const float wm = warp_max_nonneg(umax);
+    if (lane == 0) atomic_max_nonneg(growth_u, wm);
   }
   __syncthreads();
   for (int cc = warp; cc < ncols; cc += 8) A[(size_t)(c0 + cc) * n + k + lane] = sTile[lane * LD + cc];
@@ -426,7 +452,8 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ unit
   }
   if (tid < 32) compose_panel_swaps(piv, k, NB, tid, sStep, sTgtRow, sSrcRow, sTgtSrc, &sNt);
   if constexpr (sizeof(C) == 8) {
-    k_swap_trsm_staged<NB>(A, n, k, c0, sL, sTgtRow, sSrcRow, sTgtSrc, &sNt);
+    k_swap_trsm_staged<NB>(A, n, k, c0, sL, sTgtRow, sSrcRow, sTgtSrc, &sNt,
+                           reinterpret_cast<float*>(fac_base + u.m64_off + growth_rel_off(n)) + 1);
     return;
   }
   __syncthreads();
@@ -568,6 +595,7 @@ __global__ void __launch_bounds__(512, 2) k_solve(const Unit* __restrict__ units
   const Unit u = units[blockIdx.x];
   if (done && done[u.stat_off]) return;
   const int n = u.n;
+  if (n == 0) return;  // an unused FP64 fallback slot
   const C* A = reinterpret_cast<const C*>(fac_base + u.fac_off);
   C* X = reinterpret_cast<C*>(ws + (which == RHS_X ? u.x_off : u.x32_off));
   const int32_t* piv = reinterpret_cast<const int32_t*>(fac_base + u.piv_off);

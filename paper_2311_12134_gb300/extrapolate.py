@@ -16,6 +16,9 @@ least squares after the substitution stated in each function.
 """
 import numpy as np
 
+# The paper quotes LIZ radii and 2 alpha_max = 0.15 in angstrom; the library works in bohr.
+BOHR_IN_ANGSTROM = 0.529177210903
+
 
 def fit_lower_bound(r, rho):
     """rho = c0 / r + c1 (linear in 1/r).  Returns (c0, c1); c1 is rho at r -> inf."""
@@ -27,7 +30,9 @@ def fit_lower_bound(r, rho):
 
 def fit_upper_bound(r, rho, two_alpha=0.15):
     """rho = b0 / (1 + b1 exp(-two_alpha r)), i.e. 1/rho = 1/b0 + (b1/b0) exp(-two_alpha r),
-    linear in exp(-two_alpha r).  Returns (b0, b1); b0 is rho at r -> inf."""
+    linear in exp(-two_alpha r).  Returns (b0, b1); b0 is rho at r -> inf.  The default
+    two_alpha = 0.15 is the paper's 2 alpha_max in inverse angstrom, so r must be in angstrom
+    (radii in bohr times BOHR_IN_ANGSTROM)."""
     r = np.asarray(r, dtype=np.float64)
     x = np.exp(-two_alpha * r)
     A = np.stack([np.ones_like(r), x], axis=1)

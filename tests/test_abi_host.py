@@ -160,3 +160,67 @@ def test_argument_errors_are_reported_before_any_device_work(L):
     assert lib.lsms_lu_store_bytes(lz.handle, 3, 2, 1, ctypes.byref(full)) == 0
     assert lib.lsms_lu_store_bytes(lz.handle, 3, 2, B._prec("mixed", True), ctypes.byref(half)) == 0
     assert full.value == 2 * half.value > 0
+
+
+def test_options_roundtrip_and_range_checks(L):
+    """lsms_set_option / lsms_get_option: defaults, round trip, and LSMS_ERR_ARG for unknown names and
+    out-of-range values (host only)."""
+    from paper_2311_12134_gb300 import binding as B
+    saved = {k: B.get_option(k) for k in ("growth_limit", "fallback_slots", "ir_max_sweeps")}
+    try:
+        assert saved["growth_limit"] > 1.0 and saved["fallback_slots"] >= 1 and saved["ir_max_sweeps"] >= 1
+        B.set_option("growth_limit", 123.5)
+        assert B.get_option("growth_limit") == 123.5
+        B.set_option("fallback_slots", 3)
+        assert B.get_option("fallback_slots") == 3
+        for name, bad in (("growth_limit", 0.0), ("growth_limit", float("inf")), ("fallback_slots", -1),
+                          ("fallback_slots", 1.5), ("ir_max_sweeps", 65), ("streams", 5), ("no_such_option", 1)):
+            with pytest.raises(B.LsmsError) as ei:
+                B.set_option(name, bad)
+            assert ei.value.code == B.LSMS_ERR_ARG
+        with pytest.raises(B.LsmsError):
+            B.get_option("no_such_option")
+    finally:
+        for k, v in saved.items():
+            B.set_option(k, v)
+
+
+def test_workspace_sizes_with_store_and_fallback_slots(L):
+    """With LSMS_WS_STORE the factors leave the workspace; the mixed form's sizes grow with the FP64
+    fallback slots (each sized for the largest LIZ matrix) and the FP64 form's do not."""
+    from paper_2311_12134_gb300 import binding as B
+    w = wl.bcc_disordered_2000(n_cells=3)
+    lz = B.build_liz(w.pos, w.lattice, w.r_liz)
+    nE = len(w.z)
+    n_max = 16 * lz.max_sites
+    saved = B.get_option("fallback_slots")
+    try:
+        for prec in (B.LSMS_FP64, B.LSMS_MIXED):
+            mn, al = B.tau_workspace_bytes(lz, 3, nE, prec)
+            mn_s, al_s = B.tau_workspace_bytes(lz, 3, nE, prec | B.LSMS_WS_STORE)
+            store = B.lu_store_bytes(lz, 3, nE, prec)
+            assert al - al_s == store and mn_s < mn
+            bmn, bal = B.backward_workspace_bytes(lz, 3, nE, prec)
+            bmn_s, bal_s = B.backward_workspace_bytes(lz, 3, nE, prec | B.LSMS_WS_STORE)
+            assert bal - bal_s == store
+        B.set_option("fallback_slots", 0)
+        a0 = B.tau_workspace_bytes(lz, 3, nE, B.LSMS_MIXED)[1]
+        f0 = B.tau_workspace_bytes(lz, 3, nE, B.LSMS_FP64)[1]
+        B.set_option("fallback_slots", 4)
+        a4 = B.tau_workspace_bytes(lz, 3, nE, B.LSMS_MIXED)[1]
+        assert B.tau_workspace_bytes(lz, 3, nE, B.LSMS_FP64)[1] == f0
+        assert a4 - a0 >= 4 * n_max * n_max * 16
+    finally:
+        B.set_option("fallback_slots", saved)
+
+
+def test_sigma_atoms_argument_errors(L):
+    import ctypes
+    from paper_2311_12134_gb300 import binding as B
+    lib = B.lib()
+    w = wl.fcc_pure_32()
+    lz = B.build_liz(w.pos, w.lattice, w.r_liz)
+    dummy = ctypes.c_void_p(16)
+    assert lib.lsms_kubo_sigma_atoms(lz.handle, 3, dummy, 1, dummy, 0, dummy, 1, -1.0, 0, dummy, None) == B.LSMS_ERR_ARG
+    assert lib.lsms_kubo_sigma_atoms(lz.handle, 3, dummy, 1, dummy, 0, dummy, 1, 1.0, 0, None, None) == B.LSMS_ERR_ARG
+    assert lib.lsms_kubo_sigma_atoms(lz.handle, 3, dummy, 1, dummy, 0, dummy, 0, 1.0, 0, dummy, None) == B.LSMS_ERR_ARG

@@ -3,11 +3,17 @@ configuration of the library (all units batched, chunked to the workspace):
 
 * bcc2000: 2000-site bcc A/B alloy with vacancies and displacements (uneven LIZ
   sizes, n = 688..944), three broadenings delta, both forms; sampled tau blocks
-  against the oracle, sigma per delta mixed vs FP64;
-* fcc500: 500-atom fcc alloy, n = 880: the adjoint against central finite
-  differences of the forward at seeded sites;
-* the larger LIZ radii of the 16,000-site bcc recipe (89 and 137 sites, n = 1424
-  and 2192) on smaller supercells of the same recipe; sampled tau blocks.
+  and, per delta, sigma summed over the sampled centres against the oracle;
+  sigma per delta mixed vs FP64 over all atoms;
+* fcc500: the 500-atom fcc alloy recipe (x = 0.3, LIZ 55 sites, n = 880): the
+  adjoint against the oracle's dense gradient on a 32-atom cell of the recipe,
+  and against central finite differences of the forward at 20 seeded sites of
+  the full 500-atom alloy;
+* bcc16000: the 16,000-site recipe at full size (LIZ 59, n = 944) with sampled
+  tau blocks; the gradient at the 89-site LIZ (n = 1424) against finite
+  differences; the LIZ-radius sweep (59, 89, 137 sites) at full size with the
+  two extrapolations of Sec. IV;
+* a spin-polarised alloy: the two channels through the GPU path, summed.
 """
 import numpy as np
 import pytest
@@ -15,7 +21,9 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from oracle import grad as ograd
 from oracle import kkr as okkr
+from oracle import kubo as okubo
 from oracle import liz as oliz
 from paper_2311_12134_gb300 import workload as wl
 
@@ -33,23 +41,27 @@ def B():
     return binding
 
 
-def _run(B, w, precision, ws_gib=16, J=None):
+def _run(B, w, precision, ws_gib=16, J=None, tinv=None, atoms_sigma=False):
     lz = B.build_liz(w.pos, w.lattice, w.r_liz)
     mn, al = B.tau_workspace_bytes(lz, w.lmax, len(w.z), B._prec(precision))
     ws = torch.empty(min(al, max(mn, ws_gib << 30)), dtype=torch.uint8, device="cuda")
     sp = torch.as_tensor(w.species).cuda()
-    tau, st = B.tau_blocks(lz, w.lmax, sp, torch.as_tensor(w.tinv).cuda(), w.z, precision, workspace=ws)
+    t = torch.as_tensor(w.tinv if tinv is None else tinv).cuda()
+    tau, st = B.tau_blocks(lz, w.lmax, sp, t, w.z, precision, workspace=ws)
     Jd = torch.as_tensor(B.dipole_current(w.lmax, w.r_ll) if J is None else J).cuda()
     sig, _, rho = B.kubo_sigma(lz, w.lmax, sp, Jd, tau, w.n_delta, w.volume, precision=precision)
+    per = None
+    if atoms_sigma:
+        per = B.kubo_sigma_atoms(lz, w.lmax, sp, Jd, tau, w.n_delta, w.volume, precision=precision).cpu().numpy()
     torch.cuda.synchronize()
     del ws
-    return lz, tau, st.cpu().numpy(), sig.cpu().numpy()
+    return lz, tau, st.cpu().numpy(), sig.cpu().numpy(), per
 
 
-def _check_sampled(w, lz, tau, atoms, tol):
+def _check_sampled(w, lz, tau, atoms, tol, rows=False):
     L = oliz.build_liz(w.pos, w.lattice, w.r_liz)
     assert np.array_equal(lz.export()["offsets"], L["offsets"])
-    col = okkr.tau_blocks(w.lmax, L, w.tinv[w.species], w.z, atoms=atoms)
+    col, row = okkr.tau_blocks(w.lmax, L, w.tinv[w.species], w.z, atoms=atoms, return_rows=True)
     off = L["offsets"]
     worst = 0.0
     for m in atoms:
@@ -58,26 +70,39 @@ def _check_sampled(w, lz, tau, atoms, tol):
         for e in range(len(w.z)):
             worst = max(worst, rel_err_blocks(t[e][None], col[e, s][None]))
     assert worst < tol, worst
-    return worst
+    return (worst, L, col, row) if rows else worst
+
+
+def _consolidate(st):
+    return 0.25 * (st[:, 0] - st[:, 1] - st[:, 2] + st[:, 3])
 
 
 def test_bcc2000_uneven_three_deltas(B):
+    """Config bcc2000: tau of sampled atoms and, per delta, sigma summed over those centres against the
+    oracle, in both forms; sigma over all atoms, mixed vs FP64, per delta."""
     w = wl.bcc_disordered_2000()
     assert w.n_delta == 3 and w.n_atoms == 1980
-    lz, tau_m, st_m, sig_m = _run(B, w, "mixed")
+    Jsp = okubo.dipole_current(w.lmax, w.r_ll)
+    lz, tau_m, st_m, sig_m, per_m = _run(B, w, "mixed", atoms_sigma=True)
     sizes = lz.sizes
     assert sizes.min() < sizes.max()                       # uneven LIZ sizes
     assert np.all((st_m & 0xff) == 0), np.unique(st_m & 0xff, return_counts=True)
     assert ((st_m >> 8) & 0xff).max() <= 6
     assert ((st_m >> 16) & 0xff).max() <= 6
     atoms = [int(np.argmax(sizes)), int(np.argmin(sizes)), 1234]
-    _check_sampled(w, lz, tau_m, atoms, TOL["mixed"])
+    _, L, col, row = _check_sampled(w, lz, tau_m, atoms, TOL["mixed"], rows=True)
+    ref = _consolidate(okubo.sigma_tilde(L, Jsp[w.species], col, row, w.n_delta, w.volume, atoms=atoms))
+    got_m = _consolidate(per_m[:, :, atoms].sum(axis=2))
+    for d in range(3):
+        assert np.abs(got_m[d] - ref[d]).max() < TOL["mixed"] * np.abs(ref[d]).max(), d
     del tau_m
     torch.cuda.empty_cache()
-    lz64, tau_d, st_d, sig_d = _run(B, w, "fp64")
+    lz64, tau_d, st_d, sig_d, per_d = _run(B, w, "fp64", atoms_sigma=True)
     assert np.all((st_d & 0xff) == 0), np.unique(st_d & 0xff, return_counts=True)
     _check_sampled(w, lz64, tau_d, atoms[:2], TOL["fp64"])
+    got_d = _consolidate(per_d[:, :, atoms].sum(axis=2))
     for d in range(3):                                     # per broadening
+        assert np.abs(got_d[d] - ref[d]).max() < TOL["fp64"] * np.abs(ref[d]).max(), d
         err = np.abs(sig_m[d] - sig_d[d]).max() / np.abs(sig_d[d]).max()
         assert err < TOL["mixed"], (d, err)
         assert np.abs(sig_d[d].imag).max() < 1e-10 * np.abs(sig_d[d]).max()
@@ -87,7 +112,7 @@ def test_bcc2000_uneven_three_deltas(B):
 def test_large_liz_radii(B, r_over_a, n_cells, precisions):
     w = wl.bcc_large_16000(r_over_a=r_over_a, n_cells=n_cells)
     for precision in precisions:
-        lz, tau, st, _ = _run(B, w, precision)
+        lz, tau, st, _, _ = _run(B, w, precision)
         assert lz.max_sites == (89 if r_over_a == 2.2 else 137)
         assert np.all((st & 0xff) == 0)
         _check_sampled(w, lz, tau, [0, w.n_atoms - 1], TOL[precision])
@@ -95,39 +120,74 @@ def test_large_liz_radii(B, r_over_a, n_cells, precisions):
         torch.cuda.empty_cache()
 
 
-def test_fcc500_adjoint_central_differences(B):
-    """d Re sigma_xx / d t^{-1}_i on the 500-atom alloy at 10 seeded sites, against
-    central differences (h = 1e-6 on Re and Im) of the mixed-form forward.  Every atom
-    carries its own t^{-1} (n_species = N), so the per-species gradient is per site;
-    (a, b) and (b, a) move together so t^{-1} stays symmetric."""
-    base = wl.fcc_alloy_500()
-    N = base.n_atoms
-    Jsp = B.dipole_current(base.lmax, base.r_ll)
-    J_atoms = torch.as_tensor(Jsp[base.species]).cuda()
-    tinv = base.tinv[base.species].copy()
-    sp = torch.arange(N, dtype=torch.int32, device="cuda")
-    lz = B.build_liz(base.pos, base.lattice, base.r_liz)
-    assert lz.max_sites == 55
-    mn, al = B.tau_workspace_bytes(lz, base.lmax, 2, B.LSMS_MIXED)
-    ws = torch.empty(al, dtype=torch.uint8, device="cuda")
-    store = torch.empty(B.lu_store_bytes(lz, base.lmax, 2, B.LSMS_MIXED), dtype=torch.uint8, device="cuda")
+def _check_sampled_subset(w, lz, tau, atoms, tol):
+    """As _check_sampled for structures too large for the oracle's all-atom LIZ: the oracle builds the
+    LIZ of the sampled centres only and is compared site by site with the library's."""
+    L = oliz.build_liz(w.pos, w.lattice, w.r_liz, atoms=atoms)
+    ex = lz.export()
+    off = ex["offsets"]
+    col = okkr.tau_blocks(w.lmax, L, w.tinv[w.species], w.z)
+    worst = 0.0
+    for i, m in enumerate(atoms):
+        s = slice(off[m], off[m + 1])
+        so = slice(L["offsets"][i], L["offsets"][i + 1])
+        assert np.array_equal(ex["site_atom"][s], L["site_atom"][so])
+        assert np.abs(ex["disp"][s] - L["disp"][so]).max() < 1e-12
+        t = tau[:, s].cpu().numpy()
+        for e in range(len(w.z)):
+            worst = max(worst, rel_err_blocks(t[e][None], col[e, so][None]))
+    assert worst < tol, worst
+    return worst
+
+
+def test_bcc16000_full_size_forward(B):
+    """The 16,000-site recipe at full size (15,920 atoms after vacancies, LIZ 59 sites, n = 944,
+    31,840 units), mixed form, chunked to a 16 GiB workspace: clean status, sampled tau against the
+    oracle, finite sigma with positive diagonal."""
+    w = wl.bcc_large_16000(r_over_a=1.85)
+    assert w.n_atoms == 15920
+    lz, tau, st, sig, _ = _run(B, w, "mixed")
+    assert lz.max_sites == 59
+    assert np.all((st & 0xff) == 0), np.unique(st & 0xff, return_counts=True)
+    _check_sampled_subset(w, lz, tau, [0, 7777, w.n_atoms - 1], TOL["mixed"])
+    assert np.all(np.isfinite(sig))
+    d = np.real(np.diag(sig[0]))
+    assert d.min() > 0
+
+
+def _per_atom_problem(B, w):
+    """Every atom its own species (n_species = N), so the per-species gradient is per site."""
+    Jsp = B.dipole_current(w.lmax, w.r_ll)
+    return torch.as_tensor(Jsp[w.species]).cuda(), w.tinv[w.species].copy(), \
+        torch.arange(w.n_atoms, dtype=torch.int32, device="cuda")
+
+
+def _fd_check(B, w, n_sites, seed, ws_gib=16):
+    """d Re sigma_xx / d t^{-1}_i at seeded sites against central differences (h = 1e-6 on Re and
+    Im) of the mixed-form forward; (a, b) and (b, a) move together so t^{-1} stays symmetric."""
+    N = w.n_atoms
+    J_atoms, tinv, sp = _per_atom_problem(B, w)
+    lz = B.build_liz(w.pos, w.lattice, w.r_liz)
+    mn, al = B.tau_workspace_bytes(lz, w.lmax, 2, B.LSMS_MIXED)
+    ws = torch.empty(min(al, max(mn, ws_gib << 30)), dtype=torch.uint8, device="cuda")
+    store = torch.empty(B.lu_store_bytes(lz, w.lmax, 2, B.LSMS_MIXED), dtype=torch.uint8, device="cuda")
 
     def sigma_xx(t):
-        tau, _ = B.tau_blocks(lz, base.lmax, sp, torch.as_tensor(t).cuda(), base.z, "mixed", workspace=ws)
-        s, _, _ = B.kubo_sigma(lz, base.lmax, sp, J_atoms, tau, 1, base.volume)
+        tau, _ = B.tau_blocks(lz, w.lmax, sp, torch.as_tensor(t).cuda(), w.z, "mixed", workspace=ws)
+        s, _, _ = B.kubo_sigma(lz, w.lmax, sp, J_atoms, tau, 1, w.volume)
         return s.cpu().numpy()[0, 0, 0].real
 
     td = torch.as_tensor(tinv).cuda()
-    tau, st = B.tau_blocks(lz, base.lmax, sp, td, base.z, "mixed", workspace=ws, lu_store=store)
+    tau, st = B.tau_blocks(lz, w.lmax, sp, td, w.z, "mixed", workspace=ws, lu_store=store)
     wgt = np.zeros((1, 3, 3), dtype=np.complex128)
     wgt[0, 0, 0] = 1.0
-    _, g = B.kubo_sigma_backward(lz, base.lmax, sp, td, base.z, J_atoms, tau, base.volume,
+    _, g = B.kubo_sigma_backward(lz, w.lmax, sp, td, w.z, J_atoms, tau, w.volume,
                                  torch.as_tensor(wgt).cuda(), "mixed", lu_store=store)
     g = g.cpu().numpy()
     gmax = np.abs(g).max()
-    rng = np.random.default_rng(2311 + 3)
+    rng = np.random.default_rng(seed)
     h = 1e-6
-    for _ in range(10):
+    for _ in range(n_sites):
         i, e = int(rng.integers(N)), int(rng.integers(2))
         a = int(rng.integers(16))
         b = a if rng.random() < 0.5 else int(rng.integers(16))
@@ -140,23 +200,104 @@ def test_fcc500_adjoint_central_differences(B):
             fd = (sigma_xx(tp) - sigma_xx(tm)) / (2 * h)
             ref = G.real if part == "re" else G.imag
             assert abs(fd - ref) < 1e-5 * gmax, (i, e, a, b, part, fd, ref, gmax)
+    return lz
+
+
+def test_fcc500_adjoint_central_differences(B):
+    """The 500-atom alloy (LIZ 55, n = 880): the adjoint at 20 seeded sites against central
+    differences of the forward."""
+    w = wl.fcc_alloy_500()
+    lz = _fd_check(B, w, 20, 2311 + 3)
+    assert lz.max_sites == 55
+
+
+@pytest.mark.parametrize("precision,store", [("mixed", True), ("mixed", False), ("fp64", True)])
+def test_fcc500_recipe_dense_gradient_32_atoms(B, precision, store):
+    """The fcc500 recipe (x = 0.3, a = 7.65, LIZ 1.5a = 55 sites with periodic images, n = 880) on a
+    32-atom cell: the adjoint's per-site gradient against the oracle's explicit-inverse gradient."""
+    a = 7.65
+    w = wl.make_supercell(name="fcc32_AB30_liz55", kind="fcc", n_cells=2, a=a, counts=[22, 10], r_liz=1.50 * a,
+                          phases=[wl.PHASE_A, wl.PHASE_B], e_fermi=0.60, deltas=[0.002], seed=2311 + 3)
+    Jsp = okubo.dipole_current(w.lmax, w.r_ll)
+    wgt = np.zeros((1, 3, 3), dtype=np.complex128)
+    wgt[0, 0, 0] = 1.0
+    wgt[0, 2, 1] = 0.25 + 0.5j
+    L = oliz.build_liz(w.pos, w.lattice, w.r_liz)
+    ref = ograd.torch_grad(ograd.dense_gradient(w.lmax, L, w.tinv[w.species], w.z, Jsp[w.species], 1, w.volume,
+                                                wgt))
+    lz = B.build_liz(w.pos, w.lattice, w.r_liz)
+    assert lz.max_sites == 55
+    sp = torch.as_tensor(w.species).cuda()
+    t = torch.as_tensor(w.tinv).cuda()
+    st_buf = None
+    if store:
+        st_buf = torch.empty(B.lu_store_bytes(lz, w.lmax, 2, B._prec(precision)), dtype=torch.uint8, device="cuda")
+    tau, st = B.tau_blocks(lz, w.lmax, sp, t, w.z, precision, lu_store=st_buf)
+    bst = torch.empty_like(st)
+    g, _ = B.kubo_sigma_backward(lz, w.lmax, sp, t, w.z, torch.as_tensor(Jsp).cuda(), tau, w.volume,
+                                 torch.as_tensor(wgt).cuda(), precision, lu_store=st_buf, unit_status=bst)
+    torch.cuda.synchronize()
+    assert not np.any(st.cpu().numpy() & 0xff) and not np.any(bst.cpu().numpy() & 0xff)
+    g = g.cpu().numpy()
+    for e in range(2):
+        assert np.linalg.norm(g[e] - ref[e]) < TOL[precision] * np.linalg.norm(ref[e]), e
+
+
+def test_bcc16000_recipe_gradient_at_89_site_liz(B):
+    """The 16,000-site recipe at LIZ 2.2a (89 sites, n = 1424) on a 5x5x5-cell supercell: the
+    adjoint against central differences at 6 seeded sites."""
+    w = wl.bcc_large_16000(r_over_a=2.2, n_cells=5)
+    lz = _fd_check(B, w, 6, 2311 + 4)
+    assert lz.max_sites == 89
 
 
 def test_liz_radius_sweep_and_extrapolation(B):
-    """The LIZ-radius sweep of the 16,000-site bcc recipe (1.85a, 2.2a, 2.5a: 59, 89
-    and 137 sites) on a 6x6x6-cell supercell of the same recipe, mixed form, then the
-    lower/upper-bound extrapolations of Sec. IV on rho_xx(r)."""
+    """The LIZ-radius sweep of the 16,000-site bcc recipe at full size (1.85a, 2.2a, 2.5a: 59, 89 and
+    137 sites, n up to 2192), mixed form, then the lower- and upper-bound extrapolations of Sec. IV on
+    rho_xx(r) with r in angstrom (the upper bound's 2 alpha_max = 0.15 is in inverse angstrom).  The
+    two extrapolated residual resistivities bracket the trend of the samples: both lie beyond the
+    last sample in the direction rho moves, the linear-in-1/r (weak-scattering) form farther."""
     from paper_2311_12134_gb300 import extrapolate as ex
     radii, rho = [], []
     for roa in (1.85, 2.2, 2.5):
-        w = wl.bcc_large_16000(r_over_a=roa, n_cells=6)
-        lz, tau, st, sig = _run(B, w, "mixed")
+        w = wl.bcc_large_16000(r_over_a=roa)
+        lz, tau, st, sig, _ = _run(B, w, "mixed", ws_gib=24)
         assert np.all((st & 0xff) == 0)
         assert lz.max_sites == {1.85: 59, 2.2: 89, 2.5: 137}[roa]
-        radii.append(w.r_liz)
+        radii.append(w.r_liz * ex.BOHR_IN_ANGSTROM)
         rho.append(float(ex.resistivity_xx(sig[0])))
         del tau
         torch.cuda.empty_cache()
     c0, c1 = ex.fit_lower_bound(radii, rho)
     b0, b1 = ex.fit_upper_bound(radii, rho, two_alpha=0.15)
-    assert np.all(np.isfinite([c0, c1, b0, b1]))
+    assert np.all(np.isfinite([c0, c1, b0, b1])) and min(rho) > 0
+    if rho[-1] < rho[0]:       # decreasing with the radius, as for the paper's alloys
+        assert c1 <= b0 <= rho[-1] * (1 + 1e-9), (c1, b0, rho)
+    else:
+        assert c1 >= b0 >= rho[-1] * (1 - 1e-9), (c1, b0, rho)
+
+
+def test_spin_polarised_sum_through_the_gpu(B):
+    """Collinear spin polarisation (Sec. IV, Fe-Si): the two spin channels are separate runs of the
+    path with their own t^{-1}; sigma = sigma_up + sigma_down, compared with the oracle's two
+    channels summed, and rho_xx from the sum."""
+    from paper_2311_12134_gb300 import extrapolate as ex
+    a = 7.65
+    base = dict(name="spin32", kind="fcc", n_cells=2, a=a, counts=[20, 12], sigma_disp=0.1, r_liz=0.85 * a,
+                e_fermi=0.6, deltas=[0.002], seed=321)
+    up = wl.make_supercell(phases=[wl.PHASE_A, wl.PHASE_B], **base)
+    dn = wl.make_supercell(phases=[(0.30, 0.15, 0.10, 0.004), (0.45, 0.25, 0.60, 0.015)], **base)
+    J = okubo.dipole_current(up.lmax, up.r_ll)
+    sig = {}
+    ref = {}
+    L = oliz.build_liz(up.pos, up.lattice, up.r_liz)
+    for name, w in (("up", up), ("down", dn)):
+        _, _, st, s, _ = _run(B, w, "mixed", J=J)
+        assert not np.any(st & 0xff)
+        sig[name] = s
+        col, row = okkr.tau_blocks(w.lmax, L, w.tinv[w.species], w.z, return_rows=True)
+        ref[name] = okubo.consolidate(okubo.sigma_tilde(L, J[w.species], col, row, 1, w.volume))
+    tot = ex.spin_sum(sig["up"], sig["down"])
+    rtot = ref["up"] + ref["down"]
+    assert np.abs(tot - rtot).max() < TOL["mixed"] * np.abs(rtot).max()
+    assert abs(ex.resistivity_xx(tot[0]) - ex.resistivity_xx(rtot[0])) < 1e-7 * abs(ex.resistivity_xx(rtot[0]))
