@@ -319,6 +319,10 @@ int lsms_kubo_sigma_backward(const lsms_liz* liz, int lmax, const int32_t* speci
  *                     LSMS_UNIT_NOCONV (default 6; 0..64)
  *   "streams"         concurrent parts per chunk (1..4; 0 = the environment
  *                     variable LSMS_STREAMS, else 4)
+ *   "residual_tc"     1 (default): the mixed form's refinement residual for 9
+ *                     or more right-hand sides runs on the tensor cores (bf16
+ *                     fixed-point digits, exact FP32 accumulation, about 2^-48
+ *                     of |M| |X|); 0: double-float arithmetic on the FP32 pipes
  * LSMS_ERR_ARG for an unknown name or a value out of range. */
 int lsms_set_option(const char* name, double value);
 int lsms_get_option(const char* name, double* value);

@@ -17,7 +17,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblsmskubo.so")
 
-CUDA_SOURCES = ["api.cu", "lu.cu", "kubo.cu", "tc_gemm.cu"]
+CUDA_SOURCES = ["api.cu", "lu.cu", "kubo.cu", "tc_gemm.cu", "resid_tc.cu"]
 CXX_SOURCES = ["host.cpp"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

@@ -91,6 +91,8 @@ static std::atomic<double> g_opt_growth_limit{1e3};
 static std::atomic<int> g_opt_fallback_slots{8};
 static std::atomic<int> g_opt_ir_max_sweeps{kIrMaxIter};
 static std::atomic<int> g_opt_streams{0};  // 0: LSMS_STREAMS or the default
+static std::atomic<int> g_opt_residual_tc{1};
+int opt_residual_tc() { return g_opt_residual_tc.load(); }
 double opt_growth_limit() { return g_opt_growth_limit.load(); }
 int opt_fallback_slots() { return g_opt_fallback_slots.load(); }
 int opt_ir_max_sweeps() { return g_opt_ir_max_sweeps.load(); }
@@ -214,14 +216,15 @@ static UnitBytes unit_bytes(int n, int precision, int nrhs, bool backward) {
   const size_t nn = (size_t)n * n;
   ub.fac = align_up(nn * (precision == LSMS_FP64 ? 16 : 8));
   ub.piv = align_up((size_t)n * 4);  // pivots (row interchanged with row i at step i)
-  // double-float M + diagonal-block inverses + pivot-growth record
-  ub.m64 = precision == LSMS_FP64 ? 0 : (size_t)(growth_rel_off(n) + kGrowthBytes);
+  // double-float M + diagonal-block inverses + pivot-growth record + row maxima
+  ub.m64 = precision == LSMS_FP64 ? 0 : (size_t)m64_region_bytes(n);
   ub.x = align_up((size_t)n * nrhs * 16);
   ub.b = backward ? align_up((size_t)n * nrhs * 16) : 0;
   // complex64 corrections; the convergence probe uses the first kProbe columns
   ub.x32 = precision == LSMS_FP64 ? 0 : align_up((size_t)n * std::max(nrhs, kProbe) * 8);
   ub.probe = precision == LSMS_FP64 ? 0 : align_up((size_t)n * kProbe * 2 * 16);  // y_q and (B w)_q
-  ub.xdf = precision == LSMS_FP64 ? 0 : align_up((size_t)n * nrhs * 16);          // X as float4 (hi, lo)
+  // X as float4 (hi, lo) and its column maxima
+  ub.xdf = precision == LSMS_FP64 ? 0 : (size_t)(colmax_rel_off(n, nrhs) + kColmaxBytes);
   return ub;
 }
 
@@ -623,14 +626,18 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
     t0 = s_start[L * kMaxK + Lp];
     t1 = s_start[L * kMaxK + Lp + 1];
   }
+  __shared__ unsigned int s_rmax[kAsmE][kMaxK];  // mixed form: row maxima of block row p, per energy
   for (int e0 = 0; e0 < nE; e0 += kAsmE) {
     int flags[kAsmE];
     float mmax[kAsmE];  // mixed form: largest |M| entry written, per energy
+    float rmax[kAsmE];  // mixed form: largest |Re| or |Im| (high parts) in this thread's row, per energy
+    if (MIXED && tid < kAsmE * kMaxK) s_rmax[tid / kMaxK][tid % kMaxK] = 0u;  // read after the q0 loop's barriers
     const int ne = min(kAsmE, nE - e0);
 #pragma unroll
     for (int ee = 0; ee < kAsmE; ++ee) {
       flags[ee] = bad;
       mmax[ee] = 0.f;
+      rmax[ee] = 0.f;
       if (ee < ne && !(__uint_as_float(s_dmax[e0 + ee]) <= (float)kSymTol * __uint_as_float(s_amax[e0 + ee])))
         flags[ee] |= LSMS_UNIT_TINV_ASYM;
     }
@@ -708,6 +715,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
             }
             if (!(isfinite(v4.x) && isfinite(v4.z))) flags[ee] |= LSMS_UNIT_NONFINITE;
             mmax[ee] = fmaxf(mmax[ee], fabsf(v4.x) + fabsf(v4.z));
+            rmax[ee] = fmaxf(rmax[ee], fmaxf(fabsf(v4.x), fabsf(v4.z)));
             reinterpret_cast<float4*>(fac_base + u.m64_off)[idx] = make_float4(v4.x, v4.z, v4.y, v4.w);
             if (write_fac) reinterpret_cast<float2*>(fac_base + u.fac_off)[idx] = make_float2(v4.x, v4.z);
           } else {
@@ -736,7 +744,22 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
         const float wm = warp_max_nonneg(mmax[ee]);
         const Unit& u = ua[e0 + ee];
         if ((tid & 31) == 0) atomic_max_nonneg(reinterpret_cast<float*>(fac_base + u.m64_off + growth_rel_off(u.n)), wm);
+        if (act) {
+          float rm = rmax[ee] + 0.0f;
+          if (!(rm <= 3.4e38f)) rm = __int_as_float(0x7f800000);
+          atomicMax(&s_rmax[ee][L], __float_as_uint(rm));
+        }
       }
+    }
+    if (MIXED) {  // this CTA saw every column of rows K p .. K p + K - 1: their maxima are complete
+      __syncthreads();
+      if (tid < ne * kMaxK && (tid % kMaxK) < K) {
+        const int ee = tid / kMaxK, L2 = tid % kMaxK;
+        const Unit& u = ua[e0 + ee];
+        reinterpret_cast<float*>(fac_base + u.m64_off + rowmax_rel_off(u.n))[K * p + L2] =
+            __uint_as_float(s_rmax[ee][L2]);
+      }
+      __syncthreads();
     }
   }
 }
@@ -796,19 +819,35 @@ __global__ void k_copy_b(const Unit* __restrict__ units, char* ws, int nrhs, boo
   }
 }
 
-// X = X32 widened (and its double-float copy, lo parts zero).
-__global__ void k_widen(const Unit* __restrict__ units, char* ws, int nrhs) {
-  const Unit u = units[blockIdx.y];
+// X = X32 widened, its double-float copy (lo parts zero) and the column maxima
+// max_i max(|Re X_ic|, |Im X_ic|) for the tensor-core residual.  One CTA per unit.
+__global__ void __launch_bounds__(256) k_widen(const Unit* __restrict__ units, char* ws, int nrhs) {
+  const Unit u = units[blockIdx.x];
   const int n = u.n;
   const float2* X32 = reinterpret_cast<const float2*>(ws + u.x32_off);
   double2* X = reinterpret_cast<double2*>(ws + u.x_off);
   float4* Xdf = reinterpret_cast<float4*>(ws + u.xdf_off);
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)n * nrhs;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const float2 x = X32[idx];
-    X[idx] = to64(x);
-    Xdf[idx] = make_float4(x.x, 0.f, x.y, 0.f);
+  __shared__ unsigned int s_cmax[32];
+  const int tid = threadIdx.x;
+  if (tid < 32) s_cmax[tid] = 0u;
+  __syncthreads();
+  for (int c = 0; c < nrhs; ++c) {
+    for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+      const int i = i0 + tid;
+      float m = 0.f;
+      if (i < n) {
+        const size_t idx = (size_t)c * n + i;
+        const float2 x = X32[idx];
+        X[idx] = to64(x);
+        Xdf[idx] = make_float4(x.x, 0.f, x.y, 0.f);
+        m = fmaxf(fabsf(x.x), fabsf(x.y));
+      }
+      m = warp_max_nonneg(m);
+      if ((tid & 31) == 0) atomicMax(&s_cmax[c], __float_as_uint(m));
+    }
   }
+  __syncthreads();
+  if (tid < nrhs) reinterpret_cast<float*>(ws + u.xdf_off + colmax_rel_off(n, nrhs))[tid] = __uint_as_float(s_cmax[tid]);
 }
 
 // Refinement residual, FP64-accurate, on the FP32 pipes: B - M X with M held as
@@ -932,14 +971,18 @@ __global__ void __launch_bounds__(256) k_ir_update(const Unit* __restrict__ unit
   double2* BW = reinterpret_cast<double2*>(Y + (size_t)kProbe * n);
   // probe weights rounded to complex64 (exact in both products below)
   __shared__ float2 sw[kProbe][32];
+  __shared__ unsigned int s_cmax[32];  // column maxima of the high parts of the updated X
   for (int idx = threadIdx.x; idx < kProbe * 32; idx += blockDim.x)
     sw[idx / 32][idx % 32] = to32(probe_weight(u.stat_off, sweep, idx / 32, idx % 32));
+  if (threadIdx.x < 32) s_cmax[threadIdx.x] = 0u;
   __syncthreads();
   // the update in FP64 (X is the complex128 solution) and its double-float split;
   // the norms in FP32 (a ratio test), y = X w in double-float on the FP32 pipes,
   // (B w) in FP64
   float dn = 0.f, xn = 0.f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    const bool live = i < n;
     DfAcc y[kProbe];
     double2 bw[kProbe];
 #pragma unroll
@@ -948,37 +991,48 @@ __global__ void __launch_bounds__(256) k_ir_update(const Unit* __restrict__ unit
       bw[q] = mk(0.0, 0.0);
     }
     for (int c = 0; c < nrhs; ++c) {
-      const size_t idx = (size_t)c * n + i;
-      const float2 d32 = D[idx];
-      const double2 x = cadd(X[idx], to64(d32));
-      X[idx] = x;
-      const float4 xs = df_split(x);  // split once here instead of in every residual CTA
-      Xdf[idx] = xs;
-      dn = fmaf(d32.x, d32.x, fmaf(d32.y, d32.y, dn));
-      xn = fmaf(xs.x, xs.x, fmaf(xs.z, xs.z, xn));
+      float cm = 0.f;
+      if (live) {
+        const size_t idx = (size_t)c * n + i;
+        const float2 d32 = D[idx];
+        const double2 x = cadd(X[idx], to64(d32));
+        X[idx] = x;
+        const float4 xs = df_split(x);  // split once here instead of in every residual CTA
+        Xdf[idx] = xs;
+        cm = fmaxf(fabsf(xs.x), fabsf(xs.z));
+        dn = fmaf(d32.x, d32.x, fmaf(d32.y, d32.y, dn));
+        xn = fmaf(xs.x, xs.x, fmaf(xs.z, xs.z, xn));
+#pragma unroll
+        for (int q = 0; q < kProbe; ++q) {
+          const float2 w = sw[q][c & 31];
+          dfc_mac(y[q], xs, make_float4(w.x, 0.f, w.y, 0.f));
+        }
+        if (explicit_b) {
+          const double2 b = B[idx];
+#pragma unroll
+          for (int q = 0; q < kProbe; ++q) bw[q] = cfma(b, to64(sw[q][c & 31]), bw[q]);
+        }
+      }
+      cm = warp_max_nonneg(cm);
+      if ((threadIdx.x & 31) == 0) atomicMax(&s_cmax[c], __float_as_uint(cm));
+    }
+    if (live) {
 #pragma unroll
       for (int q = 0; q < kProbe; ++q) {
-        const float2 w = sw[q][c & 31];
-        dfc_mac(y[q], xs, make_float4(w.x, 0.f, w.y, 0.f));
+        // B = E0 (forward): (B w)_i = w_i for i < K
+        if (!explicit_b && i < K && i < nrhs) bw[q] = to64(sw[q][i]);
+        Y[(size_t)q * n + i] = df_value(y[q]);
+        BW[(size_t)q * n + i] = bw[q];
       }
-      if (explicit_b) {
-        const double2 b = B[idx];
-#pragma unroll
-        for (int q = 0; q < kProbe; ++q) bw[q] = cfma(b, to64(sw[q][c & 31]), bw[q]);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < kProbe; ++q) {
-      // B = E0 (forward): (B w)_i = w_i for i < K
-      if (!explicit_b && i < K && i < nrhs) bw[q] = to64(sw[q][i]);
-      Y[(size_t)q * n + i] = df_value(y[q]);
-      BW[(size_t)q * n + i] = bw[q];
     }
   }
   __shared__ double s1[256], s2[256];
   s1[threadIdx.x] = (double)dn;
   s2[threadIdx.x] = (double)xn;
   __syncthreads();
+  if (threadIdx.x < nrhs)
+    reinterpret_cast<float*>(ws + u.xdf_off + colmax_rel_off(n, nrhs))[threadIdx.x] =
+        __uint_as_float(s_cmax[threadIdx.x]);
   for (int w = 128; w > 0; w >>= 1) {
     if (threadIdx.x < w) {
       s1[threadIdx.x] += s1[threadIdx.x + w];
@@ -1334,12 +1388,16 @@ static int solve_refine(const Call& c, const Plan& p, const Chunk& ch, const cha
   if (explicit_b) LSMS_LAUNCH(k_copy_b, g1, dim3(256), 0, c.st, du, ws, nrhs, true);
   else LSMS_LAUNCH(k_rhs_identity<float2>, g1, dim3(256), 0, c.st, du, ws, (int)RHS_X32, c.K, nrhs);
   if ((rc = lu_solve_chunk<float>(du, nu, fac_base, ws, RHS_X32, nrhs, nullptr, c.st))) return rc;
-  LSMS_LAUNCH(k_widen, g1, dim3(256), 0, c.st, du, ws, nrhs);
+  LSMS_LAUNCH(k_widen, dim3(nu), dim3(256), 0, c.st, du, ws, nrhs);
   // done flags of this chunk's units start cleared (memset by the caller)
   const int max_sweeps = opt_ir_max_sweeps();
+  // the residual on the tensor cores for 9 or more right-hand sides (lmax >= 2), else double-float SIMT
+  const bool tc_resid = opt_residual_tc() && nrhs >= 9;
   for (int it = 0; it < max_sweeps; ++it) {
     const dim3 gr((ch.n_max + 63) / 64, nu);
-    switch (nrhs) {  // K or 2K for lmax = 0..3
+    if (tc_resid) {
+      if ((rc = residual_tc_chunk(du, nu, ch.n_max, fac_base, ws, c.K, nrhs, explicit_b, done, stat, c.st))) return rc;
+    } else switch (nrhs) {  // K or 2K for lmax = 0..3
 #define LSMS_RESID(NR)                                                                                 \
   case NR:                                                                                             \
     if (it == 0) LSMS_LAUNCH((k_residual<NR, false>), gr, dim3(256), 0, c.st, du, fac_base, ws, c.K, explicit_b, done); \
@@ -1535,6 +1593,9 @@ extern "C" int lsms_set_option(const char* name, double value) {
   } else if (n == "streams") {
     if (!in_int(0, kMaxParts)) return fail(LSMS_ERR_ARG, "streams must be an integer in 0..%d", kMaxParts);
     g_opt_streams.store((int)value);
+  } else if (n == "residual_tc") {
+    if (!in_int(0, 1)) return fail(LSMS_ERR_ARG, "residual_tc must be 0 or 1");
+    g_opt_residual_tc.store((int)value);
   } else {
     return fail(LSMS_ERR_ARG, "lsms_set_option: unknown option '%s'", name);
   }
@@ -1549,6 +1610,7 @@ extern "C" int lsms_get_option(const char* name, double* value) {
   else if (n == "fallback_slots") *value = g_opt_fallback_slots.load();
   else if (n == "ir_max_sweeps") *value = g_opt_ir_max_sweeps.load();
   else if (n == "streams") *value = stream_parts();
+  else if (n == "residual_tc") *value = g_opt_residual_tc.load();
   else return fail(LSMS_ERR_ARG, "lsms_get_option: unknown option '%s'", name);
   return LSMS_OK;
 }

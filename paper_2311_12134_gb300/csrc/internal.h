@@ -41,6 +41,15 @@ LSMS_HD inline int64_t diag_inv_bytes(int n) {
 // |.| = |Re| + |Im|), padded to 256 bytes.
 LSMS_HD inline int64_t growth_rel_off(int n) { return diag_inv_rel_off(n) + diag_inv_bytes(n); }
 constexpr int64_t kGrowthBytes = 256;
+// After the growth record: the largest |Re| or |Im| of the high parts of each
+// row of M (n floats), the row scales of the tensor-core refinement residual.
+LSMS_HD inline int64_t rowmax_rel_off(int n) { return growth_rel_off(n) + kGrowthBytes; }
+LSMS_HD inline int64_t m64_region_bytes(int n) { return rowmax_rel_off(n) + ((int64_t)n * 4 + 255) / 256 * 256; }
+// The double-float copy of X (n x nrhs float4) is followed by the largest |Re|
+// or |Im| of the high parts of each column (at most 32 floats), the column
+// scales of the tensor-core residual.
+LSMS_HD inline int64_t colmax_rel_off(int n, int nrhs) { return ((int64_t)n * nrhs * 16 + 255) / 256 * 256; }
+constexpr int64_t kColmaxBytes = 256;
 
 // One (atom, energy) LIZ problem inside a chunk of the batched solve.
 struct Unit {
