@@ -6,26 +6,30 @@
 // row's largest |Re| or |Im|, recorded by the assembly), column c of X by
 // 2^-F_c (recorded by k_widen / k_ir_update).  Each scaled real value, held as a
 // double-float pair, becomes six balanced base-256 digits
-//   v 2^8 = sum_{s=1..6} a_s 2^{8 (1 - s)} + rest,  a_s integers,
-//   |a_1| <= 256, |a_s| <= 128 for s > 1, |rest| <= 2^-41 (2^-49 of the scale),
-// all exact in bf16.  A digit product a_s b_t is an integer below 2^16 and
+//   v 2^7 = sum_{s=1..6} a_s 2^{8 (1 - s)} + rest,  a_s integers, |a_s| <= 129,
+//   |rest| <= 2^-41 (2^-48 of the scale),
+// all exact in bf16.  A digit product a_s b_t is an integer of at most 129^2 and
 // belongs to weight class g = s + t; the 21 pairs with g <= 7 run as bf16
 // tcgen05.mma with FP32 accumulation in tensor memory, one accumulator per class.
-// Per real K a class sum grows by at most 2^17 (at most 6 pairs, first digits up
-// to 256), so 128 real K accumulate exactly in FP32 (below 2^24): every 4 chunks
-// of 32 real K the accumulators are read with tcgen05.ld and added, scaled by
-// 2^{-8 (g - 2)}, into double-float registers.  The dropped classes (g >= 8) and
-// the digit rests stay below 2^-48 of the scales.  The complex product is the
-// real embedding
+// Per real K a class sum grows by at most 6 * 129^2 < 2^17, so 128 real K
+// accumulate exactly in FP32 (below 2^24): every 4 chunks of 32 real K the
+// accumulators are read with tcgen05.ld and added, scaled by 2^{-8 (g - 2)},
+// into double-float registers.  The dropped classes (g >= 8) and the digit
+// rests stay below 2^-48 of the scales.  The complex product is the real
+// embedding
 //   [Re MX | Im MX] = [Re M | Im M] x [[Re X, Im X], [-Im X, Re X]].
 //
 // CTA: 128 rows of one unit (TMEM lanes), 16 complex right-hand-side columns
-// (blockIdx.z picks the slice), 4 warps.  Per chunk of 16 complex columns of M:
-//   all threads  split their row's 32 real values into the six digit planes of
-//                A (no-swizzle K-major core-matrix layout in shared memory),
-//   warp 0       splits the 16 x 16 block of X into the six planes of B,
+// (blockIdx.z picks the slice), 8 warps; thread t owns row t % 128 and the
+// column half t / 128.  Per chunk of 16 complex columns of M:
+//   all threads  split their 8 elements of M (loaded during the previous
+//                chunk's products) into the six digit planes of A and one
+//                element of X into the six planes of B (no-swizzle K-major
+//                core-matrix layout in shared memory), real and imaginary
+//                parts in the two lanes of the paired FP32 instructions;
 //   one thread   issues the 42 tcgen05.mma (M = 128, N = 32, K = 16) of the
-//                chunk and commits them to an mbarrier (bounded waits).
+//                chunk and commits them to an mbarrier (bounded waits);
+//   every 4th    warps 0-3 add the real outputs, warps 4-7 the imaginary ones.
 #include <cstdint>
 
 #include <cuda_bf16.h>
@@ -41,6 +45,7 @@ constexpr int NG = 6;        // weight classes g = 2..7 (index s + t - 2 of digi
 constexpr int KCC = 16;      // complex columns of M per chunk (32 real K)
 constexpr int NC = 16;       // complex right-hand-side columns per CTA
 constexpr int TM = 128;      // rows per CTA (TMEM lanes)
+constexpr int NT = 256;      // threads: two per row (column halves)
 constexpr int NOUT = 2 * NC; // real accumulator columns per class: [Re | Im]
 constexpr int LBO = 128;     // bytes between core matrices (8 rows x 16 bytes) adjacent in K
 constexpr int SBO = 512;     // bytes between 8-row groups (the 4 core matrices of 32 K)
@@ -58,7 +63,7 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Byte offset of element (row, k) in a plane: 8 x 8 core matrices of 16-byte rows.
+// Byte offset of the 16-byte core-matrix row (row, K unit of 8 elements) in a plane.
 __device__ __forceinline__ uint32_t core_off(int row, int kunit) {
   return (uint32_t)((row >> 3) * SBO + kunit * LBO + (row & 7) * 16);
 }
@@ -105,20 +110,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t phase) {
   return ok != 0;
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // Exponent E with 0 <= m < 2^E (E = 0 for m = 0): the scale of a row or column.
@@ -128,21 +130,40 @@ __device__ __forceinline__ int scale_exp(float m) {
 }
 __device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(127 + e) << 23); }
 
-// The six digits of the double-float value (h + l) 2^8 / 2^E (scale = 2^{8 - E}):
-// d = rint(r), r = (r - d) exact, (r, c) renormalised exactly by two-sum, both
-// times 256 (exact).
-__device__ __forceinline__ void digits6(float h, float l, float scale, float* d) {
-  float r = h * scale, c = l * scale;
+// Round to the nearest integer (ties to even) for |x| < 2^22: adding and
+// removing 1.5 * 2^23 leaves no fraction bits.
+__device__ __forceinline__ float2 rint2(float2 x) {
+  const float2 big = make_float2(12582912.f, 12582912.f), nbig = make_float2(-12582912.f, -12582912.f);
+  return __fadd2_rn(__fadd2_rn(x, big), nbig);
+}
+
+// (r, c) <- (r + c, rounding error) exactly (two-sum), lane-wise.
+__device__ __forceinline__ void two_sum2(float2& r, float2& c) {
+  const float2 a = __fadd2_rn(r, c);
+  const float2 bb = __fadd2_rn(a, make_float2(-r.x, -r.y));
+  const float2 e = __fadd2_rn(__fadd2_rn(r, make_float2(bb.x - a.x, bb.y - a.y)), __fadd2_rn(c, make_float2(-bb.x, -bb.y)));
+  r = a;
+  c = e;
+}
+
+// The six digits of the double-float value (h + l) 2^7 / 2^E, sc = 2^{7 - E},
+// two values at once (lanes).  With r the remainder in units of the next digit:
+// d = rint(r), r = 256 (r - d) (exact); the low part c (|c| <= 2^-17 at the
+// start) is folded in exactly (two-sum) before digits 3 and 5, when two steps of
+// 256 have made it as large as half a unit, so every digit satisfies |d| <= 129.
+__device__ __forceinline__ void digits6x2(float2 h, float2 l, float2 sc, float2* d) {
+  const float2 k256 = make_float2(256.f, 256.f), nk256 = make_float2(-256.f, -256.f);
+  const float2 k64k = make_float2(65536.f, 65536.f);
+  float2 r = __fmul2_rn(h, sc), c = __fmul2_rn(l, sc);
 #pragma unroll
   for (int s = 0; s < ND; ++s) {
-    const float q = rintf(r);
+    if (s == 2 || s == 4) {
+      c = __fmul2_rn(c, k64k);
+      two_sum2(r, c);
+    }
+    const float2 q = rint2(r);
     d[s] = q;
-    r -= q;
-    const float a = r + c;
-    const float bb = a - r;
-    const float e = (r - (a - bb)) + (c - bb);
-    r = a * 256.f;
-    c = e * 256.f;
+    if (s + 1 < ND) r = __ffma2_rn(q, nk256, __fmul2_rn(r, k256));  // 256 r - 256 q: exact
   }
 }
 
@@ -150,15 +171,19 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // digits are small integers: exact
   return *reinterpret_cast<const uint32_t*>(&v);
 }
+__device__ __forceinline__ unsigned short bf16_bits(float x) {
+  const __nv_bfloat16 v = __float2bfloat16_rn(x);
+  return *reinterpret_cast<const unsigned short*>(&v);
+}
 
 }  // namespace rtc
 
-// grid (ceil(n_max / 128), n_units, ceil(nrhs / 16)), block 128, dynamic smem
+// grid (ceil(n_max / 128), n_units, ceil(nrhs / 16)), block 256, dynamic smem
 // rtc::SMEM_LAUNCH.  X32 = B - M X (rounded to complex64) for the unit's rows of
 // this tile and the 16 columns of this slice.  Every wait on the tensor core is
 // bounded; on a timeout the unit is flagged LSMS_UNIT_TIMEOUT (and re-solved by
 // the FP64 fallback) and the CTA returns after a second bounded wait.
-__global__ void __launch_bounds__(128) k_residual_tc(const Unit* __restrict__ units, const char* fac_base, char* ws,
+__global__ void __launch_bounds__(256, 2) k_residual_tc(const Unit* __restrict__ units, const char* fac_base, char* ws,
                                                      int K, int nrhs, bool explicit_b, const int32_t* __restrict__ done,
                                                      int32_t* stat) {
   using namespace rtc;
@@ -179,10 +204,9 @@ __global__ void __launch_bounds__(128) k_residual_tc(const Unit* __restrict__ un
   uint8_t* sB = smem + ND * PLANE_A;           // ND planes of PLANE_B
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + ND * PLANE_A + ND * PLANE_B);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + ND * PLANE_A + ND * PLANE_B + 16);
-  __shared__ float s_cscale[NC];
   __shared__ int s_cexp[NC];
 
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(TMEM_COLS));
@@ -192,22 +216,32 @@ __global__ void __launch_bounds__(128) k_residual_tc(const Unit* __restrict__ un
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  if (tid < NC) {
-    const int col = col0 + tid;
-    const int F = col < nrhs ? scale_exp(colmax[col]) : 0;
-    s_cexp[tid] = F;
-    s_cscale[tid] = pow2f(8 - F);
-  }
-  const int row = row0 + tid;
+  if (tid < NC) s_cexp[tid] = col0 + tid < nrhs ? scale_exp(colmax[col0 + tid]) : 0;
+  // A: row rl of the tile, complex columns 8 half .. 8 half + 7 of each chunk
+  const int rl = tid & (TM - 1), half = tid >> 7;
+  const int row = row0 + rl;
   const bool live = row < n;
   const int E = live ? scale_exp(rowmax[row]) : 0;
-  const float rscale = pow2f(8 - E);
-
-  // double-float accumulators of sum_g acc_g 2^{-8 g}: [Re outputs 0..15 | Im outputs 0..15]
-  float accs[NOUT], acct[NOUT];
+  const float2 rsc = make_float2(pow2f(7 - E), pow2f(7 - E));
+  // B: element (row j, column cc) of the chunk's 16 x 16 block of X
+  const int bcc = tid & 15, bj = tid >> 4;
+  const int bcol = col0 + bcc;
+  const int F_b = bcol < nrhs ? scale_exp(colmax[bcol]) : 0;
+  const float2 csc = make_float2(pow2f(7 - F_b), pow2f(7 - F_b));
+  // epilogue: warps 0-3 the real outputs, warps 4-7 the imaginary ones, of row rl
+  float accs[NC], acct[NC];
 #pragma unroll
-  for (int c = 0; c < NOUT; ++c) accs[c] = acct[c] = 0.f;
+  for (int c = 0; c < NC; ++c) accs[c] = acct[c] = 0.f;
 
+  auto load_chunk = [&](int c0, float4* mv, float4& xv) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int col = c0 + half * 8 + q;
+      mv[q] = (live && col < n) ? M[(size_t)col * n + row] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const int j = c0 + bj;
+    xv = (bcol < nrhs && j < n) ? Xdf[(size_t)bcol * n + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
   auto wait_mma = [&](int j) -> bool {
     bool ok = false;
     const uint32_t mb = smem_u32(mbar);
@@ -221,14 +255,14 @@ __global__ void __launch_bounds__(128) k_residual_tc(const Unit* __restrict__ un
     return ok;
   };
   auto flush = [&](uint32_t tmem) {
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t base = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(half * NC);
 #pragma unroll 1
     for (int g = 0; g < NG; ++g) {
-      float v[32];
-      tmem_ld32(lane_base + (uint32_t)(g * NOUT), v);
+      float v[16];
+      tmem_ld16(base + (uint32_t)(g * NOUT), v);
       const float w = pow2f(-8 * g);
 #pragma unroll
-      for (int c = 0; c < NOUT; ++c) {
+      for (int c = 0; c < NC; ++c) {
         const float x = v[c] * w;  // an integer times a power of two: exact
         const float a = accs[c] + x;
         const float bb = a - accs[c];
@@ -239,6 +273,8 @@ __global__ void __launch_bounds__(128) k_residual_tc(const Unit* __restrict__ un
   };
 
   const int nchunks = (n + KCC - 1) / KCC;
+  float4 mv[8], xv;
+  load_chunk(0, mv, xv);
   uint32_t tmem = 0;
   bool ok = true;
   int issued = -1;
@@ -247,73 +283,49 @@ __global__ void __launch_bounds__(128) k_residual_tc(const Unit* __restrict__ un
       if (!(ok = wait_mma(ch - 1))) break;          // planes free again, accumulators current
       if (ch % FLUSH == 0) flush(tmem);
     }
-    const int c0 = ch * KCC;
-    // ---- A planes: this thread's row, 16 complex columns -> 32 real K
+    // ---- A planes: this thread's 8 elements, real parts -> K unit half, imaginary -> 2 + half
     {
-      float4 mv[KCC];
+      const uint32_t o_re = core_off(rl, half), o_im = core_off(rl, 2 + half);
 #pragma unroll
-      for (int jj = 0; jj < KCC; ++jj)
-        mv[jj] = (live && c0 + jj < n) ? M[(size_t)(c0 + jj) * n + row] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int q0 = 0; q0 < 8; q0 += 4) {
+        float2 d[4][ND];
 #pragma unroll
-      for (int part = 0; part < 2; ++part) {    // 0: Re (K 0..15), 1: Im (K 16..31)
+        for (int q = 0; q < 4; ++q) {
+          const float4 v = mv[q0 + q];
+          rtc::digits6x2(make_float2(v.x, v.y), make_float2(v.z, v.w), rsc, d[q]);
+        }
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {  // 8 columns per core-matrix row
-          float d[8][ND];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const float4 v = mv[half * 8 + q];
-            digits6(part ? v.y : v.x, part ? v.w : v.z, rscale, d[q]);
-          }
-          const uint32_t off = core_off(tid, part * 2 + half);
-#pragma unroll
-          for (int s = 0; s < ND; ++s) {
-            uint4 pk;
-            pk.x = rtc::pack_bf16(d[0][s], d[1][s]);
-            pk.y = rtc::pack_bf16(d[2][s], d[3][s]);
-            pk.z = rtc::pack_bf16(d[4][s], d[5][s]);
-            pk.w = rtc::pack_bf16(d[6][s], d[7][s]);
-            *reinterpret_cast<uint4*>(sA + s * PLANE_A + off) = pk;
-          }
+        for (int s = 0; s < ND; ++s) {
+          uint2 pr, pi;
+          pr.x = rtc::pack_bf16(d[0][s].x, d[1][s].x);
+          pr.y = rtc::pack_bf16(d[2][s].x, d[3][s].x);
+          pi.x = rtc::pack_bf16(d[0][s].y, d[1][s].y);
+          pi.y = rtc::pack_bf16(d[2][s].y, d[3][s].y);
+          *reinterpret_cast<uint2*>(sA + s * PLANE_A + o_re + q0 * 2) = pr;
+          *reinterpret_cast<uint2*>(sA + s * PLANE_A + o_im + q0 * 2) = pi;
         }
       }
     }
-    // ---- B planes (warp 0): item = (complex column cc, 8 rows jg) of X
-    if (warp == 0) {
-      const int cc = lane & 15, jg = lane >> 4;
-      const int col = col0 + cc;
-      const float cs = s_cscale[cc];
-      float dr[8][ND], di[8][ND];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int j = c0 + jg * 8 + q;
-        const float4 v = (col < nrhs && j < n) ? Xdf[(size_t)col * n + j] : make_float4(0.f, 0.f, 0.f, 0.f);
-        digits6(v.x, v.y, cs, dr[q]);
-        digits6(v.z, v.w, cs, di[q]);
-      }
-      // output row cc (Re): K jg -> Re X, K 2 + jg -> -Im X; output row NC + cc (Im): K jg -> Im X, K 2 + jg -> Re X
-      const uint32_t o_re = core_off(cc, 0), o_im = core_off(NC + cc, 0);
+    // ---- B planes: one element of X; output row bcc (Re): K bj -> Re X, K 16 + bj -> -Im X;
+    // output row NC + bcc (Im): K bj -> Im X, K 16 + bj -> Re X
+    {
+      float2 d[ND];
+      rtc::digits6x2(make_float2(xv.x, xv.z), make_float2(xv.y, xv.w), csc, d);
+      const uint32_t kb = (uint32_t)((bj & 7) * 2);
+      const uint32_t o_re = core_off(bcc, bj >> 3) + kb, o_ren = core_off(bcc, 2 + (bj >> 3)) + kb;
+      const uint32_t o_im = core_off(NC + bcc, bj >> 3) + kb, o_imr = core_off(NC + bcc, 2 + (bj >> 3)) + kb;
 #pragma unroll
       for (int s = 0; s < ND; ++s) {
-        uint4 pr, pi, pn;
-        pr.x = rtc::pack_bf16(dr[0][s], dr[1][s]);
-        pr.y = rtc::pack_bf16(dr[2][s], dr[3][s]);
-        pr.z = rtc::pack_bf16(dr[4][s], dr[5][s]);
-        pr.w = rtc::pack_bf16(dr[6][s], dr[7][s]);
-        pi.x = rtc::pack_bf16(di[0][s], di[1][s]);
-        pi.y = rtc::pack_bf16(di[2][s], di[3][s]);
-        pi.z = rtc::pack_bf16(di[4][s], di[5][s]);
-        pi.w = rtc::pack_bf16(di[6][s], di[7][s]);
-        pn.x = pi.x ^ 0x80008000u;  // -Im X: flip both bf16 sign bits
-        pn.y = pi.y ^ 0x80008000u;
-        pn.z = pi.z ^ 0x80008000u;
-        pn.w = pi.w ^ 0x80008000u;
         uint8_t* plane = sB + s * PLANE_B;
-        *reinterpret_cast<uint4*>(plane + o_re + jg * LBO) = pr;
-        *reinterpret_cast<uint4*>(plane + o_re + (2 + jg) * LBO) = pn;
-        *reinterpret_cast<uint4*>(plane + o_im + jg * LBO) = pi;
-        *reinterpret_cast<uint4*>(plane + o_im + (2 + jg) * LBO) = pr;
+        const unsigned short re = rtc::bf16_bits(d[s].x), im = rtc::bf16_bits(d[s].y);
+        *reinterpret_cast<unsigned short*>(plane + o_re) = re;
+        *reinterpret_cast<unsigned short*>(plane + o_ren) = (unsigned short)(im ^ 0x8000u);  // -Im X
+        *reinterpret_cast<unsigned short*>(plane + o_im) = im;
+        *reinterpret_cast<unsigned short*>(plane + o_imr) = re;
       }
     }
+    // the next chunk's elements are loaded while this chunk's products run
+    if (ch + 1 < nchunks) load_chunk((ch + 1) * KCC, mv, xv);
     // generic-proxy stores visible to the tensor core
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -347,19 +359,22 @@ __global__ void __launch_bounds__(128) k_residual_tc(const Unit* __restrict__ un
     if ((ok = wait_mma(issued))) flush(tmem);
   }
   if (ok && live) {
+    // MX = U 2^{E + F - 14}; this thread holds the real (half 0) or imaginary (half 1) parts
     const double2* B = reinterpret_cast<const double2*>(ws + u.r_off);
-    float2* X32 = reinterpret_cast<float2*>(ws + u.x32_off);
+    float* X32 = reinterpret_cast<float*>(ws + u.x32_off);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const int col = col0 + c;
       if (col >= nrhs) continue;
-      const int sh = E + s_cexp[c] - 16;
-      const double re = ldexp((double)accs[c] + (double)acct[c], sh);
-      const double im = ldexp((double)accs[NC + c] + (double)acct[NC + c], sh);
-      double2 b;
-      if (explicit_b) b = B[(size_t)col * n + row];
-      else b = (row == col && col < K) ? mk(1.0, 0.0) : mk(0.0, 0.0);
-      X32[(size_t)col * n + row] = make_float2((float)(b.x - re), (float)(b.y - im));
+      const double mx = ldexp((double)accs[c] + (double)acct[c], E + s_cexp[c] - 14);
+      double b;
+      if (explicit_b) {
+        const double2 bb = B[(size_t)col * n + row];
+        b = half ? bb.y : bb.x;
+      } else {
+        b = (half == 0 && row == col && col < K) ? 1.0 : 0.0;
+      }
+      X32[2 * ((size_t)col * n + row) + half] = (float)(b - mx);
     }
   }
   if (!ok) {
@@ -387,8 +402,8 @@ int residual_tc_chunk(const Unit* d_units, int n_units, int n_max, const char* f
     attr_set = true;
   }
   const dim3 grid((n_max + rtc::TM - 1) / rtc::TM, n_units, (nrhs + rtc::NC - 1) / rtc::NC);
-  LSMS_LAUNCH(k_residual_tc, grid, dim3(128), rtc::SMEM_LAUNCH, st, d_units, fac_base, ws, K, nrhs, explicit_b, done,
-              stat);
+  LSMS_LAUNCH(k_residual_tc, grid, dim3(rtc::NT), rtc::SMEM_LAUNCH, st, d_units, fac_base, ws, K, nrhs, explicit_b,
+              done, stat);
   return LSMS_OK;
 }
 
