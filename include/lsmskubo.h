@@ -323,6 +323,11 @@ int lsms_kubo_sigma_backward(const lsms_liz* liz, int lmax, const int32_t* speci
  *                     or more right-hand sides runs on the tensor cores (bf16
  *                     fixed-point digits, exact FP32 accumulation, about 2^-48
  *                     of |M| |X|); 0: double-float arithmetic on the FP32 pipes
+ *   "solve_cols"      right-hand-side columns per CTA of the mixed form's
+ *                     triangular solves above 8 columns (8, 16 or 32; 0 = 8 up to
+ *                     16 columns, else 16): a tile shape the autotuner picks
+ *   "solve_regs"      0 (default): 8- and 16-column solve CTAs sized for 8 CTAs
+ *                     per SM (64 registers); 1: for 4 CTAs per SM (128 registers)
  * LSMS_ERR_ARG for an unknown name or a value out of range. */
 int lsms_set_option(const char* name, double value);
 int lsms_get_option(const char* name, double* value);

@@ -8,6 +8,7 @@ NumPy inputs in, sigma and rho out.
 """
 import numpy as np
 
+from . import autotune
 from . import binding as B
 
 
@@ -43,10 +44,14 @@ class Problem:
     raise UnitStatusError if a unit's result is invalid (a host synchronisation;
     skipped while a CUDA graph is being captured).  Set it False for timing
     loops and check with check() afterwards.
+    tuning: "auto" applies the autotuned tile and launch shapes of the problem's
+    size class (autotune.lookup; the defaults when the class is not in the
+    table), a dict applies those options, None leaves the options alone.  They
+    are set through lsms_set_option before each library call.
     """
 
     def __init__(self, pos, lattice, r_liz, lmax, species, tinv, z, J, volume, precision="fp64", device="cuda",
-                 keep_factors=True, workspace_bytes=None, conj_pairs=False, check_status=True):
+                 keep_factors=True, workspace_bytes=None, conj_pairs=False, check_status=True, tuning="auto"):
         import torch
         self.check_status = bool(check_status)
         self.generation = 0  # number of tau solves so far (the factors in lu_store belong to the latest)
@@ -83,12 +88,20 @@ class Problem:
         self.bw_status = torch.empty((nE, self.liz.n_atoms), dtype=torch.int32, device=self.device)
         self._bw_ws = None
         self._side = None  # side stream of step()
+        if tuning == "auto":
+            found = autotune.lookup(self)
+            self.tuning = dict(autotune.DEFAULTS) if found is None else found
+            self.tuning_source = "default" if found is None else "table"
+        else:
+            self.tuning = None if tuning is None else dict(tuning)
+            self.tuning_source = "given" if tuning is not None else "none"
 
     @property
     def n_units(self):
         return self.liz.n_atoms * self.z.shape[0]
 
     def solve_tau(self, tinv=None, stream=None):
+        autotune.apply(self.tuning)
         t = self.tinv if tinv is None else tinv
         B.tau_blocks(self.liz, self.lmax, self.species, t, self.z, self.precision, tau=self.tau,
                      unit_status=self.unit_status, workspace=self.workspace, lu_store=self.lu_store, stream=stream,
@@ -132,6 +145,7 @@ class Problem:
                                                 B._prec(self.precision, self.conj_pairs) | self._ws_flags)
             self._bw_ws = torch.empty(min(al, max(mn, self.workspace.numel())), dtype=torch.uint8,
                                       device=self.device)
+        autotune.apply(self.tuning)
         t = self.tinv if tinv is None else tinv
         out = B.kubo_sigma_backward(self.liz, self.lmax, self.species, t, self.z, self.J, self.tau, self.volume,
                                     grad_sigma.contiguous(), self.precision, lu_store=self.lu_store,
@@ -144,6 +158,7 @@ class Problem:
         """The gradient for an earlier forward whose tau and factors have since been overwritten:
         tau is solved again for `tinv` into private buffers and the factors are recomputed (no store)."""
         import torch
+        autotune.apply(self.tuning)
         nE = self.z.shape[0]
         prec = B._prec(self.precision, self.conj_pairs)
         mn, al = B.tau_workspace_bytes(self.liz, self.lmax, nE, prec)

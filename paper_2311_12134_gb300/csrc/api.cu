@@ -92,7 +92,11 @@ static std::atomic<int> g_opt_fallback_slots{8};
 static std::atomic<int> g_opt_ir_max_sweeps{kIrMaxIter};
 static std::atomic<int> g_opt_streams{0};  // 0: LSMS_STREAMS or the default
 static std::atomic<int> g_opt_residual_tc{1};
+static std::atomic<int> g_opt_solve_cols{0};  // 0: 8 columns per CTA up to 16 right-hand sides, else 16
+static std::atomic<int> g_opt_solve_regs{0};
 int opt_residual_tc() { return g_opt_residual_tc.load(); }
+int opt_solve_cols() { return g_opt_solve_cols.load(); }
+int opt_solve_regs() { return g_opt_solve_regs.load(); }
 double opt_growth_limit() { return g_opt_growth_limit.load(); }
 int opt_fallback_slots() { return g_opt_fallback_slots.load(); }
 int opt_ir_max_sweeps() { return g_opt_ir_max_sweeps.load(); }
@@ -1596,6 +1600,13 @@ extern "C" int lsms_set_option(const char* name, double value) {
   } else if (n == "residual_tc") {
     if (!in_int(0, 1)) return fail(LSMS_ERR_ARG, "residual_tc must be 0 or 1");
     g_opt_residual_tc.store((int)value);
+  } else if (n == "solve_cols") {
+    if (!(value == 0 || value == 8 || value == 16 || value == 32))
+      return fail(LSMS_ERR_ARG, "solve_cols must be 0, 8, 16 or 32");
+    g_opt_solve_cols.store((int)value);
+  } else if (n == "solve_regs") {
+    if (!in_int(0, 1)) return fail(LSMS_ERR_ARG, "solve_regs must be 0 or 1");
+    g_opt_solve_regs.store((int)value);
   } else {
     return fail(LSMS_ERR_ARG, "lsms_set_option: unknown option '%s'", name);
   }
@@ -1611,6 +1622,8 @@ extern "C" int lsms_get_option(const char* name, double* value) {
   else if (n == "ir_max_sweeps") *value = g_opt_ir_max_sweeps.load();
   else if (n == "streams") *value = stream_parts();
   else if (n == "residual_tc") *value = g_opt_residual_tc.load();
+  else if (n == "solve_cols") *value = g_opt_solve_cols.load();
+  else if (n == "solve_regs") *value = g_opt_solve_regs.load();
   else return fail(LSMS_ERR_ARG, "lsms_get_option: unknown option '%s'", name);
   return LSMS_OK;
 }

@@ -246,6 +246,8 @@ enum RhsField { RHS_X = 0, RHS_X32 = 1 };
 int residual_tc_chunk(const Unit* d_units, int n_units, int n_max, const char* fac_base, char* ws, int K, int nrhs,
                       bool explicit_b, const int32_t* done, int32_t* stat, cudaStream_t st);
 int opt_residual_tc();
+int opt_solve_cols();
+int opt_solve_regs();
 
 // Trailing update A22 -= L21 U12 of the complex64 LU on the tensor cores (tc_gemm.cu).
 int gemm_tc_chunk(const Unit* d_units, int n_units, int n_max, int k, char* fac_base, int32_t* stat,

@@ -782,8 +782,8 @@ __global__ void __launch_bounds__(64) k_diag_inv(const Unit* __restrict__ units,
 // multiplies them by the stored inverse of the diagonal block (all threads, no
 // serial chain), and updates the rows below (above, going back) with the block's
 // 32 columns of L (U).
-template <int NCOL, int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_solve_c64(const Unit* __restrict__ units, const char* fac_base,
+template <int NCOL, int NT, int MINB = 1024 / NT>
+__global__ void __launch_bounds__(NT, MINB) k_solve_c64(const Unit* __restrict__ units, const char* fac_base,
                                                      char* ws, int which, int nrhs, const int32_t* done) {
   static_assert(NCOL >= 2 && NCOL % 2 == 0 && NCOL <= 32, "padded column count");
   constexpr int NB = kDiagNB;
@@ -915,14 +915,34 @@ int lu_solve_chunk(const Unit* d_units, int n_units, const char* fac_base, char*
   if (nrhs < 1 || nrhs > 32) return fail(LSMS_ERR_ARG, "internal: nrhs %d out of range", nrhs);
   constexpr int NB = LuCfg<R>::NB;
   if constexpr (std::is_same<R, float>::value) {
-    // more than 8 columns: slices of 8 (16 above 16 columns) per 128-thread CTA,
-    // so that each unit's chain of block steps runs as two concurrent chains
+    // more than 8 columns: column slices per CTA (option "solve_cols"; default 8
+    // for up to 16 columns, 16 above), each slice a CTA with its own chain of
+    // block steps; wider slices read the factors fewer times, narrower ones give
+    // more concurrent chains
     const dim3 g1(n_units), b256(kSolveThreads);
     if (nrhs <= 2) LSMS_LAUNCH((k_solve_c64<2, kSolveThreads>), g1, b256, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
     else if (nrhs <= 4) LSMS_LAUNCH((k_solve_c64<4, kSolveThreads>), g1, b256, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
     else if (nrhs <= 8) LSMS_LAUNCH((k_solve_c64<8, kSolveThreads>), g1, b256, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
-    else if (nrhs <= 16) LSMS_LAUNCH((k_solve_c64<8, 128>), dim3(n_units, 2), dim3(128), 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
-    else LSMS_LAUNCH((k_solve_c64<16, 128>), dim3(n_units, 2), dim3(128), 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
+    else {
+      // option "solve_regs": 0 = 8 CTAs of 128 threads per SM (64 registers), 1 = 4 (128 registers)
+      int sl = opt_solve_cols();
+      if (sl <= 0) sl = nrhs <= 16 ? 8 : 16;
+      if (sl == 32 && nrhs <= 16) sl = 16;  // one slice holds every column
+      const bool regs = opt_solve_regs() != 0;
+      const dim3 gs(n_units, (nrhs + sl - 1) / sl);
+#define LSMS_SOLVE(NCOL, NT, MINB) \
+  LSMS_LAUNCH((k_solve_c64<NCOL, NT, MINB>), gs, dim3(NT), 0, st, d_units, fac_base, ws, which_rhs, nrhs, done)
+      if (sl == 8) {
+        if (regs) LSMS_SOLVE(8, 128, 4);
+        else LSMS_SOLVE(8, 128, 8);
+      } else if (sl == 16) {
+        if (regs) LSMS_SOLVE(16, 128, 4);
+        else LSMS_SOLVE(16, 128, 8);
+      } else {
+        LSMS_SOLVE(32, 256, 2);
+      }
+#undef LSMS_SOLVE
+    }
   } else {
     LSMS_LAUNCH((k_solve<R, NB>), dim3(n_units), dim3(512), 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
   }

@@ -250,3 +250,28 @@ def test_conductivity_host_call_matches_oracle(B, alloy, precision):
     assert np.abs(sig - ref).max() < TOL[precision] * np.abs(ref).max()
     rref = okubo.resistivity(ref)
     assert np.abs(rho - rref).max() < 10 * TOL[precision] * np.abs(rref).max()
+
+
+@pytest.mark.parametrize("cols,regs,streams", [(8, 1, 4), (16, 0, 2), (16, 1, 4), (32, 0, 1)])
+def test_tuning_options_keep_results(B, alloy, cols, regs, streams):
+    """The autotuner's shapes (solve columns per CTA, register bound, concurrent parts) change the
+    launch layout only: tau and the gradient match the default layout to rounding."""
+    w, _, _, _, J = alloy
+    Jd = torch.as_tensor(J).cuda()
+    wgt = torch.zeros((1, 3, 3), dtype=torch.complex128, device="cuda")
+    wgt[0, 0, 0] = 1.0
+    out = []
+    for opts in ({}, {"solve_cols": cols, "solve_regs": regs, "streams": streams}):
+        with options(B, **opts) if opts else contextlib.nullcontext():
+            lz = B.build_liz(w.pos, w.lattice, w.r_liz)
+            sp = torch.as_tensor(w.species).cuda()
+            t = torch.as_tensor(w.tinv).cuda()
+            store = torch.empty(B.lu_store_bytes(lz, w.lmax, 2, B.LSMS_MIXED), dtype=torch.uint8, device="cuda")
+            tau, st = B.tau_blocks(lz, w.lmax, sp, t, w.z, "mixed", lu_store=store)
+            g, _ = B.kubo_sigma_backward(lz, w.lmax, sp, t, w.z, Jd, tau, w.volume, wgt, "mixed", lu_store=store)
+            torch.cuda.synchronize()
+        assert not np.any(st.cpu().numpy() & 0xff)
+        out.append((tau.cpu().numpy(), g.cpu().numpy()))
+    (t0, g0), (t1, g1) = out
+    assert np.abs(t1 - t0).max() <= 1e-12 * np.abs(t0).max()
+    assert np.abs(g1 - g0).max() <= 1e-11 * np.abs(g0).max()
