@@ -507,6 +507,7 @@ def run_ours(args):
         return max_over_ranks(ms, active, device=dev), (B.launch_count() - l0) / steps
 
     main = make(args.precision)
+    tuning, tuning_source = main.tuning, main.tuning_source  # autotuned shapes of this size class
     units = main.n_units
     offsets = main.liz.export()["offsets"]
     sizes = np.diff(offsets)
@@ -651,7 +652,8 @@ def run_ours(args):
                    "workspace_mib": args.chunk_mb or "all units", "precision": args.precision,
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (working set > 100 GB)",
                    "step": "Problem.step: forward (assembly, LU, tau, refinement, traces, sigma, rho) + adjoint "
-                           "d Re sigma_xx / d t^-1 per delta, one CUDA graph"},
+                           "d Re sigma_xx / d t^-1 per delta, one CUDA graph",
+                   "tuning": tuning, "tuning_source": tuning_source},
         "sigma_ms": sigma_ms, "ms_per_step_eager": ms_eager,
         "timing": "CUDA-graph replay of the whole step, CUDA events on the launch stream",
         "unit_status_clean": True,

@@ -20,16 +20,17 @@
 //   [Re MX | Im MX] = [Re M | Im M] x [[Re X, Im X], [-Im X, Re X]].
 //
 // CTA: 128 rows of one unit (TMEM lanes), 16 complex right-hand-side columns
-// (blockIdx.z picks the slice), 8 warps; thread t owns row t % 128 and the
-// column half t / 128.  Per chunk of 16 complex columns of M:
-//   all threads  split their 8 elements of M (loaded during the previous
-//                chunk's products) into the six digit planes of A and one
-//                element of X into the six planes of B (no-swizzle K-major
+// (blockIdx.z picks the slice), 8 warps.  Per chunk of 16 complex columns of M:
+//   all threads  split 8 elements of M (two threads per row, loaded during the
+//                previous chunk's products) into the six digit planes of A and
+//                one element of X into the six planes of B (no-swizzle K-major
 //                core-matrix layout in shared memory), real and imaginary
 //                parts in the two lanes of the paired FP32 instructions;
 //   one thread   issues the 42 tcgen05.mma (M = 128, N = 32, K = 16) of the
-//                chunk and commits them to an mbarrier (bounded waits);
-//   every 4th    warps 0-3 add the real outputs, warps 4-7 the imaginary ones.
+//                chunk and commits them to an mbarrier (bounded waits, polled
+//                by one warp);
+//   every 4th    warps 0-3 add the real outputs of their TMEM lanes, warps 4-7
+//                the imaginary ones.
 #include <cstdint>
 
 #include <cuda_bf16.h>
@@ -217,12 +218,19 @@ __global__ void __launch_bounds__(256, 2) k_residual_tc(const Unit* __restrict__
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (tid < NC) s_cexp[tid] = col0 + tid < nrhs ? scale_exp(colmax[col0 + tid]) : 0;
-  // A: row rl of the tile, complex columns 8 half .. 8 half + 7 of each chunk
-  const int rl = tid & (TM - 1), half = tid >> 7;
+  // epilogue: TMEM lane (warp % 4) * 32 + lane = row rl; warps 0-3 the real outputs, 4-7 the imaginary ones
+  const int rl = (warp & 3) * 32 + (tid & 31), half = warp >> 2;
   const int row = row0 + rl;
   const bool live = row < n;
   const int E = live ? scale_exp(rowmax[row]) : 0;
-  const float2 rsc = make_float2(pow2f(7 - E), pow2f(7 - E));
+  // A: warp w splits rows 16 w .. 16 w + 15, two lanes per row; lane parity p takes the complex
+  // columns 4p .. 4p + 3 and 8 + 4p .. 8 + 4p + 3 of each chunk, so that a warp's 8-byte stores
+  // fill two whole core matrices (conflict-free)
+  const int arow_l = warp * 16 + ((tid & 31) >> 1), aq0 = (tid & 1) * 4;
+  const int arow = row0 + arow_l;
+  const bool alive = arow < n;
+  const int EA = alive ? scale_exp(rowmax[arow]) : 0;
+  const float2 rsc = make_float2(pow2f(7 - EA), pow2f(7 - EA));
   // B: element (row j, column cc) of the chunk's 16 x 16 block of X
   const int bcc = tid & 15, bj = tid >> 4;
   const int bcol = col0 + bcc;
@@ -235,21 +243,26 @@ __global__ void __launch_bounds__(256, 2) k_residual_tc(const Unit* __restrict__
 
   auto load_chunk = [&](int c0, float4* mv, float4& xv) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int col = c0 + half * 8 + q;
-      mv[q] = (live && col < n) ? M[(size_t)col * n + row] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < 8; ++q) {  // q < 4: columns aq0 + q; q >= 4: 8 + aq0 + q - 4
+      const int col = c0 + (q >> 2) * 8 + aq0 + (q & 3);
+      mv[q] = (alive && col < n) ? M[(size_t)col * n + arow] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const int j = c0 + bj;
     xv = (bcol < nrhs && j < n) ? Xdf[(size_t)bcol * n + j] : make_float4(0.f, 0.f, 0.f, 0.f);
   };
+  // warp 0 polls the mbarrier (bounded) while the others wait at the barrier, leaving the
+  // issue slots to the SM's other CTA
   auto wait_mma = [&](int j) -> bool {
-    bool ok = false;
-    const uint32_t mb = smem_u32(mbar);
-    for (long long it = 0; it < kWaitLimit; ++it)
-      if (mbar_try_wait(mb, (uint32_t)(j & 1))) {
-        ok = true;
-        break;
-      }
+    bool ok = true;
+    if (warp == 0) {
+      ok = false;
+      const uint32_t mb = smem_u32(mbar);
+      for (long long it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(mb, (uint32_t)(j & 1))) {
+          ok = true;
+          break;
+        }
+    }
     ok = __syncthreads_and(ok);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     return ok;
@@ -283,27 +296,26 @@ __global__ void __launch_bounds__(256, 2) k_residual_tc(const Unit* __restrict__
       if (!(ok = wait_mma(ch - 1))) break;          // planes free again, accumulators current
       if (ch % FLUSH == 0) flush(tmem);
     }
-    // ---- A planes: this thread's 8 elements, real parts -> K unit half, imaginary -> 2 + half
-    {
-      const uint32_t o_re = core_off(rl, half), o_im = core_off(rl, 2 + half);
+    // ---- A planes: this thread's 8 elements (4 in each column half); real parts -> K unit hh,
+    // imaginary parts -> K unit 2 + hh, at element offset aq0 within the 8-element unit
 #pragma unroll
-      for (int q0 = 0; q0 < 8; q0 += 4) {
-        float2 d[4][ND];
+    for (int hh = 0; hh < 2; ++hh) {
+      const uint32_t o_re = core_off(arow_l, hh) + aq0 * 2, o_im = core_off(arow_l, 2 + hh) + aq0 * 2;
+      float2 d[4][ND];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 v = mv[q0 + q];
-          rtc::digits6x2(make_float2(v.x, v.y), make_float2(v.z, v.w), rsc, d[q]);
-        }
+      for (int q = 0; q < 4; ++q) {
+        const float4 v = mv[hh * 4 + q];
+        rtc::digits6x2(make_float2(v.x, v.y), make_float2(v.z, v.w), rsc, d[q]);
+      }
 #pragma unroll
-        for (int s = 0; s < ND; ++s) {
-          uint2 pr, pi;
-          pr.x = rtc::pack_bf16(d[0][s].x, d[1][s].x);
-          pr.y = rtc::pack_bf16(d[2][s].x, d[3][s].x);
-          pi.x = rtc::pack_bf16(d[0][s].y, d[1][s].y);
-          pi.y = rtc::pack_bf16(d[2][s].y, d[3][s].y);
-          *reinterpret_cast<uint2*>(sA + s * PLANE_A + o_re + q0 * 2) = pr;
-          *reinterpret_cast<uint2*>(sA + s * PLANE_A + o_im + q0 * 2) = pi;
-        }
+      for (int s = 0; s < ND; ++s) {
+        uint2 pr, pi;
+        pr.x = rtc::pack_bf16(d[0][s].x, d[1][s].x);
+        pr.y = rtc::pack_bf16(d[2][s].x, d[3][s].x);
+        pi.x = rtc::pack_bf16(d[0][s].y, d[1][s].y);
+        pi.y = rtc::pack_bf16(d[2][s].y, d[3][s].y);
+        *reinterpret_cast<uint2*>(sA + s * PLANE_A + o_re) = pr;
+        *reinterpret_cast<uint2*>(sA + s * PLANE_A + o_im) = pi;
       }
     }
     // ---- B planes: one element of X; output row bcc (Re): K bj -> Re X, K 16 + bj -> -Im X;
