@@ -229,7 +229,15 @@ int lsms_tau_blocks(const lsms_liz* liz, int lmax, const int32_t* species, int n
  * precision    LSMS_FP64: the K x K products in FP64.  LSMS_MIXED: the K x K
  *              products and the site sums in double-float arithmetic on the FP32
  *              pipes (unit roundoff about 2^-48); the last trace, the sums over
- *              atoms and sigma, rho in FP64 in both.
+ *              atoms and sigma, rho in FP64 in both.  Optionally
+ *              | LSMS_CONJ_PAIRS: tau holds conjugate pairs, tau(z[2d+1]) =
+ *              conj tau(z[2d]) (as lsms_tau_blocks writes them with that flag;
+ *              not checked); when the current matrices also satisfy
+ *              J(-,-) = conj J(+,+) and J(-,+) = conj J(+,-) (checked on the
+ *              device to 1e-12 of the largest |J|), the (-,+) and (-,-) traces
+ *              are taken as the conjugates of the (+,-) and (+,+) ones instead of
+ *              being computed (half the trace work); otherwise all four are
+ *              computed.
  * sigma_tilde  dev [n_delta][4][3][3] output or NULL.
  * sigma        dev [n_delta][3][3] output.
  * rho          dev [n_delta][3][3] double output or NULL.

@@ -246,8 +246,9 @@ def tau_blocks(liz, lmax, species, tinv, z, precision="fp64", tau=None, unit_sta
 
 
 def kubo_sigma(liz, lmax, species, J, tau, n_delta, volume, J_delta_stride=0, sigma=None, sigma_tilde=None,
-               rho=None, stream=None, precision="fp64"):
-    """lsms_kubo_sigma.  Returns (sigma [n_delta,3,3] c128, sigma_tilde [n_delta,4,3,3] c128, rho [n_delta,3,3] f64)."""
+               rho=None, stream=None, precision="fp64", conj_pairs=False):
+    """lsms_kubo_sigma.  Returns (sigma [n_delta,3,3] c128, sigma_tilde [n_delta,4,3,3] c128, rho [n_delta,3,3] f64).
+    conj_pairs: tau holds conjugate pairs; the (-,+) and (-,-) traces are conjugates when J allows."""
     import torch
     K = (lmax + 1) ** 2
     dev = tau.device
@@ -261,7 +262,8 @@ def kubo_sigma(liz, lmax, species, J, tau, n_delta, volume, J_delta_stride=0, si
     _check(lib().lsms_kubo_sigma(liz.handle, lmax, _dev(species, torch.int32, (liz.n_atoms,), "species"), n_species,
                                  _dev(J, torch.complex128, None, "J"), int(J_delta_stride),
                                  _dev(tau, torch.complex128, (2 * n_delta, liz.total_sites, K, K), "tau"), n_delta,
-                                 float(volume), _prec(precision), _dev(sigma_tilde, torch.complex128, (n_delta, 4, 3, 3), "sigma_tilde"),
+                                 float(volume), _prec(precision, conj_pairs),
+                                 _dev(sigma_tilde, torch.complex128, (n_delta, 4, 3, 3), "sigma_tilde"),
                                  _dev(sigma, torch.complex128, (n_delta, 3, 3), "sigma"),
                                  _dev(rho, torch.float64, (n_delta, 3, 3), "rho"), _stream(stream)))
     return sigma, sigma_tilde, rho

@@ -124,7 +124,7 @@ class Problem:
     def sigma(self, stream=None):
         B.kubo_sigma(self.liz, self.lmax, self.species, self.J, self.tau, self.n_delta, self.volume,
                      sigma=self.sigma_out, sigma_tilde=self.sigma_tilde, rho=self.rho, stream=stream,
-                     precision=self.precision)
+                     precision=self.precision, conj_pairs=self.conj_pairs)
         return self.sigma_out
 
     def forward(self, tinv=None, stream=None):

@@ -63,7 +63,7 @@ void timer_end(cudaStream_t st) {
 int kubo_forward(const int64_t* offsets, const int32_t* site_atom, const int32_t* species, int n_species,
                  const double2* J, int64_t J_dstride, const double2* tau, int64_t S_total, int K, int n_atoms, int n_delta,
                  double volume, bool df, float4* jdf, double2* partial, double2* S, double2* sigma_tilde,
-                 double2* sigma, double* rho, cudaStream_t st);
+                 double2* sigma, double* rho, cudaStream_t st, int32_t* halve);
 size_t jdf_scratch_bytes(int n_species, int K, int n_delta, int64_t J_dstride);
 int kubo_atoms(const int64_t* offsets, const int32_t* site_atom, const int32_t* species, int n_species,
                const double2* J, int64_t J_dstride, const double2* tau, int64_t S_total, int K, int n_atoms,
@@ -1870,6 +1870,8 @@ extern "C" int lsms_kubo_sigma(const lsms_liz* liz_c, int lmax, const int32_t* s
                                double* rho, void* stream) {
   clear_error();
   lsms_liz* liz = const_cast<lsms_liz*>(liz_c);
+  const bool conj = (precision & LSMS_CONJ_PAIRS) != 0;  // halve the traces when J allows (checked on the device)
+  precision &= ~LSMS_CONJ_PAIRS;
   int rc = check_common(liz, lmax, species, n_species, 2 * std::max(n_delta, 1), precision);
   if (rc) return rc;
   if (n_delta < 1 || !J || !tau || !sigma) return fail(LSMS_ERR_ARG, "lsms_kubo_sigma: J, tau, sigma required, n_delta >= 1");
@@ -1883,12 +1885,13 @@ extern "C" int lsms_kubo_sigma(const lsms_liz* liz_c, int lmax, const int32_t* s
   const size_t s_bytes = align_up((size_t)n_delta * 36 * 16);
   const size_t jdf_bytes = precision == LSMS_MIXED ? jdf_scratch_bytes(n_species, K, n_delta, J_delta_stride) : 0;
   char* scratch = nullptr;
-  LSMS_CUDA_TRY(cudaMallocAsync((void**)&scratch, part_bytes + s_bytes + jdf_bytes, st));
+  LSMS_CUDA_TRY(cudaMallocAsync((void**)&scratch, part_bytes + s_bytes + jdf_bytes + kAlign, st));
   rc = kubo_forward(dd->offsets, dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J), J_delta_stride,
                     reinterpret_cast<const double2*>(tau), liz->total_sites, K, liz->n_atoms, n_delta, volume,
                     precision == LSMS_MIXED, reinterpret_cast<float4*>(scratch + part_bytes + s_bytes),
                     reinterpret_cast<double2*>(scratch), reinterpret_cast<double2*>(scratch + part_bytes),
-                    reinterpret_cast<double2*>(sigma_tilde), reinterpret_cast<double2*>(sigma), rho, st);
+                    reinterpret_cast<double2*>(sigma_tilde), reinterpret_cast<double2*>(sigma), rho, st,
+                    conj ? reinterpret_cast<int32_t*>(scratch + part_bytes + s_bytes + jdf_bytes) : nullptr);
   cudaFreeAsync(scratch, st);
   return rc;
 }

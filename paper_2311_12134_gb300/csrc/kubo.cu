@@ -39,11 +39,13 @@ __global__ void __launch_bounds__(256) k_kubo_partial(const int64_t* __restrict_
                                                       const double2* __restrict__ J, int64_t J_dstride,
                                                       const float4* __restrict__ Jdf, int64_t Jdf_dstride,
                                                       const double2* __restrict__ tau, int64_t S_total, int K,
-                                                      int n_atoms, int n_species, double2* __restrict__ partial) {
+                                                      int n_atoms, int n_species, const int32_t* __restrict__ halve,
+                                                      double2* __restrict__ partial) {
   using V = typename std::conditional<DF, float4, double2>::type;
   using Acc = typename std::conditional<DF, DfAcc, double2>::type;
   const int m = blockIdx.x;
   const int d = blockIdx.y >> 2, c = blockIdx.y & 3;
+  if (halve && c >= 2 && *halve) return;  // taken as the conjugate of combination 3 - c (k_kubo_reduce)
   const int a = c >> 1, b = c & 1;
   const int e1 = 2 * d + a, e2 = 2 * d + b;
   const int cb = swap_combo(c);
@@ -140,10 +142,15 @@ __global__ void __launch_bounds__(256) k_kubo_partial(const int64_t* __restrict_
   }
 }
 
-// grid (n_delta * 4 * 9), block 256: fixed-order sum over atoms.
+// grid (n_delta * 4 * 9), block 256: fixed-order sum over atoms.  With the halving
+// flag set, combinations (-,+) and (-,-) are the conjugates of (+,-) and (+,+).
 __global__ void __launch_bounds__(256) k_kubo_reduce(const double2* __restrict__ partial, int n_atoms,
-                                                     double2* __restrict__ S) {
-  const int dc = blockIdx.x / 9, e = blockIdx.x % 9;
+                                                     const int32_t* __restrict__ halve, double2* __restrict__ S) {
+  int dc = blockIdx.x / 9;
+  const int e = blockIdx.x % 9;
+  const int c = dc & 3;
+  const bool conj_of = halve && c >= 2 && *halve;
+  if (conj_of) dc = (dc & ~3) | (3 - c);
   double2 t = mk(0.0, 0.0);
   for (int m = threadIdx.x; m < n_atoms; m += blockDim.x) t = cadd(t, partial[((size_t)dc * n_atoms + m) * 9 + e]);
   __shared__ double2 sh[256];
@@ -153,7 +160,41 @@ __global__ void __launch_bounds__(256) k_kubo_reduce(const double2* __restrict__
     if (threadIdx.x < w) sh[threadIdx.x] = cadd(sh[threadIdx.x], sh[threadIdx.x + w]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) S[(size_t)dc * 9 + e] = sh[0];
+  if (threadIdx.x == 0) S[(size_t)(blockIdx.x / 9) * 9 + e] = conj_of ? mk(sh[0].x, -sh[0].y) : sh[0];
+}
+
+// Conjugate-pair mode: *flag = 1 when the current matrices allow the halving,
+// J(-,-) = conj J(+,+) and J(-,+) = conj J(+,-) (to 1e-12 of the largest |J|,
+// |.| = |Re| + |Im|), for every species and broadening block; else 0.  Then with
+// tau(z*) = conj tau(z) the traces of (-,-) and (-,+) are the conjugates of those
+// of (+,+) and (+,-).  One CTA; flag set before the traces run.
+__global__ void __launch_bounds__(256) k_check_conj_j(const double2* __restrict__ J, int64_t J_dstride, int n_dj,
+                                                      int64_t per_species4, int n_species, int32_t* flag) {
+  // per_species4: elements of one combination block (3 K K); J[d][s][c][...]
+  double dm = 0.0, am = 0.0;
+  const int64_t total = (int64_t)n_dj * n_species * per_species4;
+  for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+    const int64_t d = i / ((int64_t)n_species * per_species4);
+    const int64_t r = i % ((int64_t)n_species * per_species4);
+    const int64_t sp = r / per_species4, q = r % per_species4;
+    const double2* Js = J + (size_t)d * J_dstride + (size_t)sp * 4 * per_species4;
+    const double2 pp = Js[q], pm = Js[per_species4 + q], mp = Js[2 * per_species4 + q], mm = Js[3 * per_species4 + q];
+    dm = fmax(dm, fmax(fabs(mm.x - pp.x) + fabs(mm.y + pp.y), fabs(mp.x - pm.x) + fabs(mp.y + pm.y)));
+    am = fmax(am, fmax(fmax(cabs1(pp), cabs1(pm)), fmax(cabs1(mp), cabs1(mm))));
+    if (!finite2(pp) || !finite2(pm) || !finite2(mp) || !finite2(mm)) dm = INFINITY;
+  }
+  __shared__ double s1[256], s2[256];
+  s1[threadIdx.x] = dm;
+  s2[threadIdx.x] = am;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s1[threadIdx.x] = fmax(s1[threadIdx.x], s1[threadIdx.x + w]);
+      s2[threadIdx.x] = fmax(s2[threadIdx.x], s2[threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *flag = (s1[0] <= 1e-12 * s2[0]) ? 1 : 0;
 }
 
 // one block: sigma~ = -S/(pi V), sigma = (st0 - st1 - st2 + st3)/4, rho = (Re sigma)^{-1}
@@ -408,18 +449,23 @@ __global__ void __launch_bounds__(256) k_adj_species(const int32_t* __restrict__
 int kubo_forward(const int64_t* offsets, const int32_t* site_atom, const int32_t* species, int n_species,
                  const double2* J, int64_t J_dstride, const double2* tau, int64_t S_total, int K, int n_atoms, int n_delta,
                  double volume, bool df, float4* jdf, double2* partial, double2* S, double2* sigma_tilde,
-                 double2* sigma, double* rho, cudaStream_t st) {
+                 double2* sigma, double* rho, cudaStream_t st, int32_t* halve) {
+  if (halve) {
+    const int n_dj = J_dstride > 0 ? n_delta : 1;
+    LSMS_LAUNCH(k_check_conj_j, dim3(1), dim3(256), 0, st, J, J_dstride > 0 ? J_dstride : 0, n_dj,
+                (int64_t)3 * K * K, n_species, halve);
+  }
   if (df) {
     const int64_t per = (int64_t)n_species * 12 * K * K;
     const int n_dj = J_dstride > 0 ? n_delta : 1;
     LSMS_LAUNCH(k_split_j, dim3((unsigned)((per + 255) / 256), n_dj), dim3(256), 0, st, J, J_dstride, per, jdf);
     LSMS_LAUNCH(k_kubo_partial<true>, dim3(n_atoms, n_delta * 4), dim3(256), 0, st, offsets, site_atom, species, J,
-                J_dstride, jdf, J_dstride > 0 ? per : 0, tau, S_total, K, n_atoms, n_species, partial);
+                J_dstride, jdf, J_dstride > 0 ? per : 0, tau, S_total, K, n_atoms, n_species, halve, partial);
   } else {
     LSMS_LAUNCH(k_kubo_partial<false>, dim3(n_atoms, n_delta * 4), dim3(256), 0, st, offsets, site_atom, species, J,
-                J_dstride, nullptr, 0, tau, S_total, K, n_atoms, n_species, partial);
+                J_dstride, nullptr, 0, tau, S_total, K, n_atoms, n_species, halve, partial);
   }
-  LSMS_LAUNCH(k_kubo_reduce, dim3(n_delta * 4 * 9), dim3(256), 0, st, partial, n_atoms, S);
+  LSMS_LAUNCH(k_kubo_reduce, dim3(n_delta * 4 * 9), dim3(256), 0, st, partial, n_atoms, halve, S);
   LSMS_LAUNCH(k_kubo_finish, dim3(1), dim3(32), 0, st, S, n_delta, volume, sigma_tilde, sigma, rho);
   return LSMS_OK;
 }
@@ -440,10 +486,10 @@ int kubo_atoms(const int64_t* offsets, const int32_t* site_atom, const int32_t* 
     const int n_dj = J_dstride > 0 ? n_delta : 1;
     LSMS_LAUNCH(k_split_j, dim3((unsigned)((per + 255) / 256), n_dj), dim3(256), 0, st, J, J_dstride, per, jdf);
     LSMS_LAUNCH(k_kubo_partial<true>, dim3(n_atoms, n_delta * 4), dim3(256), 0, st, offsets, site_atom, species, J,
-                J_dstride, jdf, J_dstride > 0 ? per : 0, tau, S_total, K, n_atoms, n_species, out);
+                J_dstride, jdf, J_dstride > 0 ? per : 0, tau, S_total, K, n_atoms, n_species, nullptr, out);
   } else {
     LSMS_LAUNCH(k_kubo_partial<false>, dim3(n_atoms, n_delta * 4), dim3(256), 0, st, offsets, site_atom, species, J,
-                J_dstride, nullptr, 0, tau, S_total, K, n_atoms, n_species, out);
+                J_dstride, nullptr, 0, tau, S_total, K, n_atoms, n_species, nullptr, out);
   }
   const int64_t cnt = (int64_t)n_delta * 4 * n_atoms * 9;
   LSMS_LAUNCH(k_cscale, dim3((unsigned)std::min<int64_t>((cnt + 255) / 256, 4096)), dim3(256), 0, st, out, cnt,
@@ -585,5 +631,5 @@ extern "C" int lsms_kubo_sigma_noalloc(const lsms_liz* liz_c, int lmax, const in
                       reinterpret_cast<float4*>(base + part_bytes + s_bytes), reinterpret_cast<double2*>(base),
                       reinterpret_cast<double2*>(base + part_bytes),
                       reinterpret_cast<double2*>(sigma_tilde), reinterpret_cast<double2*>(sigma), rho,
-                      reinterpret_cast<cudaStream_t>(stream));
+                      reinterpret_cast<cudaStream_t>(stream), nullptr);
 }

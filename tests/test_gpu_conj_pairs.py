@@ -121,3 +121,31 @@ def test_conj_pairs_rejects_nonconjugate_energies(B):
     sp = torch.as_tensor(w.species).cuda()
     with pytest.raises(B.LsmsError):
         B.tau_blocks(lz, w.lmax, sp, torch.as_tensor(w.tinv).cuda(), z, "fp64", conj_pairs=True)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_conj_pairs_trace_halving(B, precision):
+    """With conjugate-pair tau and J(-,-) = conj J(+,+), J(-,+) = conj J(+,-) (the dipole model), the
+    halved traces (only (+,+) and (+,-) computed) give the sigma~ and sigma of all four; with current
+    matrices that break the relation all four are computed, as without the flag."""
+    w = _alloy()
+    lz = B.build_liz(w.pos, w.lattice, w.r_liz)
+    sp = torch.as_tensor(w.species).cuda()
+    tau, st = B.tau_blocks(lz, w.lmax, sp, torch.as_tensor(w.tinv).cuda(), w.z, precision, conj_pairs=True)
+    J = torch.as_tensor(B.dipole_current(w.lmax, w.r_ll)).cuda()
+    rng = np.random.default_rng(17)
+    Jr = J.clone()
+    Jr[:, 3] += torch.as_tensor(1e-3 * rng.standard_normal(Jr[:, 3].shape)).cuda()   # breaks J(-,-) = conj J(+,+)
+    for Jx, halves in ((J, True), (Jr, False)):
+        s_full, st_full, _ = B.kubo_sigma(lz, w.lmax, sp, Jx, tau, w.n_delta, w.volume, precision=precision)
+        s_half, st_half, _ = B.kubo_sigma(lz, w.lmax, sp, Jx, tau, w.n_delta, w.volume, precision=precision,
+                                          conj_pairs=True)
+        torch.cuda.synchronize()
+        a, b = st_half.cpu().numpy(), st_full.cpu().numpy()
+        if halves:
+            assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+            assert np.array_equal(a[:, 3], np.conj(a[:, 0])) and np.array_equal(a[:, 2], np.conj(a[:, 1]))
+        else:
+            assert np.array_equal(a, b)
+        sa, sb = s_half.cpu().numpy(), s_full.cpu().numpy()
+        assert np.abs(sa - sb).max() <= 1e-12 * np.abs(sb).max()
