@@ -664,9 +664,7 @@ __global__ void __launch_bounds__(512, 2) k_solve(const Unit* __restrict__ units
 // factor, G/2 16-byte shared-memory loads of the solved block and 4 G FMAs.
 constexpr int kSolveThreads = 256;  // complex64 solve CTA
 
-// WIDE: all 32 factor entries of a row are requested before any is used (more
-// loads in flight; needs the 128-register build of the kernel), else 8 at a time.
-template <int NCOL, int NT, bool WIDE = false>
+template <int NCOL, int NT>
 __device__ __forceinline__ void update_rows_c64(const float2* __restrict__ A, float2* X, const float2 (*sX)[NCOL],
                                                 int n, int k, int nbp, int r0, int r1, int nrhs, int tid) {
   constexpr int G = NCOL < 8 ? NCOL : 8;
@@ -699,20 +697,7 @@ __device__ __forceinline__ void update_rows_c64(const float2* __restrict__ A, fl
 #pragma unroll
     for (int c = 0; c < G; ++c) acc[c] = (g + c < nrhs) ? X[(size_t)(g + c) * n + i] : make_float2(0.f, 0.f);
     const float2* Ai = A + (size_t)k * n + i;
-    if (nbp == NB && WIDE) {
-      float2 l[NB];
-#pragma unroll
-      for (int jj = 0; jj < NB; ++jj) l[jj] = Ai[(size_t)jj * n];
-#pragma unroll
-      for (int jj = 0; jj < NB; ++jj) {
-#pragma unroll
-        for (int c = 0; c < G; c += 2) {
-          const float4 xx = *reinterpret_cast<const float4*>(&sX[jj][g + c]);
-          acc[c] = cfms(l[jj], make_float2(xx.x, xx.y), acc[c]);
-          acc[c + 1] = cfms(l[jj], make_float2(xx.z, xx.w), acc[c + 1]);
-        }
-      }
-    } else if (nbp == NB) {
+    if (nbp == NB) {
 #pragma unroll 1
       for (int j0 = 0; j0 < NB; j0 += 8) {
         float2 l[8];
@@ -856,7 +841,7 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_c64(const Unit* __restrict__
     }
     apply_inverse(k, nbp);
     __syncthreads();
-    update_rows_c64<NCOL, NT, (NT * MINB <= 512)>(A, X, sX, n, k, nbp, k + nbp, n, nrhs, tid);
+    update_rows_c64<NCOL, NT>(A, X, sX, n, k, nbp, k + nbp, n, nrhs, tid);
     __syncthreads();
   }
   // backward
@@ -872,7 +857,7 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_c64(const Unit* __restrict__
     __syncthreads();
     apply_inverse(k, nbp);
     __syncthreads();
-    update_rows_c64<NCOL, NT, (NT * MINB <= 512)>(A, X, sX, n, k, nbp, 0, k, nrhs, tid);
+    update_rows_c64<NCOL, NT>(A, X, sX, n, k, nbp, 0, k, nrhs, tid);
     __syncthreads();
   }
 }
