@@ -216,6 +216,20 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const Unit* __restrict__ units,
       cv[c] = (crow < n && c0 + c < n) ? A[(size_t)(c0 + c) * n + crow] : make_float2(0.f, 0.f);
   };
 
+  // C tile j requested into L2 ahead of its loads: the tile's 32 column segments
+  // of 128 rows are 256 lines of 128 bytes, two per thread (column tid / 4)
+  auto prefetch_c = [&](int j) {
+    const int col = t0 + j * TNC + (tid >> 2);
+    if (col >= n) return;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int row = row0 + ((tid & 3) * 2 + h) * 16;
+      if (row < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(A + (size_t)col * n + row));
+    }
+  };
+  prefetch_c(0);
+  if (tn > 1) prefetch_c(1);
+
   // A^ row r = [L_re(r, 0..31) | L_im(r, 0..31)]: thread r, one coalesced load per column
   {
     const int row = row0 + tid;
@@ -293,6 +307,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const Unit* __restrict__ units,
     }
     issued = j;
     if (j + 1 < tn) load_b(j + 1);
+    if (j + 2 < tn) prefetch_c(j + 2);
     if (j > 0) epilogue(j - 1, tmem);
     load_c(j);
   }
