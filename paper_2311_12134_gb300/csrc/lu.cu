@@ -268,8 +268,12 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_smem(const Unit* __rest
   }
   __syncthreads();
   int flags = 0;
-  // kept rolled: the fully unrolled complex128 instance produced wrong factors
-  // (n a multiple of 32) while every rolled build matches the oracle
+  // Rolled: the fully unrolled loop (both precisions) gives the same factors
+  // and is no faster.  Invariants the loop rests on: thread t alone writes
+  // physical row t; the pivot row's thread has logical row j during step j and
+  // does not write, so its values read by the others are those of step j - 1;
+  // the warp results of step j + 1 go to the other parity buffer than those
+  // read in step j, and the step's barrier separates both from step j + 2.
 #pragma unroll 1
   for (int j = 0; j < NB; ++j) {
     if (j < nbp) {

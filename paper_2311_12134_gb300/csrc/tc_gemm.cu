@@ -37,6 +37,7 @@ constexpr int OP_A = 2 * CHUNK_A;           // real K = 2 NB = 64 tf32 = two chu
 constexpr int OP_B = 2 * CHUNK_B;
 constexpr int SMEM_BYTES = 2 * OP_A + 2 * OP_B + 64;  // hi/lo of A and B + barrier + TMEM slot
 constexpr uint32_t TMEM_COLS = 64;
+constexpr int kPrefetchTiles = 2;            // C tiles requested into L2 ahead of their loads
 constexpr long long kWaitLimit = 1ll << 24;  // bounded mbarrier wait (polls)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -227,8 +228,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const Unit* __restrict__ units,
       if (row < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(A + (size_t)col * n + row));
     }
   };
-  prefetch_c(0);
-  if (tn > 1) prefetch_c(1);
+  for (int j = 0; j < kPrefetchTiles && j < tn; ++j) prefetch_c(j);
 
   // A^ row r = [L_re(r, 0..31) | L_im(r, 0..31)]: thread r, one coalesced load per column
   {
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const Unit* __restrict__ units,
     }
     issued = j;
     if (j + 1 < tn) load_b(j + 1);
-    if (j + 2 < tn) prefetch_c(j + 2);
+    if (j + kPrefetchTiles < tn) prefetch_c(j + kPrefetchTiles);
     if (j > 0) epilogue(j - 1, tmem);
     load_c(j);
   }
