@@ -79,9 +79,43 @@ __global__ void __launch_bounds__(256) k_kubo_partial(const int64_t* __restrict_
     if constexpr (DF) return df_join(x);
     else return x;
   };
+  auto nz = [](V x) -> bool {  // NaN counts as nonzero
+    if constexpr (DF) return x.x != 0.f || x.z != 0.f;
+    else return x.x != 0.0 || x.y != 0.0;
+  };
   const int tid = threadIdx.x;
-  const int i = tid >> 4, j = tid & 15;
+  const int i = tid >> 4, j = tid & 15, lane = tid & 31, warp = tid >> 5;
   const bool act = (i < K) && (j < K);
+  const int spm = min(max(0, species[m]), n_species - 1);
+  auto load_jm = [&]() {  // J^{m mu} of the swapped combination, into sB
+    if (act) {
+#pragma unroll
+      for (int u = 0; u < 3; ++u) sB[u][i][j] = ldJ((((size_t)spm * 4 + cb) * 3 + u) * KK + i * K + j);
+    }
+  };
+  // The trace Tr[J^{m mu} Y^nu] reads Y^nu(i, j) only where J^{m mu}(j, i) != 0
+  // for some mu (the dipole J: at most 3 of 16 entries per row), so only those
+  // entries of Y are accumulated, each by one thread of a compacted list.
+  __shared__ int sList[256], sWarpCnt[8];
+  __shared__ unsigned sJr[3][16];  // bit t of sJr[nu][x]: J^{n nu}(x, t) != 0
+  load_jm();
+  __syncthreads();
+  int cnt = 0, my = -1;
+  {
+    const bool need = act && (nz(sB[0][j][i]) || nz(sB[1][j][i]) || nz(sB[2][j][i]));
+    const unsigned bal = __ballot_sync(0xffffffffu, need);
+    if (lane == 0) sWarpCnt[warp] = __popc(bal);
+    __syncthreads();
+    int base = 0;
+    for (int w = 0; w < 8; ++w) {
+      if (w < warp) base += sWarpCnt[w];
+      cnt += sWarpCnt[w];
+    }
+    if (need) sList[base + __popc(bal & ((1u << lane) - 1u))] = tid;
+    __syncthreads();
+    if (tid < cnt) my = sList[tid];
+  }
+  const int yi = my >> 4, yj = my & 15;
   Acc Y[3];
 #pragma unroll
   for (int v = 0; v < 3; ++v) Y[v] = zero();
@@ -95,35 +129,44 @@ __global__ void __launch_bounds__(256) k_kubo_partial(const int64_t* __restrict_
       for (int v = 0; v < 3; ++v) sB[v][i][j] = ldJ((((size_t)sp * 4 + c) * 3 + v) * KK + i * K + j);
     }
     __syncthreads();
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      const unsigned br = __ballot_sync(0xffffffffu, act && nz(sB[v][i][j]));
+      if (j == 0) sJr[v][i] = (br >> (lane & 16)) & 0xffffu;
+    }
+    __syncthreads();
     if (act) {
 #pragma unroll
-      for (int v = 0; v < 3; ++v) {
+      for (int v = 0; v < 3; ++v) {  // J^nu tau^{n0}(z2) over the nonzero entries of J's row i
         Acc acc = zero();
-        for (int q = 0; q < K; ++q) mac(acc, sB[v][i][q], sT2[q][j]);  // J^nu tau^{n0}(z2)
+        for (unsigned b = sJr[v][i]; b; b &= b - 1) {
+          const int q = __ffs(b) - 1;
+          mac(acc, sB[v][i][q], sT2[q][j]);
+        }
         sP[v][i][j] = val(acc);
       }
     }
     __syncthreads();
-    if (act) {
+    if (my >= 0) {
 #pragma unroll
       for (int v = 0; v < 3; ++v)
-        for (int q = 0; q < K; ++q) mac(Y[v], sT1[q][i], sP[v][q][j]);  // tau^{0n}(z1) = tau^{n0}(z1)^T
+        for (int q = 0; q < K; ++q) mac(Y[v], sT1[q][yi], sP[v][q][yj]);  // tau^{0n}(z1) = tau^{n0}(z1)^T
     }
     __syncthreads();
   }
-  // S[mu][nu] = Tr[J^{m mu} Y^nu] = sum_ij Jm[i][j] Y[j][i]
+  // S[mu][nu] = Tr[J^{m mu} Y^nu] = sum_ij Jm[i][j] Y[j][i]; entries outside the list are 0
   if (act) {
 #pragma unroll
-    for (int v = 0; v < 3; ++v) sP[v][i][j] = val(Y[v]);
+    for (int v = 0; v < 3; ++v) sP[v][i][j] = V{};
   }
-  const int spm = min(max(0, species[m]), n_species - 1);
-  if (act) {
+  load_jm();
+  __syncthreads();
+  if (my >= 0) {
 #pragma unroll
-    for (int u = 0; u < 3; ++u) sB[u][i][j] = ldJ((((size_t)spm * 4 + cb) * 3 + u) * KK + i * K + j);
+    for (int v = 0; v < 3; ++v) sP[v][yi][yj] = val(Y[v]);
   }
   __syncthreads();
   __shared__ double2 red[9][8];
-  const int lane = tid & 31, warp = tid >> 5;
   for (int u = 0; u < 3; ++u)
     for (int v = 0; v < 3; ++v) {
       double2 t = act ? cmul(wide(sB[u][i][j]), wide(sP[v][j][i])) : mk(0.0, 0.0);
@@ -290,11 +333,26 @@ __global__ void __launch_bounds__(256) k_adj_rhs(const Unit* __restrict__ units,
   const int sp = min(max(0, species[site_atom[s]]), n_species - 1);
   const double2* Jd = J + (size_t)d * J_dstride;
   __shared__ V sT[16][17], sJ[16][17], sA[16][17], sQ[16][17];
-  const int tid = threadIdx.x, i = tid >> 4, j = tid & 15;
+  // nonzero patterns: bit t of r[x] = entry (x, t) nonzero, of c[x] = entry (t, x)
+  __shared__ unsigned sJr[16], sJc[16], sAr[16], sAc[16];
+  const int tid = threadIdx.x, i = tid >> 4, j = tid & 15, lane = tid & 31;
   const bool act = (i < K) && (j < K);
   auto load = [](double2 x) -> V {
     if constexpr (DF) return df_split(x);
     else return x;
+  };
+  auto nz = [](V x) -> bool {  // NaN counts as nonzero
+    if constexpr (DF) return x.x != 0.f || x.z != 0.f;
+    else return x.x != 0.0 || x.y != 0.0;
+  };
+  // the patterns of a 16 x 16 shared matrix: a warp holds rows 2w, 2w + 1 (16 lanes each)
+  auto patterns = [&](const V (*M)[17], unsigned* r, unsigned* c) {
+    const unsigned br = __ballot_sync(0xffffffffu, act && nz(M[i][j]));
+    const unsigned bc = __ballot_sync(0xffffffffu, act && nz(M[j][i]));
+    if (j == 0) {
+      r[i] = (br >> (lane & 16)) & 0xffffu;
+      c[i] = (bc >> (lane & 16)) & 0xffffu;
+    }
   };
   DfAcc f1 = df_zero(), f2 = df_zero();
   double2 acc1 = mk(0.0, 0.0), acc2 = mk(0.0, 0.0);
@@ -319,36 +377,56 @@ __global__ void __launch_bounds__(256) k_adj_rhs(const Unit* __restrict__ units,
             sA[i][j] = abar[ao];
           }
         }
+        // a zero Abar^nu_c (gradient weights without this nu) contributes nothing
+        if (!__syncthreads_or(act && nz(sA[i][j]))) continue;
+        // The products run over the nonzero entries only (the dipole J couples
+        // l to l +- 1, m to m, m +- 1: at most 3 of 16 per row and column), in
+        // ascending order: the same sums as the dense loops.
+        patterns(sJ, sJr, sJc);
+        patterns(sA, sAr, sAc);
         __syncthreads();
         if (act) {
           if constexpr (DF) {
             DfAcc q = df_zero();
             if (part == 0)
-              for (int t = 0; t < K; ++t) dfc_mac(q, sJ[i][t], sT[t][j]);  // J tau
+              for (unsigned mk_ = sJr[i]; mk_; mk_ &= mk_ - 1) {
+                const int t = __ffs(mk_) - 1;
+                dfc_mac(q, sJ[i][t], sT[t][j]);  // J tau
+              }
             else
-              for (int t = 0; t < K; ++t) dfc_mac(q, sJ[t][i], sT[t][j]);  // J^T tau
+              for (unsigned mk_ = sJc[i]; mk_; mk_ &= mk_ - 1) {
+                const int t = __ffs(mk_) - 1;
+                dfc_mac(q, sJ[t][i], sT[t][j]);  // J^T tau
+              }
             sQ[i][j] = df_value(q);
           } else {
             double2 q = mk(0.0, 0.0);
             if (part == 0)
-              for (int t = 0; t < K; ++t) q = cfma(sJ[i][t], sT[t][j], q);
+              for (unsigned mk_ = sJr[i]; mk_; mk_ &= mk_ - 1) {
+                const int t = __ffs(mk_) - 1;
+                q = cfma(sJ[i][t], sT[t][j], q);
+              }
             else
-              for (int t = 0; t < K; ++t) q = cfma(sJ[t][i], sT[t][j], q);
+              for (unsigned mk_ = sJc[i]; mk_; mk_ &= mk_ - 1) {
+                const int t = __ffs(mk_) - 1;
+                q = cfma(sJ[t][i], sT[t][j], q);
+              }
             sQ[i][j] = q;
           }
         }
         __syncthreads();
         if (act) {
-          if constexpr (DF) {
-            if (part == 0)
-              for (int t = 0; t < K; ++t) dfc_mac(f1, sQ[i][t], sA[t][j]);  // (J tau) Abar
-            else
-              for (int t = 0; t < K; ++t) dfc_mac(f2, sQ[i][t], sA[j][t]);  // (J^T tau) Abar^T
-          } else {
-            if (part == 0)
-              for (int t = 0; t < K; ++t) acc1 = cfma(sQ[i][t], sA[t][j], acc1);
-            else
-              for (int t = 0; t < K; ++t) acc2 = cfma(sQ[i][t], sA[j][t], acc2);
+          // part 0: (J tau) Abar over column j of Abar; part 1: (J^T tau) Abar^T over row j
+          const unsigned am = part == 0 ? sAc[j] : sAr[j];
+          for (unsigned mk_ = am; mk_; mk_ &= mk_ - 1) {
+            const int t = __ffs(mk_) - 1;
+            if constexpr (DF) {
+              if (part == 0) dfc_mac(f1, sQ[i][t], sA[t][j]);
+              else dfc_mac(f2, sQ[i][t], sA[j][t]);
+            } else {
+              if (part == 0) acc1 = cfma(sQ[i][t], sA[t][j], acc1);
+              else acc2 = cfma(sQ[i][t], sA[j][t], acc2);
+            }
           }
         }
         __syncthreads();
