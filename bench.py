@@ -430,8 +430,9 @@ def kernel_models(K, n_fwd, sweeps, n_delta, n_energy, fp32_ops, fp64_peak, tc_p
                                  float(np.sum(16.0 * n * n * (fp + bp))))
     else:
         m["k_solve"] = (float(np.sum(8.0 * n * n * 3.0 * K)), simt_peak, "triangular solves (FP64)")
-    # assembly: 708 nonzero Gaunt couplings x (complex x real) per off-diagonal block, once per forward unit
-    m["k_assemble"] = (float(np.sum(S * (S - 1))) * 708 * 4.0, df_peak if mixed else fp64_peak,
+    # assembly: 708 nonzero Gaunt couplings x (complex x real) per off-diagonal block pair (p < q; the
+    # block (q, p) is its transpose), once per forward unit
+    m["k_assemble"] = (float(np.sum(S * (S - 1) / 2)) * 708 * 4.0, df_peak if mixed else fp64_peak,
                        "Gaunt sums, %s" % ("double-float FP32" if mixed else "FP64"))
     if sparse is not None:
         adj, trace = sparse

@@ -631,6 +631,9 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
     t1 = s_start[L * kMaxK + Lp + 1];
   }
   __shared__ unsigned int s_rmax[kAsmE][kMaxK];  // mixed form: row maxima of block row p, per energy
+  // mixed form: row maxima of the transposed blocks' rows K q + L' of one round
+  __shared__ unsigned int s_tmax[kAsmE][kAsmQ][kMaxK];
+  for (int x = tid; x < kAsmE * kAsmQ * kMaxK; x += blockDim.x) (&s_tmax[0][0][0])[x] = 0u;
   for (int e0 = 0; e0 < nE; e0 += kAsmE) {
     int flags[kAsmE];
     float mmax[kAsmE];  // mixed form: largest |M| entry written, per energy
@@ -645,7 +648,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
       if (ee < ne && !(__uint_as_float(s_dmax[e0 + ee]) <= (float)kSymTol * __uint_as_float(s_amax[e0 + ee])))
         flags[ee] |= LSMS_UNIT_TINV_ASYM;
     }
-    for (int q0 = 0; q0 < S; q0 += kAsmQ) {
+    for (int q0 = p; q0 < S; q0 += kAsmQ) {  // blocks (p, q >= p); (q, p) is the transpose
       const int nq = min(kAsmQ, S - q0);
       __syncthreads();
       if (tid < kAsmQ) {
@@ -696,8 +699,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
         }
       }
       __syncthreads();
-      if (!act) continue;
-      for (int ee = 0; ee < ne; ++ee) {
+      for (int ee = 0; ee < ne && act; ++ee) {
         const Unit& u = ua[e0 + ee];
         for (int qq = 0; qq < nq; ++qq) {
           const int q = q0 + qq;
@@ -719,9 +721,17 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
             }
             if (!(isfinite(v4.x) && isfinite(v4.z))) flags[ee] |= LSMS_UNIT_NONFINITE;
             mmax[ee] = fmaxf(mmax[ee], fabsf(v4.x) + fabsf(v4.z));
-            rmax[ee] = fmaxf(rmax[ee], fmaxf(fabsf(v4.x), fabsf(v4.z)));
-            reinterpret_cast<float4*>(fac_base + u.m64_off)[idx] = make_float4(v4.x, v4.z, v4.y, v4.w);
+            const float vm = fmaxf(fabsf(v4.x), fabsf(v4.z));
+            rmax[ee] = fmaxf(rmax[ee], vm);
+            const float4 m4 = make_float4(v4.x, v4.z, v4.y, v4.w);
+            reinterpret_cast<float4*>(fac_base + u.m64_off)[idx] = m4;
             if (write_fac) reinterpret_cast<float2*>(fac_base + u.fac_off)[idx] = make_float2(v4.x, v4.z);
+            if (q != p) {  // M(K q + L', K p + L) = M(K p + L, K q + L')
+              const size_t idt = (size_t)(K * p + L) * n + K * q + Lp;
+              reinterpret_cast<float4*>(fac_base + u.m64_off)[idt] = m4;
+              if (write_fac) reinterpret_cast<float2*>(fac_base + u.fac_off)[idt] = make_float2(v4.x, v4.z);
+              atomicMax(&s_tmax[ee][qq][Lp], __float_as_uint(vm <= 3.4e38f ? vm : __int_as_float(0x7f800000)));
+            }
           } else {
             double2 v;
             if (q == p) {
@@ -738,7 +748,21 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
             }
             if (!finite2(v)) flags[ee] |= LSMS_UNIT_NONFINITE;
             reinterpret_cast<double2*>(fac_base + u.fac_off)[idx] = v;
+            if (q != p) reinterpret_cast<double2*>(fac_base + u.fac_off)[(size_t)(K * p + L) * n + K * q + Lp] = v;
           }
+        }
+      }
+      if (MIXED) {  // maxima of the transposed blocks' rows K q + L' into the units' row maxima
+        __syncthreads();
+        for (int x = tid; x < ne * nq * kMaxK; x += blockDim.x) {
+          const int ee = x / (nq * kMaxK), qq = (x / kMaxK) % nq, l2 = x % kMaxK;
+          const int q = q0 + qq;
+          if (l2 < K && q != p) {
+            const Unit& u = ua[e0 + ee];
+            atomicMax(reinterpret_cast<unsigned int*>(fac_base + u.m64_off + rowmax_rel_off(u.n)) + K * q + l2,
+                      s_tmax[ee][qq][l2]);
+          }
+          s_tmax[ee][qq][l2] = 0u;
         }
       }
     }
@@ -755,27 +779,28 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
         }
       }
     }
-    if (MIXED) {  // this CTA saw every column of rows K p .. K p + K - 1: their maxima are complete
+    if (MIXED) {  // rows K p .. K p + K - 1 over the columns of blocks q >= p (the CTAs of
+                  // sites q < p add the rest through their transposed blocks)
       __syncthreads();
       if (tid < ne * kMaxK && (tid % kMaxK) < K) {
         const int ee = tid / kMaxK, L2 = tid % kMaxK;
         const Unit& u = ua[e0 + ee];
-        reinterpret_cast<float*>(fac_base + u.m64_off + rowmax_rel_off(u.n))[K * p + L2] =
-            __uint_as_float(s_rmax[ee][L2]);
+        atomicMax(reinterpret_cast<unsigned int*>(fac_base + u.m64_off + rowmax_rel_off(u.n)) + K * p + L2,
+                  s_rmax[ee][L2]);
       }
       __syncthreads();
     }
   }
 }
 
-// Zero the pivot-growth records of the units (before k_assemble).  One thread per unit.
+// Zero the pivot-growth records and the row maxima of the units (before
+// k_assemble, which raises them by atomic maxima).  One CTA per unit.
 __global__ void k_growth_init(const Unit* __restrict__ units, int n_units, char* fac_base) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_units) return;
-  const Unit u = units[i];
+  const Unit u = units[blockIdx.x];
   float* g = reinterpret_cast<float*>(fac_base + u.m64_off + growth_rel_off(u.n));
-  g[0] = 0.f;
-  g[1] = 0.f;
+  if (threadIdx.x < 2) g[threadIdx.x] = 0.f;
+  float* rm = reinterpret_cast<float*>(fac_base + u.m64_off + rowmax_rel_off(u.n));
+  for (int i = threadIdx.x; i < u.n; i += blockDim.x) rm[i] = 0.f;
 }
 
 // Pivot growth of the complex64 factorization: LSMS_UNIT_GROWTH when
@@ -1366,7 +1391,7 @@ static int assemble_factor(const Call& c, const Plan& p, const Chunk& ch, char* 
     return lu_factor_chunk<double>(du, nu, ch.n_max, fac_base, stat, c.st);
   }
   const dim3 gu((nu + 255) / 256);
-  LSMS_LAUNCH(k_growth_init, gu, dim3(256), 0, c.st, du, nu, fac_base);
+  LSMS_LAUNCH(k_growth_init, dim3(nu), dim3(256), 0, c.st, du, nu, fac_base);
   LSMS_LAUNCH(k_assemble<true>, dim3(S_max, n_at), dim3(256), 0, c.st, du, p.fac_per_atom, c.dd->disp,
               c.dd->site_atom, c.species, c.tinv, c.n_species, c.n_energy, c.E, c.K, fac_base, ws, true, stat);
   const int rc = lu_factor_chunk<float>(du, nu, ch.n_max, fac_base, stat, c.st);
