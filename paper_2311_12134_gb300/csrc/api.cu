@@ -553,10 +553,14 @@ constexpr double kSymTol = 1e-12;
 // atom's LIZ, for all energies of that atom.  First, the t^{-1} block of site p
 // is checked for complex symmetry at every energy (M^T = M is what makes the
 // row block tau^{0n} = (tau^{n0})^T); a block that is not symmetric to kSymTol
-// flags the unit LSMS_UNIT_TINV_ASYM.  Per round of 16 column sites q:
-// 16 lanes compute Y_L(R^) (shared by the energies), 32 lanes compute
-// V[L''] = mpref h_l''(kappa R) Y_L''(R^) for 2 energies, then thread (L, L')
-// forms sum_L'' s C_{LL'L''} V[L''] for those blocks (diagonal blocks: t^{-1}).
+// flags the unit LSMS_UNIT_TINV_ASYM.  Only the blocks (p, q >= p) are formed:
+// off the diagonal M is complex symmetric (g_{L'L}(-R) = g_{LL'}(R), the Gaunt
+// coefficients being symmetric in L, L' and Y_L(-R^) = (-1)^l Y_L(R^) with
+// l + l' + l'' even), so block (q, p) is written as the transpose of (p, q).  Per
+// round of 16 column sites q: 16 lanes compute Y_L(R^) once for all energies;
+// then, 2 energies at a time, 32 lanes compute
+// V[L''] = mpref h_l''(kappa R) Y_L''(R^) and thread (L, L') forms
+// sum_L'' s C_{LL'L''} V[L''] for those blocks (diagonal blocks: t^{-1}).
 // FP64 form: FP64 sums, M (complex128) written into the factor array.
 // Mixed form: the sums in double-float arithmetic on the FP32 pipes (FP64
 // accuracy); writes M as (hi, lo) float pairs (float4 per element, at
@@ -630,42 +634,43 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
     t0 = s_start[L * kMaxK + Lp];
     t1 = s_start[L * kMaxK + Lp + 1];
   }
-  __shared__ unsigned int s_rmax[kAsmE][kMaxK];  // mixed form: row maxima of block row p, per energy
-  // mixed form: row maxima of the transposed blocks' rows K q + L' of one round
+  // mixed form: row maxima of block row p (over the columns of blocks q >= p; the
+  // CTAs of sites q < p add the rest through their transposed blocks) and the
+  // largest |M| entry, per energy of the atom; NONFINITE per energy
+  __shared__ unsigned int s_rmax[kMaxEnergies][kMaxK];
+  __shared__ unsigned int s_mmax[kMaxEnergies];
+  __shared__ int s_flags[kMaxEnergies];
+  // mixed form: row maxima of the transposed blocks' rows K q + L' of one group
   __shared__ unsigned int s_tmax[kAsmE][kAsmQ][kMaxK];
   for (int x = tid; x < kAsmE * kAsmQ * kMaxK; x += blockDim.x) (&s_tmax[0][0][0])[x] = 0u;
-  for (int e0 = 0; e0 < nE; e0 += kAsmE) {
-    int flags[kAsmE];
-    float mmax[kAsmE];  // mixed form: largest |M| entry written, per energy
-    float rmax[kAsmE];  // mixed form: largest |Re| or |Im| (high parts) in this thread's row, per energy
-    if (MIXED && tid < kAsmE * kMaxK) s_rmax[tid / kMaxK][tid % kMaxK] = 0u;  // read after the q0 loop's barriers
-    const int ne = min(kAsmE, nE - e0);
-#pragma unroll
-    for (int ee = 0; ee < kAsmE; ++ee) {
-      flags[ee] = bad;
-      mmax[ee] = 0.f;
-      rmax[ee] = 0.f;
-      if (ee < ne && !(__uint_as_float(s_dmax[e0 + ee]) <= (float)kSymTol * __uint_as_float(s_amax[e0 + ee])))
-        flags[ee] |= LSMS_UNIT_TINV_ASYM;
-    }
-    for (int q0 = p; q0 < S; q0 += kAsmQ) {  // blocks (p, q >= p); (q, p) is the transpose
-      const int nq = min(kAsmQ, S - q0);
-      __syncthreads();
-      if (tid < kAsmQ) {
-        const int q = q0 + tid;
-        if (tid < nq && q != p) {
-          const int64_t sq = u0.site_off + q;
-          const double rx = disp[3 * sq] - px, ry = disp[3 * sq + 1] - py, rz = disp[3 * sq + 2] - pz;
-          const double d = sqrt(rx * rx + ry * ry + rz * rz);
-          const double id = 1.0 / d;
-          sD[tid] = d;
-          if (MIXED)
-            ylm6_df(dd_from(rx * id), dd_from(ry * id), dd_from(rz * id),
-                    reinterpret_cast<float2*>(sYraw) + tid * kMaxK3);
-          else
-            ylm6(rx * id, ry * id, rz * id, reinterpret_cast<double*>(sYraw) + tid * kMaxK3);
-        }
+  for (int x = tid; x < nE * kMaxK; x += blockDim.x) (&s_rmax[0][0])[x] = 0u;
+  for (int x = tid; x < nE; x += blockDim.x) {
+    s_mmax[x] = 0u;
+    s_flags[x] = 0;
+  }
+  // rounds of kAsmQ column sites q >= p (block (q, p) is the transpose of (p, q));
+  // the harmonics of a round serve every energy, the Hankel set-up and the Gaunt
+  // sums run kAsmE energies at a time
+  for (int q0 = p; q0 < S; q0 += kAsmQ) {
+    const int nq = min(kAsmQ, S - q0);
+    __syncthreads();
+    if (tid < kAsmQ) {
+      const int q = q0 + tid;
+      if (tid < nq && q != p) {
+        const int64_t sq = u0.site_off + q;
+        const double rx = disp[3 * sq] - px, ry = disp[3 * sq + 1] - py, rz = disp[3 * sq + 2] - pz;
+        const double d = sqrt(rx * rx + ry * ry + rz * rz);
+        const double id = 1.0 / d;
+        sD[tid] = d;
+        if (MIXED)
+          ylm6_df(dd_from(rx * id), dd_from(ry * id), dd_from(rz * id),
+                  reinterpret_cast<float2*>(sYraw) + tid * kMaxK3);
+        else
+          ylm6(rx * id, ry * id, rz * id, reinterpret_cast<double*>(sYraw) + tid * kMaxK3);
       }
+    }
+    for (int e0 = 0; e0 < nE; e0 += kAsmE) {
+      const int ne = min(kAsmE, nE - e0);
       __syncthreads();
       if (tid < kAsmE * kAsmQ) {
         const int ee = tid / kAsmQ, qq = tid % kAsmQ, q = q0 + qq;
@@ -699,6 +704,15 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
         }
       }
       __syncthreads();
+      int nf[kAsmE];
+      float mmax[kAsmE];  // mixed form: largest |M| entry written, per energy
+      float rmax[kAsmE];  // mixed form: largest |Re| or |Im| (high parts) in this thread's row, per energy
+#pragma unroll
+      for (int ee = 0; ee < kAsmE; ++ee) {
+        nf[ee] = 0;
+        mmax[ee] = 0.f;
+        rmax[ee] = 0.f;
+      }
       for (int ee = 0; ee < ne && act; ++ee) {
         const Unit& u = ua[e0 + ee];
         for (int qq = 0; qq < nq; ++qq) {
@@ -719,7 +733,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
               }
               v4 = df_value(acc);
             }
-            if (!(isfinite(v4.x) && isfinite(v4.z))) flags[ee] |= LSMS_UNIT_NONFINITE;
+            if (!(isfinite(v4.x) && isfinite(v4.z))) nf[ee] |= LSMS_UNIT_NONFINITE;
             mmax[ee] = fmaxf(mmax[ee], fabsf(v4.x) + fabsf(v4.z));
             const float vm = fmaxf(fabsf(v4.x), fabsf(v4.z));
             rmax[ee] = fmaxf(rmax[ee], vm);
@@ -730,7 +744,14 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
               const size_t idt = (size_t)(K * p + L) * n + K * q + Lp;
               reinterpret_cast<float4*>(fac_base + u.m64_off)[idt] = m4;
               if (write_fac) reinterpret_cast<float2*>(fac_base + u.fac_off)[idt] = make_float2(v4.x, v4.z);
-              atomicMax(&s_tmax[ee][qq][Lp], __float_as_uint(vm <= 3.4e38f ? vm : __int_as_float(0x7f800000)));
+              unsigned tm = __float_as_uint(vm <= 3.4e38f ? vm : __int_as_float(0x7f800000));
+              if (K == kMaxK) {  // every lane active: the 16 lanes of row K q + L' reduce in registers
+#pragma unroll
+                for (int off = 1; off < 16; off <<= 1) tm = max(tm, __shfl_xor_sync(0xffffffffu, tm, off));
+                if (L == 0) s_tmax[ee][qq][Lp] = max(s_tmax[ee][qq][Lp], tm);
+              } else {
+                atomicMax(&s_tmax[ee][qq][Lp], tm);
+              }
             }
           } else {
             double2 v;
@@ -746,14 +767,14 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
                 v.y = fma(c, w.y, v.y);
               }
             }
-            if (!finite2(v)) flags[ee] |= LSMS_UNIT_NONFINITE;
+            if (!finite2(v)) nf[ee] |= LSMS_UNIT_NONFINITE;
             reinterpret_cast<double2*>(fac_base + u.fac_off)[idx] = v;
             if (q != p) reinterpret_cast<double2*>(fac_base + u.fac_off)[(size_t)(K * p + L) * n + K * q + Lp] = v;
           }
         }
       }
       if (MIXED) {  // maxima of the transposed blocks' rows K q + L' into the units' row maxima
-        __syncthreads();
+        __syncthreads();  // the group's transposed maxima are complete
         for (int x = tid; x < ne * nq * kMaxK; x += blockDim.x) {
           const int ee = x / (nq * kMaxK), qq = (x / kMaxK) % nq, l2 = x % kMaxK;
           const int q = q0 + qq;
@@ -765,30 +786,34 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
           s_tmax[ee][qq][l2] = 0u;
         }
       }
-    }
-    for (int ee = 0; ee < ne; ++ee) {
-      if (flags[ee]) atomicOr(&stat[ua[e0 + ee].stat_off], flags[ee]);
-      if (MIXED) {
-        const float wm = warp_max_nonneg(mmax[ee]);
-        const Unit& u = ua[e0 + ee];
-        if ((tid & 31) == 0) atomic_max_nonneg(reinterpret_cast<float*>(fac_base + u.m64_off + growth_rel_off(u.n)), wm);
-        if (act) {
-          float rm = rmax[ee] + 0.0f;
-          if (!(rm <= 3.4e38f)) rm = __int_as_float(0x7f800000);
-          atomicMax(&s_rmax[ee][L], __float_as_uint(rm));
+      for (int ee = 0; ee < ne; ++ee) {
+        if (nf[ee]) atomicOr(&s_flags[e0 + ee], nf[ee]);
+        if (MIXED) {
+          const float wm = warp_max_nonneg(mmax[ee]);
+          if ((tid & 31) == 0) atomicMax(&s_mmax[e0 + ee], __float_as_uint(wm));
+          if (act) {
+            float rm = rmax[ee] + 0.0f;
+            if (!(rm <= 3.4e38f)) rm = __int_as_float(0x7f800000);
+            atomicMax(&s_rmax[e0 + ee][L], __float_as_uint(rm));
+          }
         }
       }
     }
-    if (MIXED) {  // rows K p .. K p + K - 1 over the columns of blocks q >= p (the CTAs of
-                  // sites q < p add the rest through their transposed blocks)
-      __syncthreads();
-      if (tid < ne * kMaxK && (tid % kMaxK) < K) {
-        const int ee = tid / kMaxK, L2 = tid % kMaxK;
-        const Unit& u = ua[e0 + ee];
-        atomicMax(reinterpret_cast<unsigned int*>(fac_base + u.m64_off + rowmax_rel_off(u.n)) + K * p + L2,
-                  s_rmax[ee][L2]);
-      }
-      __syncthreads();
+  }
+  __syncthreads();
+  for (int e = tid; e < nE; e += blockDim.x) {
+    int f = bad | s_flags[e];
+    if (!(__uint_as_float(s_dmax[e]) <= (float)kSymTol * __uint_as_float(s_amax[e]))) f |= LSMS_UNIT_TINV_ASYM;
+    if (f) atomicOr(&stat[ua[e].stat_off], f);
+    if (MIXED) atomic_max_nonneg(reinterpret_cast<float*>(fac_base + ua[e].m64_off + growth_rel_off(ua[e].n)),
+                                 __uint_as_float(s_mmax[e]));
+  }
+  if (MIXED) {
+    for (int x = tid; x < nE * kMaxK; x += blockDim.x) {
+      const int e = x / kMaxK, l2 = x % kMaxK;
+      if (l2 < K)
+        atomicMax(reinterpret_cast<unsigned int*>(fac_base + ua[e].m64_off + rowmax_rel_off(ua[e].n)) + K * p + l2,
+                  s_rmax[e][l2]);
     }
   }
 }
