@@ -336,6 +336,11 @@ int lsms_kubo_sigma_backward(const lsms_liz* liz, int lmax, const int32_t* speci
  *                     16 columns, else 16): a tile shape the autotuner picks
  *   "solve_regs"      0 (default): 8- and 16-column solve CTAs sized for 8 CTAs
  *                     per SM (64 registers); 1: for 4 CTAs per SM (128 registers)
+ *   "solve_steps"     0 (default) or 1: the mixed form's triangular solves run
+ *                     as one CTA chain of block steps per unit and column slice
+ *                     (shaped by solve_cols / solve_regs); 2: as one launch per
+ *                     32-row block step over all units of a chunk, the row
+ *                     update spread over many CTAs
  * LSMS_ERR_ARG for an unknown name or a value out of range. */
 int lsms_set_option(const char* name, double value);
 int lsms_get_option(const char* name, double* value);

@@ -8,6 +8,8 @@ the batched launches have):
                   solves (8, 16 or 32): wider slices read the factors fewer
                   times, narrower slices run more independent block-step chains;
 * ``solve_regs``  8 solve CTAs per SM with 64 registers, or 4 with 128;
+* ``solve_steps`` the solves as one CTA chain per unit and slice (0) or as one
+                  launch per block step over all units (2);
 * ``streams``     concurrent parts of each chunk of units (2 or 4).
 
 ``tune`` times ``Problem.step`` (forward + adjoint) under every candidate with
@@ -35,14 +37,15 @@ TABLE = os.path.join(HERE, "tuning_gb300.json")
 N_BUCKETS = (256, 512, 768, 1024, 1536, 2048, 3072, 4096, 8192, 16384)
 U_BUCKETS = (1024, 8192, 65536, 1 << 30)
 
-DEFAULTS = {"solve_cols": 0, "solve_regs": 0, "streams": 4}
+DEFAULTS = {"solve_cols": 0, "solve_regs": 0, "solve_steps": 0, "streams": 4}
 
 
 def candidates():
     out = []
     for streams in (2, 4):
+        out.append({"solve_cols": 0, "solve_regs": 0, "solve_steps": 2, "streams": streams})
         for cols, regs in ((0, 0), (0, 1), (8, 0), (8, 1), (16, 0), (16, 1), (32, 0)):
-            out.append({"solve_cols": cols, "solve_regs": regs, "streams": streams})
+            out.append({"solve_cols": cols, "solve_regs": regs, "solve_steps": 0, "streams": streams})
     return out
 
 

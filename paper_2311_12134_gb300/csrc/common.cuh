@@ -227,16 +227,17 @@ __device__ __forceinline__ float4 ddc_scalef(float4 a, float f) { return ddc(dd_
 
 // ------------------------------------------------------------------ wrappers (lu.cu)
 // Blocked right-looking LU with partial pivoting of every unit of a chunk, in
-// place in the factor arrays (column-major, ld = n).  Pivots are applied to
-// the panel and the trailing columns only ("progressive" form; the solves
-// apply them block by block).
+// place in the factor arrays (column-major, ld = n).  Complex128: pivots are
+// applied to the panel and the trailing columns only ("progressive" form; the
+// solve applies them block by block).  Complex64: afterwards L is put in the row
+// order of the final permutation and the pivots are replaced by it (k_lapack_rows).
 template <typename R>
 int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
                     int32_t* stat, cudaStream_t st);
 // Solve L U X = P B in place for the n x nrhs column-major block at
 // ws + unit.<field> (complex<R>), skipping units whose done flag is set.
 template <typename R>
-int lu_solve_chunk(const Unit* d_units, int n_units, const char* fac_base, char* ws,
+int lu_solve_chunk(const Unit* d_units, int n_units, int n_max, const char* fac_base, char* ws,
                    int which_rhs, int nrhs, const int32_t* done, cudaStream_t st);
 
 enum RhsField { RHS_X = 0, RHS_X32 = 1 };
@@ -248,6 +249,7 @@ int residual_tc_chunk(const Unit* d_units, int n_units, int n_max, const char* f
 int opt_residual_tc();
 int opt_solve_cols();
 int opt_solve_regs();
+int opt_solve_steps();
 
 // Trailing update A22 -= L21 U12 of the complex64 LU on the tensor cores (tc_gemm.cu).
 int gemm_tc_chunk(const Unit* d_units, int n_units, int n_max, int k, char* fac_base, int32_t* stat,

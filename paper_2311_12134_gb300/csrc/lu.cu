@@ -777,15 +777,107 @@ __global__ void __launch_bounds__(64) k_diag_inv(const Unit* __restrict__ units,
   for (int i = 0; i < NB; ++i) out[i] = y[i];
 }
 
+// After the complex64 factorization L's columns are as computed: each panel's
+// rows in the order of that panel's step (LINPACK style).  k_lapack_rows applies
+// to every 32-column block of L the interchanges of all later panels, which puts
+// L in the row order of one permutation (P M = L U), and replaces the pivots by
+// that permutation: row r of P b is row perm[r] of b.  The solves then permute
+// their right-hand sides once (k_perm_rows) and substitute without interchanges,
+// so a block step of the forward substitution is the same product for every row
+// below it and can be spread over many CTAs.
+// One CTA per unit walks the blocks from the last to the first with the composed
+// permutation of the later panels in shared memory (idx: new row r takes old row
+// idx[r]; pos: the inverse).  Prepending an interchange (a, c) to the sequence
+// exchanges the values a and c in idx.  Only the rows with idx[r] != r move; a
+// pass reads all moved entries of some columns into shared memory, then writes
+// them.  Dynamic shared memory: lap_smem_bytes(n_max).
+constexpr int kLapCols = 32;
+__host__ __device__ inline size_t lap_stage_elems(int n_max) { return (size_t)(n_max > 2048 ? n_max : 2048); }
+inline size_t lap_smem_bytes(int n_max) { return lap_stage_elems(n_max) * 8 + (size_t)3 * n_max * 4; }
+
+__global__ void __launch_bounds__(256) k_lapack_rows(const Unit* __restrict__ units, char* fac_base, int n_max) {
+  constexpr int NB = 32;
+  const Unit u = units[blockIdx.x];
+  const int n = u.n;
+  float2* A = reinterpret_cast<float2*>(fac_base + u.fac_off);
+  int32_t* piv = reinterpret_cast<int32_t*>(fac_base + u.piv_off);
+  extern __shared__ __align__(16) unsigned char lap_raw[];
+  const int cap = (int)lap_stage_elems(n_max);
+  float2* stage = reinterpret_cast<float2*>(lap_raw);
+  int* idx = reinterpret_cast<int*>(stage + cap);
+  int* pos = idx + n_max;
+  int* list = pos + n_max;
+  __shared__ int s_cnt;
+  const int tid = threadIdx.x;
+  for (int r = tid; r < n; r += blockDim.x) idx[r] = pos[r] = r;
+  __syncthreads();
+  const int nb = (n + NB - 1) / NB;
+  for (int b = nb - 2; b >= -1; --b) {
+    // prepend panel b + 1's interchanges, its last one first
+    if (tid == 0) {
+      const int r0 = NB * (b + 1), r1 = min(n, r0 + NB);
+      for (int r = r1 - 1; r >= r0; --r) {
+        const int a = r, c = piv[r];
+        if (a != c) {
+          const int ra = pos[a], rc = pos[c];
+          idx[ra] = c;
+          idx[rc] = a;
+          pos[a] = rc;
+          pos[c] = ra;
+        }
+      }
+      s_cnt = 0;
+    }
+    __syncthreads();
+    if (b < 0) break;
+    for (int r = NB * (b + 1) + tid; r < n; r += blockDim.x)
+      if (idx[r] != r) list[atomicAdd(&s_cnt, 1)] = r;
+    __syncthreads();
+    const int m = s_cnt;
+    if (m == 0) continue;
+    const int cpp = max(1, min(kLapCols, cap / m));  // columns per pass
+    for (int c0 = NB * b; c0 < NB * b + NB; c0 += cpp) {
+      const int nc = min(cpp, NB * b + NB - c0);
+      for (int x = tid; x < nc * m; x += blockDim.x) {
+        const int c = c0 + x / m, i = x % m;
+        stage[x] = A[(size_t)c * n + idx[list[i]]];
+      }
+      __syncthreads();
+      for (int x = tid; x < nc * m; x += blockDim.x) {
+        const int c = c0 + x / m, i = x % m;
+        A[(size_t)c * n + list[i]] = stage[x];
+      }
+      __syncthreads();
+    }
+  }
+  for (int r = tid; r < n; r += blockDim.x) piv[r] = idx[r];
+}
+
+// Right-hand-side columns permuted by the factorization's row permutation:
+// row r of column c takes row perm[r].  grid (nrhs, n_units), block 256,
+// dynamic shared memory n_max complex64 values.
+__global__ void __launch_bounds__(256) k_perm_rows(const Unit* __restrict__ units, const char* fac_base, char* ws,
+                                                   int nrhs, const int32_t* done) {
+  const Unit u = units[blockIdx.y];
+  if (done && done[u.stat_off]) return;
+  const int c = blockIdx.x;
+  if (c >= nrhs) return;
+  const int n = u.n;
+  const int32_t* perm = reinterpret_cast<const int32_t*>(fac_base + u.piv_off);
+  float2* X = reinterpret_cast<float2*>(ws + u.x32_off) + (size_t)c * n;
+  extern __shared__ float2 sv[];
+  for (int r = threadIdx.x; r < n; r += blockDim.x) sv[r] = X[perm[r]];
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += blockDim.x) X[r] = sv[r];
+}
+
 // One CTA of NT threads per unit and slice of NCOL right-hand-side columns
 // (blockIdx.y; several CTAs resident per SM, so one chain's block phases overlap
-// the others' row updates): L y = P b (unit lower, each panel's interchanges
-// applied just before its block, LINPACK order), then U x = y, on the n x nrhs
-// column-major block X.  Each 32-row block
-// step gathers its rows (the panel's interchanges composed once into a gather),
-// multiplies them by the stored inverse of the diagonal block (all threads, no
-// serial chain), and updates the rows below (above, going back) with the block's
-// 32 columns of L (U).
+// the others' row updates): L y = P b (unit lower, L in the row order of P, the
+// right-hand sides permuted by k_perm_rows before), then U x = y, on the
+// n x nrhs column-major block X.  Each 32-row block step multiplies its rows by
+// the stored inverse of the diagonal block (all threads, no serial chain) and
+// updates the rows below (above, going back) with the block's 32 columns of L (U).
 template <int NCOL, int NT, int MINB = 1024 / NT>
 __global__ void __launch_bounds__(NT, MINB) k_solve_c64(const Unit* __restrict__ units, const char* fac_base,
                                                      char* ws, int which, int nrhs, const int32_t* done) {
@@ -801,12 +893,9 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_c64(const Unit* __restrict__
   const float2* A = reinterpret_cast<const float2*>(fac_base + u.fac_off);
   const float2* D = reinterpret_cast<const float2*>(fac_base + u.m64_off + diag_inv_rel_off(n));
   float2* X = reinterpret_cast<float2*>(ws + (which == RHS_X ? u.x_off : u.x32_off)) + (size_t)c_off * n;
-  const int32_t* piv = reinterpret_cast<const int32_t*>(fac_base + u.piv_off);
   __shared__ float2 sT[NB][NB + 1];                 // inverse of the diagonal block
   __shared__ __align__(16) float2 sX[NB][NCOL];     // the block's solved rows
   __shared__ float2 sIn[NB][NCOL + 1];              // the block's rows before the inverse
-  __shared__ float2 sTv[NB][NCOL + 1];              // new values of the rows below reached by interchanges
-  __shared__ int sStep[NB], sTgt[NB], sSrc[NB], sTgtSrc[NB], sNt;
   const int tid = threadIdx.x;
   // y = T^-1 (block rows) for every (row, column) pair of the block
   auto apply_inverse = [&](int k, int nbp) {
@@ -824,25 +913,16 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_c64(const Unit* __restrict__
       if (i < nbp && c < nrhs) X[(size_t)c * n + k + i] = y;
     }
   };
-  // forward
+  // forward (the right-hand sides already permuted by k_perm_rows)
   for (int k = 0; k < n; k += NB) {
     const int nbp = min(NB, n - k);
     const float2* Dk = D + (size_t)(k / NB) * 2 * NB * NB;  // L^-1 block
     for (int idx = tid; idx < NB * NB; idx += NT) sT[idx % NB][idx / NB] = Dk[idx];
-    if (tid < 32) compose_panel_swaps(piv, k, nbp, tid, sStep, sTgt, sSrc, sTgtSrc, &sNt);
-    __syncthreads();
-    const int nt = sNt;
     for (int idx = tid; idx < NB * NCOL; idx += NT) {
       const int i = idx % NB, c = idx / NB;
-      const bool live = c < nrhs;
-      sIn[i][c] = (live && i < nbp) ? X[(size_t)c * n + sSrc[i]] : make_float2(0.f, 0.f);
-      if (live && i < nt) sTv[i][c] = X[(size_t)c * n + sTgtSrc[i]];
+      sIn[i][c] = (c < nrhs && i < nbp) ? X[(size_t)c * n + k + i] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    for (int idx = tid; idx < NB * NCOL; idx += NT) {
-      const int q = idx % NB, c = idx / NB;
-      if (c < nrhs && q < nt) X[(size_t)c * n + sTgt[q]] = sTv[q][c];
-    }
     apply_inverse(k, nbp);
     __syncthreads();
     update_rows_c64<NCOL, NT>(A, X, sX, n, k, nbp, k + nbp, n, nrhs, tid);
@@ -863,6 +943,162 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_c64(const Unit* __restrict__
     __syncthreads();
     update_rows_c64<NCOL, NT>(A, X, sX, n, k, nbp, 0, k, nrhs, tid);
     __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ block-step solves
+// The complex64 substitutions as one launch per 32-row block step over all units
+// of a chunk, each step's row update spread over row tiles (many CTAs per unit):
+// the chain of dependent block steps moves from inside one CTA to the launch
+// sequence.  NCOL = right-hand-side columns (8, 16 or 32, padded); a tile has
+// step_rows<NCOL>() rows and 256 threads, a thread one row and step_cols<NCOL>()
+// columns.  Each thread requests its row's 32 factor entries and its X entries
+// before the block's solved rows arrive in shared memory, so one memory latency
+// covers the whole update.  The tile that holds the next block finalizes it
+// after its own update: y = T^{-1} x with the stored inverse of the diagonal block.
+template <int NCOL> __host__ __device__ constexpr int step_cols() { return NCOL < 16 ? NCOL : 16; }
+template <int NCOL> __host__ __device__ constexpr int step_rows() { return 256 * step_cols<NCOL>() / NCOL; }
+
+// Registers of one thread of a step update: X rows [row0, row0 + rows), its row
+// r = row0 + threadIdx.x % TR and CH columns from g; the factor entries
+// F[r, c0 .. c0 + nbp) (column-major, ld n; zero beyond nbp).
+template <int NCOL>
+struct StepRegs {
+  static constexpr int CH = step_cols<NCOL>();
+  float2 l[32], acc[CH];
+  int r, g;
+  bool live;
+  __device__ __forceinline__ void load(const float2* __restrict__ F, const float2* X, int n, int c0, int nbp,
+                                       int row0, int rows, int nrhs) {
+    constexpr int TR = step_rows<NCOL>();
+    r = row0 + threadIdx.x % TR;
+    g = (threadIdx.x / TR) * CH;
+    live = threadIdx.x % TR < rows;
+    if (!live) return;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) acc[c] = (g + c < nrhs) ? X[(size_t)(g + c) * n + r] : make_float2(0.f, 0.f);
+    const float2* Fr = F + (size_t)c0 * n + r;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) l[j] = j < nbp ? Fr[(size_t)j * n] : make_float2(0.f, 0.f);
+  }
+  // X[r, g ..] = acc - l y (y = sY, 32 rows, zero-padded)
+  __device__ __forceinline__ void finish(float2* X, const float2 (*sY)[NCOL], int n, int nrhs) {
+    if (!live) return;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+#pragma unroll
+      for (int c = 0; c < CH; c += 2) {
+        const float4 yy = *reinterpret_cast<const float4*>(&sY[j][g + c]);
+        acc[c] = cfms(l[j], make_float2(yy.x, yy.y), acc[c]);
+        acc[c + 1] = cfms(l[j], make_float2(yy.z, yy.w), acc[c + 1]);
+      }
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+      if (g + c < nrhs) X[(size_t)(g + c) * n + r] = acc[c];
+  }
+};
+
+// Block k (nbp rows) of X := T^{-1} X[block k], T^{-1} = Dk (32 x 32 column-major,
+// identity-padded).  Every thread of the CTA calls it; sIn / sT are scratch.
+template <int NCOL>
+__device__ __forceinline__ void step_finalize(const float2* __restrict__ Dk, float2* X, float2 (*sT)[33],
+                                              float2 (*sIn)[NCOL + 1], int n, int k, int nbp, int nrhs) {
+  constexpr int NB = 32;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < NB * NB; idx += blockDim.x) sT[idx % NB][idx / NB] = Dk[idx];
+  for (int idx = tid; idx < NB * NCOL; idx += blockDim.x) {
+    const int i = idx % NB, c = idx / NB;
+    sIn[i][c] = (c < nrhs && i < nbp) ? X[(size_t)c * n + k + i] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < NB * NCOL; idx += blockDim.x) {
+    const int i = idx % NB, c = idx / NB;
+    float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < NB; j += 2) {
+      a0 = cfma(sT[i][j], sIn[j][c], a0);
+      a1 = cfma(sT[i][j + 1], sIn[j + 1][c], a1);
+    }
+    if (i < nbp && c < nrhs) X[(size_t)c * n + k + i] = make_float2(a0.x + a1.x, a0.y + a1.y);
+  }
+}
+
+// Forward step s (L y = P b, right-hand sides permuted before): with block s
+// final, the rows below it take X[r] -= L[r, block s] y_s (tile t: rows
+// 32 (s + 1) + TR t ...); then tile 0, whose first 32 rows are block s + 1,
+// finalizes that block with L_{s+1}^{-1}.  s = -1 only finalizes block 0.
+// grid (row tiles, n_units), block 256.
+template <int NCOL>
+__global__ void __launch_bounds__(256, 2) k_fwd_step(const Unit* __restrict__ units, const char* fac_base, char* ws,
+                                                  int nrhs, const int32_t* done, int s) {
+  constexpr int NB = 32, TR = step_rows<NCOL>();
+  const Unit u = units[blockIdx.y];
+  if (done && done[u.stat_off]) return;
+  const int n = u.n;
+  const int nb = (n + NB - 1) / NB;
+  if (s + 1 >= nb) return;
+  const int r_begin = NB * (s + 1);
+  const int row0 = r_begin + blockIdx.x * TR;
+  if (row0 >= n) return;
+  const float2* A = reinterpret_cast<const float2*>(fac_base + u.fac_off);
+  float2* X = reinterpret_cast<float2*>(ws + u.x32_off);
+  __shared__ __align__(16) float2 sY[NB][NCOL];
+  __shared__ float2 sT[NB][NB + 1];
+  __shared__ float2 sIn[NB][NCOL + 1];
+  if (s >= 0) {
+    StepRegs<NCOL> t;
+    t.load(A, X, n, NB * s, NB, row0, min(TR, n - row0), nrhs);
+    for (int idx = threadIdx.x; idx < NB * NCOL; idx += blockDim.x) {
+      const int i = idx % NB, c = idx / NB;
+      sY[i][c] = c < nrhs ? X[(size_t)c * n + NB * s + i] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    t.finish(X, sY, n, nrhs);
+  }
+  if (blockIdx.x == 0) {
+    __syncthreads();  // this tile's rows of block s + 1 are updated (no other tile writes them)
+    const float2* D = reinterpret_cast<const float2*>(fac_base + u.m64_off + diag_inv_rel_off(n));
+    step_finalize<NCOL>(D + (size_t)(s + 1) * 2 * NB * NB, X, sT, sIn, n, r_begin, min(NB, n - r_begin), nrhs);
+  }
+}
+
+// Backward step s (U x = y): with block s final, rows [0, 32 s) take
+// X[r] -= U[r, block s] x_s (tile t: rows TR t ...); the tile holding block s - 1
+// then finalizes it with U_{s-1}^{-1}.  For a unit with s = its block count the
+// launch only finalizes its last block.  grid (row tiles, n_units), block 256.
+template <int NCOL>
+__global__ void __launch_bounds__(256, 2) k_bwd_step(const Unit* __restrict__ units, const char* fac_base, char* ws,
+                                                  int nrhs, const int32_t* done, int s) {
+  constexpr int NB = 32, TR = step_rows<NCOL>();
+  const Unit u = units[blockIdx.y];
+  if (done && done[u.stat_off]) return;
+  const int n = u.n;
+  const int nb = (n + NB - 1) / NB;
+  if (s > nb || s < 1) return;
+  const int fin_tile = (NB * (s - 1)) / TR;  // the tile holding block s - 1
+  const float2* A = reinterpret_cast<const float2*>(fac_base + u.fac_off);
+  float2* X = reinterpret_cast<float2*>(ws + u.x32_off);
+  __shared__ __align__(16) float2 sY[NB][NCOL];
+  __shared__ float2 sT[NB][NB + 1];
+  __shared__ float2 sIn[NB][NCOL + 1];
+  if (s < nb) {
+    const int row0 = TR * blockIdx.x;
+    if (row0 >= NB * s) return;
+    const int nbp = min(NB, n - NB * s);
+    StepRegs<NCOL> t;
+    t.load(A, X, n, NB * s, nbp, row0, min(TR, NB * s - row0), nrhs);
+    for (int idx = threadIdx.x; idx < NB * NCOL; idx += blockDim.x) {
+      const int i = idx % NB, c = idx / NB;
+      sY[i][c] = (c < nrhs && i < nbp) ? X[(size_t)c * n + NB * s + i] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    t.finish(X, sY, n, nrhs);
+  }
+  if (blockIdx.x == fin_tile) {
+    __syncthreads();
+    const float2* D = reinterpret_cast<const float2*>(fac_base + u.m64_off + diag_inv_rel_off(n));
+    const int k = NB * (s - 1);
+    step_finalize<NCOL>(D + (size_t)(s - 1) * 2 * NB * NB + NB * NB, X, sT, sIn, n, k, min(NB, n - k), nrhs);
   }
 }
 
@@ -907,18 +1143,61 @@ int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
       LSMS_LAUNCH((k_gemm<R, NB>), dim3(tiles * tiles, n_units), dim3(256), 0, st, d_units, fac_base, k, tiles);
     }
   }
-  // complex64: inverses of the diagonal blocks for the solves
-  if constexpr (std::is_same<R, float>::value)
+  // complex64: inverses of the diagonal blocks for the solves, L in the row order
+  // of the final permutation
+  if constexpr (std::is_same<R, float>::value) {
     LSMS_LAUNCH(k_diag_inv, dim3((n_max + kDiagNB - 1) / kDiagNB, n_units), dim3(64), 0, st, d_units, fac_base);
+    const size_t lap = lap_smem_bytes(n_max);
+    if (lap > 227 * 1024) return fail(LSMS_ERR_ARG, "internal: n = %d too large for the row-order pass", n_max);
+    static size_t lap_attr = 48 * 1024;
+    if (lap > lap_attr) {
+      LSMS_CUDA_TRY(cudaFuncSetAttribute(k_lapack_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lap));
+      lap_attr = lap;
+    }
+    LSMS_LAUNCH(k_lapack_rows, dim3(n_units), dim3(256), lap, st, d_units, fac_base, n_max);
+  }
+  return LSMS_OK;
+}
+
+template <int NCOL>
+static int solve_steps(const Unit* d_units, int n_units, int n_max, const char* fac_base, char* ws, int nrhs,
+                       const int32_t* done, cudaStream_t st) {
+  constexpr int NB = 32, TR = step_rows<NCOL>();
+  const int nb = (n_max + NB - 1) / NB;
+  for (int s = -1; s + 1 < nb; ++s) {
+    const int rows = n_max - NB * (s + 1);
+    const dim3 g(s < 0 ? 1 : (rows + TR - 1) / TR, n_units);
+    LSMS_LAUNCH(k_fwd_step<NCOL>, g, dim3(256), 0, st, d_units, fac_base, ws, nrhs, done, s);
+  }
+  for (int s = nb; s >= 1; --s) {
+    const dim3 g((NB * s + TR - 1) / TR, n_units);
+    LSMS_LAUNCH(k_bwd_step<NCOL>, g, dim3(256), 0, st, d_units, fac_base, ws, nrhs, done, s);
+  }
   return LSMS_OK;
 }
 
 template <typename R>
-int lu_solve_chunk(const Unit* d_units, int n_units, const char* fac_base, char* ws, int which_rhs, int nrhs,
-                   const int32_t* done, cudaStream_t st) {
+int lu_solve_chunk(const Unit* d_units, int n_units, int n_max, const char* fac_base, char* ws, int which_rhs,
+                   int nrhs, const int32_t* done, cudaStream_t st) {
   if (nrhs < 1 || nrhs > 32) return fail(LSMS_ERR_ARG, "internal: nrhs %d out of range", nrhs);
   constexpr int NB = LuCfg<R>::NB;
   if constexpr (std::is_same<R, float>::value) {
+    if (which_rhs != RHS_X32) return fail(LSMS_ERR_ARG, "internal: complex64 solves work on the X32 field");
+    // the right-hand sides in the row order of the factors' permutation
+    const size_t pb = (size_t)n_max * sizeof(float2);
+    static size_t perm_attr = 48 * 1024;
+    if (pb > perm_attr) {
+      if (pb > 227 * 1024) return fail(LSMS_ERR_ARG, "internal: n = %d too large for the permutation", n_max);
+      LSMS_CUDA_TRY(cudaFuncSetAttribute(k_perm_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pb));
+      perm_attr = pb;
+    }
+    LSMS_LAUNCH(k_perm_rows, dim3(nrhs, n_units), dim3(256), pb, st, d_units, fac_base, ws, nrhs, done);
+    // option "solve_steps": 2 = block-step launches; 0 (default), 1 = one CTA chain per unit and slice
+    if (opt_solve_steps() == 2) {
+      if (nrhs <= 8) return solve_steps<8>(d_units, n_units, n_max, fac_base, ws, nrhs, done, st);
+      if (nrhs <= 16) return solve_steps<16>(d_units, n_units, n_max, fac_base, ws, nrhs, done, st);
+      return solve_steps<32>(d_units, n_units, n_max, fac_base, ws, nrhs, done, st);
+    }
     // more than 8 columns: column slices per CTA (option "solve_cols"; default 8
     // for up to 16 columns, 16 above), each slice a CTA with its own chain of
     // block steps; wider slices read the factors fewer times, narrower ones give
@@ -955,7 +1234,7 @@ int lu_solve_chunk(const Unit* d_units, int n_units, const char* fac_base, char*
 
 template int lu_factor_chunk<double>(const Unit*, int, int, char*, int32_t*, cudaStream_t);
 template int lu_factor_chunk<float>(const Unit*, int, int, char*, int32_t*, cudaStream_t);
-template int lu_solve_chunk<double>(const Unit*, int, const char*, char*, int, int, const int32_t*, cudaStream_t);
-template int lu_solve_chunk<float>(const Unit*, int, const char*, char*, int, int, const int32_t*, cudaStream_t);
+template int lu_solve_chunk<double>(const Unit*, int, int, const char*, char*, int, int, const int32_t*, cudaStream_t);
+template int lu_solve_chunk<float>(const Unit*, int, int, const char*, char*, int, int, const int32_t*, cudaStream_t);
 
 }  // namespace lsms

@@ -252,16 +252,17 @@ def test_conductivity_host_call_matches_oracle(B, alloy, precision):
     assert np.abs(rho - rref).max() < 10 * TOL[precision] * np.abs(rref).max()
 
 
-@pytest.mark.parametrize("cols,regs,streams", [(8, 1, 4), (16, 0, 2), (16, 1, 4), (32, 0, 1)])
-def test_tuning_options_keep_results(B, alloy, cols, regs, streams):
-    """The autotuner's shapes (solve columns per CTA, register bound, concurrent parts) change the
-    launch layout only: tau and the gradient match the default layout to rounding."""
+@pytest.mark.parametrize("cols,regs,streams,steps",
+                         [(8, 1, 4, 0), (16, 0, 2, 1), (16, 1, 4, 0), (32, 0, 1, 0), (16, 1, 2, 2), (0, 0, 4, 2)])
+def test_tuning_options_keep_results(B, alloy, cols, regs, streams, steps):
+    """The autotuner's shapes (solve path, solve columns per CTA, register bound, concurrent parts)
+    change the launch layout only: tau and the gradient match the default layout to rounding."""
     w, _, _, _, J = alloy
     Jd = torch.as_tensor(J).cuda()
     wgt = torch.zeros((1, 3, 3), dtype=torch.complex128, device="cuda")
     wgt[0, 0, 0] = 1.0
     out = []
-    for opts in ({}, {"solve_cols": cols, "solve_regs": regs, "streams": streams}):
+    for opts in ({}, {"solve_cols": cols, "solve_regs": regs, "streams": streams, "solve_steps": steps}):
         with options(B, **opts) if opts else contextlib.nullcontext():
             lz = B.build_liz(w.pos, w.lattice, w.r_liz)
             sp = torch.as_tensor(w.species).cuda()
