@@ -120,6 +120,13 @@ enum lsms_precision {
 #define LSMS_UNIT_GROWTH 32     /* mixed form: pivot growth of the complex64 factors above the limit */
 #define LSMS_UNIT_FP64_FALLBACK 64  /* mixed form: re-solved in the FP64 form on the GPU (valid result) */
 #define LSMS_UNIT_TIMEOUT 128   /* a bounded device wait gave up (results invalid) */
+/* Bits 8-15 of a status word: refinement sweeps; 16-23: convergence probes;
+ * 24-30: pivot growth g = max|U| / max|M| of the complex64 factors when the
+ * call factored or re-checked them (mixed form), as the code
+ * floor(log2 g) + 64 clamped to 1..127 (127 also for a non-finite g); 0 = not
+ * recorded.  The LSMS_DEBUG_BOUNDS build also sets LSMS_UNIT_BAD_INPUT when a
+ * device-side index check fails (a pivot outside its range); the access is
+ * skipped. */
 
 /* ---------------------------------------------------------------- LIZ
  * Sec. II.A, Fig. 1: the LIZ of atom m holds every site within r_liz of it.
@@ -336,6 +343,9 @@ int lsms_kubo_sigma_backward(const lsms_liz* liz, int lmax, const int32_t* speci
  *                     16 columns, else 16): a tile shape the autotuner picks
  *   "solve_regs"      0 (default): 8- and 16-column solve CTAs sized for 8 CTAs
  *                     per SM (64 registers); 1: for 4 CTAs per SM (128 registers)
+ *   "nvtx"            1: NVTX ranges around the stages of each call (assembly +
+ *                     LU, solve + refinement, traces, adjoint right-hand sides
+ *                     and site products, FP64 fallback); 0 (default): none
  *   "solve_steps"     0 (default) or 1: the mixed form's triangular solves run
  *                     as one CTA chain of block steps per unit and column slice
  *                     (shaped by solve_cols / solve_regs); 2: as one launch per
@@ -344,6 +354,30 @@ int lsms_kubo_sigma_backward(const lsms_liz* liz, int lmax, const int32_t* speci
  * LSMS_ERR_ARG for an unknown name or a value out of range. */
 int lsms_set_option(const char* name, double value);
 int lsms_get_option(const char* name, double* value);
+
+/* ---------------------------------------------------------------- call statistics
+ * lsms_unit_stats: the unit_status words of a call (n_words of them, device
+ * memory) reduced on the device, on `stream`, into *stats (device memory,
+ * 8-byte aligned, written whole; read it after the stream's work):
+ *   units            words reduced
+ *   flag_units[b]    words with bit b set (b = 0..7: LSMS_UNIT_ZERO_PIVOT ..
+ *                    LSMS_UNIT_TIMEOUT; b = 6 counts the FP64 re-solves)
+ *   invalid_units    words with a flag other than LSMS_UNIT_FP64_FALLBACK
+ *   sweeps_sum/max   refinement sweeps (mixed form)
+ *   probes_sum/max   convergence probes (mixed form)
+ *   growth_code_max  largest pivot-growth code (bits 24-30; 0 = none recorded)
+ * One CTA, no allocation; safe inside CUDA-graph capture.  LSMS_ERR_ARG for a
+ * NULL stats pointer, a NULL unit_status with n_words > 0, n_words < 0 or a
+ * misaligned stats pointer. */
+typedef struct lsms_stats {
+  int64_t units;
+  int64_t flag_units[8];
+  int64_t invalid_units;
+  int64_t sweeps_sum, sweeps_max;
+  int64_t probes_sum, probes_max;
+  int64_t growth_code_max;
+} lsms_stats;
+int lsms_unit_stats(const int32_t* unit_status, int64_t n_words, lsms_stats* stats, void* stream);
 
 /* ---------------------------------------------------------------- misc */
 /* Message of the last error on the calling thread ("" if none). */

@@ -13,6 +13,13 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblsmskubo.so")
+# LSMS_DEBUG_BOUNDS=1 in the environment: the build with device-side index checks
+LIB_DEBUG_PATH = os.path.join(_HERE, "_lib", "liblsmskubo_debug.so")
+
+
+def lib_path():
+    """The library file this process loads (the debug-bounds build if LSMS_DEBUG_BOUNDS=1)."""
+    return LIB_DEBUG_PATH if os.environ.get("LSMS_DEBUG_BOUNDS") == "1" else LIB_PATH
 
 LSMS_FP64 = 0
 LSMS_MIXED = 1
@@ -58,6 +65,7 @@ SIGNATURES = {
     "lsms_get_option": (_I, [ctypes.c_char_p, ctypes.POINTER(_D)]),
     "lsms_kubo_sigma_backward": (_I, [_P, _I, _P, _I, _P, _P, _I, _I, _P, _I64, _P, _D, _P, _P, _SZ, _P, _P,
                                       _P, _P, _SZ, _P]),
+    "lsms_unit_stats": (_I, [_P, _I64, _P, _P]),
     "lsms_last_error": (ctypes.c_char_p, []),
     "lsms_version": (_I, []),
     "lsms_launch_count": (ctypes.c_longlong, []),
@@ -76,9 +84,11 @@ def lib():
     """The loaded library (raises if it has not been built)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"{LIB_PATH} is missing: run python -m paper_2311_12134_gb300.build")
-        L = ctypes.CDLL(LIB_PATH)
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: run python -m paper_2311_12134_gb300.build"
+                               + (" --debug-bounds" if path == LIB_DEBUG_PATH else ""))
+        L = ctypes.CDLL(path)
         for name, (res, args) in SIGNATURES.items():
             f = getattr(L, name)
             f.restype = res
@@ -288,8 +298,29 @@ def kubo_sigma_atoms(liz, lmax, species, J, tau, n_delta, volume, J_delta_stride
     return out
 
 
+STATS_FIELDS = ("units", "zero_pivot", "noconv", "nonfinite", "bad_input", "tinv_asym", "growth",
+                "fp64_fallback", "timeout", "invalid", "sweeps_sum", "sweeps_max", "probes_sum", "probes_max",
+                "growth_code_max")
+
+
+def unit_stats(unit_status, stream=None):
+    """lsms_unit_stats: the status words (device int32 tensor) reduced on the device; returns a dict
+    (flag counts, refinement sweeps and probes, the largest pivot-growth code and, decoded from it,
+    growth_max ~ 2^(code - 64), None when none was recorded)."""
+    import torch
+    st = unit_status.contiguous()
+    out = torch.empty(len(STATS_FIELDS), dtype=torch.int64, device=st.device)
+    _check(lib().lsms_unit_stats(_dev(st, torch.int32, name="unit_status"), st.numel(),
+                                 _dev(out, torch.int64, name="stats"), _stream(stream)))
+    vals = out.cpu().tolist()
+    d = dict(zip(STATS_FIELDS, vals))
+    d["growth_max"] = None if d["growth_code_max"] == 0 else 2.0 ** (d["growth_code_max"] - 64)
+    return d
+
+
 def set_option(name, value):
-    """lsms_set_option (process-wide): growth_limit, fallback_slots, ir_max_sweeps, streams."""
+    """lsms_set_option (process-wide): growth_limit, fallback_slots, ir_max_sweeps, streams, residual_tc,
+    solve_cols, solve_regs, solve_steps, nvtx."""
     _check(lib().lsms_set_option(name.encode(), float(value)))
 
 

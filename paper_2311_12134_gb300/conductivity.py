@@ -121,6 +121,20 @@ class Problem:
         if self._bw_ws is not None:
             check_unit_status(self.bw_status)
 
+    def stats(self, log=None):
+        """Per-call statistics of the last forward (and backward) on the device
+        (lsms_unit_stats): flag counts, FP64 re-solves, refinement sweeps and
+        probes, the largest pivot growth.  With ``log`` (a file object) also
+        written there as one JSON line."""
+        import json
+        out = {"forward": B.unit_stats(self.unit_status)}
+        if self._bw_ws is not None:
+            out["backward"] = B.unit_stats(self.bw_status)
+        out["units"] = self.n_units
+        if log is not None:
+            log.write(json.dumps(out) + "\n")
+        return out
+
     def sigma(self, stream=None):
         B.kubo_sigma(self.liz, self.lmax, self.species, self.J, self.tau, self.n_delta, self.volume,
                      sigma=self.sigma_out, sigma_tilde=self.sigma_tilde, rho=self.rho, stream=stream,

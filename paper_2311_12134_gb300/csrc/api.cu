@@ -16,6 +16,8 @@
 #include <cstring>
 #include <numeric>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace lsms {
@@ -94,7 +96,21 @@ static std::atomic<int> g_opt_streams{0};  // 0: LSMS_STREAMS or the default
 static std::atomic<int> g_opt_residual_tc{1};
 static std::atomic<int> g_opt_solve_cols{0};  // 0: 8 columns per CTA up to 16 right-hand sides, else 16
 static std::atomic<int> g_opt_solve_regs{0};
-static std::atomic<int> g_opt_solve_steps{0};  // 0: auto (block-step launches from 9 columns), 1: never, 2: always
+static std::atomic<int> g_opt_solve_steps{0};  // 0, 1: one CTA chain per unit and slice; 2: block-step launches
+static std::atomic<int> g_opt_nvtx{0};
+
+// NVTX range over one stage of a call (option "nvtx"; the header-only NVTX3
+// calls cost nothing without an attached tool).  Ranges mark when the host
+// enqueues a stage on its stream.
+struct NvtxRange {
+  bool on;
+  explicit NvtxRange(const char* name) : on(g_opt_nvtx.load(std::memory_order_relaxed) != 0) {
+    if (on) nvtxRangePushA(name);
+  }
+  ~NvtxRange() {
+    if (on) nvtxRangePop();
+  }
+};
 int opt_residual_tc() { return g_opt_residual_tc.load(); }
 int opt_solve_cols() { return g_opt_solve_cols.load(); }
 int opt_solve_regs() { return g_opt_solve_regs.load(); }
@@ -842,7 +858,60 @@ __global__ void k_growth_check(const Unit* __restrict__ units, int n_units, cons
   const Unit u = units[i];
   const float* g = reinterpret_cast<const float*>(fac_base + u.m64_off + growth_rel_off(u.n));
   // a non-finite M is flagged by the assembly; a finite M with a non-finite factor is growth
-  if (isfinite(g[0]) && !(g[1] <= limit * g[0])) atomicOr(&stat[u.stat_off], LSMS_UNIT_GROWTH);
+  int w = (isfinite(g[0]) && !(g[1] <= limit * g[0])) ? LSMS_UNIT_GROWTH : 0;
+  // bits 24-30: the growth's binary exponent + 64 (1..127; 127 also for a non-finite ratio)
+  if (isfinite(g[0]) && g[0] > 0.f) {
+    const float r = g[1] / g[0];
+    const int code = !isfinite(r) ? 127 : (r > 0.f ? min(127, max(1, ilogbf(r) + 64)) : 1);
+    w |= code << 24;
+  }
+  if (w) atomicOr(&stat[u.stat_off], w);
+}
+
+// lsms_unit_stats: one CTA reduces the status words into the stats record.
+__global__ void __launch_bounds__(1024) k_unit_stats(const int32_t* __restrict__ st, int64_t n, lsms_stats* out) {
+  constexpr int NF = 8;
+  __shared__ unsigned long long s_sum[NF + 3];  // flags, invalid, sweeps, probes
+  __shared__ int s_max[3];                      // sweeps, probes, growth code
+  const int tid = threadIdx.x;
+  if (tid < NF + 3) s_sum[tid] = 0ull;
+  if (tid < 3) s_max[tid] = 0;
+  __syncthreads();
+  unsigned long long f[NF] = {}, inv = 0, sw = 0, pr = 0;
+  int swm = 0, prm = 0, gm = 0;
+  for (int64_t i = tid; i < n; i += blockDim.x) {
+    const int w = st[i];
+#pragma unroll
+    for (int b = 0; b < NF; ++b) f[b] += (w >> b) & 1;
+    inv += (w & 0xff & ~LSMS_UNIT_FP64_FALLBACK) != 0;
+    const int s = (w >> 8) & 0xff, p = (w >> 16) & 0xff, g = (w >> 24) & 0x7f;
+    sw += s;
+    pr += p;
+    swm = max(swm, s);
+    prm = max(prm, p);
+    gm = max(gm, g);
+  }
+#pragma unroll
+  for (int b = 0; b < NF; ++b) atomicAdd(&s_sum[b], f[b]);
+  atomicAdd(&s_sum[NF], inv);
+  atomicAdd(&s_sum[NF + 1], sw);
+  atomicAdd(&s_sum[NF + 2], pr);
+  atomicMax(&s_max[0], swm);
+  atomicMax(&s_max[1], prm);
+  atomicMax(&s_max[2], gm);
+  __syncthreads();
+  if (tid == 0) {
+    lsms_stats r;
+    r.units = n;
+    for (int b = 0; b < NF; ++b) r.flag_units[b] = (int64_t)s_sum[b];
+    r.invalid_units = (int64_t)s_sum[NF];
+    r.sweeps_sum = (int64_t)s_sum[NF + 1];
+    r.probes_sum = (int64_t)s_sum[NF + 2];
+    r.sweeps_max = s_max[0];
+    r.probes_max = s_max[1];
+    r.growth_code_max = s_max[2];
+    *out = r;
+  }
 }
 
 // ------------------------------------------------------------------ RHS / refinement kernels
@@ -1408,6 +1477,7 @@ static int check_common(const lsms_liz* liz, int lmax, const void* species, int 
 // Assemble + factor the units of one chunk that own factors (at fac_base); the
 // mixed form also writes the double-float copy of M.
 static int assemble_factor(const Call& c, const Plan& p, const Chunk& ch, char* fac_base, char* ws, int32_t* stat) {
+  const NvtxRange range("lsms/assemble+lu");
   const Unit* du = p.d_fac_units + ch.f0;  // the units that own factors
   const int nu = ch.f1 - ch.f0;
   const int S_max = ch.n_max / c.K;
@@ -1431,6 +1501,7 @@ static int assemble_factor(const Call& c, const Plan& p, const Chunk& ch, char* 
 // complex128 block at r_off (backward).  Result in X (complex128).
 static int solve_refine(const Call& c, const Plan& p, const Chunk& ch, const char* fac_base, char* ws, int32_t* stat,
                         int32_t* done, bool explicit_b) {
+  const NvtxRange range("lsms/solve+refine");
   const Unit* du = p.d_units + ch.u0;
   const int nu = ch.u1 - ch.u0;
   const int nrhs = p.nrhs;
@@ -1493,6 +1564,7 @@ struct AdjArgs {
 static int fallback_resolve(const Call& c, const Plan& p, char* ws, const WsHeader& h, const FbLayout& f,
                             int32_t* stat, double2* tau_out, const AdjArgs* adj) {
   if (!f.slots || p.units.empty()) return LSMS_OK;
+  const NvtxRange range("lsms/fp64-fallback");
   Unit* fbu = reinterpret_cast<Unit*>(ws + h.fb + f.units_off);
   int32_t* cnt = reinterpret_cast<int32_t*>(ws + h.fb + f.count_off);
   char* region = ws + h.fb + f.region_off;
@@ -1662,6 +1734,9 @@ extern "C" int lsms_set_option(const char* name, double value) {
   } else if (n == "solve_steps") {
     if (!in_int(0, 2)) return fail(LSMS_ERR_ARG, "solve_steps must be 0, 1 or 2");
     g_opt_solve_steps.store((int)value);
+  } else if (n == "nvtx") {
+    if (!in_int(0, 1)) return fail(LSMS_ERR_ARG, "nvtx must be 0 or 1");
+    g_opt_nvtx.store((int)value);
   } else {
     return fail(LSMS_ERR_ARG, "lsms_set_option: unknown option '%s'", name);
   }
@@ -1680,7 +1755,19 @@ extern "C" int lsms_get_option(const char* name, double* value) {
   else if (n == "solve_cols") *value = g_opt_solve_cols.load();
   else if (n == "solve_regs") *value = g_opt_solve_regs.load();
   else if (n == "solve_steps") *value = g_opt_solve_steps.load();
+  else if (n == "nvtx") *value = g_opt_nvtx.load();
   else return fail(LSMS_ERR_ARG, "lsms_get_option: unknown option '%s'", name);
+  return LSMS_OK;
+}
+
+extern "C" int lsms_unit_stats(const int32_t* unit_status, int64_t n_words, lsms_stats* stats, void* stream) {
+  clear_error();
+  if (!stats || n_words < 0 || (!unit_status && n_words > 0))
+    return fail(LSMS_ERR_ARG, "lsms_unit_stats: NULL pointer or n < 0");
+  if ((reinterpret_cast<uintptr_t>(stats) & 7) != 0) return fail(LSMS_ERR_ARG, "lsms_unit_stats: stats not 8-byte aligned");
+  const NvtxRange range("lsms/unit-stats");
+  LSMS_LAUNCH(k_unit_stats, dim3(1), dim3(1024), 0, reinterpret_cast<cudaStream_t>(stream), unit_status, n_words,
+              stats);
   return LSMS_OK;
 }
 
@@ -1942,6 +2029,7 @@ extern "C" int lsms_kubo_sigma(const lsms_liz* liz_c, int lmax, const int32_t* s
   const size_t jdf_bytes = precision == LSMS_MIXED ? jdf_scratch_bytes(n_species, K, n_delta, J_delta_stride) : 0;
   char* scratch = nullptr;
   LSMS_CUDA_TRY(cudaMallocAsync((void**)&scratch, part_bytes + s_bytes + jdf_bytes + kAlign, st));
+  const NvtxRange range("lsms/traces");
   rc = kubo_forward(dd->offsets, dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J), J_delta_stride,
                     reinterpret_cast<const double2*>(tau), liz->total_sites, K, liz->n_atoms, n_delta, volume,
                     precision == LSMS_MIXED, reinterpret_cast<float4*>(scratch + part_bytes + s_bytes),
@@ -2092,15 +2180,19 @@ extern "C" int lsms_kubo_sigma_backward(const lsms_liz* liz_c, int lmax, const i
           LSMS_LAUNCH(k_growth_check, dim3((nf + 255) / 256), dim3(256), 0, st, p->d_fac_units + ch.f0, nf, fac_base,
                       (float)opt_growth_limit(), stat);
         }
-        if ((r3 = adj_rhs(du, nu, S_max, c.dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J),
-                          J_delta_stride, reinterpret_cast<const double2*>(tau), liz->total_sites, abar, jdf,
-                          jdf_dstride, abar_df, n_delta, c.K, chunk, df, st)))
-          return r3;
+        {
+          const NvtxRange range("lsms/adjoint-rhs");
+          if ((r3 = adj_rhs(du, nu, S_max, c.dd->site_atom, species, n_species, reinterpret_cast<const double2*>(J),
+                            J_delta_stride, reinterpret_cast<const double2*>(tau), liz->total_sites, abar, jdf,
+                            jdf_dstride, abar_df, n_delta, c.K, chunk, df, st)))
+            return r3;
+        }
         const dim3 gc((ch.n_max * p->nrhs + 255) / 256, nu);
         // second energy of a conjugate pair: M(conj z) = conj M(z), so X = conj(M(z)^-1 conj B)
         if (conj) LSMS_LAUNCH(k_conj_block, gc, dim3(256), 0, st, du, chunk, p->nrhs, 0);
         if ((r3 = solve_refine(cs, *p, ch, fac_base, chunk, stat, done, true))) return r3;
         if (conj) LSMS_LAUNCH(k_conj_block, gc, dim3(256), 0, st, du, chunk, p->nrhs, 1);
+        const NvtxRange range("lsms/adjoint-site");
         return adj_site(du, nu, S_max, reinterpret_cast<const double2*>(tau), liz->total_sites, c.K, chunk, G,
                         precision == LSMS_MIXED, st);
       });

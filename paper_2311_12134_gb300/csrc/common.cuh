@@ -262,6 +262,21 @@ double opt_growth_limit();
 int opt_fallback_slots();
 int opt_ir_max_sweeps();
 
+// Index checks of the LSMS_DEBUG_BOUNDS build (python -m paper_2311_12134_gb300.build
+// --debug-bounds): a value outside [lo, hi) flags the unit LSMS_UNIT_BAD_INPUT
+// and the caller skips the access; no trap.  In normal builds every check is
+// the constant true and compiles away.
+#ifdef LSMS_DEBUG_BOUNDS
+constexpr bool kDebugBounds = true;
+#else
+constexpr bool kDebugBounds = false;
+#endif
+__device__ __forceinline__ bool dbg_in(long long v, long long lo, long long hi, int32_t* stat_word) {
+  if (!kDebugBounds || (v >= lo && v < hi)) return true;
+  atomicOr(stat_word, LSMS_UNIT_BAD_INPUT);
+  return false;
+}
+
 // Non-negative float maximum into a global word (the bit patterns of
 // non-negative floats order like their values); NaN is stored as +inf.
 __device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {

@@ -274,14 +274,24 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_smem(const Unit* __rest
   // does not write, so its values read by the others are those of step j - 1;
   // the warp results of step j + 1 go to the other parity buffer than those
   // read in step j, and the step's barrier separates both from step j + 2.
+  bool dead = false;  // LSMS_DEBUG_BOUNDS: a pivot index out of range stops the panel (CTA-uniform)
 #pragma unroll 1
   for (int j = 0; j < NB; ++j) {
-    if (j < nbp) {
+    if (j < nbp && !dead) {
       const int par = j & 1;
       R best = lane < nw ? s_val[par][lane] : R(-1);  // nw <= 32 warp results
       int bl = lane < nw ? s_lg[par][lane] : m, bp = lane < nw ? s_ph[par][lane] : 0;
       warp_best(best, bl, bp);
       const int p = bl, pph = bp;
+      if (kDebugBounds) {
+        int32_t* sw = &stat[u.stat_off];
+        if (!(dbg_in(p, j, m, sw) & dbg_in(pph, 0, m, sw))) {
+          if (tid == 0)
+            for (int jj = j; jj < nbp; ++jj) piv[k + jj] = k + jj;
+          dead = true;
+          continue;
+        }
+      }
       if (tid == 0) piv[k + j] = k + p;
       lg = lg == j ? p : (lg == p ? j : lg);  // interchange logical rows j and p
       const C pv = sP[j * m + pph];
@@ -315,7 +325,7 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_smem(const Unit* __rest
     }
   }
   // write back in logical order
-  if (own)
+  if (own && dbg_in(lg, 0, m, &stat[u.stat_off]))
     for (int c = 0; c < nbp; ++c) A[(size_t)(k + c) * n + k + lg] = sP[c * m + tid];
   if (tid == 0 && flags) atomicOr(&stat[u.stat_off], flags);
   if constexpr (std::is_same<R, float>::value) {
@@ -434,7 +444,8 @@ __device__ __forceinline__ void k_swap_trsm_staged(float2* A, int n, int k, int 
 }
 
 template <typename R, int NB>
-__global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ units, char* fac_base, int k) {
+__global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ units, char* fac_base, int k,
+                                                   int32_t* stat) {
   using C = Cx<R>;
   static_assert(NB == 32, "one warp of interchanges");
   const Unit u = units[blockIdx.y];
@@ -443,6 +454,10 @@ __global__ void __launch_bounds__(256) k_swap_trsm(const Unit* __restrict__ unit
   if (c0 >= n) return;  // columns right of the panel exist only when the panel is full
   C* A = reinterpret_cast<C*>(fac_base + u.fac_off);
   const int32_t* piv = reinterpret_cast<const int32_t*>(fac_base + u.piv_off);
+  if (kDebugBounds) {  // the panel's pivots must lie in [k + j, n)
+    const bool bad = threadIdx.x < NB && !dbg_in(piv[k + threadIdx.x], k + threadIdx.x, n, &stat[u.stat_off]);
+    if (__syncthreads_or(bad)) return;
+  }
   __shared__ C sL[NB][NB + 1];
   __shared__ int sStep[NB];       // slot exchanged with slot j at interchange j (-1: none)
   __shared__ int sTgtRow[NB];     // row of target slot 32 + t
@@ -795,7 +810,8 @@ constexpr int kLapCols = 32;
 __host__ __device__ inline size_t lap_stage_elems(int n_max) { return (size_t)(n_max > 2048 ? n_max : 2048); }
 inline size_t lap_smem_bytes(int n_max) { return lap_stage_elems(n_max) * 8 + (size_t)3 * n_max * 4; }
 
-__global__ void __launch_bounds__(256) k_lapack_rows(const Unit* __restrict__ units, char* fac_base, int n_max) {
+__global__ void __launch_bounds__(256) k_lapack_rows(const Unit* __restrict__ units, char* fac_base, int n_max,
+                                                     int32_t* stat) {
   constexpr int NB = 32;
   const Unit u = units[blockIdx.x];
   const int n = u.n;
@@ -818,7 +834,7 @@ __global__ void __launch_bounds__(256) k_lapack_rows(const Unit* __restrict__ un
       const int r0 = NB * (b + 1), r1 = min(n, r0 + NB);
       for (int r = r1 - 1; r >= r0; --r) {
         const int a = r, c = piv[r];
-        if (a != c) {
+        if (a != c && dbg_in(c, r, n, &stat[u.stat_off])) {
           const int ra = pos[a], rc = pos[c];
           idx[ra] = c;
           idx[rc] = a;
@@ -1133,7 +1149,7 @@ int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
     // one warp per column right of the panel
     LSMS_LAUNCH((k_swap_trsm<R, NB>), dim3((trail + kSwapCols - 1) / kSwapCols, n_units), dim3(256),
                 sizeof(Cx<R>) == 8 ? kSwapTileBytes : 0, st, d_units,
-                fac_base, k);
+                fac_base, k, stat);
     if constexpr (std::is_same<R, float>::value) {
       // complex64: the trailing update runs on the tensor cores (3xTF32, tc_gemm.cu)
       const int rc = gemm_tc_chunk(d_units, n_units, n_max, k, fac_base, stat, st);
@@ -1154,7 +1170,7 @@ int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
       LSMS_CUDA_TRY(cudaFuncSetAttribute(k_lapack_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lap));
       lap_attr = lap;
     }
-    LSMS_LAUNCH(k_lapack_rows, dim3(n_units), dim3(256), lap, st, d_units, fac_base, n_max);
+    LSMS_LAUNCH(k_lapack_rows, dim3(n_units), dim3(256), lap, st, d_units, fac_base, n_max, stat);
   }
   return LSMS_OK;
 }

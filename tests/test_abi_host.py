@@ -174,7 +174,8 @@ def test_options_roundtrip_and_range_checks(L):
         B.set_option("fallback_slots", 3)
         assert B.get_option("fallback_slots") == 3
         for name, bad in (("growth_limit", 0.0), ("growth_limit", float("inf")), ("fallback_slots", -1),
-                          ("fallback_slots", 1.5), ("ir_max_sweeps", 65), ("streams", 5), ("no_such_option", 1)):
+                          ("fallback_slots", 1.5), ("ir_max_sweeps", 65), ("streams", 5), ("solve_steps", 3),
+                          ("nvtx", 2), ("no_such_option", 1)):
             with pytest.raises(B.LsmsError) as ei:
                 B.set_option(name, bad)
             assert ei.value.code == B.LSMS_ERR_ARG
@@ -224,3 +225,19 @@ def test_sigma_atoms_argument_errors(L):
     assert lib.lsms_kubo_sigma_atoms(lz.handle, 3, dummy, 1, dummy, 0, dummy, 1, -1.0, 0, dummy, None) == B.LSMS_ERR_ARG
     assert lib.lsms_kubo_sigma_atoms(lz.handle, 3, dummy, 1, dummy, 0, dummy, 1, 1.0, 0, None, None) == B.LSMS_ERR_ARG
     assert lib.lsms_kubo_sigma_atoms(lz.handle, 3, dummy, 1, dummy, 0, dummy, 0, 1.0, 0, dummy, None) == B.LSMS_ERR_ARG
+
+
+def test_unit_stats_argument_errors(L):
+    """lsms_unit_stats rejects NULL pointers, a negative count and a misaligned record before any launch."""
+    import ctypes
+    from paper_2311_12134_gb300 import binding as B
+    lib = B.lib()
+    words = ctypes.c_void_p(256)
+    assert lib.lsms_unit_stats(None, 4, ctypes.c_void_p(512), None) == B.LSMS_ERR_ARG
+    assert lib.lsms_unit_stats(words, 4, None, None) == B.LSMS_ERR_ARG
+    assert lib.lsms_unit_stats(words, -1, ctypes.c_void_p(512), None) == B.LSMS_ERR_ARG
+    assert lib.lsms_unit_stats(words, 4, ctypes.c_void_p(516), None) == B.LSMS_ERR_ARG
+    assert "lsms_unit_stats" in lib.lsms_last_error().decode()
+    for name in ("nvtx", "solve_steps"):
+        v = B.get_option(name)
+        assert v == 0
