@@ -342,7 +342,8 @@ int lsms_kubo_sigma_backward(const lsms_liz* liz, int lmax, const int32_t* speci
  *                     triangular solves above 8 columns (8, 16 or 32; 0 = 8 up to
  *                     16 columns, else 16): a tile shape the autotuner picks
  *   "solve_regs"      0 (default): 8- and 16-column solve CTAs sized for 8 CTAs
- *                     per SM (64 registers); 1: for 4 CTAs per SM (128 registers)
+ *                     per SM (64 registers); 1: for 4 CTAs per SM (128 registers);
+ *                     2: for 6 CTAs per SM (85 registers)
  *   "nvtx"            1: NVTX ranges around the stages of each call (assembly +
  *                     LU, solve + refinement, traces, adjoint right-hand sides
  *                     and site products, FP64 fallback); 0 (default): none

@@ -7,7 +7,8 @@ the batched launches have):
 * ``solve_cols``  right-hand-side columns per CTA of the mixed form's triangular
                   solves (8, 16 or 32): wider slices read the factors fewer
                   times, narrower slices run more independent block-step chains;
-* ``solve_regs``  8 solve CTAs per SM with 64 registers, or 4 with 128;
+* ``solve_regs``  8 solve CTAs per SM with 64 registers (0), 4 with 128 (1) or
+                  6 with 85 (2);
 * ``solve_steps`` the solves as one CTA chain per unit and slice (0) or as one
                   launch per block step over all units (2);
 * ``streams``     concurrent parts of each chunk of units (2 or 4).
@@ -44,7 +45,7 @@ def candidates():
     out = []
     for streams in (2, 4):
         out.append({"solve_cols": 0, "solve_regs": 0, "solve_steps": 2, "streams": streams})
-        for cols, regs in ((0, 0), (0, 1), (8, 0), (8, 1), (16, 0), (16, 1), (32, 0)):
+        for cols, regs in ((0, 0), (0, 1), (0, 2), (8, 0), (8, 1), (8, 2), (16, 0), (16, 1), (16, 2), (32, 0)):
             out.append({"solve_cols": cols, "solve_regs": regs, "solve_steps": 0, "streams": streams})
     return out
 

@@ -1729,7 +1729,7 @@ extern "C" int lsms_set_option(const char* name, double value) {
       return fail(LSMS_ERR_ARG, "solve_cols must be 0, 8, 16 or 32");
     g_opt_solve_cols.store((int)value);
   } else if (n == "solve_regs") {
-    if (!in_int(0, 1)) return fail(LSMS_ERR_ARG, "solve_regs must be 0 or 1");
+    if (!in_int(0, 2)) return fail(LSMS_ERR_ARG, "solve_regs must be 0, 1 or 2");
     g_opt_solve_regs.store((int)value);
   } else if (n == "solve_steps") {
     if (!in_int(0, 2)) return fail(LSMS_ERR_ARG, "solve_steps must be 0, 1 or 2");

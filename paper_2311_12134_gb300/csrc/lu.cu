@@ -1223,19 +1223,22 @@ int lu_solve_chunk(const Unit* d_units, int n_units, int n_max, const char* fac_
     else if (nrhs <= 4) LSMS_LAUNCH((k_solve_c64<4, kSolveThreads>), g1, b256, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
     else if (nrhs <= 8) LSMS_LAUNCH((k_solve_c64<8, kSolveThreads>), g1, b256, 0, st, d_units, fac_base, ws, which_rhs, nrhs, done);
     else {
-      // option "solve_regs": 0 = 8 CTAs of 128 threads per SM (64 registers), 1 = 4 (128 registers)
+      // option "solve_regs": 0 = 8 CTAs of 128 threads per SM (64 registers), 1 = 4 (128 registers),
+      // 2 = 6 (85 registers)
       int sl = opt_solve_cols();
       if (sl <= 0) sl = nrhs <= 16 ? 8 : 16;
       if (sl == 32 && nrhs <= 16) sl = 16;  // one slice holds every column
-      const bool regs = opt_solve_regs() != 0;
+      const int regs = opt_solve_regs();
       const dim3 gs(n_units, (nrhs + sl - 1) / sl);
 #define LSMS_SOLVE(NCOL, NT, MINB) \
   LSMS_LAUNCH((k_solve_c64<NCOL, NT, MINB>), gs, dim3(NT), 0, st, d_units, fac_base, ws, which_rhs, nrhs, done)
       if (sl == 8) {
-        if (regs) LSMS_SOLVE(8, 128, 4);
+        if (regs == 2) LSMS_SOLVE(8, 128, 6);
+        else if (regs) LSMS_SOLVE(8, 128, 4);
         else LSMS_SOLVE(8, 128, 8);
       } else if (sl == 16) {
-        if (regs) LSMS_SOLVE(16, 128, 4);
+        if (regs == 2) LSMS_SOLVE(16, 128, 6);
+        else if (regs) LSMS_SOLVE(16, 128, 4);
         else LSMS_SOLVE(16, 128, 8);
       } else {
         LSMS_SOLVE(32, 256, 2);
