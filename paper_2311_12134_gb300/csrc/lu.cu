@@ -403,6 +403,10 @@ __device__ __forceinline__ void k_swap_trsm_staged(float2* A, int n, int k, int 
   constexpr int LD = kSwapCols + 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ncols = min(kSwapCols, n - c0);
+  // the tile's 256-byte column segments requested into L2 at once (two lines per thread), so
+  // the warps' loads below find them there
+  for (int x = tid; x < 2 * ncols; x += blockDim.x)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(A + (size_t)(c0 + (x >> 1)) * n + k + 16 * (x & 1)));
   for (int cc = warp; cc < ncols; cc += 8) sTile[lane * LD + cc] = A[(size_t)(c0 + cc) * n + k + lane];
   __syncthreads();
   float umax = 0.f;  // pivot growth: largest |U12| entry of this column
