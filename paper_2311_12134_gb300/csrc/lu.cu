@@ -1128,7 +1128,7 @@ int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
                     cudaStream_t st) {
   constexpr int NB = LuCfg<R>::NB;
   // panels up to kPanelSmemBytes stay in shared memory; taller ones use k_panel
-  constexpr int kPanelSmemBytes = 200 * 1024;
+  constexpr int kPanelSmemBytes = 224 * 1024;
   const int max_rows = kPanelSmemBytes / (NB * (int)sizeof(Cx<R>));
   static bool attr_set = false;
   if (!attr_set) {

@@ -384,12 +384,12 @@ def test_tau_odd_sizes_several_panels(lmax, precision):
             assert rel_err_blocks(t[e, s][None], col[e, s][None]) < TOL[precision]
 
 
-@pytest.mark.parametrize("lmax,n_atoms", [(3, 2), (1, 8), (3, 24), (3, 26)])
+@pytest.mark.parametrize("lmax,n_atoms", [(3, 2), (1, 8), (3, 24), (3, 26), (3, 28), (3, 29)])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_tau_sizes_multiple_of_the_panel_width(lmax, n_atoms, precision):
-    """Clusters covered by every LIZ with n = 32, 32, 384 and 416: full last panels
-    (n a multiple of 32), a single-panel matrix, and the first panel just below and
-    above the complex128 shared-memory panel limit (400 rows)."""
+    """Clusters covered by every LIZ with n = 32, 32, 384, 416, 448 and 464: full last
+    panels (n a multiple of 32), a single-panel matrix, and the first panel at and just
+    above the complex128 shared-memory panel limit (448 rows)."""
     w = wl.cluster(n_atoms=n_atoms, lmax=lmax, r_liz=400.0, seed=11, spread=4.0 * n_atoms ** (1 / 3) + 3.0)
     lz, tau, st, _ = gpu_tau(w, precision)
     assert int((st & 0xff).abs().sum()) == 0
