@@ -176,7 +176,8 @@ int lsms_gaunt_table(int lmax, double* C);
  * species      dev [n_atoms] int32 species index of each atom (< n_species).
  * tinv         dev [n_species][n_energy][K][K] t^{-1}(z_e), complex-symmetric.
  * z            host [n_energy] complex energies (Im z != 0 recommended).
- * precision    LSMS_FP64 or LSMS_MIXED, optionally | LSMS_CONJ_PAIRS.
+ * precision    LSMS_FP64 or LSMS_MIXED, optionally | LSMS_CONJ_PAIRS.  The mixed
+ *              form takes LIZ matrices up to n = K S = 16,600 (LSMS_ERR_ARG beyond).
  * tau          dev [n_energy][S_total][K][K] output: tau[e][s] = tau^{s 0} of
  *              the LIZ that site s belongs to (row L, column L').
  * unit_status  dev [n_energy][n_atoms] int32 output, or NULL: bits 0-7 the

@@ -809,10 +809,12 @@ __global__ void __launch_bounds__(64) k_diag_inv(const Unit* __restrict__ units,
 // idx[r]; pos: the inverse).  Prepending an interchange (a, c) to the sequence
 // exchanges the values a and c in idx.  Only the rows with idx[r] != r move; a
 // pass reads all moved entries of some columns into shared memory, then writes
-// them.  Dynamic shared memory: lap_smem_bytes(n_max).
+// them.  Dynamic shared memory: lap_smem_bytes(n_max) (14 bytes per row: the
+// complex64 n <= 16,600).
 constexpr int kLapCols = 32;
+constexpr int kLapMaxN = 65535;  // row indices held as 16-bit values
 __host__ __device__ inline size_t lap_stage_elems(int n_max) { return (size_t)(n_max > 2048 ? n_max : 2048); }
-inline size_t lap_smem_bytes(int n_max) { return lap_stage_elems(n_max) * 8 + (size_t)3 * n_max * 4; }
+inline size_t lap_smem_bytes(int n_max) { return lap_stage_elems(n_max) * 8 + (size_t)3 * n_max * 2; }
 
 __global__ void __launch_bounds__(256) k_lapack_rows(const Unit* __restrict__ units, char* fac_base, int n_max,
                                                      int32_t* stat) {
@@ -824,12 +826,12 @@ __global__ void __launch_bounds__(256) k_lapack_rows(const Unit* __restrict__ un
   extern __shared__ __align__(16) unsigned char lap_raw[];
   const int cap = (int)lap_stage_elems(n_max);
   float2* stage = reinterpret_cast<float2*>(lap_raw);
-  int* idx = reinterpret_cast<int*>(stage + cap);
-  int* pos = idx + n_max;
-  int* list = pos + n_max;
+  unsigned short* idx = reinterpret_cast<unsigned short*>(stage + cap);
+  unsigned short* pos = idx + n_max;
+  unsigned short* list = pos + n_max;
   __shared__ int s_cnt;
   const int tid = threadIdx.x;
-  for (int r = tid; r < n; r += blockDim.x) idx[r] = pos[r] = r;
+  for (int r = tid; r < n; r += blockDim.x) idx[r] = pos[r] = (unsigned short)r;
   __syncthreads();
   const int nb = (n + NB - 1) / NB;
   for (int b = nb - 2; b >= -1; --b) {
@@ -840,10 +842,10 @@ __global__ void __launch_bounds__(256) k_lapack_rows(const Unit* __restrict__ un
         const int a = r, c = piv[r];
         if (a != c && dbg_in(c, r, n, &stat[u.stat_off])) {
           const int ra = pos[a], rc = pos[c];
-          idx[ra] = c;
-          idx[rc] = a;
-          pos[a] = rc;
-          pos[c] = ra;
+          idx[ra] = (unsigned short)c;
+          idx[rc] = (unsigned short)a;
+          pos[a] = (unsigned short)rc;
+          pos[c] = (unsigned short)ra;
         }
       }
       s_cnt = 0;
@@ -851,7 +853,7 @@ __global__ void __launch_bounds__(256) k_lapack_rows(const Unit* __restrict__ un
     __syncthreads();
     if (b < 0) break;
     for (int r = NB * (b + 1) + tid; r < n; r += blockDim.x)
-      if (idx[r] != r) list[atomicAdd(&s_cnt, 1)] = r;
+      if (idx[r] != r) list[atomicAdd(&s_cnt, 1)] = (unsigned short)r;
     __syncthreads();
     const int m = s_cnt;
     if (m == 0) continue;
@@ -1168,7 +1170,8 @@ int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
   if constexpr (std::is_same<R, float>::value) {
     LSMS_LAUNCH(k_diag_inv, dim3((n_max + kDiagNB - 1) / kDiagNB, n_units), dim3(64), 0, st, d_units, fac_base);
     const size_t lap = lap_smem_bytes(n_max);
-    if (lap > 227 * 1024) return fail(LSMS_ERR_ARG, "internal: n = %d too large for the row-order pass", n_max);
+    if (lap > 227 * 1024 || n_max > kLapMaxN)
+      return fail(LSMS_ERR_ARG, "n = %d too large for the complex64 form (at most 16,600)", n_max);
     static size_t lap_attr = 48 * 1024;
     if (lap > lap_attr) {
       LSMS_CUDA_TRY(cudaFuncSetAttribute(k_lapack_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lap));
