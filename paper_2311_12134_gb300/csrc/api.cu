@@ -1115,31 +1115,52 @@ __global__ void __launch_bounds__(256) k_ir_update(const Unit* __restrict__ unit
       y[q] = df_zero();
       bw[q] = mk(0.0, 0.0);
     }
-    for (int c = 0; c < nrhs; ++c) {
-      float cm = 0.f;
-      if (live) {
-        const size_t idx = (size_t)c * n + i;
-        const float2 d32 = D[idx];
-        const double2 x = cadd(X[idx], to64(d32));
-        X[idx] = x;
-        const float4 xs = df_split(x);  // split once here instead of in every residual CTA
-        Xdf[idx] = xs;
-        cm = fmaxf(fabsf(xs.x), fabsf(xs.z));
-        dn = fmaf(d32.x, d32.x, fmaf(d32.y, d32.y, dn));
-        xn = fmaf(xs.x, xs.x, fmaf(xs.z, xs.z, xn));
+    // columns in groups of 8: the group's loads are issued together, then used
+    for (int c0 = 0; c0 < nrhs; c0 += 8) {
+      float2 dv[8];
+      double2 xv[8], bv[8];
 #pragma unroll
-        for (int q = 0; q < kProbe; ++q) {
-          const float2 w = sw[q][c & 31];
-          dfc_mac(y[q], xs, make_float4(w.x, 0.f, w.y, 0.f));
-        }
-        if (explicit_b) {
-          const double2 b = B[idx];
-#pragma unroll
-          for (int q = 0; q < kProbe; ++q) bw[q] = cfma(b, to64(sw[q][c & 31]), bw[q]);
+      for (int j = 0; j < 8; ++j) {
+        const int c = c0 + j;
+        if (live && c < nrhs) {
+          const size_t idx = (size_t)c * n + i;
+          dv[j] = D[idx];
+          xv[j] = X[idx];
+          if (explicit_b) bv[j] = B[idx];
         }
       }
-      cm = warp_max_nonneg(cm);
-      if ((threadIdx.x & 31) == 0) atomicMax(&s_cmax[c], __float_as_uint(cm));
+      float cmv[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int c = c0 + j;
+        cmv[j] = 0.f;
+        if (live && c < nrhs) {
+          const size_t idx = (size_t)c * n + i;
+          const float2 d32 = dv[j];
+          const double2 x = cadd(xv[j], to64(d32));
+          X[idx] = x;
+          const float4 xs = df_split(x);  // split once here instead of in every residual CTA
+          Xdf[idx] = xs;
+          cmv[j] = fmaxf(fabsf(xs.x), fabsf(xs.z));
+          dn = fmaf(d32.x, d32.x, fmaf(d32.y, d32.y, dn));
+          xn = fmaf(xs.x, xs.x, fmaf(xs.z, xs.z, xn));
+#pragma unroll
+          for (int q = 0; q < kProbe; ++q) {
+            const float2 w = sw[q][c & 31];
+            dfc_mac(y[q], xs, make_float4(w.x, 0.f, w.y, 0.f));
+          }
+          if (explicit_b) {
+#pragma unroll
+            for (int q = 0; q < kProbe; ++q) bw[q] = cfma(bv[j], to64(sw[q][c & 31]), bw[q]);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (c0 + j >= nrhs) break;
+        const float cm = warp_max_nonneg(cmv[j]);
+        if ((threadIdx.x & 31) == 0) atomicMax(&s_cmax[c0 + j], __float_as_uint(cm));
+      }
     }
     if (live) {
 #pragma unroll
@@ -1178,8 +1199,8 @@ __global__ void __launch_bounds__(256) k_ir_update(const Unit* __restrict__ unit
 }
 
 // Convergence probe, residual half: r_q = (B w)_q - M y_q for the kProbe vectors
-// of k_ir_update, double-float as in k_residual, rounded to complex64 and
-// permuted by P into X32 columns q = 0..kProbe-1 for the probe correction solve.
+// of k_ir_update, double-float as in k_residual, rounded to complex64 into X32
+// columns q = 0..kProbe-1 for the probe correction solve (which permutes them).
 // grid (ceil(n_max / 64), n_units), block 256: 64 rows x 4 quarters of each
 // 128-column slab of M, the quarters' partial sums added in shared memory.
 __global__ void __launch_bounds__(256, 3) k_probe_residual(const Unit* __restrict__ units, const char* fac_base,
