@@ -652,6 +652,18 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
     t0 = s_start[L * kMaxK + Lp];
     t1 = s_start[L * kMaxK + Lp + 1];
   }
+  // mixed form: this thread's couplings (at most kCpPair for lmax <= 3) in registers, so a
+  // Gaunt term costs one shared-memory load (V) instead of three
+  constexpr int kCpPair = 7;
+  float2 cpc[kCpPair];
+  int cpl[kCpPair];
+  const bool cp_regs = t1 - t0 <= kCpPair;
+#pragma unroll
+  for (int t = 0; t < kCpPair; ++t) {
+    const bool in = MIXED && t0 + t < t1;
+    cpc[t] = in ? s_coef2[t0 + t] : make_float2(0.f, 0.f);
+    cpl[t] = in ? s_lpp[t0 + t] : 0;
+  }
   // mixed form: row maxima of block row p (over the columns of blocks q >= p; the
   // CTAs of sites q < p add the rest through their transposed blocks) and the
   // largest |M| entry, per energy of the atom; NONFINITE per energy
@@ -744,10 +756,12 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const Unit* __restrict__ un
             } else {
               DfAcc acc = df_zero();
               const float4* Vq = reinterpret_cast<const float4*>(sVraw) + base;
-              for (int t = t0; t < t1; ++t) {
-                const float2 c = s_coef2[t];
-                const float4 w = Vq[s_lpp[t]];
-                dfr_mac(acc, c, w);
+              if (cp_regs) {
+#pragma unroll
+                for (int t = 0; t < kCpPair; ++t)
+                  if (t0 + t < t1) dfr_mac(acc, cpc[t], Vq[cpl[t]]);
+              } else {
+                for (int t = t0; t < t1; ++t) dfr_mac(acc, s_coef2[t], Vq[s_lpp[t]]);
               }
               v4 = df_value(acc);
             }
