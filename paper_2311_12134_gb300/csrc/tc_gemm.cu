@@ -37,7 +37,7 @@ constexpr int OP_A = 2 * CHUNK_A;           // real K = 2 NB = 64 tf32 = two chu
 constexpr int OP_B = 2 * CHUNK_B;
 constexpr int SMEM_BYTES = 2 * OP_A + 2 * OP_B + 64;  // hi/lo of A and B + barrier + TMEM slot
 constexpr uint32_t TMEM_COLS = 64;
-constexpr int kPrefetchTiles = 2;            // C tiles requested into L2 ahead of their loads
+constexpr int kPrefetchTiles = 1;            // C tiles requested into L2 ahead of their loads
 constexpr long long kWaitLimit = 1ll << 24;  // bounded mbarrier wait (polls)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
