@@ -348,11 +348,13 @@ int lsms_kubo_sigma_backward(const lsms_liz* liz, int lmax, const int32_t* speci
  *   "nvtx"            1: NVTX ranges around the stages of each call (assembly +
  *                     LU, solve + refinement, traces, adjoint right-hand sides
  *                     and site products, FP64 fallback); 0 (default): none
- *   "solve_steps"     0 (default) or 1: the mixed form's triangular solves run
- *                     as one CTA chain of block steps per unit and column slice
- *                     (shaped by solve_cols / solve_regs); 2: as one launch per
- *                     32-row block step over all units of a chunk, the row
- *                     update spread over many CTAs
+ *   "solve_steps"     1: the mixed form's triangular solves run as one CTA
+ *                     chain of block steps per unit and column slice (shaped by
+ *                     solve_cols / solve_regs); 2: as one launch per 32-row block
+ *                     step over all units of a chunk, the row update spread over
+ *                     many CTAs; 0 (default): block steps when a chunk part has
+ *                     fewer than two chains per SM (few, large LIZ matrices),
+ *                     else chains
  * LSMS_ERR_ARG for an unknown name or a value out of range. */
 int lsms_set_option(const char* name, double value);
 int lsms_get_option(const char* name, double* value);

@@ -9,8 +9,9 @@ the batched launches have):
                   times, narrower slices run more independent block-step chains;
 * ``solve_regs``  8 solve CTAs per SM with 64 registers (0), 4 with 128 (1) or
                   6 with 85 (2);
-* ``solve_steps`` the solves as one CTA chain per unit and slice (0) or as one
-                  launch per block step over all units (2);
+* ``solve_steps`` the solves by the library's choice (0), as one CTA chain per
+                  unit and slice (1) or as one launch per block step over all
+                  units (2);
 * ``streams``     concurrent parts of each chunk of units (2 or 4).
 
 ``tune`` times ``Problem.step`` (forward + adjoint) under every candidate with
@@ -46,7 +47,7 @@ def candidates():
     for streams in (2, 4):
         out.append({"solve_cols": 0, "solve_regs": 0, "solve_steps": 2, "streams": streams})
         for cols, regs in ((0, 0), (0, 1), (0, 2), (8, 0), (8, 1), (8, 2), (16, 0), (16, 1), (16, 2), (32, 0)):
-            out.append({"solve_cols": cols, "solve_regs": regs, "solve_steps": 0, "streams": streams})
+            out.append({"solve_cols": cols, "solve_regs": regs, "solve_steps": 1, "streams": streams})
     return out
 
 

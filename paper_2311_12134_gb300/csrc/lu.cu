@@ -104,7 +104,7 @@ __device__ __forceinline__ void cp_async_elem(double2* dst, const double2* src) 
 
 // ------------------------------------------------------------------ panel
 template <typename R, int NB>
-__global__ void __launch_bounds__(256) k_panel(const Unit* __restrict__ units, char* fac_base, int k,
+__global__ void __launch_bounds__(1024) k_panel(const Unit* __restrict__ units, char* fac_base, int k,
                                                int32_t* stat, int max_rows) {
   using C = Cx<R>;
   const Unit u = units[blockIdx.x];
@@ -113,8 +113,8 @@ __global__ void __launch_bounds__(256) k_panel(const Unit* __restrict__ units, c
   C* A = reinterpret_cast<C*>(fac_base + u.fac_off);
   int32_t* piv = reinterpret_cast<int32_t*>(fac_base + u.piv_off);
   const int nbp = min(NB, n - k);
-  __shared__ R s_val[8];
-  __shared__ int s_idx[8];
+  __shared__ R s_val[32];
+  __shared__ int s_idx[32];
   __shared__ C s_row[NB];
   __shared__ int s_piv;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1144,7 +1144,7 @@ int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
   for (int k = 0; k < n_max; k += NB) {
     const int m_max = n_max - k;
     if (m_max > max_rows)
-      LSMS_LAUNCH((k_panel<R, NB>), dim3(n_units), dim3(256), 0, st, d_units, fac_base, k, stat, max_rows);
+      LSMS_LAUNCH((k_panel<R, NB>), dim3(n_units), dim3(1024), 0, st, d_units, fac_base, k, stat, max_rows);
     const int rows_smem = std::min(m_max, max_rows);
     // one thread per row: short panels launch fewer threads, so more CTAs fit on an SM
     const int threads = std::min(kPanelThreads, (rows_smem + 31) / 32 * 32);
@@ -1215,8 +1215,21 @@ int lu_solve_chunk(const Unit* d_units, int n_units, int n_max, const char* fac_
       perm_attr = pb;
     }
     LSMS_LAUNCH(k_perm_rows, dim3(nrhs, n_units), dim3(256), pb, st, d_units, fac_base, ws, nrhs, done);
-    // option "solve_steps": 2 = block-step launches; 0 (default), 1 = one CTA chain per unit and slice
-    if (opt_solve_steps() == 2) {
+    // option "solve_steps": 1 = one CTA chain per unit and column slice; 2 = block-step launches;
+    // 0 (default) = block steps when the chains could not fill the GPU (fewer than two per SM:
+    // few units of large LIZ matrices), else chains
+    int steps = opt_solve_steps();
+    if (steps == 0) {
+      static int sms = 0;
+      if (!sms) {
+        int dev = 0;
+        LSMS_CUDA_TRY(cudaGetDevice(&dev));
+        LSMS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      }
+      const int slices = nrhs <= 16 ? 1 : 2;
+      steps = (long long)n_units * slices < 2LL * sms ? 2 : 1;
+    }
+    if (steps == 2) {
       if (nrhs <= 8) return solve_steps<8>(d_units, n_units, n_max, fac_base, ws, nrhs, done, st);
       if (nrhs <= 16) return solve_steps<16>(d_units, n_units, n_max, fac_base, ws, nrhs, done, st);
       return solve_steps<32>(d_units, n_units, n_max, fac_base, ws, nrhs, done, st);

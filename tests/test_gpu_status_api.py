@@ -253,7 +253,7 @@ def test_conductivity_host_call_matches_oracle(B, alloy, precision):
 
 
 @pytest.mark.parametrize("cols,regs,streams,steps",
-                         [(8, 1, 4, 0), (16, 0, 2, 1), (16, 1, 4, 0), (32, 0, 1, 0), (16, 1, 2, 2), (0, 0, 4, 2)])
+                         [(8, 1, 4, 1), (16, 0, 2, 1), (16, 1, 4, 0), (32, 0, 1, 1), (16, 1, 2, 2), (0, 0, 4, 2)])
 def test_tuning_options_keep_results(B, alloy, cols, regs, streams, steps):
     """The autotuner's shapes (solve path, solve columns per CTA, register bound, concurrent parts)
     change the launch layout only: tau and the gradient match the default layout to rounding."""
