@@ -45,6 +45,7 @@ DEFAULTS = {"solve_cols": 0, "solve_regs": 0, "solve_steps": 0, "streams": 4}
 def candidates():
     out = []
     for streams in (2, 4):
+        out.append({"solve_cols": 0, "solve_regs": 0, "solve_steps": 0, "streams": streams})
         out.append({"solve_cols": 0, "solve_regs": 0, "solve_steps": 2, "streams": streams})
         for cols, regs in ((0, 0), (0, 1), (0, 2), (8, 0), (8, 1), (8, 2), (16, 0), (16, 1), (16, 2), (32, 0)):
             out.append({"solve_cols": cols, "solve_regs": regs, "solve_steps": 1, "streams": streams})
