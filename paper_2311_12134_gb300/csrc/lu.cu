@@ -21,6 +21,8 @@
 #include <algorithm>
 #include <type_traits>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace lsms {
@@ -336,6 +338,179 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_smem(const Unit* __rest
     const float wm = warp_max_nonneg(umax);
     if (lane == 0) atomic_max_nonneg(reinterpret_cast<float*>(fac_base + u.m64_off + growth_rel_off(n)) + 1, wm);
   }
+}
+
+// ------------------------------------------------------------------ tall panels on a cluster
+// Panels taller than shared memory holds (m = n - k above max_rows) on a
+// cluster of kPanelCluster CTAs per unit (thread-block cluster, distributed
+// shared memory): CTA r owns the physical rows [r R, (r + 1) R) of the panel,
+// R = ceil(m / kPanelCluster), up to kClusterRows per thread, kept in global
+// memory (the panel is L2-resident: 32 columns).  As in k_panel_smem, rows do not
+// move during the panel: each thread keeps the logical number of each of its
+// rows, a pivot exchanges two logical numbers, and the pivot search of column
+// j + 1 runs inside the update of column j.  Per column one cluster barrier:
+// every CTA publishes its best candidate (|Re| + |Im|, lowest logical row on
+// ties, NaN only if the whole column is NaN) in a parity slot of its shared
+// memory and, after the barrier, reads all kPanelCluster slots through
+// distributed shared memory, so all CTAs take the same pivot; the barrier's
+// release/acquire also orders the row updates of one column before the next
+// column's reads (those go to L2, ld.global.cg).  At the end, the at most 64 rows
+// whose logical and physical numbers differ are read into shared memory,
+// a cluster barrier, and written to their logical positions.  Same pivots and
+// arithmetic as the single-CTA panels.
+constexpr int kPanelCluster = 8;
+constexpr int kClusterThreads = 1024;
+constexpr int kClusterRows = 3;  // rows per thread: m <= 8 x 1024 x 3 = 24,576
+
+template <typename R, int NB>
+__global__ void __cluster_dims__(kPanelCluster, 1, 1) __launch_bounds__(kClusterThreads, 1)
+    k_panel_cluster(const Unit* __restrict__ units, char* fac_base, int k, int32_t* stat, int max_rows) {
+  using C = Cx<R>;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const Unit u = units[blockIdx.y];
+  const int n = u.n;
+  if (k >= n || n - k <= max_rows) return;  // the same for every CTA of the cluster (one unit)
+  const int m = n - k, nbp = min(NB, m);
+  const int per = (m + kPanelCluster - 1) / kPanelCluster;
+  if (per > kClusterRows * kClusterThreads) return;  // the host launches k_panel instead
+  C* A = reinterpret_cast<C*>(fac_base + u.fac_off);
+  int32_t* piv = reinterpret_cast<int32_t*>(fac_base + u.piv_off);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rbeg = rank * per, rend = min(m, rbeg + per);
+  __shared__ R c_val[2];  // this CTA's candidate per parity (read by the cluster)
+  __shared__ int c_lg[2], c_ph[2];
+  __shared__ R w_val[32];
+  __shared__ int w_lg[32], w_ph[32];
+  __shared__ int s_p, s_pph;
+  __shared__ C s_prow[NB];
+  __shared__ C s_move[64][NB];  // rows whose logical and physical numbers differ
+  __shared__ int s_mtgt[64], s_nmove;
+  auto at = [&](int i, int c) -> C* { return A + (size_t)(k + c) * n + k + i; };
+  auto warp_best = [](R& best, int& bl, int& bp) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+      const R ov = __shfl_xor_sync(0xffffffffu, best, off);
+      const int ol = __shfl_xor_sync(0xffffffffu, bl, off);
+      const int op = __shfl_xor_sync(0xffffffffu, bp, off);
+      if (ov > best || (ov == best && ol < bl)) { best = ov; bl = ol; bp = op; }
+    }
+  };
+  auto mag = [](C v) -> R {  // |Re| + |Im|; NaN below every number
+    const R a = cabs1(v);
+    return a >= R(0) ? a : R(-0.5);
+  };
+  // the CTA's best (value, logical, physical) into its parity slot
+  auto publish = [&](R best, int bl, int bp, int par) {
+    warp_best(best, bl, bp);
+    if (lane == 0) { w_val[warp] = best; w_lg[warp] = bl; w_ph[warp] = bp; }
+    __syncthreads();
+    if (warp == 0) {
+      best = w_val[lane];
+      bl = w_lg[lane];
+      bp = w_ph[lane];
+      warp_best(best, bl, bp);
+      if (lane == 0) { c_val[par] = best; c_lg[par] = bl; c_ph[par] = bp; }
+    }
+  };
+  int lg[kClusterRows];
+#pragma unroll
+  for (int t = 0; t < kClusterRows; ++t) lg[t] = rbeg + tid + t * kClusterThreads;
+  auto own = [&](int t) { return rbeg + tid + t * kClusterThreads < rend; };
+  {
+    R best = R(-1);
+    int bl = m, bp = 0;
+#pragma unroll
+    for (int t = 0; t < kClusterRows; ++t)
+      if (own(t)) {
+        const R v = mag(__ldcg(at(lg[t], 0)));
+        if (v > best || (v == best && lg[t] < bl)) { best = v; bl = lg[t]; bp = lg[t]; }
+      }
+    publish(best, bl, bp, 0);
+  }
+  cluster.sync();
+  int flags = 0;
+  for (int j = 0; j < nbp; ++j) {
+    const int par = j & 1;
+    if (warp == 0) {  // every CTA reduces the cluster's candidates itself: the same pivot everywhere
+      R best = R(-1);
+      int bl = m, bp = 0;
+      if (lane < kPanelCluster) {
+        best = *cluster.map_shared_rank(&c_val[par], lane);
+        bl = *cluster.map_shared_rank(&c_lg[par], lane);
+        bp = *cluster.map_shared_rank(&c_ph[par], lane);
+      }
+      warp_best(best, bl, bp);
+      if (lane == 0) { s_p = bl; s_pph = bp; }
+    }
+    __syncthreads();
+    const int p = s_p, pph = s_pph;
+    if (rank == 0 && tid == 0) piv[k + j] = k + p;
+#pragma unroll
+    for (int t = 0; t < kClusterRows; ++t) lg[t] = lg[t] == j ? p : (lg[t] == p ? j : lg[t]);
+    // the pivot row (physical pph, logical j now) was last written in column j - 1 by its owner
+    if (tid < nbp - j) s_prow[j + tid] = __ldcg(at(pph, j + tid));
+    __syncthreads();
+    const C pv = s_prow[j];
+    const bool zero = (pv.x == R(0) && pv.y == R(0));
+    if (zero) flags |= LSMS_UNIT_ZERO_PIVOT;
+    if (!finite2(pv)) flags |= LSMS_UNIT_NONFINITE;
+    const C rcp = zero ? mk(R(0), R(0)) : crcp(pv);
+    R best = R(-1);
+    int bl = m, bp = 0;
+#pragma unroll
+    for (int t = 0; t < kClusterRows; ++t) {
+      const int i = rbeg + tid + t * kClusterThreads;
+      if (i < rend && lg[t] > j) {
+        const C l = cmul(__ldcg(at(i, j)), rcp);
+        if (!zero) *at(i, j) = l;
+        for (int c = j + 1; c < nbp; ++c) {
+          const C v = cfms(l, s_prow[c], __ldcg(at(i, c)));
+          *at(i, c) = v;
+          if (c == j + 1) {
+            const R a = mag(v);
+            if (a > best || (a == best && lg[t] < bl)) { best = a; bl = lg[t]; bp = i; }
+          }
+        }
+      }
+    }
+    if (j + 1 < nbp) publish(best, bl, bp, par ^ 1);
+    cluster.sync();  // candidates and this column's row updates visible to the cluster
+  }
+  // rows out of place: read them, then (after every CTA has read its own) write them
+  if (tid == 0) s_nmove = 0;
+  __syncthreads();
+  float umax = 0.f;
+#pragma unroll
+  for (int t = 0; t < kClusterRows; ++t) {
+    const int i = rbeg + tid + t * kClusterThreads;
+    if (i >= rend) continue;
+    if constexpr (std::is_same<R, float>::value) {
+      if (lg[t] < nbp)  // a row of U: columns from its diagonal
+        for (int c = lg[t]; c < nbp; ++c) umax = fmaxf(umax, cabs1(__ldcg(at(i, c))));
+    }
+    if (lg[t] != i) {
+      const int slot = atomicAdd(&s_nmove, 1);  // at most 64 rows leave their place in a panel
+      if (slot < 64) {
+        s_mtgt[slot] = lg[t];
+        for (int c = 0; c < nbp; ++c) s_move[slot][c] = __ldcg(at(i, c));
+      }
+    }
+  }
+  cluster.sync();
+  const int nmove = min(s_nmove, 64);
+  for (int x = tid; x < nmove * nbp; x += blockDim.x) {
+    const int slot = x / nbp, c = x % nbp;
+    *at(s_mtgt[slot], c) = s_move[slot][c];
+  }
+  if (rank == 0 && tid == 0 && flags) atomicOr(&stat[u.stat_off], flags);
+  if constexpr (std::is_same<R, float>::value) {
+    const float wm = warp_max_nonneg(umax);
+    if (lane == 0 && wm > 0.f)
+      atomic_max_nonneg(reinterpret_cast<float*>(fac_base + u.m64_off + growth_rel_off(n)) + 1, wm);
+  }
+  cluster.sync();  // no CTA leaves while others may still read its shared memory
 }
 
 // ------------------------------------------------------------------ swap + trsm
@@ -1143,8 +1318,15 @@ int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
   }
   for (int k = 0; k < n_max; k += NB) {
     const int m_max = n_max - k;
-    if (m_max > max_rows)
-      LSMS_LAUNCH((k_panel<R, NB>), dim3(n_units), dim3(1024), 0, st, d_units, fac_base, k, stat, max_rows);
+    if (m_max > max_rows) {
+      // taller panels on one CTA per unit, or, from 2048 rows (few units of large LIZ
+      // matrices: the single CTA would leave most SMs idle), on a cluster of CTAs per unit
+      if (m_max > 2048 && (m_max + kPanelCluster - 1) / kPanelCluster <= kClusterRows * kClusterThreads)
+        LSMS_LAUNCH((k_panel_cluster<R, NB>), dim3(kPanelCluster, n_units), dim3(kClusterThreads), 0, st, d_units,
+                    fac_base, k, stat, max_rows);
+      else
+        LSMS_LAUNCH((k_panel<R, NB>), dim3(n_units), dim3(1024), 0, st, d_units, fac_base, k, stat, max_rows);
+    }
     const int rows_smem = std::min(m_max, max_rows);
     // one thread per row: short panels launch fewer threads, so more CTAs fit on an SM
     const int threads = std::min(kPanelThreads, (rows_smem + 31) / 32 * 32);
