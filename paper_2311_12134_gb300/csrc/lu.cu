@@ -979,9 +979,9 @@ __global__ void __launch_bounds__(64) k_diag_inv(const Unit* __restrict__ units,
 // their right-hand sides once (k_perm_rows) and substitute without interchanges,
 // so a block step of the forward substitution is the same product for every row
 // below it and can be spread over many CTAs.
-// One CTA per unit walks the blocks from the last to the first with the composed
+// A CTA walks the blocks from the last to the first with the composed
 // permutation of the later panels in shared memory (idx: new row r takes old row
-// idx[r]; pos: the inverse).  Prepending an interchange (a, c) to the sequence
+// idx[r]; pos: the inverse), moving the rows of its group of blocks.  Prepending an interchange (a, c) to the sequence
 // exchanges the values a and c in idx.  Only the rows with idx[r] != r move; a
 // pass reads all moved entries of some columns into shared memory, then writes
 // them.  Dynamic shared memory: lap_smem_bytes(n_max) (14 bytes per row: the
@@ -991,13 +991,23 @@ constexpr int kLapMaxN = 65535;  // row indices held as 16-bit values
 __host__ __device__ inline size_t lap_stage_elems(int n_max) { return (size_t)(n_max > 2048 ? n_max : 2048); }
 inline size_t lap_smem_bytes(int n_max) { return lap_stage_elems(n_max) * 8 + (size_t)3 * n_max * 2; }
 
-__global__ void __launch_bounds__(256) k_lapack_rows(const Unit* __restrict__ units, char* fac_base, int n_max,
-                                                     int32_t* stat) {
+constexpr int kLapBlocks = 8;  // 32-column blocks of L per CTA of k_lapack_rows
+
+// grid (ceil((blocks - 1) / kLapBlocks), n_units): CTA g moves the rows of blocks
+// g kLapBlocks .. g kLapBlocks + kLapBlocks - 1, after building the composition of
+// the later panels' interchanges itself (the prepends are cheap; the row moves of
+// the blocks run in parallel over the CTAs).
+__global__ void __launch_bounds__(256) k_lapack_rows(const Unit* __restrict__ units, const char* fac_base_c,
+                                                     int n_max, int32_t* stat) {
   constexpr int NB = 32;
-  const Unit u = units[blockIdx.x];
+  char* fac_base = const_cast<char*>(fac_base_c);
+  const Unit u = units[blockIdx.y];
   const int n = u.n;
+  const int nb = (n + NB - 1) / NB;
+  const int b_lo = blockIdx.x * kLapBlocks, b_hi = min(nb - 2, b_lo + kLapBlocks - 1);
+  if (b_lo > b_hi) return;
   float2* A = reinterpret_cast<float2*>(fac_base + u.fac_off);
-  int32_t* piv = reinterpret_cast<int32_t*>(fac_base + u.piv_off);
+  const int32_t* piv = reinterpret_cast<const int32_t*>(fac_base + u.piv_off);
   extern __shared__ __align__(16) unsigned char lap_raw[];
   const int cap = (int)lap_stage_elems(n_max);
   float2* stage = reinterpret_cast<float2*>(lap_raw);
@@ -1008,8 +1018,7 @@ __global__ void __launch_bounds__(256) k_lapack_rows(const Unit* __restrict__ un
   const int tid = threadIdx.x;
   for (int r = tid; r < n; r += blockDim.x) idx[r] = pos[r] = (unsigned short)r;
   __syncthreads();
-  const int nb = (n + NB - 1) / NB;
-  for (int b = nb - 2; b >= -1; --b) {
+  for (int b = nb - 2; b >= b_lo; --b) {
     // prepend panel b + 1's interchanges, its last one first
     if (tid == 0) {
       const int r0 = NB * (b + 1), r1 = min(n, r0 + NB);
@@ -1026,7 +1035,7 @@ __global__ void __launch_bounds__(256) k_lapack_rows(const Unit* __restrict__ un
       s_cnt = 0;
     }
     __syncthreads();
-    if (b < 0) break;
+    if (b > b_hi) continue;
     for (int r = NB * (b + 1) + tid; r < n; r += blockDim.x)
       if (idx[r] != r) list[atomicAdd(&s_cnt, 1)] = (unsigned short)r;
     __syncthreads();
@@ -1047,7 +1056,29 @@ __global__ void __launch_bounds__(256) k_lapack_rows(const Unit* __restrict__ un
       __syncthreads();
     }
   }
-  for (int r = tid; r < n; r += blockDim.x) piv[r] = idx[r];
+}
+
+// After k_lapack_rows (which reads the pivots): the pivots replaced by the full
+// permutation, the interchanges of all panels applied in order to the identity.
+// One CTA per unit; dynamic shared memory 2 n_max bytes.
+__global__ void __launch_bounds__(256) k_lapack_perm(const Unit* __restrict__ units, char* fac_base, int32_t* stat) {
+  const Unit u = units[blockIdx.x];
+  const int n = u.n;
+  int32_t* piv = reinterpret_cast<int32_t*>(fac_base + u.piv_off);
+  extern __shared__ unsigned short perm_raw[];
+  for (int r = threadIdx.x; r < n; r += blockDim.x) perm_raw[r] = (unsigned short)r;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int r = 0; r < n; ++r) {
+      const int c = piv[r];
+      if (c != r && dbg_in(c, r, n, &stat[u.stat_off])) {
+        const unsigned short t = perm_raw[r];
+        perm_raw[r] = perm_raw[c];
+        perm_raw[c] = t;
+      }
+    }
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += blockDim.x) piv[r] = perm_raw[r];
 }
 
 // Right-hand-side columns permuted by the factorization's row permutation:
@@ -1359,7 +1390,11 @@ int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
       LSMS_CUDA_TRY(cudaFuncSetAttribute(k_lapack_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lap));
       lap_attr = lap;
     }
-    LSMS_LAUNCH(k_lapack_rows, dim3(n_units), dim3(256), lap, st, d_units, fac_base, n_max, stat);
+    const int nb_max = (n_max + 31) / 32;
+    if (nb_max > 1)
+      LSMS_LAUNCH(k_lapack_rows, dim3((nb_max - 1 + kLapBlocks - 1) / kLapBlocks, n_units), dim3(256), lap, st,
+                  d_units, fac_base, n_max, stat);
+    LSMS_LAUNCH(k_lapack_perm, dim3(n_units), dim3(256), (size_t)n_max * 2, st, d_units, fac_base, stat);
   }
   return LSMS_OK;
 }
