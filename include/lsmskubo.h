@@ -352,9 +352,11 @@ int lsms_kubo_sigma_backward(const lsms_liz* liz, int lmax, const int32_t* speci
  *                     chain of block steps per unit and column slice (shaped by
  *                     solve_cols / solve_regs); 2: as one launch per 32-row block
  *                     step over all units of a chunk, the row update spread over
- *                     many CTAs; 0 (default): block steps when a chunk part has
- *                     fewer than two chains per SM (few, large LIZ matrices),
- *                     else chains
+ *                     many CTAs on the FP32 pipes; 3: the same with the row
+ *                     updates as 3xTF32 products on the tensor cores; 0
+ *                     (default): block steps when a chunk part has fewer than two
+ *                     chains per SM (few, large LIZ matrices; tensor cores from 9
+ *                     columns), else chains
  * LSMS_ERR_ARG for an unknown name or a value out of range. */
 int lsms_set_option(const char* name, double value);
 int lsms_get_option(const char* name, double* value);

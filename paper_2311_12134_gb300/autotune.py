@@ -11,7 +11,7 @@ the batched launches have):
                   6 with 85 (2);
 * ``solve_steps`` the solves by the library's choice (0), as one CTA chain per
                   unit and slice (1) or as one launch per block step over all
-                  units (2);
+                  units, row updates on the FP32 pipes (2) or the tensor cores (3);
 * ``streams``     concurrent parts of each chunk of units (2 or 4).
 
 ``tune`` times ``Problem.step`` (forward + adjoint) under every candidate with
@@ -47,6 +47,7 @@ def candidates():
     for streams in (2, 4):
         out.append({"solve_cols": 0, "solve_regs": 0, "solve_steps": 0, "streams": streams})
         out.append({"solve_cols": 0, "solve_regs": 0, "solve_steps": 2, "streams": streams})
+        out.append({"solve_cols": 0, "solve_regs": 0, "solve_steps": 3, "streams": streams})
         for cols, regs in ((0, 0), (0, 1), (0, 2), (8, 0), (8, 1), (8, 2), (16, 0), (16, 1), (16, 2), (32, 0)):
             out.append({"solve_cols": cols, "solve_regs": regs, "solve_steps": 1, "streams": streams})
     return out

@@ -1545,11 +1545,11 @@ static int solve_refine(const Call& c, const Plan& p, const Chunk& ch, const cha
   if (c.precision == LSMS_FP64) {
     if (explicit_b) LSMS_LAUNCH(k_copy_b, g1, dim3(256), 0, c.st, du, ws, nrhs, false);
     else LSMS_LAUNCH(k_rhs_identity<double2>, g1, dim3(256), 0, c.st, du, ws, (int)RHS_X, c.K, nrhs);
-    return lu_solve_chunk<double>(du, nu, ch.n_max, fac_base, ws, RHS_X, nrhs, nullptr, c.st);
+    return lu_solve_chunk<double>(du, nu, ch.n_max, fac_base, ws, RHS_X, nrhs, nullptr, stat, c.st);
   }
   if (explicit_b) LSMS_LAUNCH(k_copy_b, g1, dim3(256), 0, c.st, du, ws, nrhs, true);
   else LSMS_LAUNCH(k_rhs_identity<float2>, g1, dim3(256), 0, c.st, du, ws, (int)RHS_X32, c.K, nrhs);
-  if ((rc = lu_solve_chunk<float>(du, nu, ch.n_max, fac_base, ws, RHS_X32, nrhs, nullptr, c.st))) return rc;
+  if ((rc = lu_solve_chunk<float>(du, nu, ch.n_max, fac_base, ws, RHS_X32, nrhs, nullptr, stat, c.st))) return rc;
   LSMS_LAUNCH(k_widen, dim3(nu), dim3(256), 0, c.st, du, ws, nrhs);
   // done flags of this chunk's units start cleared (memset by the caller)
   const int max_sweeps = opt_ir_max_sweeps();
@@ -1570,12 +1570,12 @@ static int solve_refine(const Call& c, const Plan& p, const Chunk& ch, const cha
 #undef LSMS_RESID
       default: return fail(LSMS_ERR_ARG, "internal: no residual kernel for %d right-hand sides", nrhs);
     }
-    if ((rc = lu_solve_chunk<float>(du, nu, ch.n_max, fac_base, ws, RHS_X32, nrhs, done, c.st))) return rc;
+    if ((rc = lu_solve_chunk<float>(du, nu, ch.n_max, fac_base, ws, RHS_X32, nrhs, done, stat, c.st))) return rc;
     LSMS_LAUNCH(k_ir_update, dim3(nu), dim3(256), 0, c.st, du, ws, nrhs, c.K, explicit_b, it, kIrTol, done,
                 stat);
     // probe: would the next sweep's correction pass the test?  If so, stop here.
     LSMS_LAUNCH(k_probe_residual, gr, dim3(256), 0, c.st, du, fac_base, ws, done);
-    if ((rc = lu_solve_chunk<float>(du, nu, ch.n_max, fac_base, ws, RHS_X32, kProbe, done, c.st))) return rc;
+    if ((rc = lu_solve_chunk<float>(du, nu, ch.n_max, fac_base, ws, RHS_X32, kProbe, done, stat, c.st))) return rc;
     LSMS_LAUNCH(k_probe_check, dim3(nu), dim3(256), 0, c.st, du, ws, kIrTol, done, stat);
   }
   LSMS_LAUNCH(k_ir_finish, dim3((nu + 255) / 256), dim3(256), 0, c.st, du, nu, done, stat);
@@ -1617,7 +1617,7 @@ static int fallback_resolve(const Call& c, const Plan& p, char* ws, const WsHead
   const dim3 g1((n_max * nrhs + 255) / 256, slots);
   if (!adj) {
     LSMS_LAUNCH(k_rhs_identity<double2>, g1, dim3(256), 0, c.st, fbu, region, (int)RHS_X, c.K, nrhs);
-    if ((rc = lu_solve_chunk<double>(fbu, slots, n_max, region, region, RHS_X, nrhs, nullptr, c.st))) return rc;
+    if ((rc = lu_solve_chunk<double>(fbu, slots, n_max, region, region, RHS_X, nrhs, nullptr, stat, c.st))) return rc;
     LSMS_LAUNCH(k_write_tau, dim3(S_max, slots), dim3(256), 0, c.st, fbu, region, c.K, c.liz->total_sites, c.conj,
                 tau_out);
     return LSMS_OK;
@@ -1626,7 +1626,7 @@ static int fallback_resolve(const Call& c, const Plan& p, char* ws, const WsHead
                     c.liz->total_sites, adj->abar, nullptr, 0, nullptr, adj->n_delta, c.K, region, false, c.st)))
     return rc;
   LSMS_LAUNCH(k_copy_b, g1, dim3(256), 0, c.st, fbu, region, nrhs, false);
-  if ((rc = lu_solve_chunk<double>(fbu, slots, n_max, region, region, RHS_X, nrhs, nullptr, c.st))) return rc;
+  if ((rc = lu_solve_chunk<double>(fbu, slots, n_max, region, region, RHS_X, nrhs, nullptr, stat, c.st))) return rc;
   return adj_site(fbu, slots, S_max, adj->tau, c.liz->total_sites, c.K, region, adj->G, false, c.st);
 }
 
@@ -1767,7 +1767,7 @@ extern "C" int lsms_set_option(const char* name, double value) {
     if (!in_int(0, 2)) return fail(LSMS_ERR_ARG, "solve_regs must be 0, 1 or 2");
     g_opt_solve_regs.store((int)value);
   } else if (n == "solve_steps") {
-    if (!in_int(0, 2)) return fail(LSMS_ERR_ARG, "solve_steps must be 0, 1 or 2");
+    if (!in_int(0, 3)) return fail(LSMS_ERR_ARG, "solve_steps must be 0, 1, 2 or 3");
     g_opt_solve_steps.store((int)value);
   } else if (n == "nvtx") {
     if (!in_int(0, 1)) return fail(LSMS_ERR_ARG, "nvtx must be 0 or 1");

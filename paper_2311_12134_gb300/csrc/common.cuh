@@ -238,7 +238,7 @@ int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base,
 // ws + unit.<field> (complex<R>), skipping units whose done flag is set.
 template <typename R>
 int lu_solve_chunk(const Unit* d_units, int n_units, int n_max, const char* fac_base, char* ws,
-                   int which_rhs, int nrhs, const int32_t* done, cudaStream_t st);
+                   int which_rhs, int nrhs, const int32_t* done, int32_t* stat, cudaStream_t st);
 
 enum RhsField { RHS_X = 0, RHS_X32 = 1 };
 
@@ -251,6 +251,11 @@ int opt_solve_cols();
 int opt_solve_regs();
 int opt_solve_steps();
 
+// One block step of the complex64 triangular solves on the tensor cores (tc_gemm.cu):
+// forward X[rows >= 32 (s + 1)] -= L[., block s] X[block s], backward
+// X[rows < 32 s] -= U[., block s] X[block s], on the X32 field, nrhs <= 32.
+int step_tc_chunk(const Unit* d_units, int n_units, int n_max, const char* fac_base, char* ws, int nrhs,
+                  const int32_t* done, int32_t* stat, int s, bool forward, cudaStream_t st);
 // Trailing update A22 -= L21 U12 of the complex64 LU on the tensor cores (tc_gemm.cu).
 int gemm_tc_chunk(const Unit* d_units, int n_units, int n_max, int k, char* fac_base, int32_t* stat,
                   cudaStream_t st);

@@ -1330,6 +1330,34 @@ __global__ void __launch_bounds__(256, 2) k_bwd_step(const Unit* __restrict__ un
   }
 }
 
+// The block finalize of the tensor-core step solves: y_b = T^{-1} X[block b] with
+// the stored inverse of the diagonal block (L after forward step s: b = s + 1;
+// U after backward step s: b = s - 1; s = -1: the first block forward, the
+// unit's last block backward).  grid (n_units), block 256.
+__global__ void __launch_bounds__(256) k_step_final(const Unit* __restrict__ units, const char* fac_base, char* ws,
+                                                    int nrhs, const int32_t* done, int s, int forward) {
+  constexpr int NB = 32;
+  const Unit u = units[blockIdx.x];
+  if (done && done[u.stat_off]) return;
+  const int n = u.n, nb = (n + NB - 1) / NB;
+  int b;
+  if (forward) {
+    b = s + 1;
+    if (b > nb - 1) return;
+  } else if (s < 0) {
+    b = nb - 1;
+  } else {
+    if (s >= nb || s < 1) return;
+    b = s - 1;
+  }
+  __shared__ float2 sT[NB][NB + 1];
+  __shared__ float2 sIn[NB][NB + 1];
+  float2* X = reinterpret_cast<float2*>(ws + u.x32_off);
+  const float2* D = reinterpret_cast<const float2*>(fac_base + u.m64_off + diag_inv_rel_off(n));
+  step_finalize<NB>(D + (size_t)b * 2 * NB * NB + (forward ? 0 : NB * NB), X, sT, sIn, n, NB * b,
+                    min(NB, n - NB * b), nrhs);
+}
+
 // ------------------------------------------------------------------ wrappers
 template <typename R>
 int lu_factor_chunk(const Unit* d_units, int n_units, int n_max, char* fac_base, int32_t* stat,
@@ -1416,9 +1444,26 @@ static int solve_steps(const Unit* d_units, int n_units, int n_max, const char* 
   return LSMS_OK;
 }
 
+// The block steps with the row updates on the tensor cores (k_step_tc, whose
+// tile holding the next block finalizes it); k_step_final takes the first block
+// of each direction.
+static int solve_steps_tc(const Unit* d_units, int n_units, int n_max, const char* fac_base, char* ws, int nrhs,
+                          const int32_t* done, int32_t* stat, cudaStream_t st) {
+  constexpr int NB = 32;
+  const int nb = (n_max + NB - 1) / NB;
+  int rc;
+  LSMS_LAUNCH(k_step_final, dim3(n_units), dim3(256), 0, st, d_units, fac_base, ws, nrhs, done, -1, 1);
+  for (int s = 0; s + 1 < nb; ++s)
+    if ((rc = step_tc_chunk(d_units, n_units, n_max, fac_base, ws, nrhs, done, stat, s, true, st))) return rc;
+  LSMS_LAUNCH(k_step_final, dim3(n_units), dim3(256), 0, st, d_units, fac_base, ws, nrhs, done, -1, 0);
+  for (int s = nb - 1; s >= 1; --s)
+    if ((rc = step_tc_chunk(d_units, n_units, n_max, fac_base, ws, nrhs, done, stat, s, false, st))) return rc;
+  return LSMS_OK;
+}
+
 template <typename R>
 int lu_solve_chunk(const Unit* d_units, int n_units, int n_max, const char* fac_base, char* ws, int which_rhs,
-                   int nrhs, const int32_t* done, cudaStream_t st) {
+                   int nrhs, const int32_t* done, int32_t* stat, cudaStream_t st) {
   if (nrhs < 1 || nrhs > 32) return fail(LSMS_ERR_ARG, "internal: nrhs %d out of range", nrhs);
   constexpr int NB = LuCfg<R>::NB;
   if constexpr (std::is_same<R, float>::value) {
@@ -1432,9 +1477,10 @@ int lu_solve_chunk(const Unit* d_units, int n_units, int n_max, const char* fac_
       perm_attr = pb;
     }
     LSMS_LAUNCH(k_perm_rows, dim3(nrhs, n_units), dim3(256), pb, st, d_units, fac_base, ws, nrhs, done);
-    // option "solve_steps": 1 = one CTA chain per unit and column slice; 2 = block-step launches;
-    // 0 (default) = block steps when the chains could not fill the GPU (fewer than two per SM:
-    // few units of large LIZ matrices), else chains
+    // option "solve_steps": 1 = one CTA chain per unit and column slice; 2 = block-step launches
+    // (row updates on the FP32 pipes); 3 = block-step launches with the row updates on the tensor
+    // cores; 0 (default) = block steps when the chains could not fill the GPU (fewer than two per
+    // SM: few units of large LIZ matrices), on the tensor cores from 9 columns, else chains
     int steps = opt_solve_steps();
     if (steps == 0) {
       static int sms = 0;
@@ -1444,8 +1490,9 @@ int lu_solve_chunk(const Unit* d_units, int n_units, int n_max, const char* fac_
         LSMS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
       }
       const int slices = nrhs <= 16 ? 1 : 2;
-      steps = (long long)n_units * slices < 2LL * sms ? 2 : 1;
+      steps = (long long)n_units * slices < 2LL * sms ? (nrhs > 8 ? 3 : 2) : 1;
     }
+    if (steps == 3) return solve_steps_tc(d_units, n_units, n_max, fac_base, ws, nrhs, done, stat, st);
     if (steps == 2) {
       if (nrhs <= 8) return solve_steps<8>(d_units, n_units, n_max, fac_base, ws, nrhs, done, st);
       if (nrhs <= 16) return solve_steps<16>(d_units, n_units, n_max, fac_base, ws, nrhs, done, st);
@@ -1490,7 +1537,9 @@ int lu_solve_chunk(const Unit* d_units, int n_units, int n_max, const char* fac_
 
 template int lu_factor_chunk<double>(const Unit*, int, int, char*, int32_t*, cudaStream_t);
 template int lu_factor_chunk<float>(const Unit*, int, int, char*, int32_t*, cudaStream_t);
-template int lu_solve_chunk<double>(const Unit*, int, int, const char*, char*, int, int, const int32_t*, cudaStream_t);
-template int lu_solve_chunk<float>(const Unit*, int, int, const char*, char*, int, int, const int32_t*, cudaStream_t);
+template int lu_solve_chunk<double>(const Unit*, int, int, const char*, char*, int, int, const int32_t*, int32_t*,
+                                    cudaStream_t);
+template int lu_solve_chunk<float>(const Unit*, int, int, const char*, char*, int, int, const int32_t*, int32_t*,
+                                   cudaStream_t);
 
 }  // namespace lsms

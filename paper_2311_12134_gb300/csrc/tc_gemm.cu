@@ -346,3 +346,205 @@ int gemm_tc_chunk(const Unit* d_units, int n_units, int n_max, int k, char* fac_
 }
 
 }  // namespace lsms
+
+namespace lsms {
+
+// One block step of the complex64 triangular solves on the tensor cores, the
+// same 3xTF32 real-embedding product as k_gemm_tc with the solved block as B:
+//   forward (L y = P b):  X[r] -= L[r, 32 s .. 32 s + 31] y_s  for r >= 32 (s + 1),
+//   backward (U x = y):   X[r] -= U[r, 32 s .. 32 s + nbp - 1] x_s  for r < 32 s,
+// y_s / x_s = the rows 32 s .. of X (final before the launch), X = the unit's
+// n x nrhs complex64 right-hand-side block (nrhs <= 32: one 32-column tile, the
+// columns beyond nrhs zero); the tile that holds the next block (s + 1 forward,
+// s - 1 backward) then multiplies it by the stored inverse of its diagonal block.
+// grid (row tiles of 128, n_units), block 128, dynamic smem tc::SMEM_BYTES (so at
+// most two CTAs per SM); one 64-column TMEM accumulator; the wait on the tensor
+// core is bounded (LSMS_UNIT_TIMEOUT).
+__global__ void __launch_bounds__(128) k_step_tc(const Unit* __restrict__ units, const char* fac_base, char* ws,
+                                                 int nrhs, const int32_t* __restrict__ done, int32_t* stat, int s,
+                                                 int forward) {
+  using namespace tc;
+  const Unit u = units[blockIdx.y];
+  if (done && done[u.stat_off]) return;
+  const int n = u.n, nb = (n + NB - 1) / NB;
+  const int kc = NB * s;
+  int r_begin, r_end;
+  if (forward) {
+    if (s < 0 || s + 1 >= nb) return;
+    r_begin = kc + NB;
+    r_end = n;
+  } else {
+    if (s >= nb || s < 1) return;
+    r_begin = 0;
+    r_end = kc;
+  }
+  const int row0 = r_begin + blockIdx.x * TM;
+  if (row0 >= r_end) return;
+  const int nbp = min(NB, n - kc);
+  const float2* F = reinterpret_cast<const float2*>(fac_base + u.fac_off);
+  float2* X = reinterpret_cast<float2*>(ws + u.x32_off);
+
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sAh = smem;
+  uint8_t* sAl = smem + OP_A;
+  uint8_t* sBh = smem + 2 * OP_A;
+  uint8_t* sBl = smem + 2 * OP_A + OP_B;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * OP_A + 2 * OP_B);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 2 * OP_A + 2 * OP_B + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  auto put = [](uint8_t* sh, uint8_t* sl, int rr, int kk, int chunk, float a0, float a1, float a2, float a3) {
+    float4 h, l;
+    h.x = tf32_hi(a0); h.y = tf32_hi(a1); h.z = tf32_hi(a2); h.w = tf32_hi(a3);
+    l.x = a0 - h.x; l.y = a1 - h.y; l.z = a2 - h.z; l.w = a3 - h.w;
+    *reinterpret_cast<float4*>(sh + swz(rr, kk, chunk)) = h;
+    *reinterpret_cast<float4*>(sl + swz(rr, kk, chunk)) = l;
+  };
+  // B^ from the solved block: output column bc = tid / 4, block rows j0 .. j0 + 7
+  {
+    const int bc = tid >> 2, j0 = (tid & 3) * 8;
+    float2 w[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      w[q] = (bc < nrhs && j0 + q < nbp) ? X[(size_t)bc * n + kc + j0 + q] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float2* x = w + 4 * h;
+      const int kk = j0 + 4 * h;
+      put(sBh, sBl, bc, kk, CHUNK_B, x[0].x, x[1].x, x[2].x, x[3].x);
+      put(sBh, sBl, bc, NB + kk, CHUNK_B, -x[0].y, -x[1].y, -x[2].y, -x[3].y);
+      put(sBh, sBl, bc + TNC, kk, CHUNK_B, x[0].y, x[1].y, x[2].y, x[3].y);
+      put(sBh, sBl, bc + TNC, NB + kk, CHUNK_B, x[0].x, x[1].x, x[2].x, x[3].x);
+    }
+  }
+  // A^ row r = [F_re(r, kc ..) | F_im(r, kc ..)]: thread r, one coalesced load per column
+  {
+    const int row = row0 + tid;
+    const bool ok = row < r_end;
+    float2 v[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+      v[j] = (ok && j < nbp) ? __ldg(&F[(size_t)(kc + j) * n + row]) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < NB / 4; ++q) {
+      put(sAh, sAl, tid, 4 * q, CHUNK_A, v[4 * q].x, v[4 * q + 1].x, v[4 * q + 2].x, v[4 * q + 3].x);
+      put(sAh, sAl, tid, NB + 4 * q, CHUNK_A, v[4 * q].y, v[4 * q + 1].y, v[4 * q + 2].y, v[4 * q + 3].y);
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  if (tid == 0) {
+    const uint32_t idesc = make_idesc(TM, TN);
+    const uint32_t a_hi = smem_u32(sAh), a_lo = smem_u32(sAl), b_hi = smem_u32(sBh), b_lo = smem_u32(sBl);
+    uint32_t acc = 0;
+    for (int p = 0; p < 3; ++p) {  // hi*hi, hi*lo, lo*hi
+      const uint32_t ab = (p == 2) ? a_lo : a_hi;
+      const uint32_t bb = (p == 1) ? b_lo : b_hi;
+#pragma unroll
+      for (int c2 = 0; c2 < 2; ++c2)
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4) {
+          mma_tf32(tmem, make_desc(ab + c2 * CHUNK_A + k4 * 32), make_desc(bb + c2 * CHUNK_B + k4 * 32), idesc, acc);
+          acc = 1;
+        }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(mbar))
+                 : "memory");
+  }
+  // this thread's row of X while the products run
+  const int crow = row0 + warp * 32 + lane;
+  const bool live = crow < r_end;
+  float2 cv[TNC];
+#pragma unroll
+  for (int c = 0; c < TNC; ++c) cv[c] = (live && c < nrhs) ? X[(size_t)c * n + crow] : make_float2(0.f, 0.f);
+  bool ok = false;
+  for (long long it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(smem_u32(mbar), 0u)) {
+      ok = true;
+      break;
+    }
+  ok = __syncthreads_and(ok);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    float dre[32], dim[32];
+    tmem_ld32(lane_base + 0, dre);
+    tmem_ld32(lane_base + 32, dim);
+    if (live) {
+#pragma unroll
+      for (int c = 0; c < TNC; ++c)
+        if (c < nrhs) X[(size_t)c * n + crow] = make_float2(cv[c].x - dre[c], cv[c].y - dim[c]);
+    }
+  } else if (tid == 0) {
+    atomicOr(&stat[u.stat_off], LSMS_UNIT_TIMEOUT);
+    for (long long it = 0; it < kWaitLimit; ++it)
+      if (mbar_try_wait(smem_u32(mbar), 0u)) break;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(TMEM_COLS));
+  }
+  // the tile that holds the next block finalizes it after its own update:
+  // y = T^{-1} X[block] with the stored inverse of the diagonal block (L forward,
+  // U backward); the operand planes are free again (the products completed)
+  int fb = -1;
+  if (forward) {
+    if (blockIdx.x == 0 && s + 1 < nb) fb = s + 1;
+  } else if (s >= 1 && (int)blockIdx.x == (NB * (s - 1)) / TM) {
+    fb = s - 1;
+  }
+  if (fb >= 0 && ok) {
+    float2(*sT)[NB + 1] = reinterpret_cast<float2(*)[NB + 1]>(smem);
+    float2(*sIn)[NB + 1] = reinterpret_cast<float2(*)[NB + 1]>(smem + NB * (NB + 1) * sizeof(float2));
+    const float2* D = reinterpret_cast<const float2*>(fac_base + u.m64_off + diag_inv_rel_off(n)) +
+                      (size_t)fb * 2 * NB * NB + (forward ? 0 : NB * NB);
+    const int k0 = NB * fb, fbp = min(NB, n - k0);
+    for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+      const int i = idx % NB, c = idx / NB;
+      sT[i][c] = D[idx];
+      sIn[i][c] = (c < nrhs && i < fbp) ? X[(size_t)c * n + k0 + i] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+      const int i = idx % NB, c = idx / NB;
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < NB; j += 2) {
+        a0 = cfma(sT[i][j], sIn[j][c], a0);
+        a1 = cfma(sT[i][j + 1], sIn[j + 1][c], a1);
+      }
+      if (i < fbp && c < nrhs) X[(size_t)c * n + k0 + i] = make_float2(a0.x + a1.x, a0.y + a1.y);
+    }
+  }
+}
+
+int step_tc_chunk(const Unit* d_units, int n_units, int n_max, const char* fac_base, char* ws, int nrhs,
+                  const int32_t* done, int32_t* stat, int s, bool forward, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    LSMS_CUDA_TRY(cudaFuncSetAttribute(k_step_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+    attr_set = true;
+  }
+  if (nrhs < 1 || nrhs > tc::TNC) return fail(LSMS_ERR_ARG, "internal: step_tc_chunk nrhs %d", nrhs);
+  const int rows = forward ? n_max - tc::NB * (s + 1) : tc::NB * s;
+  if (rows <= 0) return LSMS_OK;
+  LSMS_LAUNCH(k_step_tc, dim3((rows + tc::TM - 1) / tc::TM, n_units), dim3(128), tc::SMEM_BYTES, st, d_units,
+              fac_base, ws, nrhs, done, stat, s, forward ? 1 : 0);
+  return LSMS_OK;
+}
+
+}  // namespace lsms

@@ -174,7 +174,7 @@ def test_options_roundtrip_and_range_checks(L):
         B.set_option("fallback_slots", 3)
         assert B.get_option("fallback_slots") == 3
         for name, bad in (("growth_limit", 0.0), ("growth_limit", float("inf")), ("fallback_slots", -1),
-                          ("fallback_slots", 1.5), ("ir_max_sweeps", 65), ("streams", 5), ("solve_steps", 3), ("solve_regs", 3),
+                          ("fallback_slots", 1.5), ("ir_max_sweeps", 65), ("streams", 5), ("solve_steps", 4), ("solve_regs", 3),
                           ("nvtx", 2), ("no_such_option", 1)):
             with pytest.raises(B.LsmsError) as ei:
                 B.set_option(name, bad)

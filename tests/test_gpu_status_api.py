@@ -253,10 +253,12 @@ def test_conductivity_host_call_matches_oracle(B, alloy, precision):
 
 
 @pytest.mark.parametrize("cols,regs,streams,steps",
-                         [(8, 1, 4, 1), (16, 0, 2, 1), (16, 1, 4, 0), (32, 0, 1, 1), (16, 1, 2, 2), (0, 0, 4, 2)])
+                         [(8, 1, 4, 1), (16, 0, 2, 1), (16, 1, 4, 0), (32, 0, 1, 1), (16, 1, 2, 2), (0, 0, 4, 2), (0, 0, 2, 3)])
 def test_tuning_options_keep_results(B, alloy, cols, regs, streams, steps):
     """The autotuner's shapes (solve path, solve columns per CTA, register bound, concurrent parts)
-    change the launch layout only: tau and the gradient match the default layout to rounding."""
+    change the launch layout and, between the solve paths, the complex64 rounding of the corrections
+    (FP32 pipes or 3xTF32 on the tensor cores): tau and the gradient match the default layout to the
+    refinement's tolerance (corrections below 1e-10 of the solution)."""
     w, _, _, _, J = alloy
     Jd = torch.as_tensor(J).cuda()
     wgt = torch.zeros((1, 3, 3), dtype=torch.complex128, device="cuda")
@@ -274,5 +276,5 @@ def test_tuning_options_keep_results(B, alloy, cols, regs, streams, steps):
         assert not np.any(st.cpu().numpy() & 0xff)
         out.append((tau.cpu().numpy(), g.cpu().numpy()))
     (t0, g0), (t1, g1) = out
-    assert np.abs(t1 - t0).max() <= 1e-12 * np.abs(t0).max()
-    assert np.abs(g1 - g0).max() <= 1e-11 * np.abs(g0).max()
+    assert np.abs(t1 - t0).max() <= 1e-10 * np.abs(t0).max()
+    assert np.abs(g1 - g0).max() <= 1e-9 * np.abs(g0).max()
