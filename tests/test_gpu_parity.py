@@ -296,6 +296,34 @@ def test_gradient_matches_dense_oracle(dense_grad_alloy, precision, lu_store):
         assert np.abs(gs[s] - ref_s).max() < TOL[precision] * np.abs(ref_s).max()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("weights", ["xx", "column_z", "dense"])
+def test_gradient_general_current_and_sparse_weights(precision, weights):
+    """The adjoint's right-hand sides run over the nonzero entries of J and Abar and skip a zero
+    Abar^nu: random dense J (no zero entries) and weights with zero columns nu (only d Re sigma_xx;
+    only the nu = z column) against the oracle's dense gradient."""
+    w = _alloy32(seed=5)
+    B = _B()
+    L = oliz.build_liz(w.pos, w.lattice, w.r_liz)
+    rng = np.random.default_rng(17)
+    J = rng.normal(size=(2, 4, 3, 16, 16)) + 1j * rng.normal(size=(2, 4, 3, 16, 16))
+    wgt = np.zeros((1, 3, 3), dtype=np.complex128)
+    if weights == "xx":
+        wgt[0, 0, 0] = 1.0
+    elif weights == "column_z":
+        wgt[0, :, 2] = rng.normal(size=3) + 1j * rng.normal(size=3)
+    else:
+        wgt[0] = rng.normal(size=(3, 3)) + 1j * rng.normal(size=(3, 3))
+    ref = ograd.torch_grad(ograd.dense_gradient(w.lmax, L, w.tinv[w.species], w.z, J[w.species], 1, w.volume, wgt))
+    lz, tau, st, _ = gpu_tau(w, precision)
+    sp = torch.as_tensor(w.species).cuda()
+    g, _ = B.kubo_sigma_backward(lz, w.lmax, sp, torch.as_tensor(w.tinv).cuda(), w.z, torch.as_tensor(J).cuda(), tau,
+                                 w.volume, torch.as_tensor(wgt).cuda(), precision)
+    g = g.cpu().numpy()
+    for e in range(2):
+        assert rel_err_blocks(g[e][None], ref[e][None]) < TOL[precision]
+
+
 def test_gradient_store_equals_recompute():
     a = _grad_case("fp64", False)
     b = _grad_case("fp64", True)
