@@ -403,7 +403,7 @@ def sparse_product_cmacs(J, species, offsets, site_atom, weights, K):
 
 
 def kernel_models(K, n_fwd, sweeps, n_delta, n_energy, fp32_ops, fp64_peak, tc_peak, hbm_gbs, precision, nb=32,
-                  sparse=None):
+                  sparse=None, solve_cols=0):
     """Algorithmic real flops per step and the matching peak (TFLOP/s) for each library kernel;
     1 complex multiply-add = 8 real flops.  n_fwd: n of every forward unit; sweeps: per-unit
     refinement sweeps and probes of the forward and of the adjoint."""
@@ -422,7 +422,17 @@ def kernel_models(K, n_fwd, sweeps, n_delta, n_energy, fp32_ops, fp64_peak, tc_p
     fs, fp, bs, bp = sweeps
     if mixed:
         rhs = K * (1 + fs) + 2 * K * (1 + bs) + PROBES * (fp + bp)
-        m["k_solve_c64"] = (float(np.sum(8.0 * n * n * rhs)), simt_peak, "triangular solves (complex64, FP32 pipe)")
+        def slices(ncols):  # column slices of a chain solve (the library's rule for solve_cols)
+            if ncols <= 8:
+                return 1
+            sl = solve_cols if solve_cols > 0 else (8 if ncols <= 16 else 16)
+            if sl == 32 and ncols <= 16:
+                sl = 16
+            return -(-ncols // sl)
+        # bytes: one read of the complex64 factors (8 n^2) per unit, column slice and solve
+        reads = slices(K) * (1 + fs) + slices(2 * K) * (1 + bs) + (fp + bp)
+        m["k_solve_c64"] = (float(np.sum(8.0 * n * n * rhs)), simt_peak, "triangular solves (complex64, FP32 pipe)",
+                            float(np.sum(8.0 * n * n * reads)))
         m["k_residual"] = (float(np.sum(8.0 * n * n * (K * fs + 2 * K * bs))), df_peak,
                            "FP64-accurate residual in double-float FP32 arithmetic (44 FP32 ops per complex MAC)")
         m["k_probe_residual"] = (float(np.sum(8.0 * n * n * PROBES * (fp + bp))), df_peak,
@@ -667,7 +677,8 @@ def run_ours(args):
     sparse = sparse_product_cmacs(np.asarray(J), np.asarray(w.species), ex["offsets"], ex["site_atom"], grad_sigma,
                                   w.K)
     models = kernel_models(w.K, n_fwd, (fs, fp, bs, bp), w.n_delta, len(w.z), fp32_ops, fp64_peak, tc_peak,
-                           fpk["hbm_gbs"], args.precision, sparse=sparse)
+                           fpk["hbm_gbs"], args.precision, sparse=sparse,
+                           solve_cols=int((tuning or {}).get("solve_cols", 0)))
     rows = kernel_rows(kt, models, fpk["hbm_gbs"])
     roof = None
     modelled = [r for r in rows.values() if "frac" in r]
